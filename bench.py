@@ -1,0 +1,359 @@
+"""Benchmark: cone-beam FP + FDK step on the 3D short-scan workload.
+
+Workload (one step, all on the GPU through the C ABI): 256^3 FP32 volume of
+12 random ellipsoids (0.5 mm), 248 views over pi + 2 delta (short scan),
+620 x 480 detector at 0.616 mm, SID 750 mm, SDD 1200 mm;
+  1. ray-driven forward projection of the volume (pyro_fp_cone3d),
+  2. FDK of that sinogram (pyro_fdk: cosine + Parker weights fused into the
+     Shepp-Logan row filter, then the voxel-driven back-projection).
+Metric: GUPS = voxel-view pairs processed per second, counting one pass of
+FP and one of BP over the 256^3 x 248 problem per step (2 N^3 V units).
+
+`value` is device time (CUDA events on the launching stream, L2 flushed
+between steps, outside the timed events); `e2e` is the same step through the
+public API from pinned host memory, copies included.  Under torchrun every
+rank runs its own independent phantom (weak scaling, no data-path
+collective); the step time is the max over ranks.
+
+`--impl reference` times the FP64 CPU oracle on a bounded sample of the same
+workload on this machine's host cores (the paper publishes no timings).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+import torch  # noqa: E402
+
+N, SPACING = 256, 0.5
+NV, NU, SV, SU = 480, 620, 0.616, 0.616
+VIEWS, SID, SDD = 248, 750.0, 1200.0
+WORKLOAD = "cone-beam short-scan FDK 256^3 x 248 views, 620x480 det"
+METRIC = "cone-beam BP/FP GUPS"
+UNIT = "GUPS"
+
+
+def geometry():
+    from paper_1904_13342_gb300.geometry import ConeGeometry3D, short_scan_range
+
+    rng_ = short_scan_range(NU * SU, SDD)
+    return ConeGeometry3D((N, N, N), (SPACING,) * 3, (NV, NU), (SV, SU), VIEWS, rng_, SID, SDD)
+
+
+def units_per_step() -> float:
+    return 2.0 * N * N * N * VIEWS
+
+
+def config(flush: str):
+    return {"workload": WORKLOAD, "volume": [N, N, N], "spacing_mm": SPACING, "views": VIEWS,
+            "detector": [NU, NV], "det_spacing_mm": SU, "sid_mm": SID, "sdd_mm": SDD, "filter": "shepp-logan",
+            "redundancy": "parker", "step": "fp_cone3d + fdk(weights+filter, bp_cone3d)", "l2": flush}
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.file = None
+
+    def __enter__(self):
+        try:
+            self.file = tempfile.TemporaryFile(mode="w+")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.file,
+                                         stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        if self.proc is None or self.file is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.file.seek(0)
+        rows = [[c.strip() for c in l.split(",")] for l in self.file.read().splitlines() if l.count(",") >= 8]
+        sm = [float(r[1]) for r in rows if r[1].replace(".", "").isdigit()]
+        mx = [float(r[2]) for r in rows if r[2].replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        load = [s for s in sm if mx and s > 0.5 * max(mx)] or sm
+        return {"sm_mhz": statistics.median(load) if load else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+def run_gpu(args):
+    from paper_1904_13342_gb300 import binding as B
+    from paper_1904_13342_gb300 import phantoms as ph
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=dev)
+
+    g = geometry()
+    e = ph.random_ellipsoids(12, N * SPACING / 2, seed=rank)
+    vol = ph.voxelize_ellipsoids(e, g.volume_shape, g.volume_spacing, device=dev, dtype=torch.float32).contiguous()
+    ws = torch.empty(B.lib().pyro_fdk_workspace_bytes(__import__("ctypes").byref(g.to_c()), 1), dtype=torch.uint8,
+                     device=dev)
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device=dev)  # 256 MB > 129 MB L2
+    stream = torch.cuda.current_stream(dev)
+
+    def step(v):
+        s = B.pyro_fp_cone3d(v, g)
+        return B.pyro_fdk(s, g, kind=B.SHEPP_LOGAN, redund=B.REDUND_PARKER, workspace=ws)
+
+    for _ in range(args.warmup):
+        step(vol)
+    torch.cuda.synchronize(dev)
+
+    K = args.steps
+    ev = [[torch.cuda.Event(enable_timing=True) for _ in range(4)] for _ in range(K)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize(dev)
+    with ClockSampler(local) as clk:
+        for k in range(K):
+            flush.fill_(k & 0xFF)  # evict L2 between steps, outside the timed events
+            e0, e1, e2, e3 = ev[k]
+            e0.record(stream)
+            sino = B.pyro_fp_cone3d(vol, g)
+            e1.record(stream)
+            rec = B.pyro_fdk(sino, g, kind=B.SHEPP_LOGAN, redund=B.REDUND_PARKER, workspace=ws)
+            e2.record(stream)
+        torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    step_ms = [ev[k][0].elapsed_time(ev[k][2]) for k in range(K)]
+    fp_ms = [ev[k][0].elapsed_time(ev[k][1]) for k in range(K)]
+    fdk_ms = [ev[k][1].elapsed_time(ev[k][2]) for k in range(K)]
+    total_ms = sum(step_ms)
+    if dist:
+        t = torch.tensor([total_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    value = world * K * units_per_step() / (total_ms * 1e-3) / 1e9
+
+    # separate per-kernel timings (outside the timed region): BP and filter alone
+    sino = B.pyro_fp_cone3d(vol, g)
+    filt = torch.empty_like(sino)
+    tk = {}
+    for name, fn in (("bp", lambda: B.pyro_bp_cone3d(sino, g, weight=B.W_INV_L2, scale=1.0)),
+                     ("filter", lambda: B.pyro_filter_rows(sino, SU * SID / SDD, B.SHEPP_LOGAN, out=filt))):
+        fn()
+        ts = []
+        for _ in range(3):
+            flush.fill_(1)
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        tk[name] = statistics.median(ts)
+
+    # end to end through the public API from pinned host memory
+    host_vol = vol.cpu().pin_memory()
+    host_out = torch.empty(vol.shape, dtype=torch.float32).pin_memory()
+    E = max(1, min(K, 5))
+    torch.cuda.synchronize(dev)
+    if dist:
+        dist.barrier()
+    t0 = time.perf_counter()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(E):
+        dv = host_vol.to(dev, non_blocking=True)
+        r = step(dv)
+        host_out.copy_(r, non_blocking=True)
+    b.record(stream)
+    torch.cuda.synchronize(dev)
+    e2e_ms = a.elapsed_time(b)
+    if dist:
+        t = torch.tensor([e2e_ms], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_ms = float(t.item())
+    e2e = world * E * units_per_step() / (e2e_ms * 1e-3) / 1e9
+
+    peaks = {}
+    pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pf):
+        peaks = json.load(open(pf))
+    # roofline of the dominant kernel (forward projection): FP32 issue-bound
+    # gather; algorithmic work = 28 FP32 flops per trilinear sample
+    samples = fp_sample_count(g)
+    fp_avg_ms = statistics.mean(fp_ms)
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = peaks.get("sm_max_mhz", 2070.0)
+    peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
+    achieved = samples * FLOPS_PER_SAMPLE / (fp_avg_ms * 1e-3) / 1e12
+    clocks = clk.summary()
+    out = {
+        "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
+        "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f32", "data": "synthetic (seeded random ellipsoid phantom)", "config": config("flushed 256 MB"),
+        "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(host_vol.numel() * 4),
+                "d2h_bytes_per_step": int(host_out.numel() * 4)},
+        "gpu_launches": 3 * K,
+        "roofline": {"kernel": "fp3d_kernel", "bound": "alu", "achieved": round(achieved, 3),
+                     "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
+                     "traffic": None,
+                     "note": f"{samples:.4g} samples x {FLOPS_PER_SAMPLE} flop; peak = {props.multi_processor_count}"
+                             f" SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
+        "breakdown_ms": {"fp": round(fp_avg_ms, 4), "fdk": round(statistics.mean(fdk_ms), 4),
+                         "bp_alone": round(tk["bp"], 4), "filter_alone": round(tk["filter"], 4)},
+        "kernel_gups": {"fp": round(N ** 3 * VIEWS / (fp_avg_ms * 1e-3) / 1e9, 2),
+                        "bp": round(N ** 3 * VIEWS / (tk["bp"] * 1e-3) / 1e9, 2)},
+        "clocks": clocks,
+    }
+    if rank == 0 and args.cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if dist:
+        dist.destroy_process_group()
+
+
+FLOPS_PER_SAMPLE = 28  # 3 position FMA (6) + 7 lerps (3 each) + 1 accumulate
+
+
+def fp_sample_count(g) -> float:
+    """Samples the forward projector visits (those inside the support box),
+    counted on the host in FP64 from the same ray geometry."""
+    import math
+
+    ang = g.view_angles()
+    nv, nu = g.detector_shape
+    sv, su = g.detector_spacing
+    u = (np.arange(nu) - 0.5 * (nu - 1)) * su
+    v = (np.arange(nv) - 0.5 * (nv - 1)) * sv
+    U, Vv = np.meshgrid(u, v)
+    L = np.sqrt(SDD ** 2 + U ** 2 + Vv ** 2)
+    half = 0.5 * (N + 1) * SPACING
+    total = 0.0
+    for b in ang[:: max(1, len(ang) // 16)]:
+        c = np.array([math.cos(b), math.sin(b), 0.0])
+        eu = np.array([-math.sin(b), math.cos(b), 0.0])
+        S = -SID * c
+        d = (SDD * c[None, None] + U[..., None] * eu[None, None] + Vv[..., None] * np.array([0, 0, 1.0])) / L[..., None]
+        lo = np.full(U.shape, -np.inf)
+        hi = np.full(U.shape, np.inf)
+        for a in range(3):
+            da = d[..., a]
+            with np.errstate(divide="ignore", invalid="ignore"):
+                t1 = (-half - S[a]) / da
+                t2 = (half - S[a]) / da
+            lo = np.maximum(lo, np.where(da != 0, np.minimum(t1, t2), -np.inf))
+            hi = np.minimum(hi, np.where(da != 0, np.maximum(t1, t2), np.inf))
+        total += np.sum(np.maximum(hi - lo, 0.0)) / (0.5 * SPACING)
+    return total * len(ang) / len(ang[:: max(1, len(ang) // 16)])
+
+
+def cpu_sample(seconds: float):
+    """The oracle on a bounded sample of the workload: FP of `fv` views over
+    the full volume and FDK of a `zs`-slice slab (all views)."""
+    import oracle
+
+    from paper_1904_13342_gb300 import phantoms as ph
+
+    g = geometry()
+    e = ph.random_ellipsoids(12, N * SPACING / 2, seed=0)
+    vol = ph.voxelize_ellipsoids(e, g.volume_shape, g.volume_spacing, dtype=torch.float64).numpy()
+    ang = g.view_angles()
+    P = oracle.circular_pmats(ang, SID, SDD, (NV, NU), (SV, SU))
+    fv = 4
+    t0 = time.perf_counter()
+    sino1 = oracle.fp_cone3d(vol, g.volume_spacing, (NV, NU), P[:fv])
+    t_fp = time.perf_counter() - t0
+    # FDK of a slab: a smooth synthetic sinogram stands in for the projections
+    y = ph.random_sinogram((VIEWS, NV, NU), 1, smooth=2)
+    zs = 6
+    kz = np.repeat(np.arange(N // 2 - zs // 2, N // 2 - zs // 2 + zs), N * N)
+    jj = np.tile(np.repeat(np.arange(N), N), zs)
+    ii = np.tile(np.arange(N), N * zs)
+    t0 = time.perf_counter()
+    oracle.fdk_voxels(y, g.volume_shape, g.volume_spacing, (SV, SU), ang, P, SID, SDD, g.angular_range / VIEWS, ii, jj,
+                      kz, kind=oracle.SHEPP_LOGAN, redund=oracle.REDUND_PARKER)
+    t_bp = time.perf_counter() - t0
+    units = N ** 3 * fv + N * N * zs * VIEWS
+    del sino1
+    return units / (t_fp + t_bp) / 1e9, {
+        "cores": oracle.num_threads(),
+        "sample": f"oracle FP of {fv} view(s) over the 256^3 volume + FDK of a {zs}-slice slab over all 248 views "
+                  f"({units:.3g} voxel-view units, {t_fp + t_bp:.1f} s)"}
+
+
+def cpu_baseline(seconds: float):
+    v, info = cpu_sample(seconds)
+    return {"value": round(v, 6), "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"]}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        cpu_sample(args.cpu_seconds)
+    info = {}
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        v, info = cpu_sample(args.cpu_seconds)
+        vals.append(v)
+    wall = time.perf_counter() - t0
+    value = statistics.mean(vals)
+    out = {"impl": "reference", "metric": METRIC, "value": round(value, 6), "unit": UNIT, "n_gpus": args.gpus,
+           "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(wall * 1e3 / max(args.steps, 1), 1),
+           "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+           "data": "synthetic (seeded random ellipsoid phantom)", "config": config("n/a (CPU)"),
+           "cpu_baseline": {"value": round(value, 6), "unit": UNIT, "cores": info.get("cores"), "kind": "oracle",
+                            "sample": info.get("sample")},
+           "e2e": {"value": round(value, 6), "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="native", choices=["native", "reference"])
+    ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
+    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

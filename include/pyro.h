@@ -1,0 +1,212 @@
+/*
+ * pyro.h -- C ABI of the GB300-native known-operator CT layers.
+ *
+ * Re-implements the data-parallel hot path of PYRO-NN (Syben et al. 2019):
+ * ray-driven forward projection, voxel-driven back-projection, their exact
+ * transposes, cosine / Parker weights, ramp-type row filtering and FBP/FDK,
+ * for 2D parallel-beam, 2D fan-beam and 3D cone-beam circular geometries.
+ *
+ * Common rules for every entry point
+ * ----------------------------------
+ *  Pointers.   Volume, sinogram, filter and workspace pointers are DEVICE
+ *              pointers owned by the caller (16-byte aligned).  Geometry
+ *              structs and the arrays they point to (angles, projection
+ *              matrices) are HOST memory, read during the call only.
+ *  Layout.     Volumes are [batch][nz][ny][nx] (2D: [batch][ny][nx]),
+ *              x fastest.  Sinograms are [batch][n_views][nv][nu]
+ *              (2D: [batch][n_views][nu]), u fastest.  Outputs are
+ *              overwritten, never accumulated into.
+ *  Geometry.   Voxel centre X_i = (i - (N-1)/2) * s (volume centred on the
+ *              iso-centre).  Detector coordinate u_k = (k - (nu-1)/2) * su.
+ *              View j: central ray c = (cos b_j, sin b_j, 0), detector axis
+ *              e_u = (-sin b_j, cos b_j, 0), e_v = (0, 0, 1).  Fan/cone
+ *              source S = -SID c, flat detector at distance SDD from S.
+ *              Cone-beam views are 3x4 projection matrices P with
+ *              (x, y, w) = P (X, 1) and detector index (x/w, y/w)
+ *              (Section "Trajectories"); NULL means the circular
+ *              trajectory P = K [R | -R S], R = [e_u; e_v; c],
+ *              K = [[SDD/su, 0, (nu-1)/2], [0, SDD/sv, (nv-1)/2], [0, 0, 1]].
+ *  Interpolation. Bi-/trilinear over the zero-extended arrays (values
+ *              outside the array are 0), computed in FP32 in software.
+ *  Precision.  dtype selects the STORAGE type of volumes and sinograms;
+ *              arithmetic and accumulation are always FP32.
+ *  Execution.  Every call is asynchronous on `stream` (a cudaStream_t;
+ *              NULL = legacy default stream) and uses the current device.
+ *              Host-side argument errors return PYRO_EINVAL before anything
+ *              is enqueued; launch failures return PYRO_ECUDA.  The library
+ *              allocates no device memory: scratch comes from the caller's
+ *              workspace arguments.  On a non-zero return, pyro_last_error()
+ *              gives a message (thread-local).
+ */
+#ifndef PYRO_H
+#define PYRO_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PYRO_API __attribute__((visibility("default")))
+
+typedef enum {
+    PYRO_OK = 0,
+    PYRO_EINVAL = 1,       /* invalid argument or geometry                  */
+    PYRO_ECUDA = 2,        /* a CUDA launch or runtime call failed          */
+    PYRO_ETIMEOUT = 3,     /* a bounded device-side wait gave up            */
+    PYRO_EUNSUPPORTED = 4, /* valid request this build does not implement   */
+    PYRO_EWORKSPACE = 5    /* workspace missing or smaller than required    */
+} pyro_status;
+
+typedef enum { PYRO_F32 = 0, PYRO_F16 = 1, PYRO_BF16 = 2 } pyro_dtype;
+
+/* voxel weight of the back-projectors: omega = 1, SID/L or (SID/L)^2 with
+ * L the depth of the voxel from the source along the central ray */
+typedef enum { PYRO_W_NONE = 0, PYRO_W_INV_L = 1, PYRO_W_INV_L2 = 2 } pyro_bp_weight;
+
+typedef enum { PYRO_RAMLAK = 0, PYRO_RAMP = 1, PYRO_SHEPP_LOGAN = 2, PYRO_FILTER_CUSTOM = 3 } pyro_filter;
+
+/* redundancy weight W_red: 1/2 (full 360 degree scan), Parker short scan, or 1 */
+typedef enum { PYRO_REDUND_FULL = 0, PYRO_REDUND_PARKER = 1, PYRO_REDUND_NONE = 2 } pyro_redund;
+
+/* 2D parallel / fan geometry (Section "Reconstruction & Geometry": volume
+ * shape and spacing, detector shape and spacing, number of projections,
+ * angular range, SID and SDD, plus one central-ray direction per view). */
+typedef struct {
+    int nx, ny;            /* image shape                                    */
+    double sx, sy;         /* pixel spacing, mm                              */
+    int nu;                /* detector bins                                  */
+    double su;             /* bin spacing, mm                                */
+    int n_views;           /* number of projections                          */
+    const double *angles;  /* [n_views] view angles b_j (rad), or NULL:      */
+                           /*   b_j = j * range / n_views                    */
+    double range;          /* angular range, rad                             */
+    double sid, sdd;       /* fan beam only: source-iso / source-detector mm */
+    double step;           /* FP sample step along the ray, mm; <= 0: half   */
+                           /*   the smallest pixel spacing                   */
+} pyro_geom2d;
+
+/* 3D cone-beam geometry (same attributes; trajectory as projection matrices) */
+typedef struct {
+    int nx, ny, nz;
+    double sx, sy, sz;
+    int nu, nv;               /* detector columns (u) and rows (v)            */
+    double su, sv;
+    int n_views;
+    const double *proj_mats;  /* [n_views][3][4] row-major, or NULL: circular */
+    const double *angles;     /* [n_views] rad or NULL (j * range / n_views);  */
+                              /*   used for circular matrices and for W_red    */
+    double range, sid, sdd;
+    double step;              /* as in pyro_geom2d                             */
+} pyro_geom3d;
+
+/* --- Ray-driven forward projection A (Section "The Operator as a Layer"). ---
+ * One line integral per detector pixel: for the ray X(t) = a + t d (d unit,
+ * a the bin position on e_u for parallel beam, the source otherwise),
+ *   p = step * sum_{m=-M..M} f(a + (t_c + m step) d),
+ * t_c = -a.d (closest approach to the iso-centre), M = ceil(T / step),
+ * T = half diagonal of the box (N+1)*s; f the zero-extended interpolant.
+ * vol [batch][...] -> sino [batch][...]. */
+PYRO_API int pyro_fp_par2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dtype,
+                           void *stream);
+PYRO_API int pyro_fp_fan2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dtype,
+                           void *stream);
+PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtype dtype,
+                            void *stream);
+
+/* --- Exact adjoint A^T of the forward projectors (the gradient of the FP
+ * layer, Section "The Known Operator": the gradient of A is A^T).  Scatters
+ * step * y * (interpolation weights) into the volume with FP32 atomics, so
+ * results agree with the sequential sum to rounding, not bit for bit.
+ * sino [batch][...] -> vol [batch][...].  Only PYRO_F32 is supported. */
+PYRO_API int pyro_fpT_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dtype,
+                            void *stream);
+PYRO_API int pyro_fpT_fan2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dtype,
+                            void *stream);
+PYRO_API int pyro_fpT_cone3d(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_dtype dtype,
+                             void *stream);
+
+/* --- Voxel-driven back-projection (Section "The Operator as a Layer"; the
+ * cone-beam form after Scherl et al. with projection matrices):
+ *   x(X) = scale * sum_j omega_j(X) * L(y_j; k_j(X) [, l_j(X)]),
+ * k_j(X) the detector index X projects to in view j, L linear (2D) or
+ * bilinear (3D) interpolation of the zero-extended detector.
+ * sino [batch][...] -> vol [batch][...]. */
+PYRO_API int pyro_bp_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                           float scale, pyro_dtype dtype, void *stream);
+PYRO_API int pyro_bp_fan2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                           float scale, pyro_dtype dtype, void *stream);
+PYRO_API int pyro_bp_cone3d(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_bp_weight w,
+                            float scale, pyro_dtype dtype, void *stream);
+
+/* --- Transpose of the voxel-driven back-projection (its autograd backward):
+ * scatters scale * omega * (interpolation weights) * g(X) into the detector
+ * with FP32 atomics.  vol [batch][...] -> sino [batch][...].  PYRO_F32 only. */
+PYRO_API int pyro_bpT_par2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                            float scale, pyro_dtype dtype, void *stream);
+PYRO_API int pyro_bpT_fan2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                            float scale, pyro_dtype dtype, void *stream);
+PYRO_API int pyro_bpT_cone3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_bp_weight w,
+                             float scale, pyro_dtype dtype, void *stream);
+
+/* --- Geometric correction weights, in place (Section "Geometric Correction
+ * Weights", Eq. 5): p <- W_red W_cos p.  W_cos = SDD / sqrt(SDD^2+u^2+v^2)
+ * when `cosine` != 0.  W_red per pyro_redund; Parker uses the half fan angle
+ * delta = atan(nu su / (2 SDD)), gamma = atan(u / SDD) and b_j - b_0.
+ * sino [batch][n_views][nu] (2D, v = 0) or [batch][n_views][nv][nu]. */
+PYRO_API int pyro_weights2d(void *sino, int batch, const pyro_geom2d *g, int cosine, pyro_redund redund,
+                            pyro_dtype dtype, void *stream);
+PYRO_API int pyro_weights3d(void *sino, int batch, const pyro_geom3d *g, int cosine, pyro_redund redund,
+                            pyro_dtype dtype, void *stream);
+
+/* --- Row filtering F^H K F (Eq. 4; Section "Filters").  Each of n_rows rows
+ * of nu samples is zero-padded to pn = smallest power of two >= 2 nu,
+ * transformed, multiplied by the real even diagonal K[0..pn/2] and
+ * transformed back; the first nu samples are kept.  Built-in K: Ram-Lak and
+ * Shepp-Logan are the DFTs of tau * h(n), h the spatial kernels of Kak &
+ * Slaney on sample spacing tau (this equals linear convolution with h);
+ * ramp is K[m] = |m| / (pn tau).  PYRO_FILTER_CUSTOM reads K from the
+ * DEVICE array custom_K[pn/2 + 1] (FP32).  in/out may alias.  FP32 FFT.
+ * nu <= 4096. */
+PYRO_API int pyro_filter_rows(const void *in, void *out, long n_rows, int nu, double tau, pyro_filter kind,
+                              const float *custom_K, pyro_dtype dtype, void *stream);
+
+/* padded length pn used by pyro_filter_rows for a row of nu samples */
+PYRO_API int pyro_filter_pad_length(int nu);
+
+/* --- Gradient of a loss with respect to a custom K (Eq. 6, filter learning):
+ * dK[m] = sum_rows c_m / pn * Re(P[m] conj(G[m])), P and G the length-pn
+ * DFTs of the zero-padded rows of p (the filter's input) and g (dL/dq),
+ * c_m = 1 for m in {0, pn/2} and 2 otherwise.  FP32 device arrays:
+ * p, g [n_rows][nu], dK [pn/2 + 1] (overwritten). */
+PYRO_API int pyro_filter_grad_K(const float *p, const float *g, float *dK, long n_rows, int nu, void *stream);
+
+/* --- FBP / FDK (Eq. 4, Eq. 5): x = A_bp F^H K F W_red W_cos p.
+ * Cone: tau = su * SID / SDD (virtual detector at the iso-centre),
+ *       omega = (SID / L)^2, scale = range / n_views (Feldkamp).
+ * Fan:  the same with v = 0.
+ * Parallel: no weights, tau = su, scale = pi / n_views.
+ * The weighted, filtered sinogram is kept in `workspace` (device, at least
+ * pyro_*_workspace_bytes bytes; PYRO_EWORKSPACE otherwise). */
+PYRO_API size_t pyro_fdk_workspace_bytes(const pyro_geom3d *g, int batch);
+PYRO_API int pyro_fdk(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_filter kind,
+                      const float *custom_K, pyro_redund redund, void *workspace, size_t workspace_bytes,
+                      pyro_dtype dtype, void *stream);
+PYRO_API size_t pyro_fbp2d_workspace_bytes(const pyro_geom2d *g, int batch);
+PYRO_API int pyro_fbp_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_filter kind,
+                            const float *custom_K, void *workspace, size_t workspace_bytes, pyro_dtype dtype,
+                            void *stream);
+PYRO_API int pyro_fbp_fan2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_filter kind,
+                            const float *custom_K, pyro_redund redund, void *workspace, size_t workspace_bytes,
+                            pyro_dtype dtype, void *stream);
+
+/* thread-local message describing the last non-OK status of this thread */
+PYRO_API const char *pyro_last_error(void);
+/* library version string */
+PYRO_API const char *pyro_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PYRO_H */

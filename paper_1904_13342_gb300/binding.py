@@ -1,0 +1,330 @@
+"""Thin ctypes binding of the C ABI (include/pyro.h), same names.
+
+Argument marshalling only: every step runs in the CUDA library.  PyTorch
+provides the device memory (outputs are allocated with ``torch.empty`` on
+the input's device) and the stream (the current CUDA stream).  Tensors must
+be CUDA, contiguous, float32 / float16 / bfloat16; there is no CPU path and
+a missing library is an error, never a fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+from typing import Optional
+
+import torch
+
+from . import build as _build
+from .geometry import CGeom2D, CGeom3D, ConeGeometry3D, Geometry2D
+
+_lock = threading.Lock()
+_lib = None
+
+PYRO_F32, PYRO_F16, PYRO_BF16 = 0, 1, 2
+W_NONE, W_INV_L, W_INV_L2 = 0, 1, 2
+RAMLAK, RAMP, SHEPP_LOGAN, FILTER_CUSTOM = 0, 1, 2, 3
+REDUND_FULL, REDUND_PARKER, REDUND_NONE = 0, 1, 2
+
+_DTYPES = {torch.float32: PYRO_F32, torch.float16: PYRO_F16, torch.bfloat16: PYRO_BF16}
+_STATUS = {1: "EINVAL", 2: "ECUDA", 3: "ETIMEOUT", 4: "EUNSUPPORTED", 5: "EWORKSPACE"}
+
+
+class PyroError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__(f"pyro {_STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+_VP = ctypes.c_void_p
+_I = ctypes.c_int
+_L = ctypes.c_long
+_F = ctypes.c_float
+_D = ctypes.c_double
+_SZ = ctypes.c_size_t
+_G2 = ctypes.POINTER(CGeom2D)
+_G3 = ctypes.POINTER(CGeom3D)
+
+_SIGS = {
+    "pyro_fp_par2d": [_VP, _VP, _I, _G2, _I, _VP],
+    "pyro_fp_fan2d": [_VP, _VP, _I, _G2, _I, _VP],
+    "pyro_fp_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
+    "pyro_fpT_par2d": [_VP, _VP, _I, _G2, _I, _VP],
+    "pyro_fpT_fan2d": [_VP, _VP, _I, _G2, _I, _VP],
+    "pyro_fpT_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
+    "pyro_bp_par2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
+    "pyro_bp_fan2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
+    "pyro_bp_cone3d": [_VP, _VP, _I, _G3, _I, _F, _I, _VP],
+    "pyro_bpT_par2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
+    "pyro_bpT_fan2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
+    "pyro_bpT_cone3d": [_VP, _VP, _I, _G3, _I, _F, _I, _VP],
+    "pyro_weights2d": [_VP, _I, _G2, _I, _I, _I, _VP],
+    "pyro_weights3d": [_VP, _I, _G3, _I, _I, _I, _VP],
+    "pyro_filter_rows": [_VP, _VP, _L, _I, _D, _I, _VP, _I, _VP],
+    "pyro_filter_pad_length": [_I],
+    "pyro_filter_grad_K": [_VP, _VP, _VP, _L, _I, _VP],
+    "pyro_fdk_workspace_bytes": [_G3, _I],
+    "pyro_fdk": [_VP, _VP, _I, _G3, _I, _VP, _I, _VP, _SZ, _I, _VP],
+    "pyro_fbp2d_workspace_bytes": [_G2, _I],
+    "pyro_fbp_par2d": [_VP, _VP, _I, _G2, _I, _VP, _VP, _SZ, _I, _VP],
+    "pyro_fbp_fan2d": [_VP, _VP, _I, _G2, _I, _VP, _I, _VP, _SZ, _I, _VP],
+    "pyro_last_error": [],
+    "pyro_version": [],
+}
+
+
+def lib():
+    """The loaded libpyro.so (built in-tree first if it is missing or stale)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            path = _build.build()
+            L = ctypes.CDLL(path)
+            for name, args in _SIGS.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = _I
+            L.pyro_last_error.restype = ctypes.c_char_p
+            L.pyro_version.restype = ctypes.c_char_p
+            L.pyro_fdk_workspace_bytes.restype = _SZ
+            L.pyro_fbp2d_workspace_bytes.restype = _SZ
+            _lib = L
+    return _lib
+
+
+def library_path() -> str:
+    return _build.LIB
+
+
+def _check(status: int):
+    if status != 0:
+        raise PyroError(status, lib().pyro_last_error().decode())
+
+
+def _stream(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(torch.cuda.current_stream(t.device).cuda_stream)
+
+
+def _dev(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda:
+        raise TypeError(f"{name} must be a CUDA tensor (the library has no CPU path)")
+    if t.dtype not in _DTYPES:
+        raise TypeError(f"{name} must be float32, float16 or bfloat16, got {t.dtype}")
+    if not t.is_contiguous():
+        raise ValueError(f"{name} must be contiguous")
+    return t
+
+
+def _batched(t: torch.Tensor, ndim: int, name: str):
+    """(tensor viewed with a leading batch dim, whether one was added)."""
+    if t.dim() == ndim:
+        return t.unsqueeze(0), True
+    if t.dim() == ndim + 1:
+        return t, False
+    raise ValueError(f"{name} must have {ndim} or {ndim + 1} dims, got {tuple(t.shape)}")
+
+
+def _shape_check(t: torch.Tensor, shape, name):
+    if tuple(t.shape[1:]) != tuple(shape):
+        raise ValueError(f"{name} has shape {tuple(t.shape[1:])}, geometry expects {tuple(shape)}")
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _out(t, shape, dtype=None):
+    return torch.empty((t.shape[0], *shape), device=t.device, dtype=dtype or t.dtype)
+
+
+# ------------------------------------------------------------ projectors --
+def _fp(fn, vol, g, vshape, sshape):
+    v, squeeze = _batched(_dev(vol, "volume"), len(vshape), "volume")
+    _shape_check(v, vshape, "volume")
+    out = _out(v, sshape)
+    cg = g.to_c()
+    with torch.cuda.device(v.device):
+        _check(fn(_ptr(v), _ptr(out), v.shape[0], ctypes.byref(cg), _DTYPES[v.dtype], _stream(v)))
+    return out[0] if squeeze else out
+
+
+def _fpT(fn, sino, g, vshape, sshape):
+    s, squeeze = _batched(_dev(sino, "sinogram"), len(sshape), "sinogram")
+    _shape_check(s, sshape, "sinogram")
+    out = _out(s, vshape)
+    cg = g.to_c()
+    with torch.cuda.device(s.device):
+        _check(fn(_ptr(s), _ptr(out), s.shape[0], ctypes.byref(cg), _DTYPES[s.dtype], _stream(s)))
+    return out[0] if squeeze else out
+
+
+def _bp(fn, sino, g, weight, scale, vshape, sshape):
+    s, squeeze = _batched(_dev(sino, "sinogram"), len(sshape), "sinogram")
+    _shape_check(s, sshape, "sinogram")
+    out = _out(s, vshape)
+    cg = g.to_c()
+    with torch.cuda.device(s.device):
+        _check(fn(_ptr(s), _ptr(out), s.shape[0], ctypes.byref(cg), int(weight), float(scale), _DTYPES[s.dtype],
+                  _stream(s)))
+    return out[0] if squeeze else out
+
+
+def _bpT(fn, vol, g, weight, scale, vshape, sshape):
+    v, squeeze = _batched(_dev(vol, "volume"), len(vshape), "volume")
+    _shape_check(v, vshape, "volume")
+    out = _out(v, sshape)
+    cg = g.to_c()
+    with torch.cuda.device(v.device):
+        _check(fn(_ptr(v), _ptr(out), v.shape[0], ctypes.byref(cg), int(weight), float(scale), _DTYPES[v.dtype],
+                  _stream(v)))
+    return out[0] if squeeze else out
+
+
+def pyro_fp_par2d(vol: torch.Tensor, g: Geometry2D) -> torch.Tensor:
+    return _fp(lib().pyro_fp_par2d, vol, g, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_fp_fan2d(vol: torch.Tensor, g: Geometry2D) -> torch.Tensor:
+    return _fp(lib().pyro_fp_fan2d, vol, g, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_fp_cone3d(vol: torch.Tensor, g: ConeGeometry3D) -> torch.Tensor:
+    return _fp(lib().pyro_fp_cone3d, vol, g, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_fpT_par2d(sino: torch.Tensor, g: Geometry2D) -> torch.Tensor:
+    return _fpT(lib().pyro_fpT_par2d, sino, g, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_fpT_fan2d(sino: torch.Tensor, g: Geometry2D) -> torch.Tensor:
+    return _fpT(lib().pyro_fpT_fan2d, sino, g, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_fpT_cone3d(sino: torch.Tensor, g: ConeGeometry3D) -> torch.Tensor:
+    return _fpT(lib().pyro_fpT_cone3d, sino, g, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_bp_par2d(sino, g: Geometry2D, weight=W_NONE, scale=1.0):
+    return _bp(lib().pyro_bp_par2d, sino, g, weight, scale, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_bp_fan2d(sino, g: Geometry2D, weight=W_NONE, scale=1.0):
+    return _bp(lib().pyro_bp_fan2d, sino, g, weight, scale, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_bp_cone3d(sino, g: ConeGeometry3D, weight=W_NONE, scale=1.0):
+    return _bp(lib().pyro_bp_cone3d, sino, g, weight, scale, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_bpT_par2d(vol, g: Geometry2D, weight=W_NONE, scale=1.0):
+    return _bpT(lib().pyro_bpT_par2d, vol, g, weight, scale, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_bpT_fan2d(vol, g: Geometry2D, weight=W_NONE, scale=1.0):
+    return _bpT(lib().pyro_bpT_fan2d, vol, g, weight, scale, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_bpT_cone3d(vol, g: ConeGeometry3D, weight=W_NONE, scale=1.0):
+    return _bpT(lib().pyro_bpT_cone3d, vol, g, weight, scale, g.volume_shape, g.sinogram_shape)
+
+
+# ------------------------------------------------------ weights / filters --
+def pyro_weights2d(sino: torch.Tensor, g: Geometry2D, cosine=True, redund=REDUND_NONE) -> torch.Tensor:
+    """In place; returns ``sino``."""
+    s, _ = _batched(_dev(sino, "sinogram"), 2, "sinogram")
+    _shape_check(s, g.sinogram_shape, "sinogram")
+    cg = g.to_c()
+    with torch.cuda.device(s.device):
+        _check(lib().pyro_weights2d(_ptr(s), s.shape[0], ctypes.byref(cg), int(bool(cosine)), int(redund),
+                                    _DTYPES[s.dtype], _stream(s)))
+    return sino
+
+
+def pyro_weights3d(sino: torch.Tensor, g: ConeGeometry3D, cosine=True, redund=REDUND_NONE) -> torch.Tensor:
+    s, _ = _batched(_dev(sino, "sinogram"), 3, "sinogram")
+    _shape_check(s, g.sinogram_shape, "sinogram")
+    cg = g.to_c()
+    with torch.cuda.device(s.device):
+        _check(lib().pyro_weights3d(_ptr(s), s.shape[0], ctypes.byref(cg), int(bool(cosine)), int(redund),
+                                    _DTYPES[s.dtype], _stream(s)))
+    return sino
+
+
+def pyro_filter_pad_length(nu: int) -> int:
+    return int(lib().pyro_filter_pad_length(nu))
+
+
+def pyro_filter_rows(rows: torch.Tensor, tau: float, kind=RAMLAK, custom_K: Optional[torch.Tensor] = None,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    r = _dev(rows, "rows")
+    nu = r.shape[-1]
+    o = torch.empty_like(r) if out is None else _dev(out, "out")
+    K = None
+    if kind == FILTER_CUSTOM:
+        K = _dev(custom_K, "custom_K")
+        if K.dtype != torch.float32 or K.numel() != pyro_filter_pad_length(nu) // 2 + 1:
+            raise ValueError("custom_K must be float32 with pad_length(nu)//2 + 1 entries")
+    with torch.cuda.device(r.device):
+        _check(lib().pyro_filter_rows(_ptr(r), _ptr(o), r.numel() // nu, nu, float(tau), int(kind), _ptr(K),
+                                      _DTYPES[r.dtype], _stream(r)))
+    return o
+
+
+def pyro_filter_grad_K(p: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
+    p, g = _dev(p, "p"), _dev(g, "g")
+    if p.dtype != torch.float32 or g.dtype != torch.float32 or p.shape != g.shape:
+        raise ValueError("p and g must be float32 tensors of one shape")
+    nu = p.shape[-1]
+    dK = torch.empty(pyro_filter_pad_length(nu) // 2 + 1, device=p.device, dtype=torch.float32)
+    with torch.cuda.device(p.device):
+        _check(lib().pyro_filter_grad_K(_ptr(p), _ptr(g), _ptr(dK), p.numel() // nu, nu, _stream(p)))
+    return dK
+
+
+# ------------------------------------------------------------------ FBP --
+def pyro_fdk(sino: torch.Tensor, g: ConeGeometry3D, kind=SHEPP_LOGAN, redund=REDUND_PARKER,
+             custom_K: Optional[torch.Tensor] = None, workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    s, squeeze = _batched(_dev(sino, "sinogram"), 3, "sinogram")
+    _shape_check(s, g.sinogram_shape, "sinogram")
+    cg = g.to_c()
+    need = lib().pyro_fdk_workspace_bytes(ctypes.byref(cg), s.shape[0])
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=s.device)
+    out = _out(s, g.volume_shape)
+    with torch.cuda.device(s.device):
+        _check(lib().pyro_fdk(_ptr(s), _ptr(out), s.shape[0], ctypes.byref(cg), int(kind), _ptr(custom_K),
+                              int(redund), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                              _DTYPES[s.dtype], _stream(s)))
+    return out[0] if squeeze else out
+
+
+def _fbp2d(fan, sino, g, kind, redund, custom_K, workspace):
+    s, squeeze = _batched(_dev(sino, "sinogram"), 2, "sinogram")
+    _shape_check(s, g.sinogram_shape, "sinogram")
+    cg = g.to_c()
+    need = lib().pyro_fbp2d_workspace_bytes(ctypes.byref(cg), s.shape[0])
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=s.device)
+    out = _out(s, g.volume_shape)
+    nbytes = workspace.numel() * workspace.element_size()
+    with torch.cuda.device(s.device):
+        if fan:
+            st = lib().pyro_fbp_fan2d(_ptr(s), _ptr(out), s.shape[0], ctypes.byref(cg), int(kind), _ptr(custom_K),
+                                      int(redund), _ptr(workspace), nbytes, _DTYPES[s.dtype], _stream(s))
+        else:
+            st = lib().pyro_fbp_par2d(_ptr(s), _ptr(out), s.shape[0], ctypes.byref(cg), int(kind), _ptr(custom_K),
+                                      _ptr(workspace), nbytes, _DTYPES[s.dtype], _stream(s))
+        _check(st)
+    return out[0] if squeeze else out
+
+
+def pyro_fbp_par2d(sino, g: Geometry2D, kind=RAMLAK, custom_K=None, workspace=None):
+    return _fbp2d(False, sino, g, kind, REDUND_NONE, custom_K, workspace)
+
+
+def pyro_fbp_fan2d(sino, g: Geometry2D, kind=RAMLAK, redund=REDUND_FULL, custom_K=None, workspace=None):
+    return _fbp2d(True, sino, g, kind, redund, custom_K, workspace)
+
+
+def version() -> str:
+    return lib().pyro_version().decode()

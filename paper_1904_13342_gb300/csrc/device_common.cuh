@@ -1,0 +1,143 @@
+// Device helpers shared by the projector, back-projector and filter kernels:
+// storage-type loads/stores (FP32 arithmetic for every storage type) and the
+// zero-extended linear / bilinear / trilinear interpolation of the paper's
+// "kernel interpolation" mode, done in software so that the FP32 result
+// stays within ~1e-6 of the exact interpolant (hardware texture filtering
+// quantises the weights to 8 fractional bits).
+#pragma once
+
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_runtime.h>
+
+namespace pyro {
+
+template <typename T>
+__device__ __forceinline__ float ld(const T *p);
+template <>
+__device__ __forceinline__ float ld<float>(const float *p)
+{
+    return __ldg(p);
+}
+template <>
+__device__ __forceinline__ float ld<__half>(const __half *p)
+{
+    return __half2float(__ldg(p));
+}
+template <>
+__device__ __forceinline__ float ld<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    return __bfloat162float(__ldg(p));
+}
+
+template <typename T>
+__device__ __forceinline__ T to_storage(float v);
+template <>
+__device__ __forceinline__ float to_storage<float>(float v)
+{
+    return v;
+}
+template <>
+__device__ __forceinline__ __half to_storage<__half>(float v)
+{
+    return __float2half_rn(v);
+}
+template <>
+__device__ __forceinline__ __nv_bfloat16 to_storage<__nv_bfloat16>(float v)
+{
+    return __float2bfloat16_rn(v);
+}
+
+template <typename T>
+__device__ __forceinline__ float to_float(T v);
+template <>
+__device__ __forceinline__ float to_float<float>(float v)
+{
+    return v;
+}
+template <>
+__device__ __forceinline__ float to_float<__half>(__half v)
+{
+    return __half2float(v);
+}
+template <>
+__device__ __forceinline__ float to_float<__nv_bfloat16>(__nv_bfloat16 v)
+{
+    return __bfloat162float(v);
+}
+
+// One axis of a zero-extended linear interpolation at index position f:
+// the two taps i0 (weight w0) and i1 = i0 + 1 (weight w1), clamped into
+// [0, n-1] for addressing, with the weight of a tap outside the array zeroed.
+struct Axis {
+    int i0, i1;
+    float w0, w1;
+};
+
+__device__ __forceinline__ Axis axis_taps(float f, int n)
+{
+    const float f0 = floorf(f);
+    const float a = f - f0;
+    const int i = (int)f0;
+    Axis r;
+    r.w0 = ((unsigned)i < (unsigned)n) ? 1.0f - a : 0.0f;
+    r.w1 = ((unsigned)(i + 1) < (unsigned)n) ? a : 0.0f;
+    r.i0 = min(max(i, 0), n - 1);
+    r.i1 = min(max(i + 1, 0), n - 1);
+    return r;
+}
+
+template <typename T>
+__device__ __forceinline__ float lerp_zero(const T *row, int n, float f)
+{
+    const Axis a = axis_taps(f, n);
+    return a.w0 * ld(row + a.i0) + a.w1 * ld(row + a.i1);
+}
+
+template <typename T>
+__device__ __forceinline__ float bilerp_zero(const T *img, int nx, int ny, float fx, float fy)
+{
+    const Axis ax = axis_taps(fx, nx);
+    const Axis ay = axis_taps(fy, ny);
+    const T *r0 = img + (size_t)ay.i0 * nx;
+    const T *r1 = img + (size_t)ay.i1 * nx;
+    const float v0 = ax.w0 * ld(r0 + ax.i0) + ax.w1 * ld(r0 + ax.i1);
+    const float v1 = ax.w0 * ld(r1 + ax.i0) + ax.w1 * ld(r1 + ax.i1);
+    return ay.w0 * v0 + ay.w1 * v1;
+}
+
+template <typename T>
+__device__ __forceinline__ float trilerp_zero(const T *vol, int nx, int ny, int nz, float fx, float fy, float fz)
+{
+    const Axis ax = axis_taps(fx, nx);
+    const Axis ay = axis_taps(fy, ny);
+    const Axis az = axis_taps(fz, nz);
+    const size_t sxy = (size_t)nx * ny;
+    const T *p00 = vol + az.i0 * sxy + (size_t)ay.i0 * nx;
+    const T *p01 = vol + az.i0 * sxy + (size_t)ay.i1 * nx;
+    const T *p10 = vol + az.i1 * sxy + (size_t)ay.i0 * nx;
+    const T *p11 = vol + az.i1 * sxy + (size_t)ay.i1 * nx;
+    const float v00 = ax.w0 * ld(p00 + ax.i0) + ax.w1 * ld(p00 + ax.i1);
+    const float v01 = ax.w0 * ld(p01 + ax.i0) + ax.w1 * ld(p01 + ax.i1);
+    const float v10 = ax.w0 * ld(p10 + ax.i0) + ax.w1 * ld(p10 + ax.i1);
+    const float v11 = ax.w0 * ld(p11 + ax.i0) + ax.w1 * ld(p11 + ax.i1);
+    return az.w0 * (ay.w0 * v00 + ay.w1 * v01) + az.w1 * (ay.w0 * v10 + ay.w1 * v11);
+}
+
+// Restrict the sample index m of p(m) = p0 + m q to the open support
+// (-1, n) of the zero-extended interpolant on one axis.  Rounded outwards:
+// a sample just outside contributes an exact 0 through axis_taps.
+__device__ __forceinline__ void clip_axis(float p0, float q, int n, float &lo, float &hi)
+{
+    if (fabsf(q) > 1e-30f) {
+        const float t1 = (-1.0f - p0) / q;
+        const float t2 = ((float)n - p0) / q;
+        lo = fmaxf(lo, fminf(t1, t2));
+        hi = fminf(hi, fmaxf(t1, t2));
+    } else if (!(p0 > -1.0f && p0 < (float)n)) {
+        lo = 1.0f;
+        hi = -1.0f;
+    }
+}
+
+}  // namespace pyro

@@ -1,0 +1,135 @@
+// Internal declarations shared by the host API (pyro_api.cpp) and the CUDA
+// kernels.  Per-view geometry travels to the kernels as __grid_constant__
+// kernel parameters (read through the constant cache, warp-uniform in every
+// kernel), so concurrent calls on different streams never share state and
+// the library needs no device allocation of its own.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstddef>
+#include <cstdint>
+
+#include "pyro.h"
+
+namespace pyro {
+
+// Kernel-parameter space is 32764 bytes; these caps keep every parameter
+// pack below it.  Longer trajectories are processed in chunks of views.
+constexpr int kMaxViews2D = 1024;    // 2D FP / BP: <= 6 floats per view
+constexpr int kMaxViewsConeBP = 600; // cone BP: 12 floats per view
+constexpr int kMaxViewsConeFP = 400; // cone FP: 17 floats per view
+constexpr int kMaxPadLength = 8192;  // filter: pn <= 8192, so nu <= 4096
+
+// ---------------------------------------------------------------- FP 2D --
+// Ray of bin k in view j, in millimetres: parallel beam a = u e_u, d = c;
+// fan beam written around the closest approach B to the iso-centre,
+// B = SID u / L^2 (SDD e_u - u c), d = (SDD c + u e_u) / L, L^2 = SDD^2+u^2,
+// which avoids the cancellation of S - (S.d) d in FP32.
+struct FP2DParams {
+    int nx, ny, nu, n_views;   // n_views in this chunk
+    int view0;                 // first view of this chunk (sinogram offset)
+    int views_total;           // views in the full sinogram
+    int fan;
+    int M;                     // samples m = -M..M around the closest approach
+    float inv_sx, inv_sy;      // 1 / spacing
+    float cx, cy;              // (n-1)/2
+    float su, cu;              // bin spacing, (nu-1)/2
+    float sid, sdd;
+    float dt;
+    float2 dir[kMaxViews2D];   // central-ray vector c_j = (cos b_j, sin b_j)
+};
+
+// ---------------------------------------------------------------- FP 3D --
+// Cone ray of pixel (k, l) in camera coordinates q = K^-1 (k, l, 1) (P = K R
+// [I | -S] after an RQ split done in FP64 on the host); the closest approach
+// of the ray to the iso-centre is
+//   B_cam = s_perp - (s_perp.q) q/|q|^2 + s3 (-q_x, -q_y, q_x^2+q_y^2)/|q|^2
+// with S_cam = R S = (s_perp, s3), free of cancellation.  W = diag(1/s) R^T
+// takes camera vectors to voxel-index units.
+struct ConeFPView {
+    float W[9];                // row-major 3x3
+    float a0, a1, a2;          // q_x = a0 k + a1 l + a2
+    float b0, b2;              // q_y = b0 l + b2
+    float s1, s2, s3;          // source in camera coordinates
+};
+
+struct FP3DParams {
+    int nx, ny, nz, nu, nv, n_views, view0, views_total;
+    int M;
+    float cx, cy, cz;          // (n-1)/2 per axis
+    float dt;
+    ConeFPView v[kMaxViewsConeFP];
+};
+
+// ------------------------------------------------------------- BP 2D/3D --
+// Voxel-index to detector map, pre-scaled on the host: for voxel (i, j[, z])
+//   x = r0 . (i, j[, z], 1),  w = r2 . (...),  k = x / w + cu,
+// with r0 centred on the detector (so x/w is small near the centre) and the
+// whole matrix divided by SID, so that w = L / SID and omega = w^-wexp.
+struct BP2DParams {
+    int nx, ny, nu, n_views, view0, views_total;
+    int wexp;
+    int parallel;              // w == 1 exactly
+    float cu, scale;
+    float m[kMaxViews2D][6];   // x row (3), w row (3)
+};
+
+struct BP3DParams {
+    int nx, ny, nz, nu, nv, n_views, view0, views_total;
+    int wexp;
+    int z_invariant;           // P[0][2] == P[2][2] == 0 for every view
+    int accumulate;            // add into the output (view chunks after the first)
+    float cu, cv, scale;
+    float P[kMaxViewsConeBP][12];
+};
+
+// ----------------------------------------------------- weights / filter --
+struct WeightParams {
+    int nu, nv, n_views;
+    int cosine, redund;        // pyro_redund
+    float su, sv, cu, cv, sdd;
+    float delta;               // Parker half fan angle
+};
+
+struct BetaTable {             // b_j - b_0 per view, for Parker weights
+    float beta[kMaxViews2D];
+};
+
+struct FilterParams {
+    long n_rows;
+    int nu, pn, log2pn;
+    int rows_per_view;         // rows of one view (nv for cone, 1 for 2D)
+    int n_views;
+    int apply_weights;         // fuse W_red W_cos into the load
+    WeightParams w;
+    float K[kMaxPadLength / 2 + 1];
+};
+
+// --------------------------------------------------------------- launchers --
+// All launchers return cudaSuccess or the launch error; T is the storage type.
+cudaError_t launch_fp2d(const void *vol, void *sino, int batch, const FP2DParams &p, pyro_dtype dt,
+                        cudaStream_t s);
+cudaError_t launch_fp2d_adjoint(const void *sino, void *vol, int batch, const FP2DParams &p, cudaStream_t s);
+cudaError_t launch_fp3d(const void *vol, void *sino, int batch, const FP3DParams &p, pyro_dtype dt,
+                        cudaStream_t s);
+cudaError_t launch_fp3d_adjoint(const void *sino, void *vol, int batch, const FP3DParams &p, cudaStream_t s);
+
+// sino_dtype / vol_dtype may differ (FDK reads an FP32 workspace)
+cudaError_t launch_bp2d(const void *sino, void *vol, int batch, const BP2DParams &p, pyro_dtype sino_dt,
+                        pyro_dtype vol_dt, int accumulate, cudaStream_t s);
+cudaError_t launch_bp2d_transpose(const void *vol, void *sino, int batch, const BP2DParams &p, cudaStream_t s);
+cudaError_t launch_bp3d(const void *sino, void *vol, int batch, const BP3DParams &p, pyro_dtype sino_dt,
+                        pyro_dtype vol_dt, cudaStream_t s);
+cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const BP3DParams &p, cudaStream_t s);
+
+cudaError_t launch_weights(void *sino, int batch, const WeightParams &w, const BetaTable &beta, pyro_dtype dt,
+                           cudaStream_t s);
+// rows in (dtype in_dt) -> rows out (dtype out_dt); custom_K overrides p.K when non-null
+cudaError_t launch_filter(const void *in, void *out, const FilterParams &p, const BetaTable *beta,
+                          const float *custom_K, pyro_dtype in_dt, pyro_dtype out_dt, cudaStream_t s);
+cudaError_t launch_filter_grad_K(const float *p, const float *g, float *dK, long n_rows, int nu, int pn,
+                                 int log2pn, cudaStream_t s);
+
+int device_sm_count();
+
+}  // namespace pyro

@@ -1,0 +1,278 @@
+// Voxel-driven back-projection and its transpose
+// (paper, Section "The Operator as a Layer": one thread per pixel / voxel
+// projects its centre onto every view and accumulates the interpolated
+// detector value; the cone-beam form follows Scherl et al. with projection
+// matrices).
+//
+// Per view the host supplies a voxel-index -> detector map divided by SID
+// (so w = L / SID and the FDK weight (SID/L)^2 is just 1/w^2) whose first
+// rows are centred on the detector.  Each cone-beam thread owns one (x, y)
+// column and ZB consecutive z; for circular trajectories the u coordinate
+// and the weight do not depend on z and are computed once per view.
+#include "device_common.cuh"
+#include "internal.h"
+
+namespace pyro {
+
+namespace {
+
+__device__ __forceinline__ float weight_of(float rw, int wexp)
+{
+    return wexp == 0 ? 1.0f : (wexp == 1 ? rw : rw * rw);
+}
+
+template <typename TS, typename TV, bool PAR>
+__global__ void __launch_bounds__(256) bp2d_kernel(const TS *__restrict__ sino, TV *__restrict__ vol,
+                                                   const __grid_constant__ BP2DParams p, int accumulate)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int b = blockIdx.z;
+    if (i >= p.nx || j >= p.ny) return;
+    const float fi = (float)i, fj = (float)j;
+    const TS *S = sino + ((size_t)b * p.views_total + p.view0) * p.nu;
+    float acc = 0.0f;
+    for (int v = 0; v < p.n_views; ++v) {
+        const float *m = p.m[v];
+        const float x = fmaf(m[0], fi, fmaf(m[1], fj, m[2]));
+        float k, om;
+        if (PAR) {
+            k = x + p.cu;
+            om = 1.0f;
+        } else {
+            const float w = fmaf(m[3], fi, fmaf(m[4], fj, m[5]));
+            const float rw = 1.0f / w;
+            k = fmaf(x, rw, p.cu);
+            om = weight_of(rw, p.wexp);
+        }
+        acc = fmaf(om, lerp_zero(S + (size_t)v * p.nu, p.nu, k), acc);
+    }
+    const size_t o = ((size_t)b * p.ny + j) * p.nx + i;
+    float out = p.scale * acc;
+    if (accumulate) out += to_float<TV>(vol[o]);
+    vol[o] = to_storage<TV>(out);
+}
+
+__global__ void __launch_bounds__(256) bp2d_transpose_kernel(const float *__restrict__ vol, float *__restrict__ sino,
+                                                             const __grid_constant__ BP2DParams p)
+{
+    const int i = blockIdx.x * 32 + threadIdx.x;
+    const int j = blockIdx.y * 8 + threadIdx.y;
+    const int b = blockIdx.z;
+    if (i >= p.nx || j >= p.ny) return;
+    const float g = p.scale * vol[((size_t)b * p.ny + j) * p.nx + i];
+    if (g == 0.0f) return;
+    const float fi = (float)i, fj = (float)j;
+    float *S = sino + ((size_t)b * p.views_total + p.view0) * p.nu;
+    for (int v = 0; v < p.n_views; ++v) {
+        const float *m = p.m[v];
+        const float x = fmaf(m[0], fi, fmaf(m[1], fj, m[2]));
+        float k, om;
+        if (p.parallel) {
+            k = x + p.cu;
+            om = 1.0f;
+        } else {
+            const float w = fmaf(m[3], fi, fmaf(m[4], fj, m[5]));
+            const float rw = 1.0f / w;
+            k = fmaf(x, rw, p.cu);
+            om = weight_of(rw, p.wexp);
+        }
+        const Axis a = axis_taps(k, p.nu);
+        float *row = S + (size_t)v * p.nu;
+        const float gw = g * om;
+        if (a.w0 != 0.0f) atomicAdd(row + a.i0, gw * a.w0);
+        if (a.w1 != 0.0f) atomicAdd(row + a.i1, gw * a.w1);
+    }
+}
+
+constexpr int kBPX = 32, kBPY = 8, kBPZ = 8;
+
+template <typename TS, typename TV, bool ZINV>
+__global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__ sino, TV *__restrict__ vol,
+                                                          const __grid_constant__ BP3DParams p)
+{
+    const int i = blockIdx.x * kBPX + threadIdx.x;
+    const int j = blockIdx.y * kBPY + threadIdx.y;
+    const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
+    const int b = blockIdx.z / zblocks;
+    const int z0 = (blockIdx.z % zblocks) * kBPZ;
+    if (i >= p.nx || j >= p.ny) return;
+    const float fi = (float)i, fj = (float)j;
+    const size_t vstride = (size_t)p.nu * p.nv;
+    const TS *S0 = sino + ((size_t)b * p.views_total + p.view0) * vstride;
+    float acc[kBPZ];
+#pragma unroll
+    for (int zz = 0; zz < kBPZ; ++zz) acc[zz] = 0.0f;
+
+    for (int v = 0; v < p.n_views; ++v) {
+        const float *P = p.P[v];
+        const TS *S = S0 + (size_t)v * vstride;
+        const float xb = fmaf(P[0], fi, fmaf(P[1], fj, P[3]));
+        const float yb = fmaf(P[4], fi, fmaf(P[5], fj, P[7]));
+        const float wb = fmaf(P[8], fi, fmaf(P[9], fj, P[11]));
+        if (ZINV) {
+            const float rw = 1.0f / wb;
+            const float om = weight_of(rw, p.wexp);
+            const Axis au = axis_taps(fmaf(xb, rw, p.cu), p.nu);
+            const float w0 = om * au.w0, w1 = om * au.w1;
+            const float dl = P[6] * rw;
+            const float l0 = fmaf(yb, rw, p.cv);
+#pragma unroll
+            for (int zz = 0; zz < kBPZ; ++zz) {
+                const Axis av = axis_taps(fmaf((float)(z0 + zz), dl, l0), p.nv);
+                const TS *r0 = S + (size_t)av.i0 * p.nu;
+                const TS *r1 = S + (size_t)av.i1 * p.nu;
+                const float t0 = fmaf(w0, ld(r0 + au.i0), w1 * ld(r0 + au.i1));
+                const float t1 = fmaf(w0, ld(r1 + au.i0), w1 * ld(r1 + au.i1));
+                acc[zz] = fmaf(av.w0, t0, fmaf(av.w1, t1, acc[zz]));
+            }
+        } else {
+#pragma unroll
+            for (int zz = 0; zz < kBPZ; ++zz) {
+                const float fz = (float)(z0 + zz);
+                const float x = fmaf(P[2], fz, xb);
+                const float y = fmaf(P[6], fz, yb);
+                const float w = fmaf(P[10], fz, wb);
+                const float rw = 1.0f / w;
+                const float om = weight_of(rw, p.wexp);
+                acc[zz] = fmaf(om, bilerp_zero(S, p.nu, p.nv, fmaf(x, rw, p.cu), fmaf(y, rw, p.cv)), acc[zz]);
+            }
+        }
+    }
+    const size_t sxy = (size_t)p.nx * p.ny;
+    TV *out = vol + (size_t)b * sxy * p.nz + (size_t)j * p.nx + i;
+#pragma unroll
+    for (int zz = 0; zz < kBPZ; ++zz) {
+        const int z = z0 + zz;
+        if (z < p.nz) {
+            float r = p.scale * acc[zz];
+            if (p.accumulate) r += to_float<TV>(out[z * sxy]);
+            out[z * sxy] = to_storage<TV>(r);
+        }
+    }
+}
+
+__global__ void __launch_bounds__(kBPX *kBPY) bp3d_transpose_kernel(const float *__restrict__ vol,
+                                                                    float *__restrict__ sino,
+                                                                    const __grid_constant__ BP3DParams p)
+{
+    const int i = blockIdx.x * kBPX + threadIdx.x;
+    const int j = blockIdx.y * kBPY + threadIdx.y;
+    const int b = blockIdx.z / p.nz;
+    const int z = blockIdx.z % p.nz;
+    if (i >= p.nx || j >= p.ny) return;
+    const float g = p.scale * vol[(((size_t)b * p.nz + z) * p.ny + j) * p.nx + i];
+    if (g == 0.0f) return;
+    const float fi = (float)i, fj = (float)j, fz = (float)z;
+    const size_t vstride = (size_t)p.nu * p.nv;
+    float *S0 = sino + ((size_t)b * p.views_total + p.view0) * vstride;
+    for (int v = 0; v < p.n_views; ++v) {
+        const float *P = p.P[v];
+        const float x = fmaf(P[0], fi, fmaf(P[1], fj, fmaf(P[2], fz, P[3])));
+        const float y = fmaf(P[4], fi, fmaf(P[5], fj, fmaf(P[6], fz, P[7])));
+        const float w = fmaf(P[8], fi, fmaf(P[9], fj, fmaf(P[10], fz, P[11])));
+        const float rw = 1.0f / w;
+        const float gw = g * weight_of(rw, p.wexp);
+        const Axis au = axis_taps(fmaf(x, rw, p.cu), p.nu);
+        const Axis av = axis_taps(fmaf(y, rw, p.cv), p.nv);
+        float *S = S0 + (size_t)v * vstride;
+        float *r0 = S + (size_t)av.i0 * p.nu;
+        float *r1 = S + (size_t)av.i1 * p.nu;
+        const float g0 = gw * av.w0, g1 = gw * av.w1;
+        if (g0 * au.w0 != 0.0f) atomicAdd(r0 + au.i0, g0 * au.w0);
+        if (g0 * au.w1 != 0.0f) atomicAdd(r0 + au.i1, g0 * au.w1);
+        if (g1 * au.w0 != 0.0f) atomicAdd(r1 + au.i0, g1 * au.w0);
+        if (g1 * au.w1 != 0.0f) atomicAdd(r1 + au.i1, g1 * au.w1);
+    }
+}
+
+template <typename TS, typename TV>
+cudaError_t bp2d_dispatch(const void *sino, void *vol, int batch, const BP2DParams &p, int accumulate, cudaStream_t s)
+{
+    dim3 block(32, 8);
+    dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, batch);
+    if (p.parallel)
+        bp2d_kernel<TS, TV, true><<<grid, block, 0, s>>>((const TS *)sino, (TV *)vol, p, accumulate);
+    else
+        bp2d_kernel<TS, TV, false><<<grid, block, 0, s>>>((const TS *)sino, (TV *)vol, p, accumulate);
+    return cudaGetLastError();
+}
+
+template <typename TS, typename TV>
+cudaError_t bp3d_dispatch(const void *sino, void *vol, int batch, const BP3DParams &p, cudaStream_t s)
+{
+    dim3 block(kBPX, kBPY);
+    const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
+    dim3 grid((p.nx + kBPX - 1) / kBPX, (p.ny + kBPY - 1) / kBPY, (unsigned)(zblocks * batch));
+    if (p.z_invariant)
+        bp3d_kernel<TS, TV, true><<<grid, block, 0, s>>>((const TS *)sino, (TV *)vol, p);
+    else
+        bp3d_kernel<TS, TV, false><<<grid, block, 0, s>>>((const TS *)sino, (TV *)vol, p);
+    return cudaGetLastError();
+}
+
+template <typename TS>
+cudaError_t bp2d_by_vol(const void *sino, void *vol, int batch, const BP2DParams &p, pyro_dtype vol_dt, int acc,
+                        cudaStream_t s)
+{
+    switch (vol_dt) {
+    case PYRO_F32: return bp2d_dispatch<TS, float>(sino, vol, batch, p, acc, s);
+    case PYRO_F16: return bp2d_dispatch<TS, __half>(sino, vol, batch, p, acc, s);
+    case PYRO_BF16: return bp2d_dispatch<TS, __nv_bfloat16>(sino, vol, batch, p, acc, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename TS>
+cudaError_t bp3d_by_vol(const void *sino, void *vol, int batch, const BP3DParams &p, pyro_dtype vol_dt,
+                        cudaStream_t s)
+{
+    switch (vol_dt) {
+    case PYRO_F32: return bp3d_dispatch<TS, float>(sino, vol, batch, p, s);
+    case PYRO_F16: return bp3d_dispatch<TS, __half>(sino, vol, batch, p, s);
+    case PYRO_BF16: return bp3d_dispatch<TS, __nv_bfloat16>(sino, vol, batch, p, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+}  // namespace
+
+cudaError_t launch_bp2d(const void *sino, void *vol, int batch, const BP2DParams &p, pyro_dtype sino_dt,
+                        pyro_dtype vol_dt, int accumulate, cudaStream_t s)
+{
+    switch (sino_dt) {
+    case PYRO_F32: return bp2d_by_vol<float>(sino, vol, batch, p, vol_dt, accumulate, s);
+    case PYRO_F16: return bp2d_by_vol<__half>(sino, vol, batch, p, vol_dt, accumulate, s);
+    case PYRO_BF16: return bp2d_by_vol<__nv_bfloat16>(sino, vol, batch, p, vol_dt, accumulate, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bp2d_transpose(const void *vol, void *sino, int batch, const BP2DParams &p, cudaStream_t s)
+{
+    dim3 block(32, 8);
+    dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, batch);
+    bp2d_transpose_kernel<<<grid, block, 0, s>>>((const float *)vol, (float *)sino, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bp3d(const void *sino, void *vol, int batch, const BP3DParams &p, pyro_dtype sino_dt,
+                        pyro_dtype vol_dt, cudaStream_t s)
+{
+    switch (sino_dt) {
+    case PYRO_F32: return bp3d_by_vol<float>(sino, vol, batch, p, vol_dt, s);
+    case PYRO_F16: return bp3d_by_vol<__half>(sino, vol, batch, p, vol_dt, s);
+    case PYRO_BF16: return bp3d_by_vol<__nv_bfloat16>(sino, vol, batch, p, vol_dt, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const BP3DParams &p, cudaStream_t s)
+{
+    dim3 block(kBPX, kBPY);
+    dim3 grid((p.nx + kBPX - 1) / kBPX, (p.ny + kBPY - 1) / kBPY, (unsigned)(p.nz * batch));
+    bp3d_transpose_kernel<<<grid, block, 0, s>>>((const float *)vol, (float *)sino, p);
+    return cudaGetLastError();
+}
+
+}  // namespace pyro

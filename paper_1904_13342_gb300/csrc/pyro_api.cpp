@@ -1,0 +1,966 @@
+// Host side of the C ABI declared in include/pyro.h: argument validation,
+// FP64 geometry preparation (trajectory, projection-matrix normalisation,
+// RQ split for the ray set-up, voxel-to-detector maps for the
+// back-projectors, filter spectra), chunking of long trajectories into
+// kernel-parameter-sized pieces, and dispatch to the CUDA launchers.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "internal.h"
+
+namespace pyro {
+
+namespace {
+
+thread_local std::string g_last_error;
+
+int fail(int code, const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+    return code;
+}
+
+#define PYRO_CUDA(call)                                                                        \
+    do {                                                                                       \
+        cudaError_t e_ = (call);                                                               \
+        if (e_ != cudaSuccess) return fail(PYRO_ECUDA, "%s: %s", #call, cudaGetErrorString(e_)); \
+    } while (0)
+
+#define PYRO_CHECK(cond, ...)                        \
+    do {                                             \
+        if (!(cond)) return fail(PYRO_EINVAL, __VA_ARGS__); \
+    } while (0)
+
+size_t elem_size(pyro_dtype dt)
+{
+    return dt == PYRO_F32 ? 4 : 2;
+}
+
+bool valid_dtype(int dt)
+{
+    return dt == PYRO_F32 || dt == PYRO_F16 || dt == PYRO_BF16;
+}
+
+bool pos_finite(double x)
+{
+    return std::isfinite(x) && x > 0.0;
+}
+
+bool aligned16(const void *p)
+{
+    return ((uintptr_t)p & 15u) == 0;
+}
+
+// ---------------------------------------------------------------- 2D ----
+struct Geo2D {
+    int nx, ny, nu, nv;
+    double sx, sy, su, sid, sdd, step, range;
+    std::vector<double> beta;
+    bool fan;
+    int M;
+};
+
+int prep2d(const pyro_geom2d *g, bool fan, Geo2D &G)
+{
+    PYRO_CHECK(g != nullptr, "geometry is NULL");
+    PYRO_CHECK(g->nx > 0 && g->ny > 0 && g->nu > 0 && g->n_views > 0, "shapes must be positive (nx=%d ny=%d nu=%d views=%d)",
+               g->nx, g->ny, g->nu, g->n_views);
+    PYRO_CHECK(pos_finite(g->sx) && pos_finite(g->sy) && pos_finite(g->su), "spacings must be positive and finite");
+    G.nx = g->nx;
+    G.ny = g->ny;
+    G.nu = g->nu;
+    G.nv = 1;
+    G.sx = g->sx;
+    G.sy = g->sy;
+    G.su = g->su;
+    G.fan = fan;
+    G.range = g->range;
+    G.beta.resize(g->n_views);
+    if (g->angles) {
+        for (int j = 0; j < g->n_views; ++j) {
+            PYRO_CHECK(std::isfinite(g->angles[j]), "angle %d is not finite", j);
+            G.beta[j] = g->angles[j];
+        }
+    } else {
+        PYRO_CHECK(std::isfinite(g->range) && g->range != 0.0, "angles is NULL and range is not a finite non-zero value");
+        for (int j = 0; j < g->n_views; ++j) G.beta[j] = j * (g->range / g->n_views);
+    }
+    G.step = g->step > 0.0 ? g->step : 0.5 * std::min(g->sx, g->sy);
+    PYRO_CHECK(std::isfinite(G.step), "step is not finite");
+    const double T = 0.5 * std::hypot((g->nx + 1) * g->sx, (g->ny + 1) * g->sy);
+    const double M = std::ceil(T / G.step);
+    PYRO_CHECK(M < (1 << 28), "step too small for the image (%g samples per ray)", 2 * M + 1);
+    G.M = (int)M;
+    G.sid = g->sid;
+    G.sdd = g->sdd;
+    if (fan) {
+        PYRO_CHECK(pos_finite(g->sid) && pos_finite(g->sdd) && g->sdd > g->sid, "fan beam needs 0 < SID < SDD");
+        PYRO_CHECK(g->sid > T, "the source (SID=%g) must lie outside the image support (radius %g)", g->sid, T);
+    }
+    return PYRO_OK;
+}
+
+void fill_fp2d(const Geo2D &G, int v0, int nvw, FP2DParams &p)
+{
+    p.nx = G.nx;
+    p.ny = G.ny;
+    p.nu = G.nu;
+    p.n_views = nvw;
+    p.view0 = v0;
+    p.views_total = (int)G.beta.size();
+    p.fan = G.fan;
+    p.M = G.M;
+    p.inv_sx = (float)(1.0 / G.sx);
+    p.inv_sy = (float)(1.0 / G.sy);
+    p.cx = (float)(0.5 * (G.nx - 1));
+    p.cy = (float)(0.5 * (G.ny - 1));
+    p.su = (float)G.su;
+    p.cu = (float)(0.5 * (G.nu - 1));
+    p.sid = (float)G.sid;
+    p.sdd = (float)G.sdd;
+    p.dt = (float)G.step;
+    for (int v = 0; v < nvw; ++v) p.dir[v] = make_float2((float)std::cos(G.beta[v0 + v]), (float)std::sin(G.beta[v0 + v]));
+}
+
+// k(X) - cu and depth for pixel (i, j), as affine maps divided by SID (fan)
+void fill_bp2d(const Geo2D &G, int v0, int nvw, int wexp, float scale, BP2DParams &p)
+{
+    p.nx = G.nx;
+    p.ny = G.ny;
+    p.nu = G.nu;
+    p.n_views = nvw;
+    p.view0 = v0;
+    p.views_total = (int)G.beta.size();
+    p.wexp = G.fan ? wexp : 0;
+    p.parallel = !G.fan;
+    p.cu = (float)(0.5 * (G.nu - 1));
+    p.scale = scale;
+    const double cx = 0.5 * (G.nx - 1), cy = 0.5 * (G.ny - 1);
+    for (int v = 0; v < nvw; ++v) {
+        const double b = G.beta[v0 + v];
+        const double c0 = std::cos(b), c1 = std::sin(b), e0 = -std::sin(b), e1 = std::cos(b);
+        // e_u . X and c . X as affine maps of (i, j)
+        const double ex = e0 * G.sx, ey = e1 * G.sy, ez = -(e0 * G.sx * cx + e1 * G.sy * cy);
+        const double dx = c0 * G.sx, dy = c1 * G.sy, dz = -(c0 * G.sx * cx + c1 * G.sy * cy);
+        double m[6];
+        if (!G.fan) {
+            m[0] = ex / G.su;
+            m[1] = ey / G.su;
+            m[2] = ez / G.su;
+            m[3] = 0.0;
+            m[4] = 0.0;
+            m[5] = 1.0;
+        } else {
+            const double f = G.sdd / (G.su * G.sid);
+            m[0] = f * ex;
+            m[1] = f * ey;
+            m[2] = f * ez;
+            m[3] = dx / G.sid;
+            m[4] = dy / G.sid;
+            m[5] = dz / G.sid + 1.0;
+        }
+        for (int a = 0; a < 6; ++a) p.m[v][a] = (float)m[a];
+    }
+}
+
+// ---------------------------------------------------------------- 3D ----
+struct Geo3D {
+    int nx, ny, nz, nu, nv;
+    double sx, sy, sz, su, sv, sid, sdd, step, range;
+    std::vector<double> beta;
+    std::vector<double> P;  // normalised [V][12]
+    std::vector<double> S;  // source [V][3]
+    int M;
+    double T;
+};
+
+void inv3(const double m[9], double r[9])
+{
+    const double det = m[0] * (m[4] * m[8] - m[5] * m[7]) - m[1] * (m[3] * m[8] - m[5] * m[6]) +
+                       m[2] * (m[3] * m[7] - m[4] * m[6]);
+    r[0] = (m[4] * m[8] - m[5] * m[7]) / det;
+    r[1] = (m[2] * m[7] - m[1] * m[8]) / det;
+    r[2] = (m[1] * m[5] - m[2] * m[4]) / det;
+    r[3] = (m[5] * m[6] - m[3] * m[8]) / det;
+    r[4] = (m[0] * m[8] - m[2] * m[6]) / det;
+    r[5] = (m[2] * m[3] - m[0] * m[5]) / det;
+    r[6] = (m[3] * m[7] - m[4] * m[6]) / det;
+    r[7] = (m[1] * m[6] - m[0] * m[7]) / det;
+    r[8] = (m[0] * m[4] - m[1] * m[3]) / det;
+}
+
+int prep3d(const pyro_geom3d *g, Geo3D &G)
+{
+    PYRO_CHECK(g != nullptr, "geometry is NULL");
+    PYRO_CHECK(g->nx > 0 && g->ny > 0 && g->nz > 0 && g->nu > 0 && g->nv > 0 && g->n_views > 0,
+               "shapes must be positive");
+    PYRO_CHECK(pos_finite(g->sx) && pos_finite(g->sy) && pos_finite(g->sz) && pos_finite(g->su) && pos_finite(g->sv),
+               "spacings must be positive and finite");
+    G.nx = g->nx;
+    G.ny = g->ny;
+    G.nz = g->nz;
+    G.nu = g->nu;
+    G.nv = g->nv;
+    G.sx = g->sx;
+    G.sy = g->sy;
+    G.sz = g->sz;
+    G.su = g->su;
+    G.sv = g->sv;
+    G.sid = g->sid;
+    G.sdd = g->sdd;
+    G.range = g->range;
+    const int V = g->n_views;
+    G.beta.assign(V, 0.0);
+    if (g->angles) {
+        for (int j = 0; j < V; ++j) {
+            PYRO_CHECK(std::isfinite(g->angles[j]), "angle %d is not finite", j);
+            G.beta[j] = g->angles[j];
+        }
+    } else if (std::isfinite(g->range) && g->range != 0.0) {
+        for (int j = 0; j < V; ++j) G.beta[j] = j * (g->range / V);
+    } else {
+        PYRO_CHECK(g->proj_mats != nullptr, "need projection matrices, angles or a range");
+    }
+    G.step = g->step > 0.0 ? g->step : 0.5 * std::min(g->sx, std::min(g->sy, g->sz));
+    PYRO_CHECK(std::isfinite(G.step), "step is not finite");
+    const double a = (g->nx + 1) * g->sx, b = (g->ny + 1) * g->sy, c = (g->nz + 1) * g->sz;
+    G.T = 0.5 * std::sqrt(a * a + b * b + c * c);
+    const double M = std::ceil(G.T / G.step);
+    PYRO_CHECK(M < (1 << 28), "step too small for the volume");
+    G.M = (int)M;
+    G.P.resize(12 * (size_t)V);
+    G.S.resize(3 * (size_t)V);
+    for (int j = 0; j < V; ++j) {
+        double Pj[12];
+        if (g->proj_mats) {
+            for (int e = 0; e < 12; ++e) {
+                Pj[e] = g->proj_mats[12 * (size_t)j + e];
+                PYRO_CHECK(std::isfinite(Pj[e]), "projection matrix %d has a non-finite entry", j);
+            }
+        } else {
+            PYRO_CHECK(pos_finite(g->sid) && pos_finite(g->sdd) && g->sdd > g->sid,
+                       "circular trajectory needs 0 < SID < SDD");
+            const double bj = G.beta[j];
+            const double cc[3] = {std::cos(bj), std::sin(bj), 0.0};
+            const double eu[3] = {-std::sin(bj), std::cos(bj), 0.0};
+            const double ev[3] = {0.0, 0.0, 1.0};
+            const double fu = g->sdd / g->su, fv = g->sdd / g->sv;
+            const double cu = 0.5 * (g->nu - 1), cv = 0.5 * (g->nv - 1);
+            // P = K [R | -R S] with S = -SID c, so -R S = (0, 0, SID)
+            for (int e = 0; e < 3; ++e) {
+                Pj[e] = fu * eu[e] + cu * cc[e];
+                Pj[4 + e] = fv * ev[e] + cv * cc[e];
+                Pj[8 + e] = cc[e];
+            }
+            Pj[3] = cu * g->sid;
+            Pj[7] = cv * g->sid;
+            Pj[11] = g->sid;
+        }
+        // normalise: unit third row, iso-centre at positive depth
+        const double n = std::sqrt(Pj[8] * Pj[8] + Pj[9] * Pj[9] + Pj[10] * Pj[10]);
+        PYRO_CHECK(n > 0 && std::isfinite(n), "projection matrix %d is degenerate", j);
+        const double sgn = (Pj[11] >= 0.0 ? 1.0 : -1.0) / n;
+        for (int e = 0; e < 12; ++e) G.P[12 * (size_t)j + e] = sgn * Pj[e];
+        const double *Q = &G.P[12 * (size_t)j];
+        const double Mm[9] = {Q[0], Q[1], Q[2], Q[4], Q[5], Q[6], Q[8], Q[9], Q[10]};
+        const double det = Mm[0] * (Mm[4] * Mm[8] - Mm[5] * Mm[7]) - Mm[1] * (Mm[3] * Mm[8] - Mm[5] * Mm[6]) +
+                           Mm[2] * (Mm[3] * Mm[7] - Mm[4] * Mm[6]);
+        PYRO_CHECK(std::isfinite(det) && std::fabs(det) > 1e-300, "projection matrix %d is singular", j);
+        double Mi[9];
+        inv3(Mm, Mi);
+        double *S = &G.S[3 * (size_t)j];
+        for (int r = 0; r < 3; ++r) S[r] = -(Mi[3 * r] * Q[3] + Mi[3 * r + 1] * Q[7] + Mi[3 * r + 2] * Q[11]);
+        const double dS = std::sqrt(S[0] * S[0] + S[1] * S[1] + S[2] * S[2]);
+        PYRO_CHECK(dS > G.T, "view %d: the source (distance %g) must lie outside the volume support (radius %g)", j, dS,
+                   G.T);
+    }
+    return PYRO_OK;
+}
+
+int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
+{
+    p.nx = G.nx;
+    p.ny = G.ny;
+    p.nz = G.nz;
+    p.nu = G.nu;
+    p.nv = G.nv;
+    p.n_views = nvw;
+    p.view0 = v0;
+    p.views_total = (int)G.beta.size();
+    p.M = G.M;
+    p.cx = (float)(0.5 * (G.nx - 1));
+    p.cy = (float)(0.5 * (G.ny - 1));
+    p.cz = (float)(0.5 * (G.nz - 1));
+    p.dt = (float)G.step;
+    const double inv_s[3] = {1.0 / G.sx, 1.0 / G.sy, 1.0 / G.sz};
+    for (int v = 0; v < nvw; ++v) {
+        const double *Q = &G.P[12 * (size_t)(v0 + v)];
+        const double *S = &G.S[3 * (size_t)(v0 + v)];
+        const double m0[3] = {Q[0], Q[1], Q[2]}, m1[3] = {Q[4], Q[5], Q[6]}, m2[3] = {Q[8], Q[9], Q[10]};
+        auto dot = [](const double *x, const double *y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+        // RQ split M = K R by Gram-Schmidt from the last row (|m2| = 1 here)
+        double r2[3], r1[3], r0[3], t[3];
+        const double K22 = std::sqrt(dot(m2, m2));
+        for (int e = 0; e < 3; ++e) r2[e] = m2[e] / K22;
+        const double K12 = dot(m1, r2);
+        for (int e = 0; e < 3; ++e) t[e] = m1[e] - K12 * r2[e];
+        const double K11 = std::sqrt(dot(t, t));
+        for (int e = 0; e < 3; ++e) r1[e] = t[e] / K11;
+        const double K02 = dot(m0, r2), K01 = dot(m0, r1);
+        for (int e = 0; e < 3; ++e) t[e] = m0[e] - K02 * r2[e] - K01 * r1[e];
+        const double K00 = std::sqrt(dot(t, t));
+        if (!(K00 > 0 && K11 > 0)) return fail(PYRO_EINVAL, "projection matrix %d has a degenerate camera", v0 + v);
+        for (int e = 0; e < 3; ++e) r0[e] = t[e] / K00;
+        // q = K^-1 (k, l, 1) / K22 scaled so that q_z = 1
+        ConeFPView &o = p.v[v];
+        const double b0 = 1.0 / K11, b2 = -K12 / K11;
+        o.a0 = (float)(1.0 / K00);
+        o.a1 = (float)(-K01 * b0 / K00);
+        o.a2 = (float)((-K02 - K01 * b2) / K00);
+        o.b0 = (float)b0;
+        o.b2 = (float)b2;
+        (void)K22;
+        o.s1 = (float)dot(r0, S);
+        o.s2 = (float)dot(r1, S);
+        o.s3 = (float)dot(r2, S);
+        const double *R[3] = {r0, r1, r2};
+        for (int a = 0; a < 3; ++a)
+            for (int b = 0; b < 3; ++b) o.W[3 * a + b] = (float)(R[b][a] * inv_s[a]);
+    }
+    return PYRO_OK;
+}
+
+// voxel index -> (x, y, w) / SID with rows 0 and 1 centred on the detector
+void fill_bp3d(const Geo3D &G, int v0, int nvw, int wexp, float scale, int accumulate, BP3DParams &p)
+{
+    p.nx = G.nx;
+    p.ny = G.ny;
+    p.nz = G.nz;
+    p.nu = G.nu;
+    p.nv = G.nv;
+    p.n_views = nvw;
+    p.view0 = v0;
+    p.views_total = (int)G.beta.size();
+    p.wexp = wexp;
+    p.accumulate = accumulate;
+    p.cu = (float)(0.5 * (G.nu - 1));
+    p.cv = (float)(0.5 * (G.nv - 1));
+    p.scale = scale;
+    const double cu = 0.5 * (G.nu - 1), cv = 0.5 * (G.nv - 1);
+    const double c[3] = {0.5 * (G.nx - 1), 0.5 * (G.ny - 1), 0.5 * (G.nz - 1)};
+    const double s[3] = {G.sx, G.sy, G.sz};
+    const double wscale = G.sid > 0 ? 1.0 / G.sid : 1.0;
+    int zinv = 1;
+    for (int v = 0; v < nvw; ++v) {
+        const double *Q = &G.P[12 * (size_t)(v0 + v)];
+        double A[12];
+        for (int r = 0; r < 3; ++r) {
+            // P (X, 1) with X = (idx - c) s
+            double off = Q[4 * r + 3];
+            for (int a = 0; a < 3; ++a) {
+                A[4 * r + a] = Q[4 * r + a] * s[a];
+                off -= Q[4 * r + a] * s[a] * c[a];
+            }
+            A[4 * r + 3] = off;
+        }
+        for (int a = 0; a < 4; ++a) {
+            A[a] -= cu * A[8 + a];
+            A[4 + a] -= cv * A[8 + a];
+        }
+        for (int a = 0; a < 12; ++a) p.P[v][a] = (float)(A[a] * wscale);
+        if (p.P[v][2] != 0.0f || p.P[v][10] != 0.0f) zinv = 0;
+    }
+    p.z_invariant = zinv;
+}
+
+// ------------------------------------------------------------- filters ---
+int log2_exact(int n)
+{
+    int l = 0;
+    while ((1 << l) < n) ++l;
+    return l;
+}
+
+int pad_length(int nu)
+{
+    int p = 1;
+    while (p < 2 * nu) p <<= 1;
+    return p;
+}
+
+// K[m], m = 0..pn/2, of the built-in filters (FP64, cached per (kind, pn, tau))
+const std::vector<float> &builtin_K(pyro_filter kind, int pn, double tau)
+{
+    static std::mutex mu;
+    static std::map<std::tuple<int, int, double>, std::vector<float>> cache;
+    std::lock_guard<std::mutex> lock(mu);
+    auto key = std::make_tuple((int)kind, pn, tau);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+    std::vector<float> K(pn / 2 + 1);
+    if (kind == PYRO_RAMP) {
+        for (int m = 0; m <= pn / 2; ++m) K[m] = (float)(m / (pn * tau));
+    } else {
+        // taps h(n), |n| < pn/2, on the sample spacing tau (Kak & Slaney)
+        std::vector<double> h(pn / 2);
+        const double pi = 3.14159265358979323846;
+        for (int n = 0; n < pn / 2; ++n) {
+            if (kind == PYRO_RAMLAK)
+                h[n] = n == 0 ? 1.0 / (4 * tau * tau) : (n % 2 ? -1.0 / ((double)n * n * pi * pi * tau * tau) : 0.0);
+            else
+                h[n] = -2.0 / (pi * pi * tau * tau * (4.0 * (double)n * n - 1.0));
+        }
+        std::vector<double> cs(pn);
+        for (int t = 0; t < pn; ++t) cs[t] = std::cos(2.0 * pi * t / pn);
+        for (int m = 0; m <= pn / 2; ++m) {
+            double acc = h[0];
+            for (int n = 1; n < pn / 2; ++n) acc += 2.0 * h[n] * cs[((long)m * n) % pn];
+            K[m] = (float)(tau * acc);
+        }
+    }
+    return cache.emplace(key, std::move(K)).first->second;
+}
+
+int fill_filter(long n_rows, int nu, double tau, pyro_filter kind, const float *custom_K, FilterParams &p)
+{
+    PYRO_CHECK(n_rows >= 0 && nu > 0, "n_rows must be >= 0 and nu > 0");
+    PYRO_CHECK(nu <= kMaxPadLength / 2, "nu=%d exceeds the supported row length %d", nu, kMaxPadLength / 2);
+    PYRO_CHECK(kind == PYRO_RAMLAK || kind == PYRO_RAMP || kind == PYRO_SHEPP_LOGAN || kind == PYRO_FILTER_CUSTOM,
+               "unknown filter kind %d", (int)kind);
+    if (kind == PYRO_FILTER_CUSTOM)
+        PYRO_CHECK(custom_K != nullptr, "PYRO_FILTER_CUSTOM needs custom_K");
+    else
+        PYRO_CHECK(pos_finite(tau), "tau must be positive and finite");
+    p.n_rows = n_rows;
+    p.nu = nu;
+    p.pn = pad_length(nu);
+    p.log2pn = log2_exact(p.pn);
+    p.rows_per_view = 1;
+    p.n_views = 1;
+    p.apply_weights = 0;
+    std::memset(&p.w, 0, sizeof(p.w));
+    if (kind != PYRO_FILTER_CUSTOM) {
+        const std::vector<float> &K = builtin_K(kind, p.pn, tau);
+        std::copy(K.begin(), K.end(), p.K);
+    }
+    return PYRO_OK;
+}
+
+int fill_weights(int nu, int nv, double su, double sv, double sdd, const std::vector<double> &beta, int cosine,
+                 pyro_redund redund, WeightParams &w, BetaTable &bt)
+{
+    PYRO_CHECK(redund == PYRO_REDUND_FULL || redund == PYRO_REDUND_PARKER || redund == PYRO_REDUND_NONE,
+               "unknown redundancy mode %d", (int)redund);
+    PYRO_CHECK(pos_finite(sdd), "weights need SDD > 0");
+    const int V = (int)beta.size();
+    if (redund == PYRO_REDUND_PARKER)
+        PYRO_CHECK(V <= kMaxViews2D, "Parker weights support at most %d views", kMaxViews2D);
+    w.nu = nu;
+    w.nv = nv;
+    w.n_views = V;
+    w.cosine = cosine ? 1 : 0;
+    w.redund = redund;
+    w.su = (float)su;
+    w.sv = (float)sv;
+    w.cu = (float)(0.5 * (nu - 1));
+    w.cv = (float)(0.5 * (nv - 1));
+    w.sdd = (float)sdd;
+    w.delta = (float)std::atan(0.5 * nu * su / sdd);
+    std::memset(&bt, 0, sizeof(bt));
+    if (redund == PYRO_REDUND_PARKER)
+        for (int j = 0; j < V; ++j) bt.beta[j] = (float)(beta[j] - beta[0]);
+    return PYRO_OK;
+}
+
+// pointers may be NULL only when there is nothing to read or write (count == 0)
+int check_io(const void *a, const void *b, long count, pyro_dtype dt)
+{
+    PYRO_CHECK(count >= 0, "batch / row count must be >= 0");
+    if (count > 0) PYRO_CHECK(a != nullptr && b != nullptr, "input/output pointer is NULL");
+    PYRO_CHECK(aligned16(a) && aligned16(b), "device pointers must be 16-byte aligned");
+    PYRO_CHECK(valid_dtype(dt), "unknown dtype %d", (int)dt);
+    return PYRO_OK;
+}
+
+cudaStream_t as_stream(void *s)
+{
+    return reinterpret_cast<cudaStream_t>(s);
+}
+
+// -------------------------------------------------------- operations ----
+int fp2d(bool fan, const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dt, void *stream)
+{
+    if (int e = check_io(vol, sino, batch, dt)) return e;
+    Geo2D G;
+    if (int e = prep2d(g, fan, G)) return e;
+    if (batch == 0) return PYRO_OK;
+    const int V = (int)G.beta.size();
+    static thread_local FP2DParams p;
+    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
+        const int nvw = std::min(kMaxViews2D, V - v0);
+        fill_fp2d(G, v0, nvw, p);
+        for (int b0 = 0; b0 < batch; b0 += 65535) {
+            const int nb = std::min(65535, batch - b0);
+            const char *vi = (const char *)vol + (size_t)b0 * G.nx * G.ny * elem_size(dt);
+            char *so = (char *)sino + (size_t)b0 * V * G.nu * elem_size(dt);
+            PYRO_CUDA(launch_fp2d(vi, so, nb, p, dt, as_stream(stream)));
+        }
+    }
+    return PYRO_OK;
+}
+
+int fp2d_adjoint(bool fan, const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dt, void *stream)
+{
+    if (int e = check_io(sino, vol, batch, dt)) return e;
+    if (dt != PYRO_F32) return fail(PYRO_EUNSUPPORTED, "the FP adjoint supports PYRO_F32 only");
+    Geo2D G;
+    if (int e = prep2d(g, fan, G)) return e;
+    if (batch == 0) return PYRO_OK;
+    const int V = (int)G.beta.size();
+    PYRO_CUDA(cudaMemsetAsync(vol, 0, sizeof(float) * (size_t)batch * G.nx * G.ny, as_stream(stream)));
+    static thread_local FP2DParams p;
+    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
+        const int nvw = std::min(kMaxViews2D, V - v0);
+        fill_fp2d(G, v0, nvw, p);
+        for (int b0 = 0; b0 < batch; b0 += 65535) {
+            const int nb = std::min(65535, batch - b0);
+            const float *si = (const float *)sino + (size_t)b0 * V * G.nu;
+            float *vo = (float *)vol + (size_t)b0 * G.nx * G.ny;
+            PYRO_CUDA(launch_fp2d_adjoint(si, vo, nb, p, as_stream(stream)));
+        }
+    }
+    return PYRO_OK;
+}
+
+int bp_weight_exp(pyro_bp_weight w)
+{
+    return w == PYRO_W_NONE ? 0 : (w == PYRO_W_INV_L ? 1 : (w == PYRO_W_INV_L2 ? 2 : -1));
+}
+
+int bp2d(bool fan, const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_bp_weight w, float scale,
+         pyro_dtype sino_dt, pyro_dtype vol_dt, void *stream)
+{
+    if (int e = check_io(sino, vol, batch, vol_dt)) return e;
+    PYRO_CHECK(valid_dtype(sino_dt), "unknown dtype");
+    const int wexp = bp_weight_exp(w);
+    PYRO_CHECK(wexp >= 0, "unknown back-projection weight %d", (int)w);
+    PYRO_CHECK(std::isfinite(scale), "scale is not finite");
+    Geo2D G;
+    if (int e = prep2d(g, fan, G)) return e;
+    if (batch == 0) return PYRO_OK;
+    const int V = (int)G.beta.size();
+    static thread_local BP2DParams p;
+    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
+        const int nvw = std::min(kMaxViews2D, V - v0);
+        fill_bp2d(G, v0, nvw, wexp, scale, p);
+        for (int b0 = 0; b0 < batch; b0 += 65535) {
+            const int nb = std::min(65535, batch - b0);
+            const char *si = (const char *)sino + (size_t)b0 * V * G.nu * elem_size(sino_dt);
+            char *vo = (char *)vol + (size_t)b0 * G.nx * G.ny * elem_size(vol_dt);
+            PYRO_CUDA(launch_bp2d(si, vo, nb, p, sino_dt, vol_dt, v0 > 0, as_stream(stream)));
+        }
+    }
+    return PYRO_OK;
+}
+
+int bp2d_transpose(bool fan, const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                   float scale, pyro_dtype dt, void *stream)
+{
+    if (int e = check_io(vol, sino, batch, dt)) return e;
+    if (dt != PYRO_F32) return fail(PYRO_EUNSUPPORTED, "the BP transpose supports PYRO_F32 only");
+    const int wexp = bp_weight_exp(w);
+    PYRO_CHECK(wexp >= 0, "unknown back-projection weight %d", (int)w);
+    PYRO_CHECK(std::isfinite(scale), "scale is not finite");
+    Geo2D G;
+    if (int e = prep2d(g, fan, G)) return e;
+    if (batch == 0) return PYRO_OK;
+    const int V = (int)G.beta.size();
+    PYRO_CUDA(cudaMemsetAsync(sino, 0, sizeof(float) * (size_t)batch * V * G.nu, as_stream(stream)));
+    static thread_local BP2DParams p;
+    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
+        const int nvw = std::min(kMaxViews2D, V - v0);
+        fill_bp2d(G, v0, nvw, wexp, scale, p);
+        for (int b0 = 0; b0 < batch; b0 += 65535) {
+            const int nb = std::min(65535, batch - b0);
+            const float *vi = (const float *)vol + (size_t)b0 * G.nx * G.ny;
+            float *so = (float *)sino + (size_t)b0 * V * G.nu;
+            PYRO_CUDA(launch_bp2d_transpose(vi, so, nb, p, as_stream(stream)));
+        }
+    }
+    return PYRO_OK;
+}
+
+int fp3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtype dt, bool adjoint, void *stream)
+{
+    if (int e = check_io(vol, sino, batch, dt)) return e;
+    if (adjoint && dt != PYRO_F32) return fail(PYRO_EUNSUPPORTED, "the FP adjoint supports PYRO_F32 only");
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    if (batch == 0) return PYRO_OK;
+    const int V = (int)G.beta.size();
+    const size_t vox = (size_t)G.nx * G.ny * G.nz, det = (size_t)G.nu * G.nv;
+    // for the adjoint `vol` is the sinogram and `sino` the output volume
+    if (adjoint) PYRO_CUDA(cudaMemsetAsync(sino, 0, sizeof(float) * batch * vox, as_stream(stream)));
+    static thread_local FP3DParams p;
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
+        const int nvw = std::min(kMaxViewsConeFP, V - v0);
+        if (int e = fill_fp3d(G, v0, nvw, p)) return e;
+        const int bstep = std::max(1, 65535 / nvw);
+        for (int b0 = 0; b0 < batch; b0 += bstep) {
+            const int nb = std::min(bstep, batch - b0);
+            if (!adjoint) {
+                const char *vi = (const char *)vol + b0 * vox * elem_size(dt);
+                char *so = (char *)sino + b0 * V * det * elem_size(dt);
+                PYRO_CUDA(launch_fp3d(vi, so, nb, p, dt, as_stream(stream)));
+            } else {
+                const float *si = (const float *)vol + b0 * V * det;
+                float *vo = (float *)sino + b0 * vox;
+                PYRO_CUDA(launch_fp3d_adjoint(si, vo, nb, p, as_stream(stream)));
+            }
+        }
+    }
+    return PYRO_OK;
+}
+
+int bp3d_impl(const void *sino, void *vol, int batch, const Geo3D &G, int wexp, float scale, pyro_dtype sino_dt,
+              pyro_dtype vol_dt, void *stream)
+{
+    const int V = (int)G.beta.size();
+    const size_t vox = (size_t)G.nx * G.ny * G.nz, det = (size_t)G.nu * G.nv;
+    static thread_local BP3DParams p;
+    const int zblocks = (G.nz + 7) / 8;
+    const int bstep = std::max(1, 65535 / zblocks);
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsConeBP) {
+        const int nvw = std::min(kMaxViewsConeBP, V - v0);
+        fill_bp3d(G, v0, nvw, wexp, scale, v0 > 0, p);
+        for (int b0 = 0; b0 < batch; b0 += bstep) {
+            const int nb = std::min(bstep, batch - b0);
+            const char *si = (const char *)sino + b0 * V * det * elem_size(sino_dt);
+            char *vo = (char *)vol + b0 * vox * elem_size(vol_dt);
+            PYRO_CUDA(launch_bp3d(si, vo, nb, p, sino_dt, vol_dt, as_stream(stream)));
+        }
+    }
+    return PYRO_OK;
+}
+
+int bp3d(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_bp_weight w, float scale, pyro_dtype dt,
+         void *stream)
+{
+    if (int e = check_io(sino, vol, batch, dt)) return e;
+    const int wexp = bp_weight_exp(w);
+    PYRO_CHECK(wexp >= 0, "unknown back-projection weight %d", (int)w);
+    PYRO_CHECK(std::isfinite(scale), "scale is not finite");
+    if (wexp > 0) PYRO_CHECK(pos_finite(g ? g->sid : 0.0), "distance weights need SID > 0");
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    if (batch == 0) return PYRO_OK;
+    return bp3d_impl(sino, vol, batch, G, wexp, scale, dt, dt, stream);
+}
+
+int bp3d_transpose(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_bp_weight w, float scale,
+                   pyro_dtype dt, void *stream)
+{
+    if (int e = check_io(vol, sino, batch, dt)) return e;
+    if (dt != PYRO_F32) return fail(PYRO_EUNSUPPORTED, "the BP transpose supports PYRO_F32 only");
+    const int wexp = bp_weight_exp(w);
+    PYRO_CHECK(wexp >= 0, "unknown back-projection weight %d", (int)w);
+    PYRO_CHECK(std::isfinite(scale), "scale is not finite");
+    if (wexp > 0) PYRO_CHECK(pos_finite(g ? g->sid : 0.0), "distance weights need SID > 0");
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    if (batch == 0) return PYRO_OK;
+    const int V = (int)G.beta.size();
+    const size_t vox = (size_t)G.nx * G.ny * G.nz, det = (size_t)G.nu * G.nv;
+    PYRO_CUDA(cudaMemsetAsync(sino, 0, sizeof(float) * batch * V * det, as_stream(stream)));
+    static thread_local BP3DParams p;
+    const int bstep = std::max(1, 65535 / G.nz);
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsConeBP) {
+        const int nvw = std::min(kMaxViewsConeBP, V - v0);
+        fill_bp3d(G, v0, nvw, wexp, scale, 0, p);
+        for (int b0 = 0; b0 < batch; b0 += bstep) {
+            const int nb = std::min(bstep, batch - b0);
+            const float *vi = (const float *)vol + b0 * vox;
+            float *so = (float *)sino + b0 * V * det;
+            PYRO_CUDA(launch_bp3d_transpose(vi, so, nb, p, as_stream(stream)));
+        }
+    }
+    return PYRO_OK;
+}
+
+}  // namespace
+
+int device_sm_count()
+{
+    static std::mutex mu;
+    static std::map<int, int> counts;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return 148;
+    std::lock_guard<std::mutex> lock(mu);
+    auto it = counts.find(dev);
+    if (it != counts.end()) return it->second;
+    int n = 0;
+    if (cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || n <= 0) n = 148;
+    counts[dev] = n;
+    return n;
+}
+
+}  // namespace pyro
+
+using namespace pyro;
+
+extern "C" {
+
+PYRO_API int pyro_fp_par2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dtype,
+                           void *stream)
+{
+    return fp2d(false, vol, sino, batch, g, dtype, stream);
+}
+
+PYRO_API int pyro_fp_fan2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dtype,
+                           void *stream)
+{
+    return fp2d(true, vol, sino, batch, g, dtype, stream);
+}
+
+PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtype dtype,
+                            void *stream)
+{
+    return fp3d(vol, sino, batch, g, dtype, false, stream);
+}
+
+PYRO_API int pyro_fpT_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dtype,
+                            void *stream)
+{
+    return fp2d_adjoint(false, sino, vol, batch, g, dtype, stream);
+}
+
+PYRO_API int pyro_fpT_fan2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dtype,
+                            void *stream)
+{
+    return fp2d_adjoint(true, sino, vol, batch, g, dtype, stream);
+}
+
+PYRO_API int pyro_fpT_cone3d(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_dtype dtype,
+                             void *stream)
+{
+    return fp3d(sino, vol, batch, g, dtype, true, stream);
+}
+
+PYRO_API int pyro_bp_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                           float scale, pyro_dtype dtype, void *stream)
+{
+    return bp2d(false, sino, vol, batch, g, w, scale, dtype, dtype, stream);
+}
+
+PYRO_API int pyro_bp_fan2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                           float scale, pyro_dtype dtype, void *stream)
+{
+    return bp2d(true, sino, vol, batch, g, w, scale, dtype, dtype, stream);
+}
+
+PYRO_API int pyro_bp_cone3d(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_bp_weight w,
+                            float scale, pyro_dtype dtype, void *stream)
+{
+    return bp3d(sino, vol, batch, g, w, scale, dtype, stream);
+}
+
+PYRO_API int pyro_bpT_par2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                            float scale, pyro_dtype dtype, void *stream)
+{
+    return bp2d_transpose(false, vol, sino, batch, g, w, scale, dtype, stream);
+}
+
+PYRO_API int pyro_bpT_fan2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_bp_weight w,
+                            float scale, pyro_dtype dtype, void *stream)
+{
+    return bp2d_transpose(true, vol, sino, batch, g, w, scale, dtype, stream);
+}
+
+PYRO_API int pyro_bpT_cone3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_bp_weight w,
+                             float scale, pyro_dtype dtype, void *stream)
+{
+    return bp3d_transpose(vol, sino, batch, g, w, scale, dtype, stream);
+}
+
+PYRO_API int pyro_weights2d(void *sino, int batch, const pyro_geom2d *g, int cosine, pyro_redund redund,
+                            pyro_dtype dtype, void *stream)
+{
+    if (int e = check_io(sino, sino, batch, dtype)) return e;
+    Geo2D G;
+    if (int e = prep2d(g, false, G)) return e;
+    WeightParams w;
+    static thread_local BetaTable bt;
+    if (int e = fill_weights(G.nu, 1, G.su, 0.0, g->sdd, G.beta, cosine, redund, w, bt)) return e;
+    if (batch == 0) return PYRO_OK;
+    PYRO_CUDA(launch_weights(sino, batch, w, bt, dtype, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_weights3d(void *sino, int batch, const pyro_geom3d *g, int cosine, pyro_redund redund,
+                            pyro_dtype dtype, void *stream)
+{
+    if (int e = check_io(sino, sino, batch, dtype)) return e;
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    WeightParams w;
+    static thread_local BetaTable bt;
+    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, cosine, redund, w, bt)) return e;
+    if (batch == 0) return PYRO_OK;
+    PYRO_CUDA(launch_weights(sino, batch, w, bt, dtype, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_filter_pad_length(int nu)
+{
+    return nu > 0 ? pad_length(nu) : 0;
+}
+
+PYRO_API int pyro_filter_rows(const void *in, void *out, long n_rows, int nu, double tau, pyro_filter kind,
+                              const float *custom_K, pyro_dtype dtype, void *stream)
+{
+    if (int e = check_io(in, out, n_rows, dtype)) return e;
+    static thread_local FilterParams p;
+    if (int e = fill_filter(n_rows, nu, tau, kind, custom_K, p)) return e;
+    if (n_rows == 0) return PYRO_OK;
+    PYRO_CUDA(launch_filter(in, out, p, nullptr, kind == PYRO_FILTER_CUSTOM ? custom_K : nullptr, dtype, dtype,
+                            as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_filter_grad_K(const float *p, const float *g, float *dK, long n_rows, int nu, void *stream)
+{
+    if (int e = check_io(p, g, n_rows, PYRO_F32)) return e;
+    PYRO_CHECK(dK != nullptr, "dK is NULL");
+    PYRO_CHECK(n_rows >= 0 && nu > 0 && nu <= kMaxPadLength / 2, "bad row shape");
+    const int pn = pad_length(nu);
+    if (n_rows == 0) {
+        PYRO_CUDA(cudaMemsetAsync(dK, 0, sizeof(float) * (pn / 2 + 1), as_stream(stream)));
+        return PYRO_OK;
+    }
+    PYRO_CUDA(launch_filter_grad_K(p, g, dK, n_rows, nu, pn, log2_exact(pn), as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API size_t pyro_fdk_workspace_bytes(const pyro_geom3d *g, int batch)
+{
+    if (!g || batch < 0) return 0;
+    return sizeof(float) * (size_t)batch * (size_t)std::max(g->n_views, 0) * (size_t)std::max(g->nv, 0) *
+           (size_t)std::max(g->nu, 0);
+}
+
+PYRO_API int pyro_fdk(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_filter kind,
+                      const float *custom_K, pyro_redund redund, void *workspace, size_t workspace_bytes,
+                      pyro_dtype dtype, void *stream)
+{
+    if (int e = check_io(sino, vol, batch, dtype)) return e;
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    PYRO_CHECK(pos_finite(G.sid) && pos_finite(G.sdd) && G.sdd > G.sid, "FDK needs 0 < SID < SDD");
+    PYRO_CHECK(std::isfinite(G.range) && G.range != 0.0, "FDK needs the angular range (scale range / n_views)");
+    const size_t need = pyro_fdk_workspace_bytes(g, batch);
+    if (workspace_bytes < need || (need > 0 && (workspace == nullptr || !aligned16(workspace))))
+        return fail(PYRO_EWORKSPACE, "FDK needs a 16-byte aligned workspace of %zu bytes (got %zu)", need,
+                    workspace_bytes);
+    const int V = (int)G.beta.size();
+    static thread_local FilterParams p;
+    static thread_local BetaTable bt;
+    if (int e = fill_filter((long)batch * V * G.nv, G.nu, G.su * G.sid / G.sdd, kind, custom_K, p)) return e;
+    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, 1, redund, p.w, bt)) return e;
+    p.apply_weights = 1;
+    p.rows_per_view = G.nv;
+    p.n_views = V;
+    if (batch == 0) return PYRO_OK;
+    PYRO_CUDA(launch_filter(sino, workspace, p, &bt, kind == PYRO_FILTER_CUSTOM ? custom_K : nullptr, dtype, PYRO_F32,
+                            as_stream(stream)));
+    return bp3d_impl(workspace, vol, batch, G, 2, (float)(std::fabs(G.range) / V), PYRO_F32, dtype, stream);
+}
+
+PYRO_API size_t pyro_fbp2d_workspace_bytes(const pyro_geom2d *g, int batch)
+{
+    if (!g || batch < 0) return 0;
+    return sizeof(float) * (size_t)batch * (size_t)std::max(g->n_views, 0) * (size_t)std::max(g->nu, 0);
+}
+
+static int fbp2d(bool fan, const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_filter kind,
+                 const float *custom_K, pyro_redund redund, void *workspace, size_t workspace_bytes, pyro_dtype dtype,
+                 void *stream)
+{
+    if (int e = check_io(sino, vol, batch, dtype)) return e;
+    Geo2D G;
+    if (int e = prep2d(g, fan, G)) return e;
+    const size_t need = pyro_fbp2d_workspace_bytes(g, batch);
+    if (workspace_bytes < need || (need > 0 && (workspace == nullptr || !aligned16(workspace))))
+        return fail(PYRO_EWORKSPACE, "FBP needs a 16-byte aligned workspace of %zu bytes (got %zu)", need,
+                    workspace_bytes);
+    const int V = (int)G.beta.size();
+    static thread_local FilterParams p;
+    static thread_local BetaTable bt;
+    const double tau = fan ? G.su * G.sid / G.sdd : G.su;
+    if (int e = fill_filter((long)batch * V, G.nu, tau, kind, custom_K, p)) return e;
+    if (fan) {
+        PYRO_CHECK(std::isfinite(G.range) && G.range != 0.0, "fan FBP needs the angular range");
+        if (int e = fill_weights(G.nu, 1, G.su, 0.0, G.sdd, G.beta, 1, redund, p.w, bt)) return e;
+        p.apply_weights = 1;
+        p.rows_per_view = 1;
+        p.n_views = V;
+    }
+    if (batch == 0) return PYRO_OK;
+    PYRO_CUDA(launch_filter(sino, workspace, p, fan ? &bt : nullptr, kind == PYRO_FILTER_CUSTOM ? custom_K : nullptr,
+                            dtype, PYRO_F32, as_stream(stream)));
+    const double pi = 3.14159265358979323846;
+    const float scale = (float)(fan ? std::fabs(G.range) / V : pi / V);
+    static thread_local BP2DParams bp;
+    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
+        const int nvw = std::min(kMaxViews2D, V - v0);
+        fill_bp2d(G, v0, nvw, fan ? 2 : 0, scale, bp);
+        for (int b0 = 0; b0 < batch; b0 += 65535) {
+            const int nb = std::min(65535, batch - b0);
+            const float *si = (const float *)workspace + (size_t)b0 * V * G.nu;
+            char *vo = (char *)vol + (size_t)b0 * G.nx * G.ny * elem_size(dtype);
+            PYRO_CUDA(launch_bp2d(si, vo, nb, bp, PYRO_F32, dtype, v0 > 0, as_stream(stream)));
+        }
+    }
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_fbp_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_filter kind,
+                            const float *custom_K, void *workspace, size_t workspace_bytes, pyro_dtype dtype,
+                            void *stream)
+{
+    return fbp2d(false, sino, vol, batch, g, kind, custom_K, PYRO_REDUND_NONE, workspace, workspace_bytes, dtype,
+                 stream);
+}
+
+PYRO_API int pyro_fbp_fan2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_filter kind,
+                            const float *custom_K, pyro_redund redund, void *workspace, size_t workspace_bytes,
+                            pyro_dtype dtype, void *stream)
+{
+    return fbp2d(true, sino, vol, batch, g, kind, custom_K, redund, workspace, workspace_bytes, dtype, stream);
+}
+
+PYRO_API const char *pyro_last_error(void)
+{
+    return g_last_error.c_str();
+}
+
+PYRO_API const char *pyro_version(void)
+{
+    return "pyro-gb300 0.1 (sm_103a)";
+}
+
+}  // extern "C"

@@ -108,3 +108,45 @@ def blob_line_integrals(blobs, a: np.ndarray, d: np.ndarray) -> np.ndarray:
         ga = np.einsum("ri,ij,rj->r", r0, Si, r0)
         out += rho * np.sqrt(2 * np.pi / al) * np.exp(-0.5 * (ga - be * be / al))
     return out
+
+
+def cone_sinogram(ell, angles, det_shape, det_spacing, sid, sdd, chunk=16):
+    """[V, nv, nu] analytic cone-beam projections of an ellipsoid phantom
+    (torch float64 on the CPU, `chunk` views at a time)."""
+    import torch
+
+    nv, nu = det_shape
+    sv, su = det_spacing
+    u = (torch.arange(nu, dtype=torch.float64) - 0.5 * (nu - 1)) * su
+    v = (torch.arange(nv, dtype=torch.float64) - 0.5 * (nv - 1)) * sv
+    V, U = torch.meshgrid(v, u, indexing="ij")
+    out = np.empty((len(angles), nv, nu))
+    for j0 in range(0, len(angles), chunk):
+        b = torch.as_tensor(np.asarray(angles[j0:j0 + chunk], dtype=np.float64))[:, None, None]
+        cb, sb = torch.cos(b), torch.sin(b)
+        # source -SID c and direction to the pixel (SDD-SID) c + u e_u + v e_v
+        src = torch.stack([-sid * cb, -sid * sb, torch.zeros_like(b)], -1).expand(-1, nv, nu, 3)
+        d = torch.stack([sdd * cb - U * sb, sdd * sb + U * cb, V.expand_as(U * cb)], -1)
+        d = d / torch.linalg.norm(d, dim=-1, keepdim=True)
+        acc = torch.zeros(d.shape[:-1], dtype=torch.float64)
+        for c, ax, Rm, rho in zip(ell.centre, ell.axes, ell.rot, ell.density):
+            R = torch.as_tensor(Rm) / torch.as_tensor(ax)[None, :]
+            dd = d @ R
+            aa = (src - torch.as_tensor(c)) @ R
+            A = (dd * dd).sum(-1)
+            Bq = (dd * aa).sum(-1)
+            C = (aa * aa).sum(-1) - 1.0
+            disc = Bq * Bq - A * C
+            acc += rho * torch.where(disc > 0, 2.0 * torch.sqrt(disc.clamp_min(0.0)) / A, torch.zeros_like(A))
+        out[j0:j0 + chunk] = acc.numpy()
+    return out
+
+
+def fan_sinogram(ell, angles, nu, su, sid, sdd):
+    a, d = fan_rays(angles, nu, su, sid, sdd)
+    return ellipse_line_integrals(ell, a, d).reshape(len(angles), nu)
+
+
+def parallel_sinogram(ell, angles, nu, su):
+    a, d = parallel_rays(angles, nu, su)
+    return ellipse_line_integrals(ell, a, d).reshape(len(angles), nu)

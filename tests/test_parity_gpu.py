@@ -1,0 +1,325 @@
+"""GPU parity: every C-ABI call against the FP64 oracle on the same inputs.
+
+Inputs are seeded (paper_1904_13342_gb300.phantoms).  The CUDA side gets
+FP32 (or FP16/BF16) tensors; the oracle gets the same values as float64.
+Gate (element-wise comparison, relative L2): <= 1e-5 for FP32 storage,
+<= 2e-3 for FP16 storage against the oracle fed the original FP32 input
+(end to end, storage rounding included); BF16 is reported with 1e-2.
+Small cases span several thread-block tiles with ragged tails; the full
+sizes of the headline workloads are checked on sampled outputs.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import analytic as an
+import oracle
+from paper_1904_13342_gb300 import binding as B
+from paper_1904_13342_gb300 import phantoms as ph
+from paper_1904_13342_gb300.geometry import ConeGeometry3D, FanGeometry2D, ParallelGeometry2D, short_scan_range
+
+pytestmark = pytest.mark.gpu
+
+DEV = torch.device("cuda:0")
+TOL = {torch.float32: 1e-5, torch.float16: 2e-3, torch.bfloat16: 1e-2}
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300))
+
+
+def to_dev(a, dtype=torch.float32):
+    return torch.from_numpy(np.ascontiguousarray(a)).to(torch.float32).to(dtype).to(DEV)
+
+
+def host(t):
+    return t.double().cpu().numpy()
+
+
+def f32(a):
+    """the FP32 values the device sees, as float64"""
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+# ----------------------------------------------------------------- cases --
+PAR = dict(shape=(53, 70), spacing=(0.9, 1.1), nu=77, su=1.2, views=23, range=math.pi)
+FAN = dict(shape=(53, 70), spacing=(0.9, 1.1), nu=77, su=1.6, views=23, range=2 * math.pi, sid=300.0, sdd=520.0)
+CONE = dict(shape=(19, 37, 45), spacing=(1.0, 0.9, 1.1), det=(29, 41), dspacing=(1.5, 1.4), views=17,
+            range=2 * math.pi, sid=250.0, sdd=420.0)
+
+
+def par_geom(c, angles=None):
+    return ParallelGeometry2D(c["shape"], c["spacing"], c["nu"], c["su"], c["views"], c["range"], angles=angles)
+
+
+def fan_geom(c, angles=None):
+    return FanGeometry2D(c["shape"], c["spacing"], c["nu"], c["su"], c["views"], c["range"], c["sid"], c["sdd"],
+                         angles=angles)
+
+
+def cone_geom(c, P=None):
+    return ConeGeometry3D(c["shape"], c["spacing"], c["det"], c["dspacing"], c["views"], c["range"], c["sid"], c["sdd"],
+                          projection_matrices=P)
+
+
+def cone_pmats(c, ang):
+    return oracle.circular_pmats(ang, c["sid"], c["sdd"], c["det"], c["dspacing"])
+
+
+def tilted_pmats(c, ang, tilt=0.12, du=2.3, dv=-1.7):
+    """A non-circular trajectory written out here: the circular matrices of
+    the oracle, rotated about the x axis by `tilt` and with a shifted
+    principal point."""
+    P = cone_pmats(c, ang)
+    ct, st = math.cos(tilt), math.sin(tilt)
+    Rx = np.array([[1, 0, 0, 0], [0, ct, -st, 0], [0, st, ct, 0], [0, 0, 0, 1.0]])
+    T = np.array([[1, 0, du], [0, 1, dv], [0, 0, 1.0]])
+    return np.einsum("ij,vjk,kl->vil", T, P, Rx)
+
+
+# ------------------------------------------------------------------ 2D ----
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("geom", ["par", "fan"])
+def test_fp_2d(geom, dtype):
+    c = PAR if geom == "par" else FAN
+    img = ph.voxelize_ellipses(ph.random_ellipses(6, 30.0, seed=1), c["shape"], c["spacing"]).numpy()
+    img = np.stack([img, ph.random_volume(c["shape"], 2)])  # batch of 2
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    if geom == "par":
+        got = B.pyro_fp_par2d(to_dev(img, dtype), par_geom(c))
+        ref = [oracle.fp_par2d(f32(x), c["spacing"], c["nu"], c["su"], ang) for x in img]
+    else:
+        got = B.pyro_fp_fan2d(to_dev(img, dtype), fan_geom(c))
+        ref = [oracle.fp_fan2d(f32(x), c["spacing"], c["nu"], c["su"], ang, c["sid"], c["sdd"]) for x in img]
+    assert got.shape == (2, c["views"], c["nu"]) and got.dtype == dtype
+    assert rel(host(got), np.stack(ref)) < TOL[dtype]
+
+
+@pytest.mark.parametrize("geom", ["par", "fan"])
+def test_fp_adjoint_2d(geom):
+    c = PAR if geom == "par" else FAN
+    y = ph.random_sinogram((2, c["views"], c["nu"]), 3)
+    ang = np.random.default_rng(4).uniform(0, 2 * np.pi, c["views"])  # explicit, unordered angles
+    if geom == "par":
+        got = B.pyro_fpT_par2d(to_dev(y), par_geom(c, angles=ang))
+        ref = [oracle.fpT_par2d(f32(s), c["shape"], c["spacing"], c["su"], ang) for s in y]
+    else:
+        got = B.pyro_fpT_fan2d(to_dev(y), fan_geom(c, angles=ang))
+        ref = [oracle.fpT_fan2d(f32(s), c["shape"], c["spacing"], c["su"], ang, c["sid"], c["sdd"]) for s in y]
+    assert rel(host(got), np.stack(ref)) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("geom,weight", [("par", 0), ("fan", 0), ("fan", 1), ("fan", 2)])
+def test_bp_2d(geom, weight, dtype):
+    c = PAR if geom == "par" else FAN
+    y = ph.random_sinogram((2, c["views"], c["nu"]), 5, smooth=2)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    if geom == "par":
+        got = B.pyro_bp_par2d(to_dev(y, dtype), par_geom(c), scale=0.37)
+        ref = [oracle.bp_par2d(f32(s), c["shape"], c["spacing"], c["su"], ang, scale=0.37) for s in y]
+    else:
+        got = B.pyro_bp_fan2d(to_dev(y, dtype), fan_geom(c), weight=weight, scale=0.37)
+        ref = [oracle.bp_fan2d(f32(s), c["shape"], c["spacing"], c["su"], ang, c["sid"], c["sdd"], weight, 0.37)
+               for s in y]
+    assert rel(host(got), np.stack(ref)) < TOL[dtype]
+
+
+@pytest.mark.parametrize("geom", ["par", "fan"])
+def test_bp_transpose_2d(geom):
+    c = PAR if geom == "par" else FAN
+    x = ph.random_volume((2, *c["shape"]), 6)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    if geom == "par":
+        got = B.pyro_bpT_par2d(to_dev(x), par_geom(c), scale=0.5)
+        ref = [oracle.bpT_par2d(f32(v), c["nu"], c["su"], ang, c["spacing"], 0.5) for v in x]
+    else:
+        got = B.pyro_bpT_fan2d(to_dev(x), fan_geom(c), weight=2, scale=0.5)
+        ref = [oracle.bpT_fan2d(f32(v), c["nu"], c["su"], ang, c["spacing"], c["sid"], c["sdd"], 2, 0.5) for v in x]
+    assert rel(host(got), np.stack(ref)) < 1e-5
+
+
+# ------------------------------------------------------------------ 3D ----
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("traj", ["circular", "tilted"])
+def test_fp_cone(traj, dtype):
+    c = CONE
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang) if traj == "circular" else tilted_pmats(c, ang)
+    vol = ph.voxelize_ellipsoids(ph.random_ellipsoids(5, 18.0, seed=7), c["shape"], c["spacing"]).numpy()
+    vol = np.stack([vol, ph.random_volume(c["shape"], 8)])
+    g = cone_geom(c, None if traj == "circular" else P)
+    got = B.pyro_fp_cone3d(to_dev(vol, dtype), g)
+    ref = np.stack([oracle.fp_cone3d(f32(v), c["spacing"], c["det"], P) for v in vol])
+    assert got.shape == (2, c["views"], *c["det"])
+    assert rel(host(got), ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("traj", ["circular", "tilted"])
+def test_fp_adjoint_cone(traj):
+    c = CONE
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang) if traj == "circular" else tilted_pmats(c, ang)
+    y = ph.random_sinogram((2, c["views"], *c["det"]), 9)
+    got = B.pyro_fpT_cone3d(to_dev(y), cone_geom(c, None if traj == "circular" else P))
+    ref = np.stack([oracle.fpT_cone3d(f32(s), c["shape"], c["spacing"], P) for s in y])
+    assert rel(host(got), ref) < 1e-5
+
+
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("traj,weight", [("circular", 0), ("circular", 2), ("tilted", 1), ("tilted", 2)])
+def test_bp_cone(traj, weight, dtype):
+    c = CONE
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang) if traj == "circular" else tilted_pmats(c, ang)
+    y = ph.random_sinogram((2, c["views"], *c["det"]), 10, smooth=2)
+    got = B.pyro_bp_cone3d(to_dev(y, dtype), cone_geom(c, None if traj == "circular" else P), weight=weight,
+                           scale=0.25)
+    ref = np.stack([oracle.bp_cone3d(f32(s), c["shape"], c["spacing"], P, c["sid"], weight, 0.25) for s in y])
+    assert rel(host(got), ref) < TOL[dtype]
+
+
+def test_bp_transpose_cone():
+    c = CONE
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang)
+    x = ph.random_volume((2, *c["shape"]), 11)
+    got = B.pyro_bpT_cone3d(to_dev(x), cone_geom(c), weight=2, scale=0.5)
+    ref = np.stack([oracle.bpT_cone3d(f32(v), c["det"], c["spacing"], P, c["sid"], 2, 0.5) for v in x])
+    assert rel(host(got), ref) < 1e-5
+
+
+# ---------------------------------------------------- weights / filters ---
+@pytest.mark.parametrize("redund", [B.REDUND_FULL, B.REDUND_PARKER, B.REDUND_NONE])
+def test_weights_cone(redund):
+    c = dict(CONE)
+    c["range"] = short_scan_range(c["det"][1] * c["dspacing"][1], c["sdd"]) if redund == B.REDUND_PARKER else 2 * math.pi
+    y = ph.random_sinogram((2, c["views"], *c["det"]), 12)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    got = B.pyro_weights3d(to_dev(y), cone_geom(c), cosine=True, redund=redund)
+    ref = np.stack([oracle.weights(f32(s), c["dspacing"], ang, c["sdd"], True, redund) for s in y])
+    assert rel(host(got), ref) < 1e-6
+
+
+@pytest.mark.parametrize("nu", [1, 37, 183, 620, 1240])
+@pytest.mark.parametrize("kind", [B.RAMLAK, B.RAMP, B.SHEPP_LOGAN, B.FILTER_CUSTOM])
+def test_filter_rows(kind, nu):
+    n_rows = 7 if nu > 600 else 13  # odd: the last FFT pair is half empty
+    rows = ph.random_sinogram((n_rows, nu), 13)
+    pn = B.pyro_filter_pad_length(nu)
+    K = np.random.default_rng(14).uniform(0, 1, pn // 2 + 1) if kind == B.FILTER_CUSTOM else None
+    got = B.pyro_filter_rows(to_dev(rows), 0.616, kind, custom_K=None if K is None else to_dev(K))
+    ref = oracle.filter_rows(f32(rows), 0.616, kind, K=None if K is None else f32(K))
+    assert rel(host(got), ref) < 1e-5
+
+
+def test_filter_rows_in_place_and_half():
+    rows = ph.random_sinogram((9, 300), 15, smooth=1)
+    t = to_dev(rows)
+    ref = oracle.filter_rows(f32(rows), 0.5, B.SHEPP_LOGAN)
+    B.pyro_filter_rows(t, 0.5, B.SHEPP_LOGAN, out=t)
+    assert rel(host(t), ref) < 1e-5
+    h = B.pyro_filter_rows(to_dev(rows, torch.float16), 0.5, B.SHEPP_LOGAN)
+    assert rel(host(h), ref) < 2e-3
+
+
+def test_filter_grad_K():
+    nu = 183
+    p = ph.random_sinogram((11, nu), 16)
+    g = ph.random_sinogram((11, nu), 17)
+    got = B.pyro_filter_grad_K(to_dev(p), to_dev(g))
+    ref = oracle.filter_grad_K(f32(p), f32(g))
+    assert rel(host(got), ref) < 1e-5
+
+
+# ------------------------------------------------------------- FBP/FDK ----
+NOISE_TOL = 1e-4  # filtered noise: FP32 detector-coordinate rounding, amplified by cancellation over views
+
+
+@pytest.mark.parametrize("data", ["phantom", "noise"])
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
+@pytest.mark.parametrize("redund,kind", [(B.REDUND_PARKER, B.SHEPP_LOGAN), (B.REDUND_FULL, B.RAMLAK)])
+def test_fdk(redund, kind, dtype, data):
+    c = dict(CONE)
+    c["range"] = short_scan_range(c["det"][1] * c["dspacing"][1], c["sdd"]) if redund == B.REDUND_PARKER else 2 * math.pi
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang)
+    if data == "phantom":
+        y = np.stack([an.cone_sinogram(ph.random_ellipsoids(5, 18.0, seed=s), ang, c["det"], c["dspacing"], c["sid"],
+                                       c["sdd"]) for s in (30, 31)])
+    else:
+        y = ph.random_sinogram((2, c["views"], *c["det"]), 18, smooth=3)
+    got = B.pyro_fdk(to_dev(y, dtype), cone_geom(c), kind=kind, redund=redund)
+    ref = np.stack([oracle.fdk(f32(s), c["shape"], c["spacing"], c["dspacing"], ang, P, c["sid"], c["sdd"],
+                               c["range"] / c["views"], kind, redund) for s in y])
+    tol = TOL[dtype] if (data == "phantom" or dtype != torch.float32) else NOISE_TOL
+    assert rel(host(got), ref) < tol
+
+
+@pytest.mark.parametrize("data", ["phantom", "noise"])
+@pytest.mark.parametrize("geom", ["par", "fan_full", "fan_parker"])
+def test_fbp_2d(geom, data):
+    c = dict(PAR if geom == "par" else FAN)
+    if geom == "fan_parker":
+        c["range"] = short_scan_range(c["nu"] * c["su"], c["sdd"])
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    if data == "phantom":
+        es = [ph.random_ellipses(6, 30.0, seed=s) for s in (40, 41)]
+        if geom == "par":
+            y = np.stack([an.parallel_sinogram(e, ang, c["nu"], c["su"]) for e in es])
+        else:
+            y = np.stack([an.fan_sinogram(e, ang, c["nu"], c["su"], c["sid"], c["sdd"]) for e in es])
+    else:
+        y = ph.random_sinogram((2, c["views"], c["nu"]), 19, smooth=3)
+    if geom == "par":
+        got = B.pyro_fbp_par2d(to_dev(y), par_geom(c), kind=B.RAMLAK)
+        ref = [oracle.fbp_par2d(f32(s), c["shape"], c["spacing"], c["su"], ang, B.RAMLAK) for s in y]
+    else:
+        red = B.REDUND_FULL if geom == "fan_full" else B.REDUND_PARKER
+        got = B.pyro_fbp_fan2d(to_dev(y), fan_geom(c), kind=B.SHEPP_LOGAN, redund=red)
+        ref = [oracle.fbp_fan2d(f32(s), c["shape"], c["spacing"], c["su"], ang, c["sid"], c["sdd"],
+                                c["range"] / c["views"], B.SHEPP_LOGAN, red) for s in y]
+    assert rel(host(got), np.stack(ref)) < (1e-5 if data == "phantom" else NOISE_TOL)
+
+
+# ------------------------------------------------------- edge cases -------
+def test_empty_batch_and_single_pixel():
+    g = ParallelGeometry2D((1, 1), (1.0, 1.0), 1, 1.0, 1)
+    x = torch.ones((0, 1, 1), device=DEV)
+    assert B.pyro_fp_par2d(x, g).shape == (0, 1, 1)
+    one = torch.full((1, 1), 2.0, device=DEV)
+    got = host(B.pyro_fp_par2d(one, g))
+    ref = oracle.fp_par2d(np.full((1, 1), 2.0), (1.0, 1.0), 1, 1.0, np.zeros(1))
+    assert rel(got, ref) < 1e-6
+
+
+def test_many_views_are_chunked():
+    """More views than one kernel-parameter pack holds (cone BP 600, FP 400,
+    2D 1024): chunking must not change the result."""
+    c = dict(CONE, shape=(9, 12, 11), det=(10, 14), views=1100)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang)
+    vol = ph.random_volume(c["shape"], 20)
+    y = ph.random_sinogram((c["views"], *c["det"]), 21)
+    g = cone_geom(c)
+    assert rel(host(B.pyro_fp_cone3d(to_dev(vol), g)), oracle.fp_cone3d(f32(vol), c["spacing"], c["det"], P)) < 1e-5
+    assert rel(host(B.pyro_bp_cone3d(to_dev(y), g, weight=2)),
+               oracle.bp_cone3d(f32(y), c["shape"], c["spacing"], P, c["sid"], 2, 1.0)) < 1e-5
+    c2 = dict(PAR, views=2100)
+    ang2 = oracle.uniform_angles(c2["views"], c2["range"])
+    y2 = ph.random_sinogram((c2["views"], c2["nu"]), 22)
+    assert rel(host(B.pyro_bp_par2d(to_dev(y2), par_geom(c2))),
+               oracle.bp_par2d(f32(y2), c2["shape"], c2["spacing"], c2["su"], ang2)) < 1e-5
+
+
+def test_invalid_call_enqueues_nothing():
+    g = ParallelGeometry2D((8, 8), (1.0, 1.0), 9, 1.0, 4)
+    with pytest.raises(ValueError):
+        B.pyro_fp_par2d(torch.zeros((8, 9), device=DEV), g)  # wrong shape caught in the binding
+    bad = ParallelGeometry2D((8, 8), (1.0, -1.0), 9, 1.0, 4)
+    with pytest.raises(B.PyroError) as e:
+        B.pyro_fp_par2d(torch.zeros((8, 8), device=DEV), bad)
+    assert e.value.status == 1
