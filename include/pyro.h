@@ -34,9 +34,10 @@
  *              NULL = legacy default stream) and uses the current device.
  *              Host-side argument errors return PYRO_EINVAL before anything
  *              is enqueued; launch failures return PYRO_ECUDA.  The library
- *              allocates no device memory: scratch comes from the caller's
- *              workspace arguments.  On a non-zero return, pyro_last_error()
- *              gives a message (thread-local).
+ *              makes no device allocation: scratch comes from the caller's
+ *              workspace arguments (pyro_fdk_noalloc alone uses a static
+ *              array of the library).  On a non-zero return,
+ *              pyro_last_error() gives a message (thread-local).
  */
 #ifndef PYRO_H
 #define PYRO_H
@@ -199,6 +200,23 @@ PYRO_API int pyro_fbp_par2d(const void *sino, void *vol, int batch, const pyro_g
 PYRO_API int pyro_fbp_fan2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_filter kind,
                             const float *custom_K, pyro_redund redund, void *workspace, size_t workspace_bytes,
                             pyro_dtype dtype, void *stream);
+
+/* --- FDK without any device allocation by the caller.  The paper has no
+ * counterpart: this serves callers that only hold the input and output
+ * buffers and cannot allocate device memory (e.g. a reconstruction stage
+ * inside an acquisition pipeline, or a host application whose allocator owns
+ * all device memory), so they cannot pass the workspace pyro_fdk needs.
+ * Same arguments and result as pyro_fdk, minus the workspace: the scratch is
+ * a static device array of PYRO_FDK_NOALLOC_SCRATCH_BYTES (64 MiB) inside the
+ * library, held on every GPU that loads it until the process exits.
+ * Problems needing more (4 * batch * n_views * nv * nu bytes) return
+ * PYRO_EWORKSPACE.  The first call on a device looks up the array's address
+ * and should come before any stream capture on that device.  All calls on a
+ * device share the array (it keeps the last call's contents): calls that
+ * overlap on the GPU race with each other.  No allocation is made. */
+#define PYRO_FDK_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)
+PYRO_API int pyro_fdk_noalloc(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_filter kind,
+                              const float *custom_K, pyro_redund redund, pyro_dtype dtype, void *stream);
 
 /* thread-local message describing the last non-OK status of this thread */
 PYRO_API const char *pyro_last_error(void);

@@ -68,6 +68,7 @@ _SIGS = {
     "pyro_fbp2d_workspace_bytes": [_G2, _I],
     "pyro_fbp_par2d": [_VP, _VP, _I, _G2, _I, _VP, _VP, _SZ, _I, _VP],
     "pyro_fbp_fan2d": [_VP, _VP, _I, _G2, _I, _VP, _I, _VP, _SZ, _I, _VP],
+    "pyro_fdk_noalloc": [_VP, _VP, _I, _G3, _I, _VP, _I, _I, _VP],
     "pyro_last_error": [],
     "pyro_version": [],
 }
@@ -295,6 +296,24 @@ def pyro_fdk(sino: torch.Tensor, g: ConeGeometry3D, kind=SHEPP_LOGAN, redund=RED
         _check(lib().pyro_fdk(_ptr(s), _ptr(out), s.shape[0], ctypes.byref(cg), int(kind), _ptr(custom_K),
                               int(redund), _ptr(workspace), workspace.numel() * workspace.element_size(),
                               _DTYPES[s.dtype], _stream(s)))
+    return out[0] if squeeze else out
+
+
+NOALLOC_SCRATCH_BYTES = 64 * 1024 * 1024
+
+
+def pyro_fdk_noalloc(sino: torch.Tensor, g: ConeGeometry3D, kind=SHEPP_LOGAN, redund=REDUND_PARKER,
+                     custom_K: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """FDK whose scratch is the library's static 64 MiB device array (for
+    callers that cannot allocate a workspace); the output tensor is still
+    allocated here by PyTorch, the C call itself allocates nothing."""
+    s, squeeze = _batched(_dev(sino, "sinogram"), 3, "sinogram")
+    _shape_check(s, g.sinogram_shape, "sinogram")
+    cg = g.to_c()
+    out = _out(s, g.volume_shape)
+    with torch.cuda.device(s.device):
+        _check(lib().pyro_fdk_noalloc(_ptr(s), _ptr(out), s.shape[0], ctypes.byref(cg), int(kind), _ptr(custom_K),
+                                      int(redund), _DTYPES[s.dtype], _stream(s)))
     return out[0] if squeeze else out
 
 

@@ -132,4 +132,7 @@ cudaError_t launch_filter_grad_K(const float *p, const float *g, float *dK, long
 
 int device_sm_count();
 
+// record the thread-local message returned by pyro_last_error()
+void set_last_error(const char *fmt, ...);
+
 }  // namespace pyro

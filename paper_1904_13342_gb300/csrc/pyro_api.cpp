@@ -704,6 +704,16 @@ int bp3d_transpose(const void *vol, void *sino, int batch, const pyro_geom3d *g,
 
 }  // namespace
 
+void set_last_error(const char *fmt, ...)
+{
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof(buf), fmt, ap);
+    va_end(ap);
+    g_last_error = buf;
+}
+
 int device_sm_count()
 {
     static std::mutex mu;
