@@ -20,7 +20,7 @@ def declared_symbols():
     return sorted(set(re.findall(r"PYRO_API\s+[\w\s\*]+?\b(pyro_\w+)\s*\(", src)))
 
 
-def test_header_declares_the_north_star_calls():
+def test_header_declares_the_core_calls():
     names = declared_symbols()
     for n in ("pyro_fp_par2d", "pyro_fp_fan2d", "pyro_fp_cone3d", "pyro_bp_par2d", "pyro_bp_fan2d",
               "pyro_bp_cone3d", "pyro_fdk"):
