@@ -115,6 +115,17 @@ PYRO_API int pyro_fp_fan2d(const void *vol, void *sino, int batch, const pyro_ge
 PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtype dtype,
                             void *stream);
 
+/* --- The same cone-beam forward projection, computed from a copy of the
+ * volume re-laid out z-fastest in `workspace` (device, at least
+ * pyro_fp_cone3d_workspace_bytes bytes, i.e. one volume of `dtype`;
+ * PYRO_EWORKSPACE otherwise).  This is the memory-for-speed trade the paper
+ * describes for its texture mode (the volume is held twice, Section "The
+ * Operator as a Layer"); pyro_fp_cone3d is the memory-lean mode.  Results
+ * are identical up to FP32 summation order; the workspace is scratch. */
+PYRO_API size_t pyro_fp_cone3d_workspace_bytes(const pyro_geom3d *g, pyro_dtype dtype);
+PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
+                               size_t workspace_bytes, pyro_dtype dtype, void *stream);
+
 /* --- Exact adjoint A^T of the forward projectors (the gradient of the FP
  * layer, Section "The Known Operator": the gradient of A is A^T).  Scatters
  * step * y * (interpolation weights) into the volume with FP32 atomics, so

@@ -49,6 +49,8 @@ _SIGS = {
     "pyro_fp_par2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fp_fan2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fp_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
+    "pyro_fp_cone3d_workspace_bytes": [_G3, _I],
+    "pyro_fp_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
     "pyro_fpT_par2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fpT_fan2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fpT_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
@@ -88,6 +90,7 @@ def lib():
             L.pyro_last_error.restype = ctypes.c_char_p
             L.pyro_version.restype = ctypes.c_char_p
             L.pyro_fdk_workspace_bytes.restype = _SZ
+            L.pyro_fp_cone3d_workspace_bytes.restype = _SZ
             L.pyro_fbp2d_workspace_bytes.restype = _SZ
             _lib = L
     return _lib
@@ -191,6 +194,23 @@ def pyro_fp_fan2d(vol: torch.Tensor, g: Geometry2D) -> torch.Tensor:
 
 def pyro_fp_cone3d(vol: torch.Tensor, g: ConeGeometry3D) -> torch.Tensor:
     return _fp(lib().pyro_fp_cone3d, vol, g, g.volume_shape, g.sinogram_shape)
+
+
+def pyro_fp_cone3d_ws(vol: torch.Tensor, g: ConeGeometry3D, workspace: Optional[torch.Tensor] = None,
+                      out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Cone-beam FP from a z-major copy of the volume kept in `workspace`
+    (allocated here when not given; one volume of the input dtype)."""
+    v, squeeze = _batched(_dev(vol, "volume"), 3, "volume")
+    _shape_check(v, g.volume_shape, "volume")
+    cg = g.to_c()
+    need = lib().pyro_fp_cone3d_workspace_bytes(ctypes.byref(cg), _DTYPES[v.dtype])
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=v.device)
+    o = _out(v, g.sinogram_shape) if out is None else _dev(out, "out")
+    with torch.cuda.device(v.device):
+        _check(lib().pyro_fp_cone3d_ws(_ptr(v), _ptr(o), v.shape[0], ctypes.byref(cg), _ptr(workspace),
+                                       workspace.numel() * workspace.element_size(), _DTYPES[v.dtype], _stream(v)))
+    return o[0] if squeeze and out is None else o
 
 
 def pyro_fpT_par2d(sino: torch.Tensor, g: Geometry2D) -> torch.Tensor:

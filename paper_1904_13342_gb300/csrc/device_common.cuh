@@ -124,6 +124,65 @@ __device__ __forceinline__ float trilerp_zero(const T *vol, int nx, int ny, int 
     return az.w0 * (ay.w0 * v00 + ay.w1 * v01) + az.w1 * (ay.w0 * v10 + ay.w1 * v11);
 }
 
+// Trilinear interpolation of a zero-extended volume stored with arbitrary
+// strides (elements) per axis: x-fastest [z][y][x] or the z-major copy
+// [y][x][z] used by the staged forward projector.
+template <typename T>
+__device__ __forceinline__ float trilerp_zero_strided(const T *vol, int nx, int ny, int nz, size_t stx, size_t sty,
+                                                      size_t stz, float fx, float fy, float fz)
+{
+    const Axis ax = axis_taps(fx, nx);
+    const Axis ay = axis_taps(fy, ny);
+    const Axis az = axis_taps(fz, nz);
+    const T *p00 = vol + ax.i0 * stx + ay.i0 * sty;
+    const T *p01 = vol + ax.i0 * stx + ay.i1 * sty;
+    const T *p10 = vol + ax.i1 * stx + ay.i0 * sty;
+    const T *p11 = vol + ax.i1 * stx + ay.i1 * sty;
+    const size_t z0 = az.i0 * stz, z1 = az.i1 * stz;
+    const float v00 = az.w0 * ld(p00 + z0) + az.w1 * ld(p00 + z1);
+    const float v01 = az.w0 * ld(p01 + z0) + az.w1 * ld(p01 + z1);
+    const float v10 = az.w0 * ld(p10 + z0) + az.w1 * ld(p10 + z1);
+    const float v11 = az.w0 * ld(p11 + z0) + az.w1 * ld(p11 + z1);
+    return ax.w0 * (ay.w0 * v00 + ay.w1 * v01) + ax.w1 * (ay.w0 * v10 + ay.w1 * v11);
+}
+
+__device__ __forceinline__ float lerpf(float a, float b, float t)
+{
+    return fmaf(t, b - a, a);
+}
+
+// Trilinear interpolation at a position known to be strictly inside the
+// array on every axis (0 <= f < n-1): no tap is outside, so no clamping or
+// weight masking is needed; 32-bit element offsets (arrays < 2^31 elements).
+template <typename T>
+__device__ __forceinline__ float trilerp_interior(const T *vol, int stx, int sty, int stz, float fx, float fy, float fz)
+{
+    const float x0 = floorf(fx), y0 = floorf(fy), z0 = floorf(fz);
+    const float ax = fx - x0, ay = fy - y0, az = fz - z0;
+    const T *b = vol + ((int)x0 * stx + (int)y0 * sty + (int)z0 * stz);
+    const float v00 = lerpf(ld(b), ld(b + stz), az);
+    const float v01 = lerpf(ld(b + sty), ld(b + sty + stz), az);
+    const float v10 = lerpf(ld(b + stx), ld(b + stx + stz), az);
+    const float v11 = lerpf(ld(b + stx + sty), ld(b + stx + sty + stz), az);
+    return lerpf(lerpf(v00, v01, ay), lerpf(v10, v11, ay), ax);
+}
+
+// Restrict m to samples strictly inside [margin, n-1-margin] on one axis
+// (rounded inwards), the interior where trilerp_interior applies.
+__device__ __forceinline__ void clip_axis_interior(float p0, float q, int n, float &lo, float &hi)
+{
+    const float a = 1e-3f, b = (float)(n - 1) - 1e-3f;
+    if (fabsf(q) > 1e-30f) {
+        const float t1 = (a - p0) / q;
+        const float t2 = (b - p0) / q;
+        lo = fmaxf(lo, fminf(t1, t2));
+        hi = fminf(hi, fmaxf(t1, t2));
+    } else if (!(p0 >= a && p0 <= b)) {
+        lo = 1.0f;
+        hi = -1.0f;
+    }
+}
+
 // Restrict the sample index m of p(m) = p0 + m q to the open support
 // (-1, n) of the zero-extended interpolant on one axis.  Rounded outwards:
 // a sample just outside contributes an exact 0 through axis_taps.

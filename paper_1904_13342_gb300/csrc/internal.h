@@ -113,6 +113,12 @@ cudaError_t launch_fp2d_adjoint(const void *sino, void *vol, int batch, const FP
 cudaError_t launch_fp3d(const void *vol, void *sino, int batch, const FP3DParams &p, pyro_dtype dt,
                         cudaStream_t s);
 cudaError_t launch_fp3d_adjoint(const void *sino, void *vol, int batch, const FP3DParams &p, cudaStream_t s);
+// [z][y][x] -> [y][x][z] copy of one volume
+cudaError_t launch_relayout_zmajor(const void *vol, void *vz, int nx, int ny, int nz, pyro_dtype dt, cudaStream_t s);
+// forward projection of batch item b from its z-major copy; `sino` is the whole
+// [batch][views_total][nv][nu] sinogram
+cudaError_t launch_fp3d_zmajor(const void *vz, void *sino, int b, const FP3DParams &p, pyro_dtype dt,
+                               cudaStream_t s);
 
 // sino_dtype / vol_dtype may differ (FDK reads an FP32 workspace)
 cudaError_t launch_bp2d(const void *sino, void *vol, int batch, const BP2DParams &p, pyro_dtype sino_dt,

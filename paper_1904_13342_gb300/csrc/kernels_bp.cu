@@ -113,10 +113,31 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__
         if (ZINV) {
             const float rw = 1.0f / wb;
             const float om = weight_of(rw, p.wexp);
-            const Axis au = axis_taps(fmaf(xb, rw, p.cu), p.nu);
-            const float w0 = om * au.w0, w1 = om * au.w1;
+            const float fu = fmaf(xb, rw, p.cu);
             const float dl = P[6] * rw;
             const float l0 = fmaf(yb, rw, p.cv);
+            const float la = fmaf((float)z0, dl, l0), lb = fmaf((float)(z0 + kBPZ - 1), dl, l0);
+            const float hu = (float)(p.nu - 1) - 1e-3f, hv = (float)(p.nv - 1) - 1e-3f;
+            if (fu >= 1e-3f && fu <= hu && fminf(la, lb) >= 1e-3f && fmaxf(la, lb) <= hv) {
+                // every tap of the ZB voxels lies inside the detector: no masking
+                const float fu0 = floorf(fu);
+                const float au = fu - fu0;
+                const float w1 = om * au, w0 = om - w1;
+                const TS *Sk = S + (int)fu0;
+#pragma unroll
+                for (int zz = 0; zz < kBPZ; ++zz) {
+                    const float ll = fmaf((float)(z0 + zz), dl, l0);
+                    const float fl0 = floorf(ll);
+                    const float av = ll - fl0;
+                    const TS *r0 = Sk + (int)fl0 * p.nu;
+                    const float t0 = fmaf(w0, ld(r0), w1 * ld(r0 + 1));
+                    const float t1 = fmaf(w0, ld(r0 + p.nu), w1 * ld(r0 + p.nu + 1));
+                    acc[zz] += lerpf(t0, t1, av);
+                }
+                continue;
+            }
+            const Axis au = axis_taps(fu, p.nu);
+            const float w0 = om * au.w0, w1 = om * au.w1;
 #pragma unroll
             for (int zz = 0; zz < kBPZ; ++zz) {
                 const Axis av = axis_taps(fmaf((float)(z0 + zz), dl, l0), p.nv);

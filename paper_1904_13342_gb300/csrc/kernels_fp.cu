@@ -147,6 +147,41 @@ __device__ __forceinline__ void range3d(const Ray3 &r, const FP3DParams &p, int 
     m1 = min(p.M, (int)ceilf(hi));
 }
 
+// Sum of the samples m0..m1 of one ray through a volume with element strides
+// (stx, sty, stz).  Samples strictly inside the array take the unmasked
+// interior path; the few near the faces take the zero-extended path.  The
+// sample positions are the same FMA p + m q on both paths.
+template <typename T>
+__device__ __forceinline__ float march3d(const T *vol, const FP3DParams &p, int stx, int sty, int stz, const Ray3 &r,
+                                         int m0, int m1)
+{
+    float lo = (float)m0, hi = (float)m1;
+    clip_axis_interior(r.px, r.qx, p.nx, lo, hi);
+    clip_axis_interior(r.py, r.qy, p.ny, lo, hi);
+    clip_axis_interior(r.pz, r.qz, p.nz, lo, hi);
+    int i0 = max(m0, (int)ceilf(lo)), i1 = min(m1, (int)floorf(hi));
+    if (i0 > i1) {  // no interior sample
+        i0 = m1 + 1;
+        i1 = m1;
+    }
+    float acc = 0.0f;
+    for (int m = m0; m < i0; ++m) {
+        const float fm = (float)m;
+        acc += trilerp_zero_strided(vol, p.nx, p.ny, p.nz, (size_t)stx, (size_t)sty, (size_t)stz, fmaf(fm, r.qx, r.px),
+                                    fmaf(fm, r.qy, r.py), fmaf(fm, r.qz, r.pz));
+    }
+    for (int m = i0; m <= i1; ++m) {
+        const float fm = (float)m;
+        acc += trilerp_interior(vol, stx, sty, stz, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py), fmaf(fm, r.qz, r.pz));
+    }
+    for (int m = max(i1 + 1, i0); m <= m1; ++m) {
+        const float fm = (float)m;
+        acc += trilerp_zero_strided(vol, p.nx, p.ny, p.nz, (size_t)stx, (size_t)sty, (size_t)stz, fmaf(fm, r.qx, r.px),
+                                    fmaf(fm, r.qy, r.py), fmaf(fm, r.qz, r.pz));
+    }
+    return acc;
+}
+
 constexpr int kFP3DBlockX = 32, kFP3DBlockY = 4;
 
 template <typename T>
@@ -163,12 +198,50 @@ __global__ void __launch_bounds__(kFP3DBlockX *kFP3DBlockY) fp3d_kernel(const T 
     int m0, m1;
     range3d(r, p, m0, m1);
     const T *V = vol + (size_t)b * p.nx * p.ny * p.nz;
-    float acc = 0.0f;
-    for (int m = m0; m <= m1; ++m) {
-        const float fm = (float)m;
-        acc += trilerp_zero(V, p.nx, p.ny, p.nz, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py), fmaf(fm, r.qz, r.pz));
-    }
+    const float acc = march3d(V, p, 1, p.nx, p.nx * p.ny, r, m0, m1);
     sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(p.dt * acc);
+}
+
+// Staged forward projection: the volume has been re-laid out z-fastest
+// ([y][x][z]) and each warp's 32 lanes take 32 consecutive detector rows l of
+// one column k.  Those rays differ only in elevation, so at every sample
+// the warp's taps lie in one or two short contiguous runs along z: one or two
+// cache lines per tap load, whatever the view angle.
+constexpr int kFPZLanes = 32, kFPZWarps = 4;
+
+template <typename T>
+__global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const T *__restrict__ vz,
+                                                                          T *__restrict__ sino,
+                                                                          const __grid_constant__ FP3DParams p,
+                                                                          int b)
+{
+    const int l = blockIdx.x * kFPZLanes + threadIdx.x;
+    const int k = blockIdx.y * kFPZWarps + threadIdx.y;
+    const int v = blockIdx.z;
+    if (k >= p.nu || l >= p.nv) return;
+    const Ray3 r = ray3d(p, v, k, l);
+    int m0, m1;
+    range3d(r, p, m0, m1);
+    const float acc = march3d(vz, p, p.nz, p.nz * p.nx, 1, r, m0, m1);
+    sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(p.dt * acc);
+}
+
+// [z][y][x] -> [y][x][z]: 32 x 32 tiles of one y-plane through shared memory
+template <typename T>
+__global__ void __launch_bounds__(256) relayout_zmajor_kernel(const T *__restrict__ vol, T *__restrict__ vz, int nx,
+                                                              int ny, int nz)
+{
+    __shared__ T tile[32][33];
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32, y = blockIdx.z;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int z = z0 + i, x = x0 + threadIdx.x;
+        if (z < nz && x < nx) tile[i][threadIdx.x] = vol[((size_t)z * ny + y) * nx + x];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int x = x0 + i, z = z0 + threadIdx.x;
+        if (z < nz && x < nx) vz[((size_t)y * nx + x) * nz + z] = tile[threadIdx.x][i];
+    }
 }
 
 __global__ void __launch_bounds__(kFP3DBlockX *kFP3DBlockY) fp3d_adjoint_kernel(const float *__restrict__ sino,
@@ -251,6 +324,43 @@ cudaError_t launch_fp3d(const void *vol, void *sino, int batch, const FP3DParams
         break;
     case PYRO_BF16:
         fp3d_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16 *)vol, (__nv_bfloat16 *)sino, p);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relayout_zmajor(const void *vol, void *vz, int nx, int ny, int nz, pyro_dtype dt, cudaStream_t s)
+{
+    dim3 block(32, 8), grid((nx + 31) / 32, (nz + 31) / 32, ny);
+    switch (dt) {
+    case PYRO_F32:
+        relayout_zmajor_kernel<float><<<grid, block, 0, s>>>((const float *)vol, (float *)vz, nx, ny, nz);
+        break;
+    case PYRO_F16:
+        relayout_zmajor_kernel<__half><<<grid, block, 0, s>>>((const __half *)vol, (__half *)vz, nx, ny, nz);
+        break;
+    case PYRO_BF16:
+        relayout_zmajor_kernel<__nv_bfloat16>
+            <<<grid, block, 0, s>>>((const __nv_bfloat16 *)vol, (__nv_bfloat16 *)vz, nx, ny, nz);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp3d_zmajor(const void *vz, void *sino, int b, const FP3DParams &p, pyro_dtype dt, cudaStream_t s)
+{
+    dim3 block(kFPZLanes, kFPZWarps);
+    dim3 grid((p.nv + kFPZLanes - 1) / kFPZLanes, (p.nu + kFPZWarps - 1) / kFPZWarps, (unsigned)p.n_views);
+    switch (dt) {
+    case PYRO_F32:
+        fp3d_zmajor_kernel<float><<<grid, block, 0, s>>>((const float *)vz, (float *)sino, p, b);
+        break;
+    case PYRO_F16:
+        fp3d_zmajor_kernel<__half><<<grid, block, 0, s>>>((const __half *)vz, (__half *)sino, p, b);
+        break;
+    case PYRO_BF16:
+        fp3d_zmajor_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16 *)vz, (__nv_bfloat16 *)sino,
+                                                                   p, b);
         break;
     }
     return cudaGetLastError();

@@ -637,6 +637,33 @@ int fp3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtyp
     return PYRO_OK;
 }
 
+// staged cone FP: per batch item, a z-major copy of the volume in `work`
+int fp3d_staged(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *work, size_t work_bytes,
+                pyro_dtype dt, void *stream)
+{
+    if (int e = check_io(vol, sino, batch, dt)) return e;
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    const size_t vox = (size_t)G.nx * G.ny * G.nz;
+    const size_t need = vox * elem_size(dt);
+    if (work_bytes < need || work == nullptr || !aligned16(work))
+        return fail(PYRO_EWORKSPACE, "the staged forward projector needs a 16-byte aligned workspace of %zu bytes "
+                                     "(got %zu)", need, work_bytes);
+    if (batch == 0) return PYRO_OK;
+    const int V = (int)G.beta.size();
+    static thread_local FP3DParams p;
+    for (int b = 0; b < batch; ++b) {
+        const char *vi = (const char *)vol + b * vox * elem_size(dt);
+        PYRO_CUDA(launch_relayout_zmajor(vi, work, G.nx, G.ny, G.nz, dt, as_stream(stream)));
+        for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
+            const int nvw = std::min(kMaxViewsConeFP, V - v0);
+            if (int e = fill_fp3d(G, v0, nvw, p)) return e;
+            PYRO_CUDA(launch_fp3d_zmajor(work, sino, b, p, dt, as_stream(stream)));
+        }
+    }
+    return PYRO_OK;
+}
+
 int bp3d_impl(const void *sino, void *vol, int batch, const Geo3D &G, int wexp, float scale, pyro_dtype sino_dt,
               pyro_dtype vol_dt, void *stream)
 {
@@ -751,6 +778,18 @@ PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_g
                             void *stream)
 {
     return fp3d(vol, sino, batch, g, dtype, false, stream);
+}
+
+PYRO_API size_t pyro_fp_cone3d_workspace_bytes(const pyro_geom3d *g, pyro_dtype dtype)
+{
+    if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !valid_dtype(dtype)) return 0;
+    return (size_t)g->nx * g->ny * g->nz * elem_size(dtype);
+}
+
+PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
+                               size_t workspace_bytes, pyro_dtype dtype, void *stream)
+{
+    return fp3d_staged(vol, sino, batch, g, workspace, workspace_bytes, dtype, stream);
 }
 
 PYRO_API int pyro_fpT_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dtype,

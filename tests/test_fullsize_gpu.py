@@ -48,9 +48,10 @@ def cone():
     return g, vol, ang, P
 
 
-def test_cone_fp_full_size_sampled_rays(cone):
+@pytest.mark.parametrize("mode", ["direct", "staged"])
+def test_cone_fp_full_size_sampled_rays(cone, mode):
     g, vol, ang, P = cone
-    sino = B.pyro_fp_cone3d(vol, g)
+    sino = B.pyro_fp_cone3d(vol, g) if mode == "direct" else B.pyro_fp_cone3d_ws(vol, g)
     torch.cuda.synchronize()
     rng = np.random.default_rng(1)
     nvw, (nv, nu) = g.number_of_projections, g.detector_shape

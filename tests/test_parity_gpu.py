@@ -158,6 +158,34 @@ def test_fp_cone(traj, dtype):
     assert rel(host(got), ref) < TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("traj", ["circular", "tilted"])
+def test_fp_cone_staged(traj, dtype):
+    """z-major staged projector: same values as the oracle (and the direct path)."""
+    c = CONE
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang) if traj == "circular" else tilted_pmats(c, ang)
+    vol = ph.voxelize_ellipsoids(ph.random_ellipsoids(5, 18.0, seed=27), c["shape"], c["spacing"]).numpy()
+    vol = np.stack([vol, ph.random_volume(c["shape"], 28), vol[::-1].copy()])
+    g = cone_geom(c, None if traj == "circular" else P)
+    got = B.pyro_fp_cone3d_ws(to_dev(vol, dtype), g)
+    ref = np.stack([oracle.fp_cone3d(f32(v), c["spacing"], c["det"], P) for v in vol])
+    assert got.shape == (3, c["views"], *c["det"])
+    assert rel(host(got), ref) < TOL[dtype]
+    direct = B.pyro_fp_cone3d(to_dev(vol, dtype), g)
+    assert rel(host(got), host(direct)) < TOL[dtype]
+
+
+def test_fp_cone_staged_workspace_checks():
+    c = CONE
+    g = cone_geom(c)
+    vol = to_dev(ph.random_volume(c["shape"], 29))
+    small = torch.empty(vol.numel() * 4 - 16, dtype=torch.uint8, device=DEV)
+    with pytest.raises(B.PyroError) as e:
+        B.pyro_fp_cone3d_ws(vol, g, workspace=small)
+    assert e.value.status == 5
+
+
 @pytest.mark.parametrize("traj", ["circular", "tilted"])
 def test_fp_adjoint_cone(traj):
     c = CONE
