@@ -186,6 +186,11 @@ PYRO_API int pyro_filter_rows(const void *in, void *out, long n_rows, int nu, do
 /* padded length pn used by pyro_filter_rows for a row of nu samples */
 PYRO_API int pyro_filter_pad_length(int nu);
 
+/* The diagonal K[0..pn/2] of a built-in filter (Ram-Lak, ramp or
+ * Shepp-Logan on sample spacing tau), written to the HOST array K_out of
+ * pn/2 + 1 floats: the initial value of a learnable filter (Eq. 6). */
+PYRO_API int pyro_filter_spectrum(pyro_filter kind, int nu, double tau, float *K_out);
+
 /* --- Gradient of a loss with respect to a custom K (Eq. 6, filter learning):
  * dK[m] = sum_rows c_m / pn * Re(P[m] conj(G[m])), P and G the length-pn
  * DFTs of the zero-padded rows of p (the filter's input) and g (dL/dq),
@@ -211,6 +216,22 @@ PYRO_API int pyro_fbp_par2d(const void *sino, void *vol, int batch, const pyro_g
 PYRO_API int pyro_fbp_fan2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_filter kind,
                             const float *custom_K, pyro_redund redund, void *workspace, size_t workspace_bytes,
                             pyro_dtype dtype, void *stream);
+
+/* --- Total variation for the iterative reconstruction of Eq. 7
+ * (min |A x - p|^2 + lambda TV(x)), in the smoothed anisotropic form
+ *   TV(x) = sum_{axes a} sum_i phi(x_{i+e_a} - x_i),  phi(d) = sqrt(d^2+eps^2) - eps,
+ * over the forward differences that stay inside the volume.  FP32 device
+ * arrays [batch][nz][ny][nx].  grad (may be NULL) receives
+ * alpha * base + lambda * dTV/dx (base may be NULL = 0 and may alias grad);
+ * value (may be NULL) receives TV(x) per batch item, reduced in FP32
+ * (block sums, then FP32 atomics: not bit-reproducible across runs). */
+PYRO_API int pyro_tv(const float *x, float *grad, const float *base, float alpha, float lambda, float *value,
+                     int batch, int nz, int ny, int nx, float eps, void *stream);
+/* y = a x + b y over n FP32 device values (the gradient step of Eq. 7) */
+PYRO_API int pyro_axpby(const float *x, float *y, long n, float a, float b, void *stream);
+/* out[0] = sum a_i b_i over n FP32 device values; out is a DEVICE float,
+ * reduced in FP32 (block sums, then FP32 atomics) */
+PYRO_API int pyro_dot(const float *a, const float *b, long n, float *out, void *stream);
 
 /* --- FDK without any device allocation by the caller.  The paper has no
  * counterpart: this serves callers that only hold the input and output

@@ -418,3 +418,44 @@ def tv_grad(x, eps):
     out = np.empty_like(x)
     _load().oracle_tv_grad(_p(x), nx, ny, nz, eps, _p(out))
     return out.reshape(shp)
+
+
+# ------------------------------------------------------ iterative TV (Eq. 7) --
+def lipschitz(fwd, adj, shape, iters=20, seed=0) -> float:
+    """Largest eigenvalue of 2 A^T A by power iteration (FP64)."""
+    v = np.random.default_rng(seed).uniform(size=shape)
+    lam = 0.0
+    for _ in range(iters):
+        w = adj(fwd(v))
+        lam = np.linalg.norm(w) / np.linalg.norm(v)
+        v = w / np.linalg.norm(w)
+    return 2.0 * lam
+
+
+def tv_solve(p, fwd, adj, lam, eps, n_iter, L_est, clamp=10.0, x0=None):
+    """Gradient descent with Barzilai-Borwein steps on J(x) = |A x - p|^2 +
+    lam TV(x) (Eq. 7), from x = 0:
+      g_k = 2 A^T (A x_k - p) + lam grad TV(x_k),
+      alpha_0 = 1/L_est, alpha_k = (s.s)/(s.dy) clamped to [0, clamp/L_est],
+      x_{k+1} = x_k - alpha_k g_k.
+    Returns (x, objective per iterate including the last)."""
+    p = _f64(p)
+    x = np.zeros_like(adj(p)) if x0 is None else _f64(x0).copy()
+    x_prev = g_prev = None
+    obj = []
+    for k in range(n_iter):
+        r = fwd(x) - p
+        g = 2.0 * adj(r) + lam * tv_grad(x, eps)
+        obj.append(float(np.sum(r * r)) + lam * tv_value(x, eps))
+        if k == 0:
+            alpha = 1.0 / L_est
+        else:
+            s, dy = x - x_prev, g - g_prev
+            sy = float(np.sum(s * dy))
+            alpha = float(np.sum(s * s)) / sy if sy > 0 else 1.0 / L_est
+            alpha = min(max(alpha, 0.0), clamp / L_est)
+        x_prev, g_prev = x, g
+        x = x - alpha * g
+    r = fwd(x) - p
+    obj.append(float(np.sum(r * r)) + lam * tv_value(x, eps))
+    return x, obj

@@ -64,6 +64,7 @@ _SIGS = {
     "pyro_weights3d": [_VP, _I, _G3, _I, _I, _I, _VP],
     "pyro_filter_rows": [_VP, _VP, _L, _I, _D, _I, _VP, _I, _VP],
     "pyro_filter_pad_length": [_I],
+    "pyro_filter_spectrum": [_I, _I, _D, ctypes.POINTER(ctypes.c_float)],
     "pyro_filter_grad_K": [_VP, _VP, _VP, _L, _I, _VP],
     "pyro_fdk_workspace_bytes": [_G3, _I],
     "pyro_fdk": [_VP, _VP, _I, _G3, _I, _VP, _I, _VP, _SZ, _I, _VP],
@@ -71,6 +72,9 @@ _SIGS = {
     "pyro_fbp_par2d": [_VP, _VP, _I, _G2, _I, _VP, _VP, _SZ, _I, _VP],
     "pyro_fbp_fan2d": [_VP, _VP, _I, _G2, _I, _VP, _I, _VP, _SZ, _I, _VP],
     "pyro_fdk_noalloc": [_VP, _VP, _I, _G3, _I, _VP, _I, _I, _VP],
+    "pyro_tv": [_VP, _VP, _VP, _F, _F, _VP, _I, _I, _I, _I, _F, _VP],
+    "pyro_axpby": [_VP, _VP, _L, _F, _F, _VP],
+    "pyro_dot": [_VP, _VP, _L, _VP, _VP],
     "pyro_last_error": [],
     "pyro_version": [],
 }
@@ -275,6 +279,14 @@ def pyro_filter_pad_length(nu: int) -> int:
     return int(lib().pyro_filter_pad_length(nu))
 
 
+def pyro_filter_spectrum(kind: int, nu: int, tau: float) -> torch.Tensor:
+    """K[0..pn/2] of a built-in filter, computed by the library (CPU tensor)."""
+    K = torch.empty(pyro_filter_pad_length(nu) // 2 + 1, dtype=torch.float32)
+    _check(lib().pyro_filter_spectrum(int(kind), int(nu), float(tau),
+                                      ctypes.cast(K.data_ptr(), ctypes.POINTER(ctypes.c_float))))
+    return K
+
+
 def pyro_filter_rows(rows: torch.Tensor, tau: float, kind=RAMLAK, custom_K: Optional[torch.Tensor] = None,
                      out: Optional[torch.Tensor] = None) -> torch.Tensor:
     r = _dev(rows, "rows")
@@ -363,6 +375,55 @@ def pyro_fbp_par2d(sino, g: Geometry2D, kind=RAMLAK, custom_K=None, workspace=No
 
 def pyro_fbp_fan2d(sino, g: Geometry2D, kind=RAMLAK, redund=REDUND_FULL, custom_K=None, workspace=None):
     return _fbp2d(True, sino, g, kind, redund, custom_K, workspace)
+
+
+# ------------------------------------------------------------ TV / vectors --
+def _f32(t, name):
+    t = _dev(t, name)
+    if t.dtype != torch.float32:
+        raise TypeError(f"{name} must be float32")
+    return t
+
+
+def pyro_tv(x: torch.Tensor, eps: float, lam: float = 1.0, base: Optional[torch.Tensor] = None, alpha: float = 0.0,
+            want_grad: bool = True, want_value: bool = True):
+    """(grad, value): grad = alpha * base + lam * dTV/dx, value = TV(x) per
+    batch item; x is [nz, ny, nx] or [batch, nz, ny, nx] (2D: nz = 1)."""
+    xv = _f32(x, "x")
+    shp = xv.shape
+    if xv.dim() == 2:
+        xv = xv.reshape(1, 1, *shp)
+    elif xv.dim() == 3:
+        xv = xv.unsqueeze(0)
+    bsz, nz, ny, nx = xv.shape
+    grad = torch.empty_like(xv) if want_grad else None
+    value = torch.empty(bsz, device=xv.device, dtype=torch.float32) if want_value else None
+    b = None if base is None else _f32(base, "base")
+    with torch.cuda.device(xv.device):
+        _check(lib().pyro_tv(_ptr(xv), _ptr(grad), _ptr(b), float(alpha), float(lam), _ptr(value), bsz, nz, ny, nx,
+                             float(eps), _stream(xv)))
+    return (None if grad is None else grad.reshape(shp)), value
+
+
+def pyro_axpby(x: torch.Tensor, y: torch.Tensor, a: float, b: float) -> torch.Tensor:
+    """y <- a x + b y in place."""
+    x, y = _f32(x, "x"), _f32(y, "y")
+    if x.numel() != y.numel():
+        raise ValueError("x and y must have the same size")
+    with torch.cuda.device(y.device):
+        _check(lib().pyro_axpby(_ptr(x), _ptr(y), y.numel(), float(a), float(b), _stream(y)))
+    return y
+
+
+def pyro_dot(a: torch.Tensor, b: torch.Tensor, out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """sum a_i b_i as a one-element float32 device tensor (FP32 reduction)."""
+    a, b = _f32(a, "a"), _f32(b, "b")
+    if a.numel() != b.numel():
+        raise ValueError("a and b must have the same size")
+    o = torch.empty(1, device=a.device, dtype=torch.float32) if out is None else out
+    with torch.cuda.device(a.device):
+        _check(lib().pyro_dot(_ptr(a), _ptr(b), a.numel(), _ptr(o), _stream(a)))
+    return o
 
 
 def version() -> str:

@@ -136,6 +136,11 @@ cudaError_t launch_filter(const void *in, void *out, const FilterParams &p, cons
 cudaError_t launch_filter_grad_K(const float *p, const float *g, float *dK, long n_rows, int nu, int pn,
                                  int log2pn, cudaStream_t s);
 
+cudaError_t launch_tv(const float *x, float *grad, const float *base, float alpha, float lambda, float *value,
+                      int batch, int nz, int ny, int nx, float eps, cudaStream_t s);
+cudaError_t launch_axpby(const float *x, float *y, long n, float a, float b, cudaStream_t s);
+cudaError_t launch_dot(const float *a, const float *b, long n, float *out, cudaStream_t s);
+
 int device_sm_count();
 
 // record the thread-local message returned by pyro_last_error()

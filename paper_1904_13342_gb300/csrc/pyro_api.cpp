@@ -879,6 +879,18 @@ PYRO_API int pyro_filter_pad_length(int nu)
     return nu > 0 ? pad_length(nu) : 0;
 }
 
+PYRO_API int pyro_filter_spectrum(pyro_filter kind, int nu, double tau, float *K_out)
+{
+    PYRO_CHECK(K_out != nullptr, "K_out is NULL");
+    PYRO_CHECK(nu > 0 && nu <= kMaxPadLength / 2, "nu=%d outside [1, %d]", nu, kMaxPadLength / 2);
+    PYRO_CHECK(kind == PYRO_RAMLAK || kind == PYRO_RAMP || kind == PYRO_SHEPP_LOGAN, "not a built-in filter: %d",
+               (int)kind);
+    PYRO_CHECK(pos_finite(tau), "tau must be positive and finite");
+    const std::vector<float> &K = builtin_K(kind, pad_length(nu), tau);
+    std::copy(K.begin(), K.end(), K_out);
+    return PYRO_OK;
+}
+
 PYRO_API int pyro_filter_rows(const void *in, void *out, long n_rows, int nu, double tau, pyro_filter kind,
                               const float *custom_K, pyro_dtype dtype, void *stream)
 {
@@ -1000,6 +1012,41 @@ PYRO_API int pyro_fbp_fan2d(const void *sino, void *vol, int batch, const pyro_g
                             pyro_dtype dtype, void *stream)
 {
     return fbp2d(true, sino, vol, batch, g, kind, custom_K, redund, workspace, workspace_bytes, dtype, stream);
+}
+
+PYRO_API int pyro_tv(const float *x, float *grad, const float *base, float alpha, float lambda, float *value,
+                     int batch, int nz, int ny, int nx, float eps, void *stream)
+{
+    PYRO_CHECK(batch >= 0 && nz > 0 && ny > 0 && nx > 0, "bad volume shape");
+    PYRO_CHECK(batch <= 65535, "batch must be <= 65535");
+    PYRO_CHECK(std::isfinite(eps) && eps > 0.0f, "eps must be positive");
+    PYRO_CHECK(std::isfinite(alpha) && std::isfinite(lambda), "alpha / lambda must be finite");
+    if (batch == 0) return PYRO_OK;
+    PYRO_CHECK(x != nullptr && (grad != nullptr || value != nullptr), "need x and at least one of grad / value");
+    PYRO_CHECK(aligned16(x) && aligned16(grad) && aligned16(base), "device pointers must be 16-byte aligned");
+    PYRO_CUDA(launch_tv(x, grad, base, alpha, lambda, value, batch, nz, ny, nx, eps, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_axpby(const float *x, float *y, long n, float a, float b, void *stream)
+{
+    PYRO_CHECK(n >= 0, "n must be >= 0");
+    if (n == 0) return PYRO_OK;
+    PYRO_CHECK(x != nullptr && y != nullptr, "NULL pointer");
+    PYRO_CUDA(launch_axpby(x, y, n, a, b, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_dot(const float *a, const float *b, long n, float *out, void *stream)
+{
+    PYRO_CHECK(n >= 0 && out != nullptr, "bad arguments");
+    if (n > 0) PYRO_CHECK(a != nullptr && b != nullptr, "NULL pointer");
+    if (n == 0) {
+        PYRO_CUDA(cudaMemsetAsync(out, 0, sizeof(float), as_stream(stream)));
+        return PYRO_OK;
+    }
+    PYRO_CUDA(launch_dot(a, b, n, out, as_stream(stream)));
+    return PYRO_OK;
 }
 
 PYRO_API const char *pyro_last_error(void)

@@ -521,3 +521,43 @@ def test_tv_closed_form_and_gradient():
         xm[idx] -= h
         fd = (oracle.tv_value(xp, eps) - oracle.tv_value(xm, eps)) / (2 * h)
         assert abs(fd - g[idx]) < 1e-6
+
+
+def test_tv_solver_zero_lambda_reaches_least_squares():
+    """With lambda = 0 the iteration of Eq. 7 minimises |A x - p|^2: on an
+    8x8 parallel problem it reaches the least-squares optimum of the explicit
+    system matrix (numpy lstsq)."""
+    n, nu = 8, 13
+    ang = oracle.uniform_angles(12, np.pi)
+    fwd = lambda v: oracle.fp_par2d(v, (1.0, 1.0), nu, 1.0, ang)
+    adj = lambda s: oracle.fpT_par2d(s, (n, n), (1.0, 1.0), 1.0, ang)
+    A = np.stack([fwd(np.eye(n * n)[i].reshape(n, n)).ravel() for i in range(n * n)], axis=1)
+    rng = np.random.default_rng(19)
+    p = fwd(rng.uniform(0, 1, (n, n))) + 0.01 * rng.standard_normal((12, nu))
+    x_ls = np.linalg.lstsq(A, p.ravel(), rcond=None)[0]
+    j_ls = float(np.sum((A @ x_ls - p.ravel()) ** 2))
+    L = oracle.lipschitz(fwd, adj, (n, n))
+    assert abs(L - 2 * np.linalg.eigvalsh(A.T @ A).max()) < 1e-6 * L
+    x, obj = oracle.tv_solve(p, fwd, adj, 0.0, 1e-3, 400, L)
+    assert obj[-1] <= obj[0]
+    assert abs(obj[-1] - j_ls) < 1e-6 * obj[0]
+
+
+def test_tv_solver_is_first_order_optimal_with_lambda():
+    n, nu = 8, 13
+    ang = oracle.uniform_angles(12, np.pi)
+    fwd = lambda v: oracle.fp_par2d(v, (1.0, 1.0), nu, 1.0, ang)
+    adj = lambda s: oracle.fpT_par2d(s, (n, n), (1.0, 1.0), 1.0, ang)
+    rng = np.random.default_rng(20)
+    truth = np.zeros((n, n))
+    truth[2:6, 3:7] = 1.0
+    p = fwd(truth) + 0.05 * rng.standard_normal((12, nu))
+    L = oracle.lipschitz(fwd, adj, (n, n))
+    lam, eps = 0.5, 1e-2
+    x, obj = oracle.tv_solve(p, fwd, adj, lam, eps, 600, L)
+    g = 2 * adj(fwd(x) - p) + lam * oracle.tv_grad(x, eps)
+    g0 = 2 * adj(-p)
+    assert np.linalg.norm(g) < 1e-4 * np.linalg.norm(g0)
+    # the TV term lowers the error against the piecewise-constant truth vs plain least squares
+    x0, _ = oracle.tv_solve(p, fwd, adj, 0.0, eps, 600, L)
+    assert np.linalg.norm(x - truth) < np.linalg.norm(x0 - truth)

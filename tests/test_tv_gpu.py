@@ -1,0 +1,97 @@
+"""TV kernels and the iterative reconstruction of Eq. 7 on the GPU.
+
+* pyro_tv (value and gradient), pyro_axpby, pyro_dot against the oracle.
+* The GPU iteration (FP32 kernels) follows the oracle's FP64 iteration of the
+  same algorithm step for step.
+* The paper's sparse-view experiment (Section "Iterative Reconstruction":
+  30 parallel views over 180 degrees, 2 % additive Gaussian noise): the TV
+  reconstruction is closer to the phantom than FBP.
+"""
+import math
+
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1904_13342_gb300 import binding as B
+from paper_1904_13342_gb300 import phantoms as ph
+from paper_1904_13342_gb300 import tv as TV
+from paper_1904_13342_gb300.geometry import ParallelGeometry2D
+
+pytestmark = pytest.mark.gpu
+DEV = torch.device("cuda:0")
+
+
+def rel(a, b):
+    a, b = np.asarray(a, np.float64), np.asarray(b, np.float64)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+def f32(a):
+    return np.asarray(a, np.float32).astype(np.float64)
+
+
+def dev(a):
+    return torch.from_numpy(np.ascontiguousarray(a)).float().to(DEV)
+
+
+@pytest.mark.parametrize("shape", [(13, 17, 19), (1, 40, 33), (2, 9, 10, 11)])
+def test_tv_value_and_gradient(shape):
+    rng = np.random.default_rng(1)
+    x = rng.standard_normal(shape)
+    base = rng.standard_normal(shape)
+    eps = 0.05
+    grad, val = B.pyro_tv(dev(x), eps, lam=0.7, base=dev(base), alpha=2.0)
+    xs = x if len(shape) == 4 else x[None]
+    bs = base if len(shape) == 4 else base[None]
+    ref_g = np.stack([2.0 * f32(b) + 0.7 * oracle.tv_grad(f32(v), eps) for v, b in zip(xs, bs)]).reshape(shape)
+    ref_v = np.array([oracle.tv_value(f32(v), eps) for v in xs])
+    assert rel(grad.double().cpu().numpy(), ref_g) < 1e-5
+    assert rel(val.double().cpu().numpy(), ref_v) < 1e-5
+
+
+def test_axpby_and_dot():
+    rng = np.random.default_rng(2)
+    a, b = rng.standard_normal(100003), rng.standard_normal(100003)
+    ta, tb = dev(a), dev(b)
+    B.pyro_axpby(ta, tb, 0.5, -2.0)
+    assert rel(tb.double().cpu().numpy(), 0.5 * f32(a) - 2.0 * f32(b)) < 1e-6
+    d = B.pyro_dot(ta, ta).item()
+    assert abs(d - np.sum(f32(a) ** 2)) < 1e-5 * np.sum(f32(a) ** 2)
+
+
+def parallel_problem(n=32, views=30, noise=0.02, seed=0):
+    g = ParallelGeometry2D((n, n), (1.0, 1.0), int(1.43 * n), 1.0, views, math.pi)
+    e = ph.random_ellipses(6, n / 2, seed=seed)
+    truth = f32(ph.voxelize_ellipses(e, (n, n), (1.0, 1.0), supersample=4).numpy())
+    ang = g.view_angles()
+    nu = g.detector_shape
+    fwd = lambda v: oracle.fp_par2d(v, (1.0, 1.0), nu, 1.0, ang)
+    adj = lambda s: oracle.fpT_par2d(s, (n, n), (1.0, 1.0), 1.0, ang)
+    p = fwd(truth)
+    p = f32(p + noise * p.max() * np.random.default_rng(seed + 1).standard_normal(p.shape))
+    return g, truth, p, fwd, adj, ang
+
+
+def test_tv_iteration_follows_the_oracle():
+    g, truth, p, fwd, adj, ang = parallel_problem()
+    L = oracle.lipschitz(fwd, adj, g.volume_shape)
+    lam, eps, it = 4.0, 1e-3, 12
+    x_ref, obj_ref = oracle.tv_solve(p, fwd, adj, lam, eps, it, L)
+    res = TV.tv_reconstruct(dev(p), g, it, lam, eps, L_est=L, track_objective=True)
+    assert rel(res.x.double().cpu().numpy(), x_ref) < 1e-4
+    assert rel(res.objective, obj_ref) < 1e-4
+    assert res.objective[-1] < 0.15 * res.objective[0]
+
+
+def test_sparse_view_tv_beats_fbp():
+    """30 parallel views over 180 degrees, 2 % Gaussian noise, 128^2 phantom
+    of 10 random ellipses: TV (200 iterations) has a lower RMSE than FBP."""
+    g, truth, p, fwd, adj, ang = parallel_problem(n=128, views=30, noise=0.02, seed=0)
+    fbp = B.pyro_fbp_par2d(dev(p), g, kind=B.RAMLAK).double().cpu().numpy()
+    res = TV.tv_reconstruct(dev(p), g, 200, 4.0, 1e-3)
+    x = res.x.double().cpu().numpy()
+    rmse = lambda a: float(np.sqrt(np.mean((a - truth) ** 2)))
+    print(f"sparse-view RMSE: TV {rmse(x):.4f}, FBP {rmse(fbp):.4f}")
+    assert rmse(x) < 0.6 * rmse(fbp)
