@@ -87,12 +87,17 @@ __global__ void __launch_bounds__(256) bp2d_transpose_kernel(const float *__rest
 
 constexpr int kBPX = 32, kBPY = 8, kBPZ = 8;
 
+// The 32 x 8 voxel tile of a block is cut into 8 x 4 tiles per warp (not 32 x 1
+// rows): a warp's voxels then project onto ~16 detector columns instead of
+// ~40, one cache line per detector row.
 template <typename TS, typename TV, bool ZINV>
 __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__ sino, TV *__restrict__ vol,
                                                           const __grid_constant__ BP3DParams p)
 {
-    const int i = blockIdx.x * kBPX + threadIdx.x;
-    const int j = blockIdx.y * kBPY + threadIdx.y;
+    const int t = threadIdx.y * kBPX + threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    const int i = blockIdx.x * kBPX + (warp & 3) * 8 + (lane & 7);
+    const int j = blockIdx.y * kBPY + (warp >> 2) * 4 + (lane >> 3);
     const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
     const int b = blockIdx.z / zblocks;
     const int z0 = (blockIdx.z % zblocks) * kBPZ;

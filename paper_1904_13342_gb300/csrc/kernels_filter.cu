@@ -93,26 +93,6 @@ __device__ void fft_dif(float2 *z, const float2 *tw, int pn, int log2pn)
     }
 }
 
-// Inverse DIT FFT (unnormalised): bit-reversed order in, natural order out.
-__device__ void ifft_dit(float2 *z, const float2 *tw, int pn, int log2pn)
-{
-    const int half_n = pn >> 1;
-    for (int s = 1; s <= log2pn; ++s) {
-        const int half = 1 << (s - 1);
-        const int tstride = pn >> s;
-        for (int i = threadIdx.x; i < half_n; i += blockDim.x) {
-            const int pos = i & (half - 1);
-            const int a = ((i >> (s - 1)) << s) + pos;
-            const int b = a + half;
-            const float2 x = z[a];
-            const float2 t = cmul_conj(z[b], tw[pos * tstride]);
-            z[a] = make_float2(x.x + t.x, x.y + t.y);
-            z[b] = make_float2(x.x - t.x, x.y - t.y);
-        }
-        __syncthreads();
-    }
-}
-
 __device__ __forceinline__ int bitrev(int x, int bits)
 {
     return (int)(__brev((unsigned)x) >> (32 - bits));
@@ -129,59 +109,231 @@ __device__ void init_twiddles(float2 *tw, int pn)
 
 constexpr int kFilterThreads = 256;
 
+// ---- Stockham autosort FFT (natural order in and out), radix 8 passes in
+// registers, a final radix-4 or radix-2 pass when log2(pn) is not a
+// multiple of 3.  Pass i reads element j + r*pn/R of buffer `src`, applies
+// the twiddles w^(r k), w = exp(-2 pi i / (Ns R)), k = j mod Ns, runs an
+// R-point DFT and writes X[r] to (j / Ns) Ns R + k + r Ns of `dst`.
+// Pass i (0-based) of a length-2^L transform: radix 8 with Ns = 8^i, except
+// the last pass which has radix 2^(L - 3 (P-1)); its twiddle table (Ns
+// entries) starts at (8^i - 1) / 7.
+__host__ __device__ inline int n_passes(int log2pn)
+{
+    return (log2pn + 2) / 3;
+}
+
+__host__ __device__ inline int twiddle_total(int log2pn)
+{
+    const int P = n_passes(log2pn);
+    return ((1 << (3 * P)) - 1) / 7;  // sum of 8^i, i < P (bounds the last pass's Ns too)
+}
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 mul_negi(float2 a) { return make_float2(a.y, -a.x); }  // a * (-i)
+
+// R-point DFTs X[k] = sum v[n] exp(-2 pi i n k / R), natural order out
+__device__ __forceinline__ void dft4(float2 *v)
+{
+    const float2 e0 = cadd(v[0], v[2]), e1 = cadd(v[1], v[3]);
+    const float2 o0 = csub(v[0], v[2]), o1 = mul_negi(csub(v[1], v[3]));
+    v[0] = cadd(e0, e1);
+    v[2] = csub(e0, e1);
+    v[1] = cadd(o0, o1);
+    v[3] = csub(o0, o1);
+}
+
+__device__ __forceinline__ void dft8(float2 *v)
+{
+    const float h = 0.70710678118654752440f;
+    float2 a[4], c[4];
+#pragma unroll
+    for (int n = 0; n < 4; ++n) {
+        a[n] = cadd(v[n], v[n + 4]);
+        c[n] = csub(v[n], v[n + 4]);
+    }
+    // c[n] *= exp(-2 pi i n / 8)
+    c[1] = make_float2(h * (c[1].x + c[1].y), h * (c[1].y - c[1].x));
+    c[2] = mul_negi(c[2]);
+    c[3] = make_float2(h * (c[3].y - c[3].x), -h * (c[3].x + c[3].y));
+    dft4(a);
+    dft4(c);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        v[2 * k] = a[k];
+        v[2 * k + 1] = c[k];
+    }
+}
+
+// Shared-memory index with one pad slot per 8 complex values: spreads the
+// strided Stockham stores over all banks.
+__device__ __forceinline__ int sp(int i)
+{
+    return i + (i >> 3);
+}
+
+// One pass over `groups` independent transforms of length pn stored back to back.
+template <int R>
+__device__ __forceinline__ void stockham_pass(const float2 *src, float2 *dst, const float2 *tw, int pn, int ns,
+                                              int groups)
+{
+    const int nb = pn / R;
+    for (int b = threadIdx.x; b < groups * nb; b += blockDim.x) {
+        const int g = b / nb, j = b - g * nb;
+        const float2 *s = src + g * sp(pn);
+        float2 *d = dst + g * sp(pn);
+        const int k = j & (ns - 1);
+        float2 v[R];
+        const float2 w1 = tw[k];
+        float2 w = make_float2(1.0f, 0.0f);
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const float2 x = s[sp(j + r * nb)];
+            v[r] = r == 0 ? x : cmul(x, w);
+            w = cmul(w, w1);
+        }
+        if (R == 8) dft8(v);
+        if (R == 4) dft4(v);
+        if (R == 2) {
+            const float2 t = v[0];
+            v[0] = cadd(t, v[1]);
+            v[1] = csub(t, v[1]);
+        }
+        const int base = (j - k) * R + k;
+#pragma unroll
+        for (int r = 0; r < R; ++r) d[sp(base + r * ns)] = v[r];
+    }
+}
+
+// Full forward transform of `groups` rows; returns the buffer holding the result.
+__device__ float2 *stockham_fft(float2 *a, float2 *b, const float2 *tw, int log2pn, int pn, int groups)
+{
+    const int P = n_passes(log2pn);
+    for (int i = 0; i < P; ++i) {
+        const int ns = 1 << (3 * i);
+        const float2 *t = tw + (ns - 1) / 7;
+        const int rb = i < P - 1 ? 3 : log2pn - 3 * (P - 1);
+        if (rb == 3) stockham_pass<8>(a, b, t, pn, ns, groups);
+        else if (rb == 2) stockham_pass<4>(a, b, t, pn, ns, groups);
+        else stockham_pass<2>(a, b, t, pn, ns, groups);
+        __syncthreads();
+        float2 *tmp = a;
+        a = b;
+        b = tmp;
+    }
+    return a;
+}
+
+__device__ void init_stockham_twiddles(float2 *tw, int log2pn)
+{
+    const int P = n_passes(log2pn);
+    for (int i = 0; i < P; ++i) {
+        const int ns = 1 << (3 * i);
+        const int rb = i < P - 1 ? 3 : log2pn - 3 * (P - 1);
+        const int nr = ns << rb;
+        for (int k = threadIdx.x; k < ns; k += blockDim.x) {
+            float s, c;
+            sincospif(2.0f * (float)k / (float)nr, &s, &c);
+            tw[(ns - 1) / 7 + k] = make_float2(c, -s);
+        }
+    }
+}
+
+// rows per CTA pass: enough pairs to fill a 2048-point buffer
+__host__ __device__ inline int pairs_per_cta(int pn)
+{
+    return pn >= 2048 ? 1 : 2048 / pn;
+}
+
 template <typename TI, typename TO>
-__global__ void __launch_bounds__(kFilterThreads) filter_kernel(const TI *__restrict__ in, TO *__restrict__ out,
-                                                                const __grid_constant__ FilterParams p,
-                                                                const __grid_constant__ BetaTable bt,
-                                                                const float *__restrict__ customK)
+__global__ void __launch_bounds__(kFilterThreads) filter_stockham_kernel(const TI *__restrict__ in,
+                                                                         TO *__restrict__ out,
+                                                                         const __grid_constant__ FilterParams p,
+                                                                         const __grid_constant__ BetaTable bt,
+                                                                         const float *__restrict__ customK)
 {
     extern __shared__ float2 smem[];
     const int pn = p.pn, nu = p.nu;
-    float2 *z = smem;
-    float2 *tw = smem + pn;
-    float *Kb = reinterpret_cast<float *>(tw + pn / 2);  // K in bit-reversed order, pn entries
-    init_twiddles(tw, pn);
-    for (int t = threadIdx.x; t < pn; t += blockDim.x) {
-        const int m = bitrev(t, p.log2pn);
-        const int mm = m <= pn / 2 ? m : pn - m;
-        Kb[t] = customK ? customK[mm] : p.K[mm];
-    }
-    __syncthreads();
+    const int ppc = pairs_per_cta(pn);
+    const int stride = sp(pn);  // padded length of one transform
+    float2 *A = smem;
+    float2 *Bf = A + (size_t)ppc * stride;
+    float2 *tw = Bf + (size_t)ppc * stride;
+    float *Kh = reinterpret_cast<float *>(tw + twiddle_total(p.log2pn));  // K[0..pn/2] / pn
+    float *wrow = Kh + pn / 2 + 1;                                          // W_red of the current view, nu
+    int cached_view = -1;
+    init_stockham_twiddles(tw, p.log2pn);
     const float inv_pn = 1.0f / (float)pn;
+    for (int m = threadIdx.x; m <= pn / 2; m += blockDim.x) Kh[m] = (customK ? customK[m] : p.K[m]) * inv_pn;
+    __syncthreads();
+    // each CTA takes a contiguous run of pairs, so consecutive pairs share a view
     const long n_pairs = (p.n_rows + 1) / 2;
-    for (long pr = blockIdx.x; pr < n_pairs; pr += gridDim.x) {
-        const long r0 = 2 * pr, r1 = r0 + 1;
-        const bool has1 = r1 < p.n_rows;
-        int view0 = 0, l0 = 0, view1 = 0, l1 = 0;
-        if (p.apply_weights) {
-            view0 = (int)((r0 / p.rows_per_view) % p.n_views);
-            l0 = (int)(r0 % p.rows_per_view);
-            view1 = (int)((r1 / p.rows_per_view) % p.n_views);
-            l1 = (int)(r1 % p.rows_per_view);
+    const long per_cta = (n_pairs + gridDim.x - 1) / gridDim.x;
+    const long first = (long)blockIdx.x * per_cta, last = min(n_pairs, first + per_cta);
+    for (long pr0 = first; pr0 < last; pr0 += ppc) {
+        const int groups = (int)min((long)ppc, last - pr0);
+        if (p.apply_weights && p.w.redund == PYRO_REDUND_PARKER) {
+            // Parker weight depends on (view, u) only: one row per view, cached
+            const int view = (int)(((2 * pr0) / p.rows_per_view) % p.n_views);
+            const int view_end = (int)(((2 * (pr0 + groups) - 1) / p.rows_per_view) % p.n_views);
+            if (view == view_end && view != cached_view) {
+                for (int k = threadIdx.x; k < nu; k += blockDim.x) {
+                    const float u = ((float)k - p.w.cu) * p.w.su;
+                    wrow[k] = parker_weight(bt.beta[view], atanf(u / p.w.sdd), p.w.delta);
+                }
+                cached_view = view;
+                __syncthreads();
+            } else if (view != view_end) {
+                cached_view = -1;
+            }
         }
-        for (int n = threadIdx.x; n < pn; n += blockDim.x) {
+        // load: two weighted rows per complex sequence, zero-padded to pn
+        for (int e = threadIdx.x; e < groups * pn; e += blockDim.x) {
+            const int g = e / pn, n = e - g * pn;
+            const long r0 = 2 * (pr0 + g), r1 = r0 + 1;
             float a = 0.0f, c = 0.0f;
             if (n < nu) {
                 a = ld(in + r0 * nu + n);
+                const bool has1 = r1 < p.n_rows;
                 if (has1) c = ld(in + r1 * nu + n);
                 if (p.apply_weights) {
-                    a *= total_weight(p.w, bt, view0, l0, n);
-                    if (has1) c *= total_weight(p.w, bt, view1, l1, n);
+                    if (cached_view >= 0) {
+                        // W_cos (and the cached Parker row)
+                        const float u = ((float)n - p.w.cu) * p.w.su;
+                        const float v0 = ((float)(r0 % p.rows_per_view) - p.w.cv) * p.w.sv;
+                        const float v1 = ((float)(r1 % p.rows_per_view) - p.w.cv) * p.w.sv;
+                        const float wr = wrow[n];
+                        a *= wr * cosine_weight(p.w, u, v0);
+                        c *= wr * cosine_weight(p.w, u, v1);
+                    } else {
+                        a *= total_weight(p.w, bt, (int)((r0 / p.rows_per_view) % p.n_views),
+                                          (int)(r0 % p.rows_per_view), n);
+                        if (has1)
+                            c *= total_weight(p.w, bt, (int)((r1 / p.rows_per_view) % p.n_views),
+                                              (int)(r1 % p.rows_per_view), n);
+                    }
                 }
             }
-            z[n] = make_float2(a, c);
+            A[g * stride + sp(n)] = make_float2(a, c);
         }
         __syncthreads();
-        fft_dif(z, tw, pn, p.log2pn);
-        for (int t = threadIdx.x; t < pn; t += blockDim.x) {
-            const float k = Kb[t] * inv_pn;
-            z[t] = make_float2(z[t].x * k, z[t].y * k);
+        float2 *X = stockham_fft(A, Bf, tw, p.log2pn, pn, groups);
+        float2 *Y = X == A ? Bf : A;
+        // conj(K X): the inverse transform as conj(FFT(conj(.)))
+        for (int e = threadIdx.x; e < groups * pn; e += blockDim.x) {
+            const int g = e / pn, m = e - g * pn;
+            const float k = Kh[m <= pn / 2 ? m : pn - m];
+            const int q = g * stride + sp(m);
+            X[q] = make_float2(X[q].x * k, -X[q].y * k);
         }
         __syncthreads();
-        ifft_dit(z, tw, pn, p.log2pn);
-        for (int n = threadIdx.x; n < nu; n += blockDim.x) {
-            out[r0 * nu + n] = to_storage<TO>(z[n].x);
-            if (has1) out[r1 * nu + n] = to_storage<TO>(z[n].y);
+        float2 *Z = stockham_fft(X, Y, tw, p.log2pn, pn, groups);
+        for (int e = threadIdx.x; e < groups * nu; e += blockDim.x) {
+            const int g = e / nu, n = e - g * nu;
+            const long r0 = 2 * (pr0 + g), r1 = r0 + 1;
+            const float2 z = Z[g * stride + sp(n)];
+            out[r0 * nu + n] = to_storage<TO>(z.x);
+            if (r1 < p.n_rows) out[r1 * nu + n] = to_storage<TO>(-z.y);
         }
         __syncthreads();
     }
@@ -242,16 +394,20 @@ template <typename TI, typename TO>
 cudaError_t filter_dispatch(const void *in, void *out, const FilterParams &p, const BetaTable &bt,
                             const float *customK, cudaStream_t s)
 {
-    const size_t smem = sizeof(float2) * (size_t)p.pn * 3 / 2 + sizeof(float) * (size_t)p.pn;
-    cudaError_t e = cudaFuncSetAttribute(filter_kernel<TI, TO>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    const int ppc = pairs_per_cta(p.pn);
+    const size_t padded = (size_t)p.pn + (p.pn >> 3);
+    const size_t smem = sizeof(float2) * (2 * ppc * padded + twiddle_total(p.log2pn)) +
+                        sizeof(float) * ((size_t)(p.pn / 2 + 1) + p.nu);
+    auto kern = filter_stockham_kernel<TI, TO>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, filter_kernel<TI, TO>, kFilterThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kFilterThreads, smem);
     if (e != cudaSuccess) return e;
     const long pairs = (p.n_rows + 1) / 2;
-    const long grid = std::min<long>(pairs, (long)device_sm_count() * std::max(per_sm, 1));
-    filter_kernel<TI, TO><<<(unsigned)grid, kFilterThreads, smem, s>>>((const TI *)in, (TO *)out, p, bt, customK);
+    const long ctas = (pairs + ppc - 1) / ppc;
+    const long grid = std::min<long>(ctas, (long)device_sm_count() * std::max(per_sm, 1));
+    kern<<<(unsigned)grid, kFilterThreads, smem, s>>>((const TI *)in, (TO *)out, p, bt, customK);
     return cudaGetLastError();
 }
 
