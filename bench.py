@@ -278,7 +278,8 @@ def fp_sample_count(g) -> float:
                 t2 = (half - S[a]) / da
             lo = np.maximum(lo, np.where(da != 0, np.minimum(t1, t2), -np.inf))
             hi = np.minimum(hi, np.where(da != 0, np.maximum(t1, t2), np.inf))
-        total += np.sum(np.maximum(hi - lo, 0.0)) / (0.5 * SPACING)
+        # samples lie on depth planes dt apart: a chord of length c holds c / (dt |g|) samples, |g| = L / SDD
+        total += np.sum(np.maximum(hi - lo, 0.0) * SDD / L) / (0.5 * SPACING)
     return total * len(ang) / len(ang[:: max(1, len(ang) // 16)])
 
 

@@ -102,12 +102,14 @@ typedef struct {
 } pyro_geom3d;
 
 /* --- Ray-driven forward projection A (Section "The Operator as a Layer"). ---
- * One line integral per detector pixel: for the ray X(t) = a + t d (d unit,
- * a the bin position on e_u for parallel beam, the source otherwise),
- *   p = step * sum_{m=-M..M} f(a + (t_c + m step) d),
- * t_c = -a.d (closest approach to the iso-centre), M = ceil(T / step),
- * T = half diagonal of the box (N+1)*s; f the zero-extended interpolant.
- * vol [batch][...] -> sino [batch][...]. */
+ * One line integral per detector pixel.  The ray is X(w) = a + w g,
+ * parametrised by the depth w along the view's principal axis (g has unit
+ * depth; a is the bin position u e_u for parallel beam, the source
+ * otherwise), and sampled on equally spaced depth planes:
+ *   p = step |g| sum_{m=-M..M} f(a + (w0 + m step) g),
+ * w0 the depth of the iso-centre (0 for parallel beam, SID otherwise),
+ * M = ceil(T / step), T = half diagonal of the box (N+1)*s, f the
+ * zero-extended interpolant.  vol [batch][...] -> sino [batch][...]. */
 PYRO_API int pyro_fp_par2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dtype,
                            void *stream);
 PYRO_API int pyro_fp_fan2d(const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dtype,

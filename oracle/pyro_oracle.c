@@ -31,6 +31,8 @@
  *   interpolation: bi-/trilinear in index space over the ZERO-EXTENDED
  *           array (values outside [0, N-1] are 0), i.e. the border mode of
  *           a CUDA texture.
+ *   FP samples: on equally spaced planes of depth along the view's
+ *           principal axis (see the forward-projection section).
  */
 #include <math.h>
 #include <stdlib.h>
@@ -188,16 +190,11 @@ static void pmat_inverse(const double *P, double Minv[3][3], double S[3])
     for (int r = 0; r < 3; ++r) S[r] = -(Minv[r][0] * P[3] + Minv[r][1] * P[7] + Minv[r][2] * P[11]);
 }
 
-/* cone ray of detector pixel (k, l): source S and unit direction d */
-static void cone_ray(const double Minv[3][3], double k, double l, double d[3])
+/* cone ray of detector pixel (k, l) of a normalised P: g = M^-1 (k, l, 1), the
+ * direction with unit depth (P (S + w g, 1) = w (k, l, 1)) */
+static void cone_ray(const double Minv[3][3], double k, double l, double g[3])
 {
-    double n2 = 0.0;
-    for (int r = 0; r < 3; ++r) {
-        d[r] = Minv[r][0] * k + Minv[r][1] * l + Minv[r][2];
-        n2 += d[r] * d[r];
-    }
-    double n = sqrt(n2);
-    for (int r = 0; r < 3; ++r) d[r] /= n;
+    for (int r = 0; r < 3; ++r) g[r] = Minv[r][0] * k + Minv[r][1] * l + Minv[r][2];
 }
 
 /* Half diagonal of the interpolant's support box: (N+1)*s per axis. */
@@ -215,69 +212,72 @@ static double support_radius2(int nx, int ny, double sx, double sy)
 
 /* ------------------------------------------------------------------------ */
 /* Ray-driven forward projection (Section "The Operator as a Layer")        */
-/*   p = dt * sum_{m=-M..M} I(a + (t_c + m dt) d),  t_c = -a.d,             */
-/*   M = ceil(T / dt), T = half diagonal of the support box.                */
+/*   The ray of a detector pixel is X(w) = a + w g, parametrised by the     */
+/*   depth w along the view's principal axis (g has unit depth component).  */
+/*   Samples lie on equally spaced depth planes w_m = w0 + m dt, m = -M..M, */
+/*   w0 the depth of the iso-centre, M = ceil(T / dt), T the half diagonal  */
+/*   of the support box:  p = dt |g| sum_m f(a + w_m g)                     */
+/*   (a Riemann sum of the line integral with step dt |g| along the ray).   */
 /* ------------------------------------------------------------------------ */
 
 static double line_integral2(const double *img, int nx, int ny, double sx, double sy, double dt,
-                             const double a[2], const double d[2])
+                             const double a[2], const double g[2], double w0)
 {
     double T = support_radius2(nx, ny, sx, sy);
     long M = (long)ceil(T / dt);
-    double tc = -(a[0] * d[0] + a[1] * d[1]);
     double acc = 0.0;
     for (long m = -M; m <= M; ++m) {
-        double t = tc + (double)m * dt;
-        double X = a[0] + t * d[0], Y = a[1] + t * d[1];
+        double w = w0 + (double)m * dt;
+        double X = a[0] + w * g[0], Y = a[1] + w * g[1];
         acc += interp2(img, nx, ny, X / sx + 0.5 * (nx - 1), Y / sy + 0.5 * (ny - 1));
     }
-    return dt * acc;
+    return dt * sqrt(g[0] * g[0] + g[1] * g[1]) * acc;
 }
 
 static void line_scatter2(double *img, int nx, int ny, double sx, double sy, double dt,
-                          const double a[2], const double d[2], double val)
+                          const double a[2], const double g[2], double w0, double val)
 {
     double T = support_radius2(nx, ny, sx, sy);
     long M = (long)ceil(T / dt);
-    double tc = -(a[0] * d[0] + a[1] * d[1]);
+    double wt = dt * sqrt(g[0] * g[0] + g[1] * g[1]) * val;
     for (long m = -M; m <= M; ++m) {
-        double t = tc + (double)m * dt;
-        double X = a[0] + t * d[0], Y = a[1] + t * d[1];
-        scatter2(img, nx, ny, X / sx + 0.5 * (nx - 1), Y / sy + 0.5 * (ny - 1), dt * val);
+        double w = w0 + (double)m * dt;
+        double X = a[0] + w * g[0], Y = a[1] + w * g[1];
+        scatter2(img, nx, ny, X / sx + 0.5 * (nx - 1), Y / sy + 0.5 * (ny - 1), wt);
     }
 }
 
 static double line_integral3(const double *vol, int nx, int ny, int nz, double sx, double sy, double sz,
-                             double dt, const double a[3], const double d[3])
+                             double dt, const double a[3], const double g[3], double w0)
 {
     double T = support_radius3(nx, ny, nz, sx, sy, sz);
     long M = (long)ceil(T / dt);
-    double tc = -(a[0] * d[0] + a[1] * d[1] + a[2] * d[2]);
     double acc = 0.0;
     for (long m = -M; m <= M; ++m) {
-        double t = tc + (double)m * dt;
-        double X = a[0] + t * d[0], Y = a[1] + t * d[1], Z = a[2] + t * d[2];
+        double w = w0 + (double)m * dt;
+        double X = a[0] + w * g[0], Y = a[1] + w * g[1], Z = a[2] + w * g[2];
         acc += interp3(vol, nx, ny, nz, X / sx + 0.5 * (nx - 1), Y / sy + 0.5 * (ny - 1), Z / sz + 0.5 * (nz - 1));
     }
-    return dt * acc;
+    return dt * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) * acc;
 }
 
 static void line_scatter3(double *vol, int nx, int ny, int nz, double sx, double sy, double sz, double dt,
-                          const double a[3], const double d[3], double val)
+                          const double a[3], const double g[3], double w0, double val)
 {
     double T = support_radius3(nx, ny, nz, sx, sy, sz);
     long M = (long)ceil(T / dt);
-    double tc = -(a[0] * d[0] + a[1] * d[1] + a[2] * d[2]);
+    double wt = dt * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) * val;
     for (long m = -M; m <= M; ++m) {
-        double t = tc + (double)m * dt;
-        double X = a[0] + t * d[0], Y = a[1] + t * d[1], Z = a[2] + t * d[2];
-        scatter3(vol, nx, ny, nz, X / sx + 0.5 * (nx - 1), Y / sy + 0.5 * (ny - 1), Z / sz + 0.5 * (nz - 1),
-                 dt * val);
+        double w = w0 + (double)m * dt;
+        double X = a[0] + w * g[0], Y = a[1] + w * g[1], Z = a[2] + w * g[2];
+        scatter3(vol, nx, ny, nz, X / sx + 0.5 * (nx - 1), Y / sy + 0.5 * (ny - 1), Z / sz + 0.5 * (nz - 1), wt);
     }
 }
 
-/* ray of bin k of a 2D view: parallel (fan == 0) or fan beam */
-static void ray2d(int fan, double beta, double sid, double sdd, int nu, double su, int k, double a[2], double d[2])
+/* ray of bin k of a 2D view: parallel beam a = u e_u, g = c, w0 = 0;
+ * fan beam a = S = -SID c, g = c + (u / SDD) e_u (unit depth), w0 = SID */
+static void ray2d(int fan, double beta, double sid, double sdd, int nu, double su, int k, double a[2], double g[2],
+                  double *w0)
 {
     double c[2] = {cos(beta), sin(beta)};
     double eu[2] = {-sin(beta), cos(beta)};
@@ -285,15 +285,15 @@ static void ray2d(int fan, double beta, double sid, double sdd, int nu, double s
     if (!fan) {
         a[0] = u * eu[0];
         a[1] = u * eu[1];
-        d[0] = c[0];
-        d[1] = c[1];
+        g[0] = c[0];
+        g[1] = c[1];
+        *w0 = 0.0;
     } else {
         a[0] = -sid * c[0];
         a[1] = -sid * c[1];
-        double g0 = sdd * c[0] + u * eu[0], g1 = sdd * c[1] + u * eu[1];
-        double n = sqrt(g0 * g0 + g1 * g1);
-        d[0] = g0 / n;
-        d[1] = g1 / n;
+        g[0] = c[0] + (u / sdd) * eu[0];
+        g[1] = c[1] + (u / sdd) * eu[1];
+        *w0 = sid;
     }
 }
 
@@ -303,9 +303,9 @@ static void fp2d(int fan, const double *img, int nx, int ny, double sx, double s
 #pragma omp parallel for schedule(dynamic, 1)
     for (int j = 0; j < n_views; ++j)
         for (int k = 0; k < nu; ++k) {
-            double a[2], d[2];
-            ray2d(fan, angles[j], sid, sdd, nu, su, k, a, d);
-            sino[IDX2(j, k, nu)] = line_integral2(img, nx, ny, sx, sy, dt, a, d);
+            double a[2], g[2], w0;
+            ray2d(fan, angles[j], sid, sdd, nu, su, k, a, g, &w0);
+            sino[IDX2(j, k, nu)] = line_integral2(img, nx, ny, sx, sy, dt, a, g, w0);
         }
 }
 
@@ -315,9 +315,9 @@ static void fp2d_adjoint(int fan, const double *sino, int nx, int ny, double sx,
     memset(img, 0, sizeof(double) * (size_t)nx * ny);
     for (int j = 0; j < n_views; ++j)
         for (int k = 0; k < nu; ++k) {
-            double a[2], d[2];
-            ray2d(fan, angles[j], sid, sdd, nu, su, k, a, d);
-            line_scatter2(img, nx, ny, sx, sy, dt, a, d, sino[IDX2(j, k, nu)]);
+            double a[2], g[2], w0;
+            ray2d(fan, angles[j], sid, sdd, nu, su, k, a, g, &w0);
+            line_scatter2(img, nx, ny, sx, sy, dt, a, g, w0, sino[IDX2(j, k, nu)]);
         }
 }
 
@@ -350,13 +350,14 @@ void oracle_fp_cone3d(const double *vol, int nx, int ny, int nz, double sx, doub
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int j = 0; j < n_views; ++j) {
-        double Minv[3][3], S[3];
-        pmat_inverse(pmats + 12 * (size_t)j, Minv, S);
+        double Pn[12], Minv[3][3], S[3];
+        normalise_pmat(pmats + 12 * (size_t)j, Pn);
+        pmat_inverse(Pn, Minv, S);
         for (int l = 0; l < nv; ++l)
             for (int k = 0; k < nu; ++k) {
-                double d[3];
-                cone_ray(Minv, (double)k, (double)l, d);
-                sino[IDX3(j, l, k, nv, nu)] = line_integral3(vol, nx, ny, nz, sx, sy, sz, dt, S, d);
+                double g[3];
+                cone_ray(Minv, (double)k, (double)l, g);
+                sino[IDX3(j, l, k, nv, nu)] = line_integral3(vol, nx, ny, nz, sx, sy, sz, dt, S, g, Pn[11]);
             }
     }
 }
@@ -368,10 +369,11 @@ void oracle_fp_cone3d_rays(const double *vol, int nx, int ny, int nz, double sx,
 {
 #pragma omp parallel for schedule(dynamic, 1)
     for (int r = 0; r < n_rays; ++r) {
-        double Minv[3][3], S[3], d[3];
-        pmat_inverse(pmats + 12 * (size_t)view[r], Minv, S);
-        cone_ray(Minv, (double)kk[r], (double)ll[r], d);
-        out[r] = line_integral3(vol, nx, ny, nz, sx, sy, sz, dt, S, d);
+        double Pn[12], Minv[3][3], S[3], g[3];
+        normalise_pmat(pmats + 12 * (size_t)view[r], Pn);
+        pmat_inverse(Pn, Minv, S);
+        cone_ray(Minv, (double)kk[r], (double)ll[r], g);
+        out[r] = line_integral3(vol, nx, ny, nz, sx, sy, sz, dt, S, g, Pn[11]);
     }
 }
 
@@ -380,13 +382,14 @@ void oracle_fpT_cone3d(const double *sino, int nx, int ny, int nz, double sx, do
 {
     memset(vol, 0, sizeof(double) * (size_t)nx * ny * nz);
     for (int j = 0; j < n_views; ++j) {
-        double Minv[3][3], S[3];
-        pmat_inverse(pmats + 12 * (size_t)j, Minv, S);
+        double Pn[12], Minv[3][3], S[3];
+        normalise_pmat(pmats + 12 * (size_t)j, Pn);
+        pmat_inverse(Pn, Minv, S);
         for (int l = 0; l < nv; ++l)
             for (int k = 0; k < nu; ++k) {
-                double d[3];
-                cone_ray(Minv, (double)k, (double)l, d);
-                line_scatter3(vol, nx, ny, nz, sx, sy, sz, dt, S, d, sino[IDX3(j, l, k, nv, nu)]);
+                double g[3];
+                cone_ray(Minv, (double)k, (double)l, g);
+                line_scatter3(vol, nx, ny, nz, sx, sy, sz, dt, S, g, Pn[11], sino[IDX3(j, l, k, nv, nu)]);
             }
     }
 }

@@ -200,6 +200,12 @@ def pyro_fp_cone3d(vol: torch.Tensor, g: ConeGeometry3D) -> torch.Tensor:
     return _fp(lib().pyro_fp_cone3d, vol, g, g.volume_shape, g.sinogram_shape)
 
 
+def fp_cone3d_workspace_bytes(g: ConeGeometry3D, dtype=torch.float32) -> int:
+    """Workspace pyro_fp_cone3d_ws needs for one volume of `dtype`."""
+    cg = g.to_c()
+    return int(lib().pyro_fp_cone3d_workspace_bytes(ctypes.byref(cg), _DTYPES[dtype]))
+
+
 def pyro_fp_cone3d_ws(vol: torch.Tensor, g: ConeGeometry3D, workspace: Optional[torch.Tensor] = None,
                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
     """Cone-beam FP from a z-major copy of the volume kept in `workspace`

@@ -3,11 +3,15 @@
 // casts its ray and accumulates interpolated samples; the cone-beam rays
 // come from projection matrices, after Galigekere et al.).
 //
-// Every ray is sampled at t_c + m * dt, m = -M..M, t_c the closest approach
-// of the line to the iso-centre; only the m whose sample can touch the
-// support (-1, N) of the zero-extended interpolant are visited (the others
-// contribute exactly zero).  Arithmetic is FP32, accumulation along the ray
-// is FP32; storage is FP32, FP16 or BF16.
+// Every ray X(w) = a + w g (g with unit depth along the view's principal
+// axis) is sampled on the depth planes w_m = w0 + m dt, m = -M..M, w0 the
+// depth of the iso-centre, and p = dt |g| sum_m f(X(w_m)).  Only the m whose
+// sample can touch the support (-1, N) of the zero-extended interpolant are
+// visited (the others contribute exactly zero).  Rays of one detector column
+// lie in one plane through the source, so on a given depth plane they share
+// their (x, y) point: the warps below put consecutive detector rows on
+// consecutive lanes.  Arithmetic and accumulation are FP32; storage is FP32,
+// FP16 or BF16.
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -17,34 +21,37 @@ namespace {
 
 // ---- 2D ray set-up: sample position p0 + m q in pixel-index units --------
 struct Ray2 {
-    float px, py, qx, qy;
+    float px, py, qx, qy, w;  // sample m at (px + m qx, py + m qy); weight w = dt |g|
 };
 
+// parallel beam: a = u e_u, g = c, w0 = 0; fan beam: g = c + (u / SDD) e_u and
+// the sample on the iso-centre's depth plane is a + SID g = (SID u / SDD) e_u
 __device__ __forceinline__ Ray2 ray2d(const FP2DParams &p, int v, int k)
 {
     const float2 c = p.dir[v];
     const float u = ((float)k - p.cu) * p.su;
-    float bx, by, dx, dy;
+    float bx, by, gx, gy, w;
     if (p.fan) {
-        const float L2 = fmaf(p.sdd, p.sdd, u * u);
-        const float f = p.sid * u / L2;
-        // e_u = (-c.y, c.x); B = f (SDD e_u - u c)
-        bx = f * fmaf(-p.sdd, c.y, -u * c.x);
-        by = f * fmaf(p.sdd, c.x, -u * c.y);
-        const float rL = 1.0f / sqrtf(L2);
-        dx = fmaf(p.sdd, c.x, -u * c.y) * rL;
-        dy = fmaf(p.sdd, c.y, u * c.x) * rL;
+        const float t = u / p.sdd;
+        const float f = p.sid * t;
+        bx = -f * c.y;  // e_u = (-c.y, c.x)
+        by = f * c.x;
+        gx = fmaf(-t, c.y, c.x);
+        gy = fmaf(t, c.x, c.y);
+        w = p.dt * sqrtf(fmaf(t, t, 1.0f));
     } else {
         bx = -u * c.y;
         by = u * c.x;
-        dx = c.x;
-        dy = c.y;
+        gx = c.x;
+        gy = c.y;
+        w = p.dt;
     }
     Ray2 r;
     r.px = fmaf(bx, p.inv_sx, p.cx);
     r.py = fmaf(by, p.inv_sy, p.cy);
-    r.qx = dx * p.dt * p.inv_sx;
-    r.qy = dy * p.dt * p.inv_sy;
+    r.qx = gx * p.dt * p.inv_sx;
+    r.qy = gy * p.dt * p.inv_sy;
+    r.w = w;
     return r;
 }
 
@@ -74,7 +81,7 @@ __global__ void __launch_bounds__(128) fp2d_kernel(const T *__restrict__ vol, T 
         const float fm = (float)m;
         acc += bilerp_zero(img, p.nx, p.ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
     }
-    sino[((size_t)b * p.views_total + p.view0 + v) * p.nu + k] = to_storage<T>(p.dt * acc);
+    sino[((size_t)b * p.views_total + p.view0 + v) * p.nu + k] = to_storage<T>(r.w * acc);
 }
 
 __global__ void __launch_bounds__(128) fp2d_adjoint_kernel(const float *__restrict__ sino, float *__restrict__ vol,
@@ -84,9 +91,10 @@ __global__ void __launch_bounds__(128) fp2d_adjoint_kernel(const float *__restri
     const int v = blockIdx.y;
     const int b = blockIdx.z;
     if (k >= p.nu) return;
-    const float y = p.dt * sino[((size_t)b * p.views_total + p.view0 + v) * p.nu + k];
-    if (y == 0.0f) return;
+    const float y0s = sino[((size_t)b * p.views_total + p.view0 + v) * p.nu + k];
+    if (y0s == 0.0f) return;
     const Ray2 r = ray2d(p, v, k);
+    const float y = r.w * y0s;
     int m0, m1;
     range2d(r, p, m0, m1);
     float *img = vol + (size_t)b * p.nx * p.ny;
@@ -106,34 +114,29 @@ __global__ void __launch_bounds__(128) fp2d_adjoint_kernel(const float *__restri
 
 // ---- 3D cone ray set-up --------------------------------------------------
 struct Ray3 {
-    float px, py, pz, qx, qy, qz;
+    float px, py, pz, qx, qy, qz, w;  // sample m at p + m q (voxel-index units); weight w = dt |g|
 };
 
+// In camera coordinates the ray of pixel (k, l) is S + w q, q = K^-1 (k, l, 1)
+// = (q_x, q_y, 1) (unit depth).  Its sample on the iso-centre's depth plane
+// (w0 = -s3) is (s1 - s3 q_x, s2 - s3 q_y, 0): no FP32 cancellation.
 __device__ __forceinline__ Ray3 ray3d(const FP3DParams &p, int v, int k, int l)
 {
     const ConeFPView &V = p.v[v];
     const float fk = (float)k, fl = (float)l;
     const float qx = fmaf(V.a0, fk, fmaf(V.a1, fl, V.a2));
     const float qy = fmaf(V.b0, fl, V.b2);
-    const float q2 = fmaf(qx, qx, qy * qy);
-    const float n2 = q2 + 1.0f;
-    const float rn2 = 1.0f / n2;
-    const float sq = fmaf(V.s1, qx, V.s2 * qy);  // s_perp . q
-    const float g = (sq + V.s3) * rn2;
-    // closest approach in camera coordinates
-    const float c0 = fmaf(-g, qx, V.s1);
-    const float c1 = fmaf(-g, qy, V.s2);
-    const float c2 = fmaf(V.s3, q2, -sq) * rn2;
-    const float rn = 1.0f / sqrtf(n2);
+    const float c0 = fmaf(-V.s3, qx, V.s1);
+    const float c1 = fmaf(-V.s3, qy, V.s2);
     const float *W = V.W;
     Ray3 r;
-    r.px = fmaf(W[0], c0, fmaf(W[1], c1, fmaf(W[2], c2, p.cx)));
-    r.py = fmaf(W[3], c0, fmaf(W[4], c1, fmaf(W[5], c2, p.cy)));
-    r.pz = fmaf(W[6], c0, fmaf(W[7], c1, fmaf(W[8], c2, p.cz)));
-    const float s = p.dt * rn;
-    r.qx = s * fmaf(W[0], qx, fmaf(W[1], qy, W[2]));
-    r.qy = s * fmaf(W[3], qx, fmaf(W[4], qy, W[5]));
-    r.qz = s * fmaf(W[6], qx, fmaf(W[7], qy, W[8]));
+    r.px = fmaf(W[0], c0, fmaf(W[1], c1, p.cx));
+    r.py = fmaf(W[3], c0, fmaf(W[4], c1, p.cy));
+    r.pz = fmaf(W[6], c0, fmaf(W[7], c1, p.cz));
+    r.qx = p.dt * fmaf(W[0], qx, fmaf(W[1], qy, W[2]));
+    r.qy = p.dt * fmaf(W[3], qx, fmaf(W[4], qy, W[5]));
+    r.qz = p.dt * fmaf(W[6], qx, fmaf(W[7], qy, W[8]));
+    r.w = p.dt * sqrtf(fmaf(qx, qx, fmaf(qy, qy, 1.0f)));
     return r;
 }
 
@@ -199,7 +202,7 @@ __global__ void __launch_bounds__(kFP3DBlockX *kFP3DBlockY) fp3d_kernel(const T 
     range3d(r, p, m0, m1);
     const T *V = vol + (size_t)b * p.nx * p.ny * p.nz;
     const float acc = march3d(V, p, 1, p.nx, p.nx * p.ny, r, m0, m1);
-    sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(p.dt * acc);
+    sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(r.w * acc);
 }
 
 // Staged forward projection: the volume has been re-laid out z-fastest
@@ -222,8 +225,57 @@ __global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const
     const Ray3 r = ray3d(p, v, k, l);
     int m0, m1;
     range3d(r, p, m0, m1);
-    const float acc = march3d(vz, p, p.nz, p.nz * p.nx, 1, r, m0, m1);
-    sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(p.dt * acc);
+    // samples strictly inside the volume take the unmasked path; the rest the zero-extended one
+    float lo = (float)m0, hi = (float)m1;
+    clip_axis_interior(r.px, r.qx, p.nx, lo, hi);
+    clip_axis_interior(r.py, r.qy, p.ny, lo, hi);
+    clip_axis_interior(r.pz, r.qz, p.nz, lo, hi);
+    int i0 = max(m0, (int)ceilf(lo)), i1 = min(m1, (int)floorf(hi));
+    if (i0 > i1) {
+        i0 = m1 + 1;
+        i1 = m1;
+    }
+    const size_t sx = (size_t)p.nz, sy = (size_t)p.nz * p.nx;
+    float acc = 0.0f;
+    for (int m = m0; m < i0; ++m) {
+        const float fm = (float)m;
+        acc += trilerp_zero_strided(vz, p.nx, p.ny, p.nz, sx, sy, (size_t)1, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py),
+                                    fmaf(fm, r.qz, r.pz));
+    }
+    // interior: consecutive samples are half a voxel apart and the warp's rays
+    // (consecutive detector rows) sit at one (x, y) point on every depth plane,
+    // so the 8 taps of the current cell stay in registers until the cell changes
+    const int stx = p.nz, sty = p.nz * p.nx;
+    int cur = -1;
+    float c000 = 0.f, c001 = 0.f, c010 = 0.f, c011 = 0.f, c100 = 0.f, c101 = 0.f, c110 = 0.f, c111 = 0.f;
+    for (int m = i0; m <= i1; ++m) {
+        const float fm = (float)m;
+        const float fx = fmaf(fm, r.qx, r.px), fy = fmaf(fm, r.qy, r.py), fz = fmaf(fm, r.qz, r.pz);
+        const float x0 = floorf(fx), y0 = floorf(fy), z0 = floorf(fz);
+        const int cell = (int)x0 * stx + (int)y0 * sty + (int)z0;
+        if (cell != cur) {
+            const T *q = vz + cell;
+            c000 = ld(q);
+            c001 = ld(q + 1);
+            c010 = ld(q + sty);
+            c011 = ld(q + sty + 1);
+            c100 = ld(q + stx);
+            c101 = ld(q + stx + 1);
+            c110 = ld(q + stx + sty);
+            c111 = ld(q + stx + sty + 1);
+            cur = cell;
+        }
+        const float ax = fx - x0, ay = fy - y0, az = fz - z0;
+        const float v00 = lerpf(c000, c001, az), v01 = lerpf(c010, c011, az);
+        const float v10 = lerpf(c100, c101, az), v11 = lerpf(c110, c111, az);
+        acc += lerpf(lerpf(v00, v01, ay), lerpf(v10, v11, ay), ax);
+    }
+    for (int m = max(i1 + 1, i0); m <= m1; ++m) {
+        const float fm = (float)m;
+        acc += trilerp_zero_strided(vz, p.nx, p.ny, p.nz, sx, sy, (size_t)1, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py),
+                                    fmaf(fm, r.qz, r.pz));
+    }
+    sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(r.w * acc);
 }
 
 // [z][y][x] -> [y][x][z]: 32 x 32 tiles of one y-plane through shared memory
@@ -253,9 +305,10 @@ __global__ void __launch_bounds__(kFP3DBlockX *kFP3DBlockY) fp3d_adjoint_kernel(
     const int v = blockIdx.z % p.n_views;
     const int b = blockIdx.z / p.n_views;
     if (k >= p.nu || l >= p.nv) return;
-    const float y = p.dt * sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k];
-    if (y == 0.0f) return;
+    const float y0s = sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k];
+    if (y0s == 0.0f) return;
     const Ray3 r = ray3d(p, v, k, l);
+    const float y = r.w * y0s;
     int m0, m1;
     range3d(r, p, m0, m1);
     float *V = vol + (size_t)b * p.nx * p.ny * p.nz;

@@ -37,7 +37,7 @@ def _ops(g):
 
         def A(x, out=None):
             if "w" not in ws:
-                ws["w"] = torch.empty(x.numel() * 4, dtype=torch.uint8, device=x.device)
+                ws["w"] = torch.empty(B.fp_cone3d_workspace_bytes(g, x.dtype), dtype=torch.uint8, device=x.device)
             return B.pyro_fp_cone3d_ws(x, g, workspace=ws["w"], out=out)
 
         return A, lambda y: B.pyro_fpT_cone3d(y, g)

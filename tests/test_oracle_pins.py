@@ -95,27 +95,39 @@ def _tent(f, n):
     return np.maximum(0.0, 1.0 - np.abs(f[:, None] - np.arange(n)[None, :]))
 
 
-def _brute_line2(img, s, dt, a, d):
+def _depth_param(a, d, parallel):
+    """Ray written as X(w) = a + w g with unit depth along the view's
+    principal axis c: parallel beam c = d, w0 = 0; fan / cone c points from
+    the source a to the iso-centre, w0 = |a| (the iso-centre's depth)."""
+    if parallel:
+        return d, 0.0
+    c = -a / np.linalg.norm(a)
+    return d / (d @ c), float(np.linalg.norm(a))
+
+
+def _brute_line2(img, s, dt, a, d, parallel):
     ny, nx = img.shape
     T = 0.5 * np.hypot((nx + 1) * s[1], (ny + 1) * s[0])
     M = int(np.ceil(T / dt))
-    t = -(a @ d) + np.arange(-M, M + 1) * dt
-    X = a[None, :] + t[:, None] * d[None, :]
+    g, w0 = _depth_param(a, d, parallel)
+    w = w0 + np.arange(-M, M + 1) * dt
+    X = a[None, :] + w[:, None] * g[None, :]
     hx = _tent(X[:, 0] / s[1] + 0.5 * (nx - 1), nx)
     hy = _tent(X[:, 1] / s[0] + 0.5 * (ny - 1), ny)
-    return dt * np.einsum("mj,ji,mi->", hy, img, hx)
+    return dt * np.linalg.norm(g) * np.einsum("mj,ji,mi->", hy, img, hx)
 
 
 def _brute_line3(vol, s, dt, a, d):
     nz, ny, nx = vol.shape
     T = 0.5 * np.sqrt(((nx + 1) * s[2]) ** 2 + ((ny + 1) * s[1]) ** 2 + ((nz + 1) * s[0]) ** 2)
     M = int(np.ceil(T / dt))
-    t = -(a @ d) + np.arange(-M, M + 1) * dt
-    X = a[None, :] + t[:, None] * d[None, :]
+    g, w0 = _depth_param(a, d, False)
+    w = w0 + np.arange(-M, M + 1) * dt
+    X = a[None, :] + w[:, None] * g[None, :]
     hx = _tent(X[:, 0] / s[2] + 0.5 * (nx - 1), nx)
     hy = _tent(X[:, 1] / s[1] + 0.5 * (ny - 1), ny)
     hz = _tent(X[:, 2] / s[0] + 0.5 * (nz - 1), nz)
-    return dt * np.einsum("mk,mj,mi,kji->", hz, hy, hx, vol)
+    return dt * np.linalg.norm(g) * np.einsum("mk,mj,mi,kji->", hz, hy, hx, vol)
 
 
 def test_fp_bruteforce_tent_basis_2d():
@@ -127,10 +139,10 @@ def test_fp_bruteforce_tent_basis_2d():
     par = oracle.fp_par2d(img, s, 9, 1.3, ang, step=dt)
     fan = oracle.fp_fan2d(img, s, 9, 1.3, ang, 40.0, 70.0, step=dt)
     a, d = an.parallel_rays(ang, 9, 1.3)
-    ref = np.array([_brute_line2(img, s, dt, a[r], d[r]) for r in range(a.shape[0])]).reshape(5, 9)
+    ref = np.array([_brute_line2(img, s, dt, a[r], d[r], True) for r in range(a.shape[0])]).reshape(5, 9)
     assert np.max(np.abs(par - ref)) < 1e-12 * np.max(np.abs(ref))
     a, d = an.fan_rays(ang, 9, 1.3, 40.0, 70.0)
-    ref = np.array([_brute_line2(img, s, dt, a[r], d[r]) for r in range(a.shape[0])]).reshape(5, 9)
+    ref = np.array([_brute_line2(img, s, dt, a[r], d[r], False) for r in range(a.shape[0])]).reshape(5, 9)
     assert np.max(np.abs(fan - ref)) < 1e-12 * np.max(np.abs(ref))
 
 
