@@ -221,6 +221,7 @@ def run_gpu(args):
     peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = samples * FLOPS_PER_SAMPLE / (fp_avg_ms * 1e-3) / 1e12
     clocks = clk.summary()
+    traffic = fp_traffic_per_launch()
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -230,7 +231,7 @@ def run_gpu(args):
         "gpu_launches": 4 * K,
         "roofline": {"kernel": "fp3d_zmajor_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
-                     "traffic": None,
+                     "traffic": traffic,
                      "note": f"{samples:.4g} samples x {FLOPS_PER_SAMPLE} flop; peak = {props.multi_processor_count}"
                              f" SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
         "breakdown_ms": {"fp": round(fp_avg_ms, 4), "fdk": round(statistics.mean(fdk_ms), 4),
@@ -248,6 +249,22 @@ def run_gpu(args):
 
 
 FLOPS_PER_SAMPLE = 28  # 3 position FMA (6) + 7 lerps (3 each) + 1 accumulate
+
+
+def fp_traffic_per_launch():
+    """DRAM bytes (read + write) of one forward-projection launch from the
+    committed ncu summary, or None when the kernel source changed since."""
+    import hashlib
+
+    rec = os.path.join(ROOT, "profiles", "roofline_traffic.json")
+    src = os.path.join(ROOT, "paper_1904_13342_gb300", "csrc", "kernels_fp.cu")
+    try:
+        info = json.load(open(rec))
+        if hashlib.sha256(open(src, "rb").read()).hexdigest() != info.get("source_sha256"):
+            return None
+        return int(info["dram_bytes_per_launch"])
+    except (OSError, ValueError, KeyError):
+        return None
 
 
 def fp_sample_count(g) -> float:
@@ -295,13 +312,13 @@ def cpu_sample(seconds: float):
     vol = ph.voxelize_ellipsoids(e, g.volume_shape, g.volume_spacing, dtype=torch.float64).numpy()
     ang = g.view_angles()
     P = oracle.circular_pmats(ang, SID, SDD, (NV, NU), (SV, SU))
-    fv = 4
+    fv = 12
     t0 = time.perf_counter()
     sino1 = oracle.fp_cone3d(vol, g.volume_spacing, (NV, NU), P[:fv])
     t_fp = time.perf_counter() - t0
     # FDK of a slab: a smooth synthetic sinogram stands in for the projections
     y = ph.random_sinogram((VIEWS, NV, NU), 1, smooth=2)
-    zs = 6
+    zs = 18
     kz = np.repeat(np.arange(N // 2 - zs // 2, N // 2 - zs // 2 + zs), N * N)
     jj = np.tile(np.repeat(np.arange(N), N), zs)
     ii = np.tile(np.arange(N), N * zs)
