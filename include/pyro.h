@@ -235,6 +235,54 @@ PYRO_API int pyro_axpby(const float *x, float *y, long n, float a, float b, void
  * reduced in FP32 (block sums, then FP32 atomics) */
 PYRO_API int pyro_dot(const float *a, const float *b, long n, float *out, void *stream);
 
+/* --- Residual 3D CNN used as a learned initialiser of the iterative
+ * reconstruction.  The paper has no network of its own; its "learned parts"
+ * outlook (Section "Network Architectures") is met by this small BF16
+ * network trained with the library's operators.  Activations are
+ * channels-last BF16 [batch][nz][ny][nx][c]; weights are BF16
+ * [27][cout][cin] (tap = (dz*3+dy)*3+dx of a 3x3x3 window, stride 1, zero
+ * padding 1); bias, gradients of weights and biases are FP32.  Supported
+ * (cin, cout): both in {16, 32, 64} (tensor cores, mma.sync bf16 -> fp32),
+ * or (1, 16) / (16, 1) (CUDA cores).  The tensor-core shapes work on
+ * blocks of 128 voxels TX x TY x TZ with TX = min(nx, 64),
+ * TY = min(ny, 128 / TX), TZ = 128 / (TX TY): nx must be 8, 16, 32 or a
+ * multiple of 64, and ny, nz must be multiples of TY, TZ.
+ * pyro_conv3d:        y = [relu](conv(x, w) + bias), bias may be NULL.
+ * pyro_conv3d_wgrad:  dw[tap][co][ci] = sum_v dy[v][co] x[v + tap][ci]
+ *                     (overwritten; FP32 atomics across blocks).
+ * pyro_conv3d_flip_weights: wf[t][ci][co] = w[26 - t][co][ci], the weights
+ *                     of the data gradient dx = conv(dy, wf) (cin <-> cout). */
+PYRO_API int pyro_conv3d(const void *x, const void *w, const float *bias, void *y, int batch, int nz, int ny, int nx,
+                         int cin, int cout, int relu, void *stream);
+PYRO_API int pyro_conv3d_wgrad(const void *x, const void *dy, float *dw, int batch, int nz, int ny, int nx, int cin,
+                               int cout, void *stream);
+PYRO_API int pyro_conv3d_flip_weights(const void *w, void *wf, int cin, int cout, void *stream);
+
+/* elementwise steps of the network; n = number of elements WRITTEN to y.
+ * (nz, ny, nx) are the full-resolution dims for AVGPOOL2 and AVGPOOL2_BWD,
+ * and the half-resolution dims for UPSAMPLE2 and UPSAMPLE2_BWD. */
+typedef enum {
+    PYRO_CNN_RELU_BWD = 0,     /* y(bf16 grad, in place) *= (a(bf16 activation) > 0)      */
+    PYRO_CNN_AVGPOOL2 = 1,     /* y = 2x2x2 mean of a                                     */
+    PYRO_CNN_AVGPOOL2_BWD = 2, /* y = a(upper level) / 8 spread over the 8 children       */
+    PYRO_CNN_UPSAMPLE2 = 3,    /* y = nearest 2x upsampling of a, plus b (skip) if b != 0 */
+    PYRO_CNN_UPSAMPLE2_BWD = 4,/* y = sum of a over the 8 children                        */
+    PYRO_CNN_ADD = 5,          /* y = a + b (bf16)                                        */
+    PYRO_CNN_F32_TO_BF16 = 6,  /* y(bf16) = a(f32)                                        */
+    PYRO_CNN_BF16_TO_F32 = 7,  /* y(f32) = a(bf16)                                        */
+    PYRO_CNN_RESIDUAL = 8      /* y(f32) = f(f32) + a(bf16)                               */
+} pyro_cnn_op_kind;
+PYRO_API int pyro_cnn_op(int op, const void *a, const void *b, void *y, const float *f, long n, int nz, int ny, int nx,
+                         int c, void *stream);
+/* db[c] = sum over nvox voxels of dy[v][c] (dy bf16 channels-last, db FP32, overwritten) */
+PYRO_API int pyro_cnn_bias_grad(const void *dy, float *db, long nvox, int c, void *stream);
+/* loss[0] = mean (out - target)^2 (FP32, device); grad (bf16, may be NULL) = 2 (out - target) / n */
+PYRO_API int pyro_cnn_mse(const float *out, const float *target, void *grad, float *loss, long n, void *stream);
+/* Adam step on FP32 master parameters p with gradient g and moments m, v
+ * (step counts from 1); p16 (may be NULL) receives the bf16 copy of p. */
+PYRO_API int pyro_cnn_adam(float *p, const float *g, float *m, float *v, void *p16, long n, float lr, float beta1,
+                           float beta2, float eps, int step, void *stream);
+
 /* --- FDK without any device allocation by the caller.  The paper has no
  * counterpart: this serves callers that only hold the input and output
  * buffers and cannot allocate device memory (e.g. a reconstruction stage

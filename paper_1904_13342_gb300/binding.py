@@ -73,6 +73,13 @@ _SIGS = {
     "pyro_fbp_fan2d": [_VP, _VP, _I, _G2, _I, _VP, _I, _VP, _SZ, _I, _VP],
     "pyro_fdk_noalloc": [_VP, _VP, _I, _G3, _I, _VP, _I, _I, _VP],
     "pyro_tv": [_VP, _VP, _VP, _F, _F, _VP, _I, _I, _I, _I, _F, _VP],
+    "pyro_conv3d": [_VP, _VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _I, _VP],
+    "pyro_conv3d_wgrad": [_VP, _VP, _VP, _I, _I, _I, _I, _I, _I, _VP],
+    "pyro_conv3d_flip_weights": [_VP, _VP, _I, _I, _VP],
+    "pyro_cnn_op": [_I, _VP, _VP, _VP, _VP, _L, _I, _I, _I, _I, _VP],
+    "pyro_cnn_bias_grad": [_VP, _VP, _L, _I, _VP],
+    "pyro_cnn_mse": [_VP, _VP, _VP, _VP, _L, _VP],
+    "pyro_cnn_adam": [_VP, _VP, _VP, _VP, _VP, _L, _F, _F, _F, _F, _I, _VP],
     "pyro_axpby": [_VP, _VP, _L, _F, _F, _VP],
     "pyro_dot": [_VP, _VP, _L, _VP, _VP],
     "pyro_last_error": [],
@@ -430,6 +437,86 @@ def pyro_dot(a: torch.Tensor, b: torch.Tensor, out: Optional[torch.Tensor] = Non
     with torch.cuda.device(a.device):
         _check(lib().pyro_dot(_ptr(a), _ptr(b), a.numel(), _ptr(o), _stream(a)))
     return o
+
+
+# ------------------------------------------------------------ residual CNN --
+CNN_RELU_BWD, CNN_AVGPOOL2, CNN_AVGPOOL2_BWD, CNN_UPSAMPLE2, CNN_UPSAMPLE2_BWD, CNN_ADD = 0, 1, 2, 3, 4, 5
+CNN_F32_TO_BF16, CNN_BF16_TO_F32, CNN_RESIDUAL = 6, 7, 8
+
+
+def _cuda(t, name, dtype):
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous() or t.dtype != dtype:
+        raise TypeError(f"{name} must be a contiguous CUDA {dtype} tensor")
+    return t
+
+
+def pyro_conv3d(x: torch.Tensor, w: torch.Tensor, bias: Optional[torch.Tensor], relu: bool,
+                out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """x [B, D, H, W, cin] bf16, w [27, cout, cin] bf16, bias [cout] f32 -> [B, D, H, W, cout] bf16."""
+    _cuda(x, "x", torch.bfloat16)
+    _cuda(w, "w", torch.bfloat16)
+    B_, D, H, W, cin = x.shape
+    cout = w.shape[1]
+    if w.shape != (27, cout, cin):
+        raise ValueError("w must be [27, cout, cin]")
+    if bias is not None:
+        _cuda(bias, "bias", torch.float32)
+    y = torch.empty((B_, D, H, W, cout), device=x.device, dtype=torch.bfloat16) if out is None else out
+    with torch.cuda.device(x.device):
+        _check(lib().pyro_conv3d(_ptr(x), _ptr(w), _ptr(bias), _ptr(y), B_, D, H, W, cin, cout, int(relu), _stream(x)))
+    return y
+
+
+def pyro_conv3d_wgrad(x: torch.Tensor, dy: torch.Tensor) -> torch.Tensor:
+    _cuda(x, "x", torch.bfloat16)
+    _cuda(dy, "dy", torch.bfloat16)
+    B_, D, H, W, cin = x.shape
+    cout = dy.shape[-1]
+    dw = torch.empty((27, cout, cin), device=x.device, dtype=torch.float32)
+    with torch.cuda.device(x.device):
+        _check(lib().pyro_conv3d_wgrad(_ptr(x), _ptr(dy), _ptr(dw), B_, D, H, W, cin, cout, _stream(x)))
+    return dw
+
+
+def pyro_conv3d_flip_weights(w: torch.Tensor) -> torch.Tensor:
+    _cuda(w, "w", torch.bfloat16)
+    _, cout, cin = w.shape
+    wf = torch.empty((27, cin, cout), device=w.device, dtype=torch.bfloat16)
+    with torch.cuda.device(w.device):
+        _check(lib().pyro_conv3d_flip_weights(_ptr(w), _ptr(wf), cin, cout, _stream(w)))
+    return wf
+
+
+def pyro_cnn_op(op: int, a: torch.Tensor, y: torch.Tensor, b: Optional[torch.Tensor] = None,
+                f: Optional[torch.Tensor] = None, dims=(0, 0, 0, 0)) -> torch.Tensor:
+    nz, ny, nx, c = dims
+    with torch.cuda.device(a.device):
+        _check(lib().pyro_cnn_op(int(op), _ptr(a), _ptr(b), _ptr(y), _ptr(f), y.numel(), nz, ny, nx, c, _stream(a)))
+    return y
+
+
+def pyro_cnn_bias_grad(dy: torch.Tensor) -> torch.Tensor:
+    _cuda(dy, "dy", torch.bfloat16)
+    c = dy.shape[-1]
+    db = torch.empty(c, device=dy.device, dtype=torch.float32)
+    with torch.cuda.device(dy.device):
+        _check(lib().pyro_cnn_bias_grad(_ptr(dy), _ptr(db), dy.numel() // c, c, _stream(dy)))
+    return db
+
+
+def pyro_cnn_mse(out: torch.Tensor, target: torch.Tensor, grad: Optional[torch.Tensor] = None) -> torch.Tensor:
+    _cuda(out, "out", torch.float32)
+    _cuda(target, "target", torch.float32)
+    loss = torch.empty(1, device=out.device, dtype=torch.float32)
+    with torch.cuda.device(out.device):
+        _check(lib().pyro_cnn_mse(_ptr(out), _ptr(target), _ptr(grad), _ptr(loss), out.numel(), _stream(out)))
+    return loss
+
+
+def pyro_cnn_adam(p, g, m, v, p16, lr, step, beta1=0.9, beta2=0.999, eps=1e-8):
+    with torch.cuda.device(p.device):
+        _check(lib().pyro_cnn_adam(_ptr(p), _ptr(g), _ptr(m), _ptr(v), _ptr(p16), p.numel(), float(lr), float(beta1),
+                                   float(beta2), float(eps), int(step), _stream(p)))
 
 
 def version() -> str:

@@ -141,6 +141,20 @@ cudaError_t launch_tv(const float *x, float *grad, const float *base, float alph
 cudaError_t launch_axpby(const float *x, float *y, long n, float a, float b, cudaStream_t s);
 cudaError_t launch_dot(const float *a, const float *b, long n, float *out, cudaStream_t s);
 
+// residual CNN (kernels_cnn.cu)
+bool conv_supported(int cin, int cout);
+cudaError_t launch_conv3d(const void *X, const void *W, const float *bias, void *Y, int B, int D, int H, int Wd,
+                          int cin, int cout, int relu, cudaStream_t s);
+cudaError_t launch_conv3d_wgrad(const void *X, const void *dY, float *dW, int B, int D, int H, int Wd, int cin,
+                                int cout, cudaStream_t s);
+cudaError_t launch_weight_flip(const void *W, void *Wf, int cin, int cout, cudaStream_t s);
+cudaError_t launch_cnn_elementwise(int op, const void *a, const void *b, void *y, const float *f, long n, int D,
+                                   int H, int W, int C, cudaStream_t s);
+cudaError_t launch_bias_grad(const void *dy, float *db, long nvox, int C, cudaStream_t s);
+cudaError_t launch_mse(const float *out, const float *target, void *grad, float *loss, long n, cudaStream_t s);
+cudaError_t launch_adam(float *p, const float *g, float *m, float *v, void *p16, long n, float lr, float b1, float b2,
+                        float eps, int step, cudaStream_t s);
+
 int device_sm_count();
 
 // record the thread-local message returned by pyro_last_error()

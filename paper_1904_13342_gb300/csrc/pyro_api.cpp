@@ -1049,6 +1049,98 @@ PYRO_API int pyro_dot(const float *a, const float *b, long n, float *out, void *
     return PYRO_OK;
 }
 
+static int conv_dims_ok(int batch, int nz, int ny, int nx, int cin, int cout)
+{
+    PYRO_CHECK(batch >= 0 && nz > 0 && ny > 0 && nx > 0, "bad activation shape");
+    PYRO_CHECK(conv_supported(cin, cout), "unsupported channel pair (%d, %d)", cin, cout);
+    if (cin != 1 && cout != 1) {
+        // blocks of 128 output voxels: TX = min(nx, 64), TY = min(ny, 128 / TX), TZ = 128 / (TX TY)
+        PYRO_CHECK(nx == 8 || nx == 16 || nx == 32 || (nx >= 64 && nx % 64 == 0),
+                   "nx=%d must be 8, 16, 32 or a multiple of 64", nx);
+        const int tx = nx >= 64 ? 64 : nx;
+        const int ty = std::min(ny, 128 / tx);
+        PYRO_CHECK(ny % ty == 0 && (128 / tx) % ty == 0, "ny=%d does not tile by %d", ny, ty);
+        const int tz = 128 / (tx * ty);
+        PYRO_CHECK(nz % tz == 0, "nz=%d must be a multiple of %d", nz, tz);
+        PYRO_CHECK((long)batch * (nz / tz) * (ny / ty) * (nx / tx) < (1L << 31), "too many voxel tiles");
+    }
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_conv3d(const void *x, const void *w, const float *bias, void *y, int batch, int nz, int ny, int nx,
+                         int cin, int cout, int relu, void *stream)
+{
+    if (int e = conv_dims_ok(batch, nz, ny, nx, cin, cout)) return e;
+    if (batch == 0) return PYRO_OK;
+    PYRO_CHECK(x && w && y, "NULL pointer");
+    PYRO_CHECK(aligned16(x) && aligned16(w) && aligned16(y) && aligned16(bias), "pointers must be 16-byte aligned");
+    PYRO_CUDA(launch_conv3d(x, w, bias, y, batch, nz, ny, nx, cin, cout, relu, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_conv3d_wgrad(const void *x, const void *dy, float *dw, int batch, int nz, int ny, int nx, int cin,
+                               int cout, void *stream)
+{
+    if (int e = conv_dims_ok(batch, nz, ny, nx, cin, cout)) return e;
+    PYRO_CHECK(dw != nullptr, "NULL pointer");
+    if (batch == 0) {
+        PYRO_CUDA(cudaMemsetAsync(dw, 0, sizeof(float) * 27 * cin * cout, as_stream(stream)));
+        return PYRO_OK;
+    }
+    PYRO_CHECK(x && dy, "NULL pointer");
+    PYRO_CHECK(aligned16(x) && aligned16(dy), "pointers must be 16-byte aligned");
+    PYRO_CUDA(launch_conv3d_wgrad(x, dy, dw, batch, nz, ny, nx, cin, cout, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_conv3d_flip_weights(const void *w, void *wf, int cin, int cout, void *stream)
+{
+    PYRO_CHECK(w && wf && cin > 0 && cout > 0, "bad arguments");
+    PYRO_CUDA(launch_weight_flip(w, wf, cin, cout, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_cnn_op(int op, const void *a, const void *b, void *y, const float *f, long n, int nz, int ny, int nx,
+                         int c, void *stream)
+{
+    PYRO_CHECK(op >= 0 && op <= 8, "unknown CNN op %d", op);
+    PYRO_CHECK(n >= 0, "n must be >= 0");
+    if (n == 0) return PYRO_OK;
+    PYRO_CHECK(a && y, "NULL pointer");
+    if (op == PYRO_CNN_ADD) PYRO_CHECK(b != nullptr, "ADD needs b");
+    if (op == PYRO_CNN_RESIDUAL) PYRO_CHECK(f != nullptr, "RESIDUAL needs f");
+    if (op >= 1 && op <= 4) {
+        PYRO_CHECK(nz > 0 && ny > 0 && nx > 0 && c > 0, "bad shape");
+        if (op <= 2) PYRO_CHECK(nz % 2 == 0 && ny % 2 == 0 && nx % 2 == 0, "pooling needs even dims");
+    }
+    PYRO_CUDA(launch_cnn_elementwise(op, a, b, y, f, n, nz, ny, nx, c, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_cnn_bias_grad(const void *dy, float *db, long nvox, int c, void *stream)
+{
+    PYRO_CHECK(dy && db && nvox >= 0 && c > 0 && c <= 65535, "bad arguments");
+    PYRO_CUDA(launch_bias_grad(dy, db, nvox, c, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_cnn_mse(const float *out, const float *target, void *grad, float *loss, long n, void *stream)
+{
+    PYRO_CHECK(out && target && loss && n > 0, "bad arguments");
+    PYRO_CUDA(launch_mse(out, target, grad, loss, n, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_cnn_adam(float *p, const float *g, float *m, float *v, void *p16, long n, float lr, float beta1,
+                           float beta2, float eps, int step, void *stream)
+{
+    PYRO_CHECK(p && g && m && v && n >= 0 && step >= 1, "bad arguments");
+    PYRO_CHECK(std::isfinite(lr) && beta1 >= 0 && beta1 < 1 && beta2 >= 0 && beta2 < 1 && eps > 0, "bad Adam settings");
+    if (n == 0) return PYRO_OK;
+    PYRO_CUDA(launch_adam(p, g, m, v, p16, n, lr, beta1, beta2, eps, step, as_stream(stream)));
+    return PYRO_OK;
+}
+
 PYRO_API const char *pyro_last_error(void)
 {
     return g_last_error.c_str();

@@ -573,3 +573,50 @@ def test_tv_solver_is_first_order_optimal_with_lambda():
     # the TV term lowers the error against the piecewise-constant truth vs plain least squares
     x0, _ = oracle.tv_solve(p, fwd, adj, 0.0, eps, 600, L)
     assert np.linalg.norm(x - truth) < np.linalg.norm(x0 - truth)
+
+
+# --------------------------------------------------------- CNN reference ---
+
+def test_cnn_reference_conv_pins():
+    """The reference convolution against closed forms: a centre-tap identity
+    kernel copies the input; a kernel of ones sums the 3x3x3 neighbourhood
+    (zero padding); wgrad is the adjoint of the map w -> conv(x, w)."""
+    import torch
+    from oracle import cnn as R
+    rng = np.random.default_rng(21)
+    x = torch.from_numpy(rng.standard_normal((1, 4, 5, 6, 2)))
+    w = torch.zeros(27, 2, 2, dtype=torch.float64)
+    w[13, 0, 0] = w[13, 1, 1] = 1.0  # tap (1,1,1) is the centre
+    assert torch.allclose(R.conv3d(x, w), x)
+    ones = torch.ones(27, 1, 1, dtype=torch.float64)
+    s = torch.from_numpy(rng.standard_normal((1, 4, 5, 6, 1)))
+    box = R.conv3d(s, ones)[0, 1, 2, 3, 0]
+    assert abs(float(box) - float(s[0, 0:3, 1:4, 2:5, 0].sum())) < 1e-12
+    corner = R.conv3d(s, ones)[0, 0, 0, 0, 0]
+    assert abs(float(corner) - float(s[0, 0:2, 0:2, 0:2, 0].sum())) < 1e-12
+    # tap convention: a kernel with only tap (dz,dy,dx) = (2,1,1) reads x[z+1]
+    w1 = torch.zeros(27, 1, 1, dtype=torch.float64)
+    w1[(2 * 3 + 1) * 3 + 1] = 1.0
+    y = R.conv3d(s, w1)
+    assert torch.allclose(y[:, :-1], s[:, 1:]) and torch.all(y[:, -1] == 0)
+    dy = torch.from_numpy(rng.standard_normal((1, 4, 5, 6, 3)))
+    wr = torch.from_numpy(rng.standard_normal((27, 3, 2)))
+    lhs = float((R.conv3d(x, wr) * dy).sum())
+    rhs = float((R.conv3d_wgrad(x, dy) * wr).sum())
+    assert abs(lhs - rhs) < 1e-10 * abs(lhs)
+
+
+def test_cnn_reference_network_pins():
+    """Zero last layer: the residual network returns its input exactly;
+    pooling / upsampling are the mean / copy they are defined to be."""
+    import torch
+    from oracle import cnn as R
+    rng = np.random.default_rng(22)
+    params = {n: (torch.from_numpy(rng.standard_normal((27, co, ci)) * 0.1), torch.zeros(co, dtype=torch.float64))
+              for n, ci, co in R.LAYERS}
+    params["c11"] = (torch.zeros(27, 1, 16, dtype=torch.float64), torch.zeros(1, dtype=torch.float64))
+    x = torch.from_numpy(rng.standard_normal((1, 16, 16, 16)))
+    assert torch.equal(R.network(x, params), x)
+    v = torch.from_numpy(rng.standard_normal((1, 4, 4, 4, 3)))
+    assert torch.allclose(R.avgpool2(v)[0, 1, 0, 1], v[0, 2:4, 0:2, 2:4].mean(dim=(0, 1, 2)))
+    assert torch.equal(R.upsample2(v)[0, 5, 2, 7], v[0, 2, 1, 3])
