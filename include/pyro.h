@@ -119,8 +119,8 @@ PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_g
 
 /* --- The same cone-beam forward projection, computed from a copy of the
  * volume re-laid out z-fastest in `workspace` (device, at least
- * pyro_fp_cone3d_workspace_bytes bytes, i.e. one volume of `dtype`;
- * PYRO_EWORKSPACE otherwise).  This is the memory-for-speed trade the paper
+ * pyro_fp_cone3d_workspace_bytes bytes, i.e. one volume of `dtype` padded
+ * by one voxel on every face; PYRO_EWORKSPACE otherwise).  This is the memory-for-speed trade the paper
  * describes for its texture mode (the volume is held twice, Section "The
  * Operator as a Layer"); pyro_fp_cone3d is the memory-lean mode.  Results
  * are identical up to FP32 summation order; the workspace is scratch. */
@@ -139,6 +139,18 @@ PYRO_API int pyro_fpT_fan2d(const void *sino, void *vol, int batch, const pyro_g
                             void *stream);
 PYRO_API int pyro_fpT_cone3d(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_dtype dtype,
                              void *stream);
+
+/* --- The same exact adjoint of the cone-beam projector, accumulated in a
+ * zero-padded z-major FP32 copy of the volume in `workspace` (device, at
+ * least pyro_fpT_cone3d_workspace_bytes bytes; PYRO_EWORKSPACE otherwise):
+ * for circular-type trajectories (the detector's v axis along the volume's
+ * z axis) each warp spreads 32 rays over a 32-voxel run of z in shared
+ * memory and issues four global atomics per 32 samples instead of eight per
+ * sample.  Other trajectories fall back to pyro_fpT_cone3d.  Results agree
+ * with it to FP32 rounding; the workspace is scratch.  PYRO_F32 only. */
+PYRO_API size_t pyro_fpT_cone3d_workspace_bytes(const pyro_geom3d *g);
+PYRO_API int pyro_fpT_cone3d_ws(const void *sino, void *vol, int batch, const pyro_geom3d *g, void *workspace,
+                                size_t workspace_bytes, pyro_dtype dtype, void *stream);
 
 /* --- Voxel-driven back-projection (Section "The Operator as a Layer"; the
  * cone-beam form after Scherl et al. with projection matrices):

@@ -41,7 +41,7 @@ def _fp(x, g):
 
 def _fpT(y, g):
     if _is3d(g):
-        return B.pyro_fpT_cone3d(y, g)
+        return B.pyro_fpT_cone3d_ws(y, g)
     return B.pyro_fpT_fan2d(y, g) if g.fan else B.pyro_fpT_par2d(y, g)
 
 

@@ -54,6 +54,8 @@ _SIGS = {
     "pyro_fpT_par2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fpT_fan2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fpT_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
+    "pyro_fpT_cone3d_workspace_bytes": [_G3],
+    "pyro_fpT_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
     "pyro_bp_par2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
     "pyro_bp_fan2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
     "pyro_bp_cone3d": [_VP, _VP, _I, _G3, _I, _F, _I, _VP],
@@ -102,6 +104,7 @@ def lib():
             L.pyro_version.restype = ctypes.c_char_p
             L.pyro_fdk_workspace_bytes.restype = _SZ
             L.pyro_fp_cone3d_workspace_bytes.restype = _SZ
+            L.pyro_fpT_cone3d_workspace_bytes.restype = _SZ
             L.pyro_fbp2d_workspace_bytes.restype = _SZ
             _lib = L
     return _lib
@@ -240,6 +243,29 @@ def pyro_fpT_fan2d(sino: torch.Tensor, g: Geometry2D) -> torch.Tensor:
 
 def pyro_fpT_cone3d(sino: torch.Tensor, g: ConeGeometry3D) -> torch.Tensor:
     return _fpT(lib().pyro_fpT_cone3d, sino, g, g.volume_shape, g.sinogram_shape)
+
+
+def fpT_cone3d_workspace_bytes(g: ConeGeometry3D) -> int:
+    """Workspace pyro_fpT_cone3d_ws needs (one padded FP32 volume)."""
+    cg = g.to_c()
+    return int(lib().pyro_fpT_cone3d_workspace_bytes(ctypes.byref(cg)))
+
+
+def pyro_fpT_cone3d_ws(sino: torch.Tensor, g: ConeGeometry3D, workspace: Optional[torch.Tensor] = None,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Exact adjoint of the cone-beam FP accumulated in a padded z-major copy
+    kept in `workspace` (allocated here when not given)."""
+    s, squeeze = _batched(_dev(sino, "sinogram"), 3, "sinogram")
+    _shape_check(s, g.sinogram_shape, "sinogram")
+    cg = g.to_c()
+    need = lib().pyro_fpT_cone3d_workspace_bytes(ctypes.byref(cg))
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=s.device)
+    o = _out(s, g.volume_shape) if out is None else _dev(out, "out")
+    with torch.cuda.device(s.device):
+        _check(lib().pyro_fpT_cone3d_ws(_ptr(s), _ptr(o), s.shape[0], ctypes.byref(cg), _ptr(workspace),
+                                        workspace.numel() * workspace.element_size(), _DTYPES[s.dtype], _stream(s)))
+    return o[0] if squeeze and out is None else o
 
 
 def pyro_bp_par2d(sino, g: Geometry2D, weight=W_NONE, scale=1.0):

@@ -55,6 +55,7 @@ struct ConeFPView {
 
 struct FP3DParams {
     int nx, ny, nz, nu, nv, n_views, view0, views_total;
+    int column_shared;         // every view: rows of a detector column share (x, y) (see fill_fp3d)
     int M;
     float cx, cy, cz;          // (n-1)/2 per axis
     float dt;
@@ -115,6 +116,10 @@ cudaError_t launch_fp3d(const void *vol, void *sino, int batch, const FP3DParams
 cudaError_t launch_fp3d_adjoint(const void *sino, void *vol, int batch, const FP3DParams &p, cudaStream_t s);
 // [z][y][x] -> [y][x][z] copy of one volume
 cudaError_t launch_relayout_zmajor(const void *vol, void *vz, int nx, int ny, int nz, pyro_dtype dt, cudaStream_t s);
+cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt, cudaStream_t s);
+cudaError_t launch_fp3d_column(const void *vp, void *sino, int b, const FP3DParams &p, pyro_dtype dt, cudaStream_t s);
+cudaError_t launch_fp3d_column_adjoint(const void *sino, void *vp, int b, const FP3DParams &p, cudaStream_t s);
+cudaError_t launch_relayout_unpad(const void *vp, void *vol, int nx, int ny, int nz, cudaStream_t s);
 // forward projection of batch item b from its z-major copy; `sino` is the whole
 // [batch][views_total][nv][nu] sinogram
 cudaError_t launch_fp3d_zmajor(const void *vz, void *sino, int b, const FP3DParams &p, pyro_dtype dt,

@@ -278,6 +278,300 @@ __global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const
     sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(r.w * acc);
 }
 
+// Column-shared projection.  When the detector's v axis maps onto the
+// volume's z axis (circular and helical-free trajectories: no skew, camera y
+// axis = z), all rays of one detector column k share their (x, y) point on
+// every depth plane; only z differs, and it grows monotonically with the row
+// l.  A warp takes column k and R windows of 32 consecutive rows.  On each
+// depth plane it computes the (x, y) cell and its bilinear weights once; in
+// each window every lane loads the four (x, y) columns at one z of the
+// window's 32-voxel run (one coalesced 128-byte load per column) and
+// combines them in x and y, and each lane then takes the two z taps of its
+// own ray from the lanes holding them (two shuffles).  The host checks that
+// 31 row steps stay below 29.5 voxels in z, so a window's taps always fall in
+// its 32-voxel run.  The volume copy is [ny+2][nx+2][nz+2] with a zero voxel
+// on every face: loads need no bounds test, and the zero-extended
+// interpolant comes out of the padding.
+constexpr int kFPCWarps = 4;
+
+// floor(x) for |x| < 2^22 on the FMA pipe: x + 1.5 * 2^23 rounded toward
+// -inf is exactly 1.5 * 2^23 + floor(x) (unit spacing there), so the float
+// floor and the integer floor (low bits of the sum) both follow without a
+// conversion instruction.
+constexpr float kFloorMagic = 12582912.0f;  // 1.5 * 2^23, bit pattern 0x4B400000
+__device__ __forceinline__ float floor_magic(float x) { return __fadd_rd(x, kFloorMagic); }
+__device__ __forceinline__ float magic_to_float(float t) { return t - kFloorMagic; }
+__device__ __forceinline__ int magic_to_int(float t) { return __float_as_int(t) - 0x4B400000; }
+
+struct ColumnWindow {
+    float pz, qz;    // this lane's ray: z(m) = pz + m qz
+    float pzb, qzb;  // the window's lowest row
+    float w;         // ray weight dt |g|
+    float acc;       // forward: the ray sum; adjoint: w times the ray's datum
+    int ma, mb;      // samples of the window's rows that can touch the volume
+};
+
+// (x, y) cell of depth plane m shared by the column's rays: bilinear weights
+// and the padded element index of (x0, y0, z = 0)
+struct PlaneXY {
+    float w00, w10, w01, w11;
+    int col;
+};
+
+__device__ __forceinline__ PlaneXY plane_xy(float fm, const Ray3 &rc, int sxp, int syp)
+{
+    const float fx = fmaf(fm, rc.qx, rc.px), fy = fmaf(fm, rc.qy, rc.py);
+    const float tx = floor_magic(fx), ty = floor_magic(fy);
+    const float ax = fx - magic_to_float(tx), ay = fy - magic_to_float(ty);
+    const float bx = 1.0f - ax, by = 1.0f - ay;
+    PlaneXY q;
+    q.w00 = bx * by;
+    q.w10 = ax * by;
+    q.w01 = bx * ay;
+    q.w11 = ax * ay;
+    q.col = (magic_to_int(ty) + 1) * syp + (magic_to_int(tx) + 1) * sxp + 1;
+    return q;
+}
+
+// One depth plane of one window: the lane's x/y-interpolated value at
+// z = zb + lane, then its own ray's z interpolation from two lanes.
+template <typename T>
+__device__ __forceinline__ void column_step(ColumnWindow &W, float fm, int lane, int nz, const T *const (&c)[4],
+                                            const PlaneXY &q)
+{
+    const float tzb = floor_magic(fmaf(fm, W.qzb, W.pzb));
+    const int zi = min(max(magic_to_int(tzb) + lane, -1), nz);
+    const float g = q.w00 * ld(c[0] + zi) + q.w10 * ld(c[1] + zi) + q.w01 * ld(c[2] + zi) + q.w11 * ld(c[3] + zi);
+    const float fz = fmaf(fm, W.qz, W.pz);
+    const float tz = floor_magic(fz);
+    const int j = __float_as_int(tz) - __float_as_int(tzb);  // own cell relative to the window's run
+    const float g0 = __shfl_sync(0xffffffffu, g, j), g1 = __shfl_sync(0xffffffffu, g, j + 1);
+    W.acc += fmaf(fz - magic_to_float(tz), g1 - g0, g0);
+}
+
+// Transpose of column_step: the lane's ray datum y is split between the two
+// z cells of its sample in the window's run (a shared-memory array of 32
+// sums), then each lane spreads the sum of its cell over the four (x, y)
+// columns with global atomics: four atomics per 32 samples.
+__device__ __forceinline__ void column_step_adjoint(const ColumnWindow &W, float fm, int lane, int nz,
+                                                    float *const (&c)[4], const PlaneXY &q, float *run)
+{
+    const float tzb = floor_magic(fmaf(fm, W.qzb, W.pzb));
+    const int zi = min(max(magic_to_int(tzb) + lane, -1), nz);
+    const float fz = fmaf(fm, W.qz, W.pz);
+    const float tz = floor_magic(fz);
+    // 0..30 for every real row (host-checked); clamped so that no shared
+    // access leaves the run
+    const int j = min(max(__float_as_int(tz) - __float_as_int(tzb), 0), 30);
+    const float az = fz - magic_to_float(tz);
+    const float y = W.acc;
+    if (y != 0.0f) {
+        atomicAdd(run + j, fmaf(-az, y, y));
+        atomicAdd(run + j + 1, az * y);
+    }
+    __syncwarp();
+    const float d = run[lane];
+    run[lane] = 0.0f;
+    __syncwarp();
+    if (d != 0.0f) {
+        atomicAdd(c[0] + zi, q.w00 * d);
+        atomicAdd(c[1] + zi, q.w10 * d);
+        atomicAdd(c[2] + zi, q.w01 * d);
+        atomicAdd(c[3] + zi, q.w11 * d);
+    }
+}
+
+// Depth planes m0..m1 of all R windows.  CHECK skips the windows whose rows
+// cannot touch the volume on a plane (outside the planes every window
+// reaches; elsewhere the skipped terms would be exact zeros anyway: the
+// forward reads the zero padding, the adjoint writes into it).
+template <typename T, int R, bool CHECK, bool ADJ>
+__device__ __forceinline__ void column_planes(ColumnWindow (&W)[R], int m0, int m1, const Ray3 &rc, int lane, T *vp,
+                                              int nz, int sxp, int syp, float *runs)
+{
+    float fm = (float)m0;
+#pragma unroll 2
+    for (int m = m0; m <= m1; ++m, fm += 1.0f) {
+        const PlaneXY q = plane_xy(fm, rc, sxp, syp);
+        T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
+            if constexpr (ADJ) {
+                column_step_adjoint(W[r], fm, lane, nz, c, q, runs + 32 * r);
+            } else {
+                const T *const cr[4] = {c[0], c[1], c[2], c[3]};
+                column_step(W[r], fm, lane, nz, cr, q);
+            }
+        }
+    }
+}
+
+// Set-up shared by the forward and adjoint column kernels: the column's
+// (x, y) track rc, the windows' rays and ranges; returns the union [mlo, mhi]
+// of the windows' ranges and the planes [clo, chi] every window reaches.
+template <int R>
+__device__ __forceinline__ void column_setup(const FP3DParams &p, int v, int k, int row0, int lane, Ray3 &rc,
+                                             ColumnWindow (&W)[R], int &mlo, int &mhi, int &clo, int &chi)
+{
+    const unsigned full = 0xffffffffu;
+    rc = ray3d(p, v, k, row0);  // (x, y) track of the column, common to all its rows
+    float lo = -(float)p.M, hi = (float)p.M;
+    clip_axis(rc.px, rc.qx, p.nx, lo, hi);
+    clip_axis(rc.py, rc.qy, p.ny, lo, hi);
+    int m0 = max(-p.M, (int)floorf(lo)), m1 = min(p.M, (int)ceilf(hi));
+    // keep the samples whose cell (x0, y0) lies in [-1, n-1]^2; the clip above
+    // is rounded outwards by at most one sample
+    auto inside = [&](int m) {
+        const float fx = fmaf((float)m, rc.qx, rc.px), fy = fmaf((float)m, rc.qy, rc.py);
+        return fx >= -1.0f && fx < (float)p.nx && fy >= -1.0f && fy < (float)p.ny;
+    };
+    while (m0 <= m1 && !inside(m0)) ++m0;
+    while (m1 >= m0 && !inside(m1)) --m1;
+    mlo = INT_MAX;
+    mhi = INT_MIN;
+    clo = INT_MIN;
+    chi = INT_MAX;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int l = row0 + 32 * r + lane;
+        const Ray3 rr = ray3d(p, v, k, l);
+        W[r].pz = rr.pz;
+        W[r].qz = rr.qz;
+        W[r].w = rr.w;
+        W[r].acc = 0.0f;
+        // the window's lowest z is at its first or its last row (depth > 0)
+        const float z_first = __shfl_sync(full, rr.pz, 0), z_last = __shfl_sync(full, rr.pz, 31);
+        const int src = z_last >= z_first ? 0 : 31;
+        W[r].pzb = __shfl_sync(full, rr.pz, src);
+        W[r].qzb = __shfl_sync(full, rr.qz, src);
+        float zl = (float)m0, zh = (float)m1;
+        clip_axis(rr.pz, rr.qz, p.nz, zl, zh);
+        int a = max(m0, (int)floorf(zl)), e = min(m1, (int)ceilf(zh));
+        if (l >= p.nv || a > e) {  // no sample of this row touches the volume
+            a = INT_MAX;
+            e = INT_MIN;
+        }
+        W[r].ma = __reduce_min_sync(full, a);
+        W[r].mb = __reduce_max_sync(full, e);
+        if (W[r].ma <= W[r].mb) {
+            mlo = min(mlo, W[r].ma);
+            mhi = max(mhi, W[r].mb);
+            clo = max(clo, W[r].ma);
+            chi = min(chi, W[r].mb);
+        }
+    }
+    if (mlo <= mhi && clo > chi) {  // no plane common to all windows
+        clo = mhi + 1;
+        chi = mhi;
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__restrict__ vp,
+                                                                     T *__restrict__ sino,
+                                                                     const __grid_constant__ FP3DParams p, int b)
+{
+    const int lane = threadIdx.x;
+    const int k = blockIdx.y * kFPCWarps + threadIdx.y;
+    const int v = blockIdx.z;
+    if (k >= p.nu) return;  // whole warp
+    const int row0 = blockIdx.x * (32 * R);
+    Ray3 rc;
+    ColumnWindow W[R];
+    int mlo, mhi, clo, chi;
+    column_setup<R>(p, v, k, row0, lane, rc, W, mlo, mhi, clo, chi);
+    const int sxp = p.nz + 2, syp = (p.nx + 2) * (p.nz + 2);
+    if (mlo <= mhi) {
+        T *vq = const_cast<T *>(vp);  // read only on the forward path
+        column_planes<T, R, true, false>(W, mlo, clo - 1, rc, lane, vq, p.nz, sxp, syp, nullptr);
+        column_planes<T, R, false, false>(W, clo, chi, rc, lane, vq, p.nz, sxp, syp, nullptr);
+        column_planes<T, R, true, false>(W, max(chi + 1, clo), mhi, rc, lane, vq, p.nz, sxp, syp, nullptr);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int l = row0 + 32 * r + lane;
+        if (l < p.nv)
+            sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(W[r].w * W[r].acc);
+    }
+}
+
+// Exact adjoint of fp3d_column_kernel, accumulated into a zeroed padded
+// z-major FP32 volume (the padding collects the terms of samples outside the
+// volume and is discarded afterwards).
+template <int R>
+__global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_adjoint_kernel(const float *__restrict__ sino,
+                                                                             float *__restrict__ vp,
+                                                                             const __grid_constant__ FP3DParams p,
+                                                                             int b)
+{
+    __shared__ float runs[kFPCWarps][R * 32];
+    const int lane = threadIdx.x;
+    const int k = blockIdx.y * kFPCWarps + threadIdx.y;
+    const int v = blockIdx.z;
+    if (k >= p.nu) return;  // whole warp
+    float *run = runs[threadIdx.y];
+#pragma unroll
+    for (int r = 0; r < R; ++r) run[32 * r + lane] = 0.0f;
+    __syncwarp();
+    const int row0 = blockIdx.x * (32 * R);
+    Ray3 rc;
+    ColumnWindow W[R];
+    int mlo, mhi, clo, chi;
+    column_setup<R>(p, v, k, row0, lane, rc, W, mlo, mhi, clo, chi);
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const int l = row0 + 32 * r + lane;
+        W[r].acc = l < p.nv ? W[r].w * sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] : 0.0f;
+    }
+    const int sxp = p.nz + 2, syp = (p.nx + 2) * (p.nz + 2);
+    if (mlo <= mhi) {
+        column_planes<float, R, true, true>(W, mlo, clo - 1, rc, lane, vp, p.nz, sxp, syp, run);
+        column_planes<float, R, false, true>(W, clo, chi, rc, lane, vp, p.nz, sxp, syp, run);
+        column_planes<float, R, true, true>(W, max(chi + 1, clo), mhi, rc, lane, vp, p.nz, sxp, syp, run);
+    }
+}
+
+// interior of the padded z-major array -> [z][y][x]
+__global__ void __launch_bounds__(256) relayout_unpad_kernel(const float *__restrict__ vp, float *__restrict__ vol,
+                                                             int nx, int ny, int nz)
+{
+    __shared__ float tile[32][33];
+    const int nxp = nx + 2, nzp = nz + 2;
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32, y = blockIdx.z;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int x = x0 + i, z = z0 + threadIdx.x;
+        if (x < nx && z < nz) tile[i][threadIdx.x] = vp[((size_t)(y + 1) * nxp + x + 1) * nzp + z + 1];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int z = z0 + i, x = x0 + threadIdx.x;
+        if (x < nx && z < nz) vol[((size_t)z * ny + y) * nx + x] = tile[threadIdx.x][i];
+    }
+}
+
+// [z][y][x] -> [y+1][x+1][z+1] of a zero-padded (ny+2)(nx+2)(nz+2) array:
+// every padded element is written once (source voxel or 0)
+template <typename T>
+__global__ void __launch_bounds__(256) relayout_padded_kernel(const T *__restrict__ vol, T *__restrict__ vp, int nx,
+                                                              int ny, int nz)
+{
+    __shared__ T tile[32][33];
+    const int nxp = nx + 2, nzp = nz + 2;
+    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32, yp = blockIdx.z;
+    const int y = yp - 1;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int z = z0 + i - 1, x = x0 + threadIdx.x - 1;
+        const bool in = y >= 0 && y < ny && z >= 0 && z < nz && x >= 0 && x < nx;
+        tile[i][threadIdx.x] = in ? vol[((size_t)z * ny + y) * nx + x] : to_storage<T>(0.0f);
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int xp = x0 + i, zp = z0 + threadIdx.x;
+        if (zp < nzp && xp < nxp) vp[((size_t)yp * nxp + xp) * nzp + zp] = tile[threadIdx.x][i];
+    }
+}
+
 // [z][y][x] -> [y][x][z]: 32 x 32 tiles of one y-plane through shared memory
 template <typename T>
 __global__ void __launch_bounds__(256) relayout_zmajor_kernel(const T *__restrict__ vol, T *__restrict__ vz, int nx,
@@ -416,6 +710,118 @@ cudaError_t launch_fp3d_zmajor(const void *vz, void *sino, int b, const FP3DPara
                                                                    p, b);
         break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt, cudaStream_t s)
+{
+    dim3 block(32, 8), grid((nx + 2 + 31) / 32, (nz + 2 + 31) / 32, ny + 2);
+    switch (dt) {
+    case PYRO_F32:
+        relayout_padded_kernel<float><<<grid, block, 0, s>>>((const float *)vol, (float *)vp, nx, ny, nz);
+        break;
+    case PYRO_F16:
+        relayout_padded_kernel<__half><<<grid, block, 0, s>>>((const __half *)vol, (__half *)vp, nx, ny, nz);
+        break;
+    case PYRO_BF16:
+        relayout_padded_kernel<__nv_bfloat16>
+            <<<grid, block, 0, s>>>((const __nv_bfloat16 *)vol, (__nv_bfloat16 *)vp, nx, ny, nz);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+template <typename T, int R>
+static void column_launch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
+{
+    dim3 block(32, kFPCWarps);
+    dim3 grid((p.nv + 32 * R - 1) / (32 * R), (p.nu + kFPCWarps - 1) / kFPCWarps, (unsigned)p.n_views);
+    fp3d_column_kernel<T, R><<<grid, block, 0, s>>>((const T *)vp, (T *)sino, p, b);
+}
+
+// 32-row windows per column, 1 to 5 per warp.  Cost model in issue slots
+// per warp and depth plane: about 28 per window (windows past the last row
+// included) plus about 30 shared by the warp's windows.
+static int column_windows_per_warp(int nv)
+{
+    const int windows = (nv + 31) / 32;
+    int best = 1, cost = INT_MAX;
+    for (int r = 1; r <= 5 && r <= windows; ++r) {
+        const int c = (windows + r - 1) / r * (28 * r + 30);
+        if (c <= cost) {
+            best = r;
+            cost = c;
+        }
+    }
+    return best;
+}
+
+template <typename T>
+static void column_dispatch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
+{
+    const int best = column_windows_per_warp(p.nv);
+    if (best == 5)
+        column_launch<T, 5>(vp, sino, b, p, s);
+    else if (best == 4)
+        column_launch<T, 4>(vp, sino, b, p, s);
+    else if (best == 3)
+        column_launch<T, 3>(vp, sino, b, p, s);
+    else if (best == 2)
+        column_launch<T, 2>(vp, sino, b, p, s);
+    else
+        column_launch<T, 1>(vp, sino, b, p, s);
+}
+
+cudaError_t launch_fp3d_column(const void *vp, void *sino, int b, const FP3DParams &p, pyro_dtype dt, cudaStream_t s)
+{
+    switch (dt) {
+    case PYRO_F32:
+        column_dispatch<float>(vp, sino, b, p, s);
+        break;
+    case PYRO_F16:
+        column_dispatch<__half>(vp, sino, b, p, s);
+        break;
+    case PYRO_BF16:
+        column_dispatch<__nv_bfloat16>(vp, sino, b, p, s);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+template <int R>
+static void column_adjoint_launch(const float *sino, float *vp, int b, const FP3DParams &p, cudaStream_t s)
+{
+    dim3 block(32, kFPCWarps);
+    dim3 grid((p.nv + 32 * R - 1) / (32 * R), (p.nu + kFPCWarps - 1) / kFPCWarps, (unsigned)p.n_views);
+    fp3d_column_adjoint_kernel<R><<<grid, block, 0, s>>>(sino, vp, p, b);
+}
+
+cudaError_t launch_fp3d_column_adjoint(const void *sino, void *vp, int b, const FP3DParams &p, cudaStream_t s)
+{
+    switch (column_windows_per_warp(p.nv)) {
+    case 5:
+        column_adjoint_launch<5>((const float *)sino, (float *)vp, b, p, s);
+        break;
+    case 4:
+        column_adjoint_launch<4>((const float *)sino, (float *)vp, b, p, s);
+        break;
+    case 3:
+        column_adjoint_launch<3>((const float *)sino, (float *)vp, b, p, s);
+        break;
+    case 2:
+        column_adjoint_launch<2>((const float *)sino, (float *)vp, b, p, s);
+        break;
+    default:
+        column_adjoint_launch<1>((const float *)sino, (float *)vp, b, p, s);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_relayout_unpad(const void *vp, void *vol, int nx, int ny, int nz, cudaStream_t s)
+{
+    dim3 block(32, 8), grid((nx + 31) / 32, (nz + 31) / 32, ny);
+    relayout_unpad_kernel<<<grid, block, 0, s>>>((const float *)vp, (float *)vol, nx, ny, nz);
     return cudaGetLastError();
 }
 

@@ -308,6 +308,7 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
     p.cz = (float)(0.5 * (G.nz - 1));
     p.dt = (float)G.step;
     const double inv_s[3] = {1.0 / G.sx, 1.0 / G.sy, 1.0 / G.sz};
+    p.column_shared = 1;
     for (int v = 0; v < nvw; ++v) {
         const double *Q = &G.P[12 * (size_t)(v0 + v)];
         const double *S = &G.S[3 * (size_t)(v0 + v)];
@@ -326,11 +327,22 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
         const double K00 = std::sqrt(dot(t, t));
         if (!(K00 > 0 && K11 > 0)) return fail(PYRO_EINVAL, "projection matrix %d has a degenerate camera", v0 + v);
         for (int e = 0; e < 3; ++e) r0[e] = t[e] / K00;
+        // Rows of a detector column share their (x, y) point when the camera's
+        // y axis is the volume's z axis and K has no skew.  FP64 rounding of
+        // the split leaves ~1e-16 in those entries; below 1e-12 they are set
+        // to exact zeros so that the FP32 (x, y) of every row agree bit for bit.
+        double K01s = K01;
+        const bool col = std::fabs(r1[0]) < 1e-12 && std::fabs(r1[1]) < 1e-12 && std::fabs(K01) < 1e-12 * K00;
+        if (col) {
+            r1[0] = r1[1] = 0.0;
+            r1[2] = r1[2] > 0 ? 1.0 : -1.0;
+            K01s = 0.0;
+        }
         // q = K^-1 (k, l, 1) / K22 scaled so that q_z = 1
         ConeFPView &o = p.v[v];
         const double b0 = 1.0 / K11, b2 = -K12 / K11;
         o.a0 = (float)(1.0 / K00);
-        o.a1 = (float)(-K01 * b0 / K00);
+        o.a1 = (float)(-K01s * b0 / K00);
         o.a2 = (float)((-K02 - K01 * b2) / K00);
         o.b0 = (float)b0;
         o.b2 = (float)b2;
@@ -341,6 +353,11 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
         const double *R[3] = {r0, r1, r2};
         for (int a = 0; a < 3; ++a)
             for (int b = 0; b < 3; ++b) o.W[3 * a + b] = (float)(R[b][a] * inv_s[a]);
+        // one row step moves a sample by b0 W_zy w voxels in z at depth w; the
+        // column kernel needs 31 steps below 29.5 voxels over the sampled depths
+        const double w_far = -dot(r2, S) + G.M * G.step;
+        const double dz_row = std::fabs(b0 * r1[2] * inv_s[2]) * w_far;
+        if (!col || !(31.0 * dz_row <= 29.5)) p.column_shared = 0;
     }
     return PYRO_OK;
 }
@@ -637,6 +654,20 @@ int fp3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtyp
     return PYRO_OK;
 }
 
+// The column-shared kernels (padded z-major copy) serve a geometry when every
+// view allows them and the padded copy is int-indexable.
+int column_path(const Geo3D &G, FP3DParams &p, bool &column)
+{
+    const size_t padded = (size_t)(G.nx + 2) * (G.ny + 2) * (G.nz + 2);
+    const int V = (int)G.beta.size();
+    column = padded < (size_t)INT32_MAX;
+    for (int v0 = 0; v0 < V && column; v0 += kMaxViewsConeFP) {
+        if (int e = fill_fp3d(G, v0, std::min(kMaxViewsConeFP, V - v0), p)) return e;
+        column = p.column_shared != 0;
+    }
+    return PYRO_OK;
+}
+
 // staged cone FP: per batch item, a z-major copy of the volume in `work`
 int fp3d_staged(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *work, size_t work_bytes,
                 pyro_dtype dt, void *stream)
@@ -645,21 +676,64 @@ int fp3d_staged(const void *vol, void *sino, int batch, const pyro_geom3d *g, vo
     Geo3D G;
     if (int e = prep3d(g, G)) return e;
     const size_t vox = (size_t)G.nx * G.ny * G.nz;
-    const size_t need = vox * elem_size(dt);
+    const size_t padded = (size_t)(G.nx + 2) * (G.ny + 2) * (G.nz + 2);
+    const size_t need = padded * elem_size(dt);
     if (work_bytes < need || work == nullptr || !aligned16(work))
         return fail(PYRO_EWORKSPACE, "the staged forward projector needs a 16-byte aligned workspace of %zu bytes "
                                      "(got %zu)", need, work_bytes);
     if (batch == 0) return PYRO_OK;
     const int V = (int)G.beta.size();
     static thread_local FP3DParams p;
+    bool column;
+    if (int e = column_path(G, p, column)) return e;
     for (int b = 0; b < batch; ++b) {
         const char *vi = (const char *)vol + b * vox * elem_size(dt);
-        PYRO_CUDA(launch_relayout_zmajor(vi, work, G.nx, G.ny, G.nz, dt, as_stream(stream)));
+        if (column)
+            PYRO_CUDA(launch_relayout_padded(vi, work, G.nx, G.ny, G.nz, dt, as_stream(stream)));
+        else
+            PYRO_CUDA(launch_relayout_zmajor(vi, work, G.nx, G.ny, G.nz, dt, as_stream(stream)));
         for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
             const int nvw = std::min(kMaxViewsConeFP, V - v0);
             if (int e = fill_fp3d(G, v0, nvw, p)) return e;
-            PYRO_CUDA(launch_fp3d_zmajor(work, sino, b, p, dt, as_stream(stream)));
+            if (column)
+                PYRO_CUDA(launch_fp3d_column(work, sino, b, p, dt, as_stream(stream)));
+            else
+                PYRO_CUDA(launch_fp3d_zmajor(work, sino, b, p, dt, as_stream(stream)));
         }
+    }
+    return PYRO_OK;
+}
+
+// staged exact adjoint: per batch item the column adjoint accumulates into
+// a zeroed padded z-major FP32 volume in `work`, whose interior is then
+// copied to the output; geometries the column kernels do not serve take the
+// per-sample scatter of fp3d (the workspace is then unused)
+int fp3d_adjoint_staged(const void *sino, void *vol, int batch, const pyro_geom3d *g, void *work, size_t work_bytes,
+                        pyro_dtype dt, void *stream)
+{
+    if (int e = check_io(sino, vol, batch, dt)) return e;
+    if (dt != PYRO_F32) return fail(PYRO_EUNSUPPORTED, "the FP adjoint supports PYRO_F32 only");
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    const size_t vox = (size_t)G.nx * G.ny * G.nz;
+    const size_t need = (size_t)(G.nx + 2) * (G.ny + 2) * (G.nz + 2) * sizeof(float);
+    if (work_bytes < need || work == nullptr || !aligned16(work))
+        return fail(PYRO_EWORKSPACE, "the staged FP adjoint needs a 16-byte aligned workspace of %zu bytes (got %zu)",
+                    need, work_bytes);
+    if (batch == 0) return PYRO_OK;
+    static thread_local FP3DParams p;
+    bool column;
+    if (int e = column_path(G, p, column)) return e;
+    if (!column) return fp3d(sino, vol, batch, g, dt, true, stream);
+    const int V = (int)G.beta.size();
+    for (int b = 0; b < batch; ++b) {
+        PYRO_CUDA(cudaMemsetAsync(work, 0, need, as_stream(stream)));
+        for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
+            const int nvw = std::min(kMaxViewsConeFP, V - v0);
+            if (int e = fill_fp3d(G, v0, nvw, p)) return e;
+            PYRO_CUDA(launch_fp3d_column_adjoint(sino, work, b, p, as_stream(stream)));
+        }
+        PYRO_CUDA(launch_relayout_unpad(work, (float *)vol + b * vox, G.nx, G.ny, G.nz, as_stream(stream)));
     }
     return PYRO_OK;
 }
@@ -783,7 +857,7 @@ PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_g
 PYRO_API size_t pyro_fp_cone3d_workspace_bytes(const pyro_geom3d *g, pyro_dtype dtype)
 {
     if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !valid_dtype(dtype)) return 0;
-    return (size_t)g->nx * g->ny * g->nz * elem_size(dtype);
+    return (size_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2) * elem_size(dtype);
 }
 
 PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
@@ -808,6 +882,18 @@ PYRO_API int pyro_fpT_cone3d(const void *sino, void *vol, int batch, const pyro_
                              void *stream)
 {
     return fp3d(sino, vol, batch, g, dtype, true, stream);
+}
+
+PYRO_API size_t pyro_fpT_cone3d_workspace_bytes(const pyro_geom3d *g)
+{
+    if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return 0;
+    return (size_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2) * sizeof(float);
+}
+
+PYRO_API int pyro_fpT_cone3d_ws(const void *sino, void *vol, int batch, const pyro_geom3d *g, void *workspace,
+                                size_t workspace_bytes, pyro_dtype dtype, void *stream)
+{
+    return fp3d_adjoint_staged(sino, vol, batch, g, workspace, workspace_bytes, dtype, stream);
 }
 
 PYRO_API int pyro_bp_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_bp_weight w,

@@ -40,7 +40,12 @@ def _ops(g):
                 ws["w"] = torch.empty(B.fp_cone3d_workspace_bytes(g, x.dtype), dtype=torch.uint8, device=x.device)
             return B.pyro_fp_cone3d_ws(x, g, workspace=ws["w"], out=out)
 
-        return A, lambda y: B.pyro_fpT_cone3d(y, g)
+        def AT(y):
+            if "wT" not in ws:
+                ws["wT"] = torch.empty(B.fpT_cone3d_workspace_bytes(g), dtype=torch.uint8, device=y.device)
+            return B.pyro_fpT_cone3d_ws(y, g, workspace=ws["wT"])
+
+        return A, AT
     if g.fan:
         return (lambda x, out=None: B.pyro_fp_fan2d(x, g)), (lambda y: B.pyro_fpT_fan2d(y, g))
     return (lambda x, out=None: B.pyro_fp_par2d(x, g)), (lambda y: B.pyro_fpT_par2d(y, g))
@@ -61,8 +66,10 @@ def estimate_lipschitz(g, shape, device, iters: int = 20, seed: int = 0) -> floa
 
 
 def tv_reconstruct(p: torch.Tensor, g, n_iter: int, lam: float, eps: float, L_est: Optional[float] = None,
-                   x0: Optional[torch.Tensor] = None, clamp: float = 10.0, track_objective: bool = False) -> TVResult:
-    """Minimise |A x - p|^2 + lam TV(x) (Eq. 7); p is one FP32 sinogram."""
+                   x0: Optional[torch.Tensor] = None, clamp: float = 10.0, track_objective: bool = False,
+                   callback=None) -> TVResult:
+    """Minimise |A x - p|^2 + lam TV(x) (Eq. 7); p is one FP32 sinogram.
+    `callback(k, x)`, when given, sees the iterate after each step k."""
     A, AT = _ops(g)
     shape = tuple(g.volume_shape)
     dev = p.device
@@ -93,6 +100,8 @@ def tv_reconstruct(p: torch.Tensor, g, n_iter: int, lam: float, eps: float, L_es
         B.pyro_axpby(x, x_prev, 1.0, 0.0)
         B.pyro_axpby(grad, g_prev, 1.0, 0.0)
         B.pyro_axpby(grad, x, -alpha, 1.0)
+        if callback is not None:
+            callback(k + 1, x)
     if track_objective:
         r = A(x, out=r) if isinstance(g, ConeGeometry3D) else A(x)
         B.pyro_axpby(p, r, -1.0, 1.0)

@@ -176,6 +176,57 @@ def test_fp_cone_staged(traj, dtype):
     assert rel(host(got), host(direct)) < TOL[dtype]
 
 
+# Circular cases that take the column-shared staged kernel (rows of a detector
+# column share (x, y); 31 row steps stay below 29.5 voxels in z): one to four
+# 32-row windows per warp with ragged tails, and a row step of 0.94 voxel that
+# puts the last taps at the end of a window's 32-voxel run.  CONE itself
+# (a row step just above one voxel) and every tilted trajectory take the
+# general z-major kernel.
+COLUMN_CASES = {
+    "one_window": dict(CONE, det=(20, 41), dspacing=(1.2, 1.4)),
+    "three_windows": dict(CONE, shape=(23, 37, 45), det=(70, 41), dspacing=(0.45, 1.4)),
+    "four_windows": dict(CONE, shape=(23, 37, 45), det=(150, 43), dspacing=(0.2, 1.3)),
+    "wide_rows": dict(CONE, det=(64, 41), dspacing=(1.4, 1.4)),
+}
+
+
+@pytest.mark.parametrize("case", sorted(COLUMN_CASES))
+def test_fp_cone_staged_column_kernel(case):
+    c = COLUMN_CASES[case]
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang)
+    vol = ph.voxelize_ellipsoids(ph.random_ellipsoids(5, 18.0, seed=31), c["shape"], c["spacing"]).numpy()
+    vol = np.stack([vol, ph.random_volume(c["shape"], 32)])
+    g = cone_geom(c)
+    got = B.pyro_fp_cone3d_ws(to_dev(vol), g)
+    ref = np.stack([oracle.fp_cone3d(f32(v), c["spacing"], c["det"], P) for v in vol])
+    assert rel(host(got), ref) < 1e-5
+    # every ray, including the first and last rows and columns
+    assert np.max(np.abs(host(got) - ref)) < 1e-4 * np.max(np.abs(ref))
+    for dtype in (torch.float16, torch.bfloat16):
+        assert rel(host(B.pyro_fp_cone3d_ws(to_dev(vol, dtype), g)), ref) < TOL[dtype]
+
+
+@pytest.mark.parametrize("case", sorted(COLUMN_CASES) + ["general", "tilted"])
+def test_fp_adjoint_cone_staged(case):
+    """Exact adjoint through the padded z-major copy: the oracle's A^T, the
+    per-sample scatter, and <A x, y> = <x, A^T y> against the staged FP."""
+    c = COLUMN_CASES.get(case, CONE)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = tilted_pmats(c, ang) if case == "tilted" else cone_pmats(c, ang)
+    g = cone_geom(c, P if case == "tilted" else None)
+    y = ph.random_sinogram((2, c["views"], *c["det"]), 41)
+    got = B.pyro_fpT_cone3d_ws(to_dev(y), g)
+    ref = np.stack([oracle.fpT_cone3d(f32(s), c["shape"], c["spacing"], P) for s in y])
+    assert rel(host(got), ref) < 1e-5
+    assert rel(host(got), host(B.pyro_fpT_cone3d(to_dev(y), g))) < 1e-5
+    x = ph.random_volume(c["shape"], 42)
+    ax = host(B.pyro_fp_cone3d_ws(to_dev(x), g))
+    lhs = float(np.sum(ax * f32(y[0])))
+    rhs = float(np.sum(f32(x) * host(got[0])))
+    assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
 def test_fp_cone_staged_workspace_checks():
     c = CONE
     g = cone_geom(c)
@@ -184,6 +235,13 @@ def test_fp_cone_staged_workspace_checks():
     with pytest.raises(B.PyroError) as e:
         B.pyro_fp_cone3d_ws(vol, g, workspace=small)
     assert e.value.status == 5
+    sino = B.pyro_fp_cone3d(vol, g)
+    with pytest.raises(B.PyroError) as e:
+        B.pyro_fpT_cone3d_ws(sino, g, workspace=small)
+    assert e.value.status == 5
+    with pytest.raises(B.PyroError) as e:  # the adjoint is FP32 only
+        B.pyro_fpT_cone3d_ws(sino.half(), g)
+    assert e.value.status == 4
 
 
 @pytest.mark.parametrize("traj", ["circular", "tilted"])
