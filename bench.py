@@ -18,6 +18,14 @@ collective); the step time is the max over ranks.
 
 `--impl reference` times the FP64 CPU oracle on a bounded sample of the same
 workload on this machine's host cores (the paper publishes no timings).
+
+`--workload learned-init` runs the sparse-view study instead (one GPU): a
+batch of 32 test phantoms, 128^3 at 1 mm, 60 views over 360 degrees, 256 x 200
+detector at 1 mm; FDK -> residual CNN -> TV against plain TV from zero.  The
+CNN is trained first on library-made pairs (not timed); lambda comes from a
+small grid on training phantoms.  `value` is the seconds the CNN path needs
+to reach the mean PSNR of 200 plain TV steps; the plain path's seconds, the
+PSNRs and the fixed-budget comparison (CNN + 20 TV steps) ride along.
 """
 from __future__ import annotations
 
@@ -363,6 +371,45 @@ def run_reference(args):
     print(json.dumps(out), flush=True)
 
 
+def run_learned_init(args):
+    from paper_1904_13342_gb300 import learned_init as LI
+
+    dev = torch.device("cuda:0")
+    setup = LI.SparseViewSetup()
+    maker = LI.PairMaker(setup, dev)
+    L_est = LI.lipschitz(maker)
+    eps = 1e-3
+    t0 = time.perf_counter()
+    net, losses = LI.train_initializer(maker, list(range(1000, 1064)), steps=args.train_steps, batch=4)
+    torch.cuda.synchronize()
+    train_s = time.perf_counter() - t0
+    grid = LI.choose_lambda(maker, list(range(1000, 1008)), [1.0, 3.0, 10.0, 30.0], 200, eps, L_est)
+    lam = max(grid, key=grid.get)
+    test = list(range(32))
+    res = LI.ab_test(maker, net, test, lam, eps, L_est, short_iter=20, long_iter=200)
+    sm = res.summary()
+    value = sm["seconds_to_target"]
+    line = {
+        "metric": "sparse-view recon s to PSNR (CNN-initialised TV vs plain TV)",
+        "value": round(value, 4) if value is not None else None,
+        "unit": "s", "higher_is_better": False, "n_gpus": 1, "steps": 1, "warmup": 0,
+        "dtype": "f32 (CNN bf16/f32-accumulate)", "data": "synthetic (seeded random ellipsoid phantoms)",
+        "vs_baseline": None,
+        "config": {"workload": "learned initializer: 32 x 128^3 (1 mm), 60 views / 360 deg, 256x200 det (1 mm), "
+                               "SID 750 mm, SDD 1200 mm", "test_seeds": [0, 31], "train_seeds": [1000, 1063],
+                   "train_steps": args.train_steps, "lambda": lam, "eps": eps, "lambda_grid": grid},
+        "plain_tv_200_s": round(sm["seconds_plain"], 4),
+        "speedup_vs_plain": round(sm["seconds_plain"] / value, 3) if value else None,
+        "iters_to_target": sm["iters_to_target"],
+        "psnr_db": {k: round(sm[k], 3) for k in ("psnr_fdk", "psnr_cnn", "psnr_learned", "psnr_short_tv",
+                                                 "psnr_plain", "psnr_to_target")},
+        "fixed_budget": {"cnn_plus_20_tv_s": round(sm["seconds_learned"], 4),
+                         "tv_20_s": round(sm["seconds_short_tv"], 4)},
+        "train_s": round(train_s, 2), "train_loss": [round(losses[0], 6), round(float(np.mean(losses[-50:])), 6)],
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -371,8 +418,12 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--workload", default="fdk-256", choices=["fdk-256", "learned-init"])
+    ap.add_argument("--train-steps", type=int, default=1000)
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "learned-init":
+        run_learned_init(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

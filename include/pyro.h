@@ -117,6 +117,15 @@ PYRO_API int pyro_fp_fan2d(const void *vol, void *sino, int batch, const pyro_ge
 PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtype dtype,
                             void *stream);
 
+/* --- The projection matrices the cone-beam calls use for geometry `g`
+ * (the circular trajectory's when g->proj_mats is NULL, else the given
+ * ones), normalised as the calls normalise them: third row (the depth) of
+ * unit norm in its first three entries, positive depth at the iso-centre.
+ * out: HOST array [n_views][3][4] (row-major doubles) owned by the caller.
+ * Host-only (no device work): lets a caller hand a subset of views, or
+ * matrices shifted to a sub-volume, back to the calls as proj_mats. */
+PYRO_API int pyro_cone_projection_matrices(const pyro_geom3d *g, double *out);
+
 /* --- The same cone-beam forward projection, computed from a copy of the
  * volume re-laid out z-fastest in `workspace` (device, at least
  * pyro_fp_cone3d_workspace_bytes bytes, i.e. one volume of `dtype` padded

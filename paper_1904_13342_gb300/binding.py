@@ -55,6 +55,7 @@ _SIGS = {
     "pyro_fpT_fan2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fpT_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
     "pyro_fpT_cone3d_workspace_bytes": [_G3],
+    "pyro_cone_projection_matrices": [_G3, _VP],
     "pyro_fpT_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
     "pyro_bp_par2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
     "pyro_bp_fan2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],

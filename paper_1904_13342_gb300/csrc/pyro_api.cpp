@@ -854,6 +854,15 @@ PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_g
     return fp3d(vol, sino, batch, g, dtype, false, stream);
 }
 
+PYRO_API int pyro_cone_projection_matrices(const pyro_geom3d *g, double *out)
+{
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    PYRO_CHECK(out != nullptr, "out is NULL");
+    std::copy(G.P.begin(), G.P.end(), out);
+    return PYRO_OK;
+}
+
 PYRO_API size_t pyro_fp_cone3d_workspace_bytes(const pyro_geom3d *g, pyro_dtype dtype)
 {
     if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !valid_dtype(dtype)) return 0;
