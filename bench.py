@@ -237,7 +237,7 @@ def run_gpu(args):
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(host_vol.numel() * 4),
                 "d2h_bytes_per_step": int(host_out.numel() * 4)},
         "gpu_launches": 4 * K,
-        "roofline": {"kernel": "fp3d_zmajor_kernel", "bound": "alu", "achieved": round(achieved, 3),
+        "roofline": {"kernel": "fp3d_column_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                      "traffic": traffic,
                      "note": f"{samples:.4g} samples x {FLOPS_PER_SAMPLE} flop; peak = {props.multi_processor_count}"
@@ -320,13 +320,13 @@ def cpu_sample(seconds: float):
     vol = ph.voxelize_ellipsoids(e, g.volume_shape, g.volume_spacing, dtype=torch.float64).numpy()
     ang = g.view_angles()
     P = oracle.circular_pmats(ang, SID, SDD, (NV, NU), (SV, SU))
-    fv = 12
+    fv = 36
     t0 = time.perf_counter()
     sino1 = oracle.fp_cone3d(vol, g.volume_spacing, (NV, NU), P[:fv])
     t_fp = time.perf_counter() - t0
     # FDK of a slab: a smooth synthetic sinogram stands in for the projections
     y = ph.random_sinogram((VIEWS, NV, NU), 1, smooth=2)
-    zs = 18
+    zs = 48
     kz = np.repeat(np.arange(N // 2 - zs // 2, N // 2 - zs // 2 + zs), N * N)
     jj = np.tile(np.repeat(np.arange(N), N), zs)
     ii = np.tile(np.arange(N), N * zs)
