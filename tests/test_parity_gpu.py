@@ -394,6 +394,14 @@ def test_many_views_are_chunked():
     assert rel(host(B.pyro_fp_cone3d(to_dev(vol), g)), oracle.fp_cone3d(f32(vol), c["spacing"], c["det"], P)) < 1e-5
     assert rel(host(B.pyro_bp_cone3d(to_dev(y), g, weight=2)),
                oracle.bp_cone3d(f32(y), c["shape"], c["spacing"], P, c["sid"], 2, 1.0)) < 1e-5
+    # the staged projector and its adjoint through the column-shared kernels
+    c3 = dict(c, dspacing=(0.6, 1.4))
+    P3 = cone_pmats(c3, ang)
+    g3 = cone_geom(c3)
+    assert rel(host(B.pyro_fp_cone3d_ws(to_dev(vol), g3)),
+               oracle.fp_cone3d(f32(vol), c3["spacing"], c3["det"], P3)) < 1e-5
+    assert rel(host(B.pyro_fpT_cone3d_ws(to_dev(y), g3)),
+               oracle.fpT_cone3d(f32(y), c3["shape"], c3["spacing"], P3)) < 1e-5
     c2 = dict(PAR, views=2100)
     ang2 = oracle.uniform_angles(c2["views"], c2["range"])
     y2 = ph.random_sinogram((c2["views"], c2["nu"]), 22)
