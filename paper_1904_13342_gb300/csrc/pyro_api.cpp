@@ -309,6 +309,8 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
     p.dt = (float)G.step;
     const double inv_s[3] = {1.0 / G.sx, 1.0 / G.sy, 1.0 / G.sz};
     p.column_shared = 1;
+    p.zs0 = 0;
+    p.zs1 = G.nz;
     for (int v = 0; v < nvw; ++v) {
         const double *Q = &G.P[12 * (size_t)(v0 + v)];
         const double *S = &G.S[3 * (size_t)(v0 + v)];
@@ -730,7 +732,7 @@ int fp3d_adjoint_staged(const void *sino, void *vol, int batch, const pyro_geom3
         PYRO_CUDA(cudaMemsetAsync(work, 0, need, as_stream(stream)));
         for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
             const int nvw = std::min(kMaxViewsConeFP, V - v0);
-            if (int e = fill_fp3d(G, v0, nvw, p)) return e;
+            if (int e = fill_fp3d(G, v0, nvw, p)) return e;  // the whole volume: zs0 = 0, zs1 = nz
             PYRO_CUDA(launch_fp3d_column_adjoint(sino, work, b, p, as_stream(stream)));
         }
         PYRO_CUDA(launch_relayout_unpad(work, (float *)vol + b * vox, G.nx, G.ny, G.nz, as_stream(stream)));

@@ -227,6 +227,27 @@ def test_fp_adjoint_cone_staged(case):
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
 
 
+def test_fp_adjoint_cone_staged_large_footprint():
+    """A 512 x 512 footprint (100 slices, 1 mm detector columns): the staged
+    adjoint against the oracle, and against the per-sample scatter on the
+    GPU (same FP32 coordinates: agreement to summation order)."""
+    shape, spacing = (100, 512, 512), (0.5, 0.5, 0.5)
+    det, dsp, views = (60, 420), (0.5, 1.0), 6
+    g = ConeGeometry3D(shape, spacing, det, dsp, views, 2 * math.pi, 750.0, 1200.0)
+    P = oracle.circular_pmats(oracle.uniform_angles(views, 2 * math.pi), 750.0, 1200.0, det, dsp)
+    # a smooth sinogram (white noise would bring in the FP32 coordinate
+    # rounding that the noise gate allows for)
+    v, l, k = np.meshgrid(np.arange(views), np.arange(det[0]), np.arange(det[1]), indexing="ij")
+    y = 1.0 + 0.5 * np.sin(2 * np.pi * k / det[1] + v) * np.cos(2 * np.pi * l / det[0])
+    got = host(B.pyro_fpT_cone3d_ws(to_dev(y), g))
+    ref = oracle.fpT_cone3d(f32(y), shape, spacing, P)
+    assert rel(got, ref) < 1e-5
+    assert rel(got, host(B.pyro_fpT_cone3d(to_dev(y), g))) < 1e-6
+    noise = ph.random_sinogram((views, *det), 43)
+    assert rel(host(B.pyro_fpT_cone3d_ws(to_dev(noise), g)),
+               oracle.fpT_cone3d(f32(noise), shape, spacing, P)) < NOISE_TOL
+
+
 def test_fp_cone_staged_workspace_checks():
     c = CONE
     g = cone_geom(c)
