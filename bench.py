@@ -254,7 +254,7 @@ def run_gpu(args):
         "clocks": clocks,
     }
     if rank == 0 and args.cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds)
+        out["cpu_baseline"] = cpu_baseline(args.cpu_seconds, vol)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if dist:
@@ -313,42 +313,50 @@ def fp_sample_count(g) -> float:
     return total * len(ang) / len(ang[:: max(1, len(ang) // 16)])
 
 
-def cpu_sample(seconds: float):
+class CpuSample:
     """The oracle on a bounded sample of the workload: FP of `fv` views over
-    the full volume and FDK of a `zs`-slice slab (all views)."""
-    import oracle
+    the full volume and FDK of a `zs`-slice slab over all views.  The inputs
+    (phantom, matrices, a smooth sinogram) are made once."""
 
-    from paper_1904_13342_gb300 import phantoms as ph
+    def __init__(self, vol=None):
+        import oracle
 
-    g = geometry()
-    e = ph.random_ellipsoids(12, N * SPACING / 2, seed=0)
-    vol = ph.voxelize_ellipsoids(e, g.volume_shape, g.volume_spacing, dtype=torch.float64).numpy()
-    ang = g.view_angles()
-    P = oracle.circular_pmats(ang, SID, SDD, (NV, NU), (SV, SU))
-    fv = 36
-    t0 = time.perf_counter()
-    sino1 = oracle.fp_cone3d(vol, g.volume_spacing, (NV, NU), P[:fv])
-    t_fp = time.perf_counter() - t0
-    # FDK of a slab: a smooth synthetic sinogram stands in for the projections
-    y = ph.random_sinogram((VIEWS, NV, NU), 1, smooth=2)
-    zs = 48
-    kz = np.repeat(np.arange(N // 2 - zs // 2, N // 2 - zs // 2 + zs), N * N)
-    jj = np.tile(np.repeat(np.arange(N), N), zs)
-    ii = np.tile(np.arange(N), N * zs)
-    t0 = time.perf_counter()
-    oracle.fdk_voxels(y, g.volume_shape, g.volume_spacing, (SV, SU), ang, P, SID, SDD, g.angular_range / VIEWS, ii, jj,
-                      kz, kind=oracle.SHEPP_LOGAN, redund=oracle.REDUND_PARKER)
-    t_bp = time.perf_counter() - t0
-    units = N ** 3 * fv + N * N * zs * VIEWS
-    del sino1
-    return units / (t_fp + t_bp) / 1e9, {
-        "cores": oracle.num_threads(),
-        "sample": f"oracle FP of {fv} view(s) over the 256^3 volume + FDK of a {zs}-slice slab over all 248 views "
-                  f"({units:.3g} voxel-view units, {t_fp + t_bp:.1f} s)"}
+        from paper_1904_13342_gb300 import phantoms as ph
+
+        self.oracle = oracle
+        self.g = g = geometry()
+        if vol is None:
+            e = ph.random_ellipsoids(12, N * SPACING / 2, seed=0)
+            vol = ph.voxelize_ellipsoids(e, g.volume_shape, g.volume_spacing, dtype=torch.float32)
+        self.vol = np.ascontiguousarray(vol.double().cpu().numpy() if torch.is_tensor(vol) else vol, np.float64)
+        self.ang = g.view_angles()
+        self.P = oracle.circular_pmats(self.ang, SID, SDD, (NV, NU), (SV, SU))
+        # FDK of a slab: a smooth synthetic sinogram stands in for the projections
+        self.y = ph.random_sinogram((VIEWS, NV, NU), 1, smooth=2)
+
+    def run(self, fv: int, zs: int):
+        o, g = self.oracle, self.g
+        t0 = time.perf_counter()
+        o.fp_cone3d(self.vol, g.volume_spacing, (NV, NU), self.P[:fv])
+        t_fp = time.perf_counter() - t0
+        kz = np.repeat(np.arange(N // 2 - zs // 2, N // 2 - zs // 2 + zs), N * N)
+        jj = np.tile(np.repeat(np.arange(N), N), zs)
+        ii = np.tile(np.arange(N), N * zs)
+        t0 = time.perf_counter()
+        o.fdk_voxels(self.y, g.volume_shape, g.volume_spacing, (SV, SU), self.ang, self.P, SID, SDD,
+                     g.angular_range / VIEWS, ii, jj, kz, kind=o.SHEPP_LOGAN, redund=o.REDUND_PARKER)
+        t_bp = time.perf_counter() - t0
+        units = N ** 3 * fv + N * N * zs * VIEWS
+        return units / (t_fp + t_bp) / 1e9, {
+            "cores": o.num_threads(),
+            "sample": f"oracle FP of {fv} view(s) over the 256^3 volume + FDK of a {zs}-slice slab over all 248 "
+                      f"views ({units:.3g} voxel-view units, {t_fp + t_bp:.1f} s)"}
 
 
-def cpu_baseline(seconds: float):
-    v, info = cpu_sample(seconds)
+def cpu_baseline(seconds: float, vol=None):
+    """About `seconds` of oracle work (36 views + 48 slices take ~15 s on 16 Arm cores)."""
+    scale = max(seconds / 15.0, 0.1)
+    v, info = CpuSample(vol).run(max(1, round(36 * scale)), max(2, round(48 * scale)))
     return {"value": round(v, 6), "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"]}
 
 
@@ -356,13 +364,15 @@ def run_reference(args):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
+    # each step: about 3 s of oracle work, so that --steps K --warmup W ends in minutes
+    sample = CpuSample()
     vals = []
     for _ in range(args.warmup):
-        cpu_sample(args.cpu_seconds)
+        sample.run(8, 10)
     info = {}
     t0 = time.perf_counter()
     for _ in range(args.steps):
-        v, info = cpu_sample(args.cpu_seconds)
+        v, info = sample.run(8, 10)
         vals.append(v)
     wall = time.perf_counter() - t0
     value = statistics.mean(vals)
@@ -494,7 +504,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
-    ap.add_argument("--cpu-seconds", type=float, default=20.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--workload", default="fdk-256", choices=["fdk-256", "learned-init", "tv-512"])
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--tv-lambda", type=float, default=10.0)
