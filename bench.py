@@ -31,6 +31,9 @@ PSNRs and the fixed-budget comparison (CNN + 20 TV steps) ride along.
 496 views, 1240 x 960 detector, 1 % noise: seconds per gradient step after
 `--warmup` steps, FP32 against FP16 volume storage for the projector, and
 the error on the central 64^3 crop.
+
+`--workload configs` times the 2D workloads (128^2 parallel beam; a batch of
+16 512^2 fan-beam phantoms) on the GPU and through the oracle.
 """
 from __future__ import annotations
 
@@ -497,6 +500,119 @@ def run_tv512(args):
     print(json.dumps(line), flush=True)
 
 
+def run_configs(args):
+    """The two 2D workloads on the GPU (CUDA events, median of 10 after 3
+    warm-ups) and through the FP64 oracle on the host cores (one run):
+    128^2 parallel beam (180 views, 183 bins) and a batch of 16 512^2
+    fan-beam phantoms (360 views, 1024 bins, SID 750, SDD 1200, step 0.25 mm).
+    Units: FP samples/s, BP voxel-view updates/s (GUPS = 1e9 of them)."""
+    import math
+
+    import oracle
+
+    from paper_1904_13342_gb300 import binding as B
+    from paper_1904_13342_gb300 import phantoms as ph
+    from paper_1904_13342_gb300.geometry import FanGeometry2D, ParallelGeometry2D
+
+    dev = torch.device("cuda:0")
+    stream = torch.cuda.current_stream(dev)
+
+    def gpu_ms(fn):
+        for _ in range(3):
+            fn()
+        ts = []
+        for _ in range(10):
+            a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            fn()
+            b.record(stream)
+            torch.cuda.synchronize(dev)
+            ts.append(a.elapsed_time(b))
+        return statistics.median(ts)
+
+    def cpu_s(fn):
+        t0 = time.perf_counter()
+        fn()
+        return time.perf_counter() - t0
+
+    def samples2d(g, n_img):
+        """samples the projector visits: chord length / (dt |g|) summed over rays (host, FP64)"""
+        ny, nx = g.volume_shape
+        sy, sx = g.volume_spacing
+        half = np.array([0.5 * (nx + 1) * sx, 0.5 * (ny + 1) * sy])
+        u = (np.arange(g.detector_shape) - 0.5 * (g.detector_shape - 1)) * g.detector_spacing
+        dt = g.step if g.step > 0 else 0.5 * min(sx, sy)
+        total = 0.0
+        for b in g.view_angles():
+            c = np.array([math.cos(b), math.sin(b)])
+            eu = np.array([-math.sin(b), math.cos(b)])
+            if g.fan:
+                S = -g.sid * c
+                d = c[None] * g.sdd + u[:, None] * eu[None]
+                gl = np.linalg.norm(d, axis=1) / g.sdd
+                a = np.repeat(S[None], len(u), 0)
+            else:
+                d = np.repeat(c[None], len(u), 0)
+                gl = np.ones(len(u))
+                a = u[:, None] * eu[None]
+            d = d / np.linalg.norm(d, axis=1, keepdims=True)
+            lo, hi = np.full(len(u), -np.inf), np.full(len(u), np.inf)
+            for ax in range(2):
+                with np.errstate(divide="ignore", invalid="ignore"):
+                    t1, t2 = (-half[ax] - a[:, ax]) / d[:, ax], (half[ax] - a[:, ax]) / d[:, ax]
+                lo = np.maximum(lo, np.where(d[:, ax] != 0, np.minimum(t1, t2), -np.inf))
+                hi = np.minimum(hi, np.where(d[:, ax] != 0, np.maximum(t1, t2), np.inf))
+            total += np.sum(np.maximum(hi - lo, 0.0) / (dt * gl))
+        return total * n_img
+
+    out = {}
+    # 128^2 parallel beam
+    gp = ParallelGeometry2D((128, 128), (1.0, 1.0), 183, 1.0, 180, math.pi)
+    img = ph.voxelize_ellipses(ph.random_ellipses(10, 64.0, seed=0), (128, 128), (1.0, 1.0), device=dev,
+                               dtype=torch.float32)
+    sino = B.pyro_fp_par2d(img, gp)
+    ang = gp.view_angles()
+    i64, s64 = img.double().cpu().numpy(), sino.double().cpu().numpy()
+    ns, nb = samples2d(gp, 1), 128 * 128 * 180
+    t = {"fp": gpu_ms(lambda: B.pyro_fp_par2d(img, gp)), "bp": gpu_ms(lambda: B.pyro_bp_par2d(sino, gp)),
+         "fbp": gpu_ms(lambda: B.pyro_fbp_par2d(sino, gp, kind=B.RAMLAK))}
+    c = {"fp": cpu_s(lambda: oracle.fp_par2d(i64, (1.0, 1.0), 183, 1.0, ang)),
+         "bp": cpu_s(lambda: oracle.bp_par2d(s64, (128, 128), (1.0, 1.0), 1.0, ang)),
+         "fbp": cpu_s(lambda: oracle.fbp_par2d(s64, (128, 128), (1.0, 1.0), 1.0, ang))}
+    out["par2d_128"] = {"gpu_ms": {k: round(v, 4) for k, v in t.items()},
+                        "oracle_s": {k: round(v, 4) for k, v in c.items()},
+                        "fp_gsamples_per_s": round(ns / (t["fp"] * 1e-3) / 1e9, 2),
+                        "bp_gups": round(nb / (t["bp"] * 1e-3) / 1e9, 2),
+                        "oracle_fp_gsamples_per_s": round(ns / c["fp"] / 1e9, 4),
+                        "oracle_bp_gups": round(nb / c["bp"] / 1e9, 4)}
+    # 16 x 512^2 fan beam
+    gf = FanGeometry2D((512, 512), (0.5, 0.5), 1024, 1.0, 360, 2 * math.pi, 750.0, 1200.0, step=0.25)
+    imgs = torch.stack([ph.voxelize_ellipses(ph.random_ellipses(10, 128.0, seed=s), (512, 512), (0.5, 0.5),
+                                             device=dev, dtype=torch.float32) for s in range(16)])
+    sf = B.pyro_fp_fan2d(imgs, gf)
+    angf = gf.view_angles()
+    i0, s0 = imgs[0].double().cpu().numpy(), sf[0].double().cpu().numpy()
+    ns, nb = samples2d(gf, 16), 16 * 512 * 512 * 360
+    t = {"fp": gpu_ms(lambda: B.pyro_fp_fan2d(imgs, gf)), "fpT": gpu_ms(lambda: B.pyro_fpT_fan2d(sf, gf)),
+         "bp": gpu_ms(lambda: B.pyro_bp_fan2d(sf, gf, weight=B.W_INV_L2, scale=1.0))}
+    c = {"fp": cpu_s(lambda: oracle.fp_fan2d(i0, (0.5, 0.5), 1024, 1.0, angf, 750.0, 1200.0, step=0.25)),
+         "fpT": cpu_s(lambda: oracle.fpT_fan2d(s0, (512, 512), (0.5, 0.5), 1.0, angf, 750.0, 1200.0, step=0.25)),
+         "bp": cpu_s(lambda: oracle.bp_fan2d(s0, (512, 512), (0.5, 0.5), 1.0, angf, 750.0, 1200.0, 2, 1.0))}
+    out["fan2d_16x512"] = {"gpu_ms": {k: round(v, 4) for k, v in t.items()},
+                           "oracle_s_one_phantom": {k: round(v, 4) for k, v in c.items()},
+                           "fp_gsamples_per_s": round(ns / (t["fp"] * 1e-3) / 1e9, 2),
+                           "fpT_gsamples_per_s": round(ns / (t["fpT"] * 1e-3) / 1e9, 2),
+                           "bp_gups": round(nb / (t["bp"] * 1e-3) / 1e9, 2),
+                           "oracle_fp_gsamples_per_s": round(ns / 16 / c["fp"] / 1e9, 4),
+                           "oracle_bp_gups": round(nb / 16 / c["bp"] / 1e9, 4)}
+    line = {"metric": "2D workloads: FP samples/s and BP GUPS, GPU against the oracle", "value": out["fan2d_16x512"]["bp_gups"],
+            "unit": "GUPS (fan BP)", "higher_is_better": True, "n_gpus": 1, "dtype": "f32",
+            "data": "synthetic (seeded random ellipses)", "vs_baseline": None, "oracle_cores": oracle.num_threads(),
+            "config": {"workload": "2D parallel 128^2 x 180 views x 183 bins; fan 16 x 512^2 x 360 views x 1024 bins"},
+            "results": out}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -505,7 +621,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="fdk-256", choices=["fdk-256", "learned-init", "tv-512"])
+    ap.add_argument("--workload", default="fdk-256", choices=["fdk-256", "learned-init", "tv-512", "configs"])
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--tv-lambda", type=float, default=10.0)
     args = ap.parse_args()
@@ -513,6 +629,8 @@ def main():
         run_learned_init(args)
     elif args.workload == "tv-512":
         run_tv512(args)
+    elif args.workload == "configs":
+        run_configs(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

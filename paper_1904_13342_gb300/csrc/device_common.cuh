@@ -167,6 +167,17 @@ __device__ __forceinline__ float trilerp_interior(const T *vol, int stx, int sty
     return lerpf(lerpf(v00, v01, ay), lerpf(v10, v11, ay), ax);
 }
 
+// Bilinear interpolation at a point whose four taps are all inside the
+// image (no masking); strides in elements.
+template <typename T>
+__device__ __forceinline__ float bilerp_interior(const T *img, int stx, int sty, float fx, float fy)
+{
+    const float x0 = floorf(fx), y0 = floorf(fy);
+    const float ax = fx - x0, ay = fy - y0;
+    const T *b = img + ((int)x0 * stx + (int)y0 * sty);
+    return lerpf(lerpf(ld(b), ld(b + stx), ax), lerpf(ld(b + sty), ld(b + sty + stx), ax), ay);
+}
+
 // Restrict m to samples strictly inside [margin, n-1-margin] on one axis
 // (rounded inwards), the interior where trilerp_interior applies.
 __device__ __forceinline__ void clip_axis_interior(float p0, float q, int n, float &lo, float &hi)

@@ -76,8 +76,33 @@ __global__ void __launch_bounds__(128) fp2d_kernel(const T *__restrict__ vol, T 
     int m0, m1;
     range2d(r, p, m0, m1);
     const T *img = vol + (size_t)b * p.nx * p.ny;
+    // samples whose four taps are all inside the image take the unmasked path
+    float lo = (float)m0, hi = (float)m1;
+    clip_axis_interior(r.px, r.qx, p.nx, lo, hi);
+    clip_axis_interior(r.py, r.qy, p.ny, lo, hi);
+    int i0 = max(m0, (int)ceilf(lo)), i1 = min(m1, (int)floorf(hi));
+    if (i0 > i1) {  // no interior sample
+        i0 = m1 + 1;
+        i1 = m1;
+    }
     float acc = 0.0f;
-    for (int m = m0; m <= m1; ++m) {
+    for (int m = m0; m < i0; ++m) {
+        const float fm = (float)m;
+        acc += bilerp_zero(img, p.nx, p.ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
+    }
+    // two samples per iteration with separate partial sums (unrolled twice
+    // more by the compiler), so that several samples' loads are in flight
+    float acc2 = 0.0f;
+    int m = i0;
+#pragma unroll 2
+    for (; m + 1 <= i1; m += 2) {
+        const float fa = (float)m, fb = (float)(m + 1);
+        acc += bilerp_interior(img, 1, p.nx, fmaf(fa, r.qx, r.px), fmaf(fa, r.qy, r.py));
+        acc2 += bilerp_interior(img, 1, p.nx, fmaf(fb, r.qx, r.px), fmaf(fb, r.qy, r.py));
+    }
+    if (m <= i1) acc += bilerp_interior(img, 1, p.nx, fmaf((float)m, r.qx, r.px), fmaf((float)m, r.qy, r.py));
+    acc += acc2;
+    for (int m = max(i1 + 1, i0); m <= m1; ++m) {
         const float fm = (float)m;
         acc += bilerp_zero(img, p.nx, p.ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
     }
