@@ -167,6 +167,15 @@ __device__ __forceinline__ float trilerp_interior(const T *vol, int stx, int sty
     return lerpf(lerpf(v00, v01, ay), lerpf(v10, v11, ay), ax);
 }
 
+// floor(x) for |x| < 2^22 on the FMA pipe: x + 1.5 * 2^23 rounded toward
+// -inf is exactly 1.5 * 2^23 + floor(x) (unit spacing there), so the float
+// floor and the integer floor (low bits of the sum) both follow without a
+// conversion instruction.
+constexpr float kFloorMagic = 12582912.0f;  // 1.5 * 2^23, bit pattern 0x4B400000
+__device__ __forceinline__ float floor_magic(float x) { return __fadd_rd(x, kFloorMagic); }
+__device__ __forceinline__ float magic_to_float(float t) { return t - kFloorMagic; }
+__device__ __forceinline__ int magic_to_int(float t) { return __float_as_int(t) - 0x4B400000; }
+
 // Bilinear interpolation at a point whose four taps are all inside the
 // image (no masking); strides in elements.
 template <typename T>

@@ -132,9 +132,9 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__
 #pragma unroll
                 for (int zz = 0; zz < kBPZ; ++zz) {
                     const float ll = fmaf((float)(z0 + zz), dl, l0);
-                    const float fl0 = floorf(ll);
-                    const float av = ll - fl0;
-                    const TS *r0 = Sk + (int)fl0 * p.nu;
+                    const float tl = floor_magic(ll);
+                    const float av = ll - magic_to_float(tl);
+                    const TS *r0 = Sk + magic_to_int(tl) * p.nu;
                     const float t0 = fmaf(w0, ld(r0), w1 * ld(r0 + 1));
                     const float t1 = fmaf(w0, ld(r0 + p.nu), w1 * ld(r0 + p.nu + 1));
                     acc[zz] += lerpf(t0, t1, av);
