@@ -207,6 +207,21 @@ PYRO_API int pyro_filter_rows(const void *in, void *out, long n_rows, int nu, do
                               const float *custom_K, pyro_dtype dtype, void *stream);
 
 /* padded length pn used by pyro_filter_rows for a row of nu samples */
+/* --- Learnable redundancy weights (Section "Geometric Correction Weights":
+ * the paper proposes learning W_red of Eq. 5 like the filter).
+ * pyro_weights3d_table: sino [batch][V][nv][nu] *= (cosine ? W_cos : 1) *
+ * table[view][k], in place; table is a DEVICE FP32 array [V][nu] owned by
+ * the caller (one weight per view and detector column, as the short-scan
+ * weights are).  pyro_redundancy_grad: out[view][k] = sum over the batch and
+ * the rows of a * g (DEVICE FP32, [batch][V][nv][nu] each; out [V][nu]):
+ * with a = W_cos p and g the filtered back-projected gradient (the filter
+ * and the cosine weight are symmetric), the gradient of a loss with respect
+ * to the table.  Errors as for pyro_weights3d. */
+PYRO_API int pyro_weights3d_table(void *sino, int batch, const pyro_geom3d *g, const float *table, int cosine,
+                                  pyro_dtype dtype, void *stream);
+PYRO_API int pyro_redundancy_grad(const float *a, const float *g, float *out, int batch, int n_views, int nv, int nu,
+                                  void *stream);
+
 PYRO_API int pyro_filter_pad_length(int nu);
 
 /* The diagonal K[0..pn/2] of a built-in filter (Ram-Lak, ramp or

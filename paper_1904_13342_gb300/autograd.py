@@ -190,3 +190,75 @@ class FDK(torch.nn.Module):
 
     def forward(self, p: torch.Tensor) -> torch.Tensor:
         return _FDK.apply(p, self.K, self.g, self.redund)
+
+
+def parker_table(g: ConeGeometry3D, device) -> torch.Tensor:
+    """[V, nu] Parker weights of the geometry (computed by the library)."""
+    from dataclasses import replace
+
+    g1 = replace(g, detector_shape=(1, g.detector_shape[1]), _keep=[])
+    ones = torch.ones((g.number_of_projections, 1, g.detector_shape[1]), device=device, dtype=torch.float32)
+    return B.pyro_weights3d(ones, g1, cosine=False, redund=B.REDUND_PARKER)[:, 0].contiguous()
+
+
+class _FDKTable(torch.autograd.Function):
+    """x = A_bp F^H K F (W_cos * table) p, with the redundancy weights a
+    learnable [V, nu] table (Section "Geometric Correction Weights").
+    Backward: g_q = A_bp^T g_x; g_f = F^H K F g_q (the filter is symmetric);
+    g_table = sum over rows and batch of (W_cos p) g_f; g_p = W_cos table g_f."""
+
+    @staticmethod
+    def forward(ctx, p, table, K, g):
+        p = p.contiguous().float()
+        ctx.save_for_backward(p, table, K)
+        ctx.g = g
+        tau = g.detector_spacing[1] * g.sid / g.sdd
+        w = B.pyro_weights3d_table(p.clone(), g, table.detach(), cosine=True)
+        q = B.pyro_filter_rows(w, tau, B.FILTER_CUSTOM, custom_K=K.detach().contiguous())
+        return B.pyro_bp_cone3d(q, g, B.W_INV_L2, abs(g.angular_range) / g.number_of_projections)
+
+    @staticmethod
+    def backward(ctx, gx):
+        p, table, K = ctx.saved_tensors
+        g = ctx.g
+        tau = g.detector_spacing[1] * g.sid / g.sdd
+        gq = B.pyro_bpT_cone3d(gx.contiguous().float(), g, B.W_INV_L2,
+                               abs(g.angular_range) / g.number_of_projections)
+        gf = B.pyro_filter_rows(gq, tau, B.FILTER_CUSTOM, custom_K=K.detach().contiguous())
+        gp = gt = gK = None
+        if ctx.needs_input_grad[1]:
+            wc = B.pyro_weights3d(p.clone(), g, cosine=True, redund=B.REDUND_NONE)
+            gt = B.pyro_redundancy_grad(wc, gf)
+        if ctx.needs_input_grad[2]:
+            wp = B.pyro_weights3d_table(p.clone(), g, table.detach(), cosine=True)
+            nu = p.shape[-1]
+            gK = B.pyro_filter_grad_K(wp.reshape(-1, nu), gq.reshape(-1, nu))
+        if ctx.needs_input_grad[0]:
+            gp = B.pyro_weights3d_table(gf, g, table.detach(), cosine=True)
+        return gp, gt, gK, None
+
+
+class RedundancyFDK(torch.nn.Module):
+    """FDK (Eq. 5) whose redundancy weights W_red are a learnable [V, nu]
+    table; the filter K is fixed unless `learnable_filter`.  `init`:
+    "parker", "full" (1/2 everywhere) or a [V, nu] tensor."""
+
+    def __init__(self, g: ConeGeometry3D, kind: int = B.SHEPP_LOGAN, init="parker", learnable_filter: bool = False,
+                 device="cuda"):
+        super().__init__()
+        self.g = g
+        tau = g.detector_spacing[1] * g.sid / g.sdd
+        if isinstance(init, torch.Tensor):
+            t = init.to(device=device, dtype=torch.float32)
+        elif init == "parker":
+            t = parker_table(g, device)
+        elif init == "full":
+            t = torch.full((g.number_of_projections, g.detector_shape[1]), 0.5, device=device)
+        else:
+            raise ValueError("init must be 'parker', 'full' or a tensor")
+        self.table = torch.nn.Parameter(t.clone())
+        self.K = torch.nn.Parameter(filter_taps(kind, g.detector_shape[1], tau, device),
+                                    requires_grad=learnable_filter)
+
+    def forward(self, p: torch.Tensor) -> torch.Tensor:
+        return _FDKTable.apply(p, self.table, self.K, self.g)

@@ -56,6 +56,8 @@ _SIGS = {
     "pyro_fpT_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
     "pyro_fpT_cone3d_workspace_bytes": [_G3],
     "pyro_cone_projection_matrices": [_G3, _VP],
+    "pyro_weights3d_table": [_VP, _I, _G3, _VP, _I, _I, _VP],
+    "pyro_redundancy_grad": [_VP, _VP, _VP, _I, _I, _I, _I, _VP],
     "pyro_fpT_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
     "pyro_bp_par2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
     "pyro_bp_fan2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
@@ -303,6 +305,34 @@ def pyro_weights2d(sino: torch.Tensor, g: Geometry2D, cosine=True, redund=REDUND
         _check(lib().pyro_weights2d(_ptr(s), s.shape[0], ctypes.byref(cg), int(bool(cosine)), int(redund),
                                     _DTYPES[s.dtype], _stream(s)))
     return sino
+
+
+def pyro_weights3d_table(sino: torch.Tensor, g: ConeGeometry3D, table: torch.Tensor, cosine=True) -> torch.Tensor:
+    """In place: sino *= (cosine ? W_cos : 1) * table[view][column]; returns ``sino``."""
+    s, _ = _batched(_dev(sino, "sinogram"), 3, "sinogram")
+    _shape_check(s, g.sinogram_shape, "sinogram")
+    t = _dev(table, "table")
+    if t.dtype != torch.float32 or tuple(t.shape) != (g.number_of_projections, g.detector_shape[1]):
+        raise ValueError("table must be float32 [n_views, nu]")
+    t = t.contiguous()
+    cg = g.to_c()
+    with torch.cuda.device(s.device):
+        _check(lib().pyro_weights3d_table(_ptr(s), s.shape[0], ctypes.byref(cg), _ptr(t), int(bool(cosine)),
+                                          _DTYPES[s.dtype], _stream(s)))
+    return sino
+
+
+def pyro_redundancy_grad(a: torch.Tensor, g: torch.Tensor) -> torch.Tensor:
+    """[V, nu] = sum over batch and rows of a * g; a, g float32 [..., V, nv, nu]."""
+    a_, g_ = _dev(a, "a").contiguous(), _dev(g, "g").contiguous()
+    if a_.shape != g_.shape or a_.dtype != torch.float32 or g_.dtype != torch.float32 or a_.dim() < 3:
+        raise ValueError("a and g must be float32 tensors of one shape [..., V, nv, nu]")
+    V, nv, nu = a_.shape[-3:]
+    batch = a_.numel() // (V * nv * nu)
+    out = torch.empty((V, nu), device=a_.device, dtype=torch.float32)
+    with torch.cuda.device(a_.device):
+        _check(lib().pyro_redundancy_grad(_ptr(a_), _ptr(g_), _ptr(out), batch, V, nv, nu, _stream(a_)))
+    return out
 
 
 def pyro_weights3d(sino: torch.Tensor, g: ConeGeometry3D, cosine=True, redund=REDUND_NONE) -> torch.Tensor:

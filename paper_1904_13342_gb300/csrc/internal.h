@@ -134,6 +134,10 @@ cudaError_t launch_bp3d(const void *sino, void *vol, int batch, const BP3DParams
                         pyro_dtype vol_dt, cudaStream_t s);
 cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const BP3DParams &p, cudaStream_t s);
 
+cudaError_t launch_weights_table(void *sino, int batch, const WeightParams &w, const float *table, pyro_dtype dt,
+                                 cudaStream_t s);
+cudaError_t launch_redundancy_grad(const float *a, const float *g, float *out, int batch, int n_views, int nv, int nu,
+                                   cudaStream_t s);
 cudaError_t launch_weights(void *sino, int batch, const WeightParams &w, const BetaTable &beta, pyro_dtype dt,
                            cudaStream_t s);
 // rows in (dtype in_dt) -> rows out (dtype out_dt); custom_K overrides p.K when non-null

@@ -63,6 +63,45 @@ __global__ void weights_kernel(T *__restrict__ sino, long n, const __grid_consta
     }
 }
 
+// Cosine weight times a redundancy table W_red[view][k] (learnable weights,
+// one value per view and detector column), in place.
+template <typename T>
+__global__ void weights_table_kernel(T *__restrict__ sino, long n, const __grid_constant__ WeightParams w,
+                                     const float *__restrict__ table)
+{
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const int k = (int)(e % w.nu);
+        const long r = e / w.nu;
+        const int l = (int)(r % w.nv);
+        const int view = (int)((r / w.nv) % w.n_views);
+        float f = table[(size_t)view * w.nu + k];
+        if (w.cosine) f *= cosine_weight(w, ((float)k - w.cu) * w.su, ((float)l - w.cv) * w.sv);
+        sino[e] = to_storage<T>(to_float<T>(sino[e]) * f);
+    }
+}
+
+// out[view][k] = sum over the batch and the rows l of a[b][view][l][k] g[b][view][l][k]:
+// one thread per (view, k), reading rows along k (coalesced)
+__global__ void __launch_bounds__(256) redundancy_grad_kernel(const float *__restrict__ a,
+                                                              const float *__restrict__ g, float *__restrict__ out,
+                                                              int batch, int n_views, int nv, int nu)
+{
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    const int view = blockIdx.y;
+    if (k >= nu) return;
+    float s0 = 0.0f, s1 = 0.0f;
+    for (int b = 0; b < batch; ++b) {
+        const size_t base = (((size_t)b * n_views + view) * nv) * nu + k;
+        int l = 0;
+        for (; l + 1 < nv; l += 2) {
+            s0 = fmaf(a[base + (size_t)l * nu], g[base + (size_t)l * nu], s0);
+            s1 = fmaf(a[base + (size_t)(l + 1) * nu], g[base + (size_t)(l + 1) * nu], s1);
+        }
+        if (l < nv) s0 = fmaf(a[base + (size_t)l * nu], g[base + (size_t)l * nu], s0);
+    }
+    out[(size_t)view * nu + k] = s0 + s1;
+}
+
 __device__ __forceinline__ float2 cmul(float2 a, float2 b)
 {
     return make_float2(fmaf(a.x, b.x, -a.y * b.y), fmaf(a.x, b.y, a.y * b.x));
@@ -441,6 +480,33 @@ cudaError_t launch_weights(void *sino, int batch, const WeightParams &w, const B
         weights_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>((__nv_bfloat16 *)sino, n, w, beta);
         break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_weights_table(void *sino, int batch, const WeightParams &w, const float *table, pyro_dtype dt,
+                                 cudaStream_t s)
+{
+    const long n = (long)batch * w.n_views * w.nv * w.nu;
+    const long blocks = std::min<long>((n + 255) / 256, (long)device_sm_count() * 16);
+    switch (dt) {
+    case PYRO_F32:
+        weights_table_kernel<float><<<(unsigned)blocks, 256, 0, s>>>((float *)sino, n, w, table);
+        break;
+    case PYRO_F16:
+        weights_table_kernel<__half><<<(unsigned)blocks, 256, 0, s>>>((__half *)sino, n, w, table);
+        break;
+    case PYRO_BF16:
+        weights_table_kernel<__nv_bfloat16><<<(unsigned)blocks, 256, 0, s>>>((__nv_bfloat16 *)sino, n, w, table);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_redundancy_grad(const float *a, const float *g, float *out, int batch, int n_views, int nv, int nu,
+                                   cudaStream_t s)
+{
+    dim3 grid((nu + 255) / 256, n_views);
+    redundancy_grad_kernel<<<grid, 256, 0, s>>>(a, g, out, batch, n_views, nv, nu);
     return cudaGetLastError();
 }
 

@@ -971,6 +971,36 @@ PYRO_API int pyro_weights3d(void *sino, int batch, const pyro_geom3d *g, int cos
     return PYRO_OK;
 }
 
+PYRO_API int pyro_weights3d_table(void *sino, int batch, const pyro_geom3d *g, const float *table, int cosine,
+                                  pyro_dtype dtype, void *stream)
+{
+    if (int e = check_io(sino, sino, batch, dtype)) return e;
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    if (batch > 0) PYRO_CHECK(table != nullptr, "table is NULL");
+    WeightParams w;
+    static thread_local BetaTable bt;
+    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, cosine, PYRO_REDUND_NONE, w, bt)) return e;
+    if (batch == 0) return PYRO_OK;
+    PYRO_CUDA(launch_weights_table(sino, batch, w, table, dtype, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_redundancy_grad(const float *a, const float *g, float *out, int batch, int n_views, int nv, int nu,
+                                  void *stream)
+{
+    PYRO_CHECK(batch >= 0 && n_views > 0 && nv > 0 && nu > 0, "sizes must be positive (batch >= 0)");
+    PYRO_CHECK(n_views <= 65535, "n_views=%d above 65535", n_views);
+    PYRO_CHECK(out != nullptr, "out is NULL");
+    if (batch > 0) PYRO_CHECK(a != nullptr && g != nullptr, "input pointer is NULL");
+    if (batch == 0) {
+        PYRO_CUDA(cudaMemsetAsync(out, 0, sizeof(float) * (size_t)n_views * nu, as_stream(stream)));
+        return PYRO_OK;
+    }
+    PYRO_CUDA(launch_redundancy_grad(a, g, out, batch, n_views, nv, nu, as_stream(stream)));
+    return PYRO_OK;
+}
+
 PYRO_API int pyro_filter_pad_length(int nu)
 {
     return nu > 0 ? pad_length(nu) : 0;
