@@ -478,7 +478,7 @@ def run_tv512(args):
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     with ClockSampler(0) as clk:
         a.record(stream)
-        res = tv_reconstruct(p, g, args.steps, lam, eps, L_est=L_est, x0=warm.x)
+        res = tv_reconstruct(p, g, args.steps, lam, eps, L_est=L_est, x0=warm.x, graph=True)
         b.record(stream)
         torch.cuda.synchronize(dev)
     step_s = a.elapsed_time(b) / 1e3 / args.steps

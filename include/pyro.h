@@ -270,6 +270,18 @@ PYRO_API int pyro_axpby(const float *x, float *y, long n, float a, float b, void
 /* out[0] = sum a_i b_i over n FP32 device values; out is a DEVICE float,
  * reduced in FP32 (block sums, then FP32 atomics) */
 PYRO_API int pyro_dot(const float *a, const float *b, long n, float *out, void *stream);
+/* --- The Barzilai-Borwein step of the iteration, kept on the device (no
+ * host read of a scalar, so that an iteration can be captured in a CUDA
+ * graph).  pyro_bb_dots: dots[0] = |x - x_prev|^2, dots[1] =
+ * (x - x_prev).(g - g_prev) (DEVICE float[2], overwritten; FP32 reduction).
+ * pyro_bb_update: alpha = alpha0 when `first` (or when dots[1] <= 0), else
+ * dots[0] / dots[1] clamped to [0, alpha_max]; then x_prev = x, g_prev = g,
+ * x -= alpha g over n FP32 device values; alpha_out (DEVICE float, may be
+ * NULL) receives the alpha used. */
+PYRO_API int pyro_bb_dots(const float *x, const float *x_prev, const float *g, const float *g_prev, long n,
+                          float *dots, void *stream);
+PYRO_API int pyro_bb_update(float *x, float *x_prev, const float *g, float *g_prev, long n, const float *dots,
+                            float alpha0, float alpha_max, int first, float *alpha_out, void *stream);
 
 /* --- Residual 3D CNN used as a learned initialiser of the iterative
  * reconstruction.  The paper has no network of its own; its "learned parts"

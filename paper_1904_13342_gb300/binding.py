@@ -57,6 +57,8 @@ _SIGS = {
     "pyro_fpT_cone3d_workspace_bytes": [_G3],
     "pyro_cone_projection_matrices": [_G3, _VP],
     "pyro_weights3d_table": [_VP, _I, _G3, _VP, _I, _I, _VP],
+    "pyro_bb_dots": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, _VP],
+    "pyro_bb_update": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, ctypes.c_float, ctypes.c_float, _I, _VP, _VP],
     "pyro_redundancy_grad": [_VP, _VP, _VP, _I, _I, _I, _I, _VP],
     "pyro_fpT_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
     "pyro_bp_par2d": [_VP, _VP, _I, _G2, _I, _F, _I, _VP],
@@ -494,6 +496,29 @@ def pyro_dot(a: torch.Tensor, b: torch.Tensor, out: Optional[torch.Tensor] = Non
     with torch.cuda.device(a.device):
         _check(lib().pyro_dot(_ptr(a), _ptr(b), a.numel(), _ptr(o), _stream(a)))
     return o
+
+
+def pyro_bb_dots(x, x_prev, g, g_prev, dots: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """[|x - x_prev|^2, (x - x_prev).(g - g_prev)] as a float32 device tensor of 2."""
+    t = [_f32(a, n) for a, n in ((x, "x"), (x_prev, "x_prev"), (g, "g"), (g_prev, "g_prev"))]
+    if len({a.numel() for a in t}) != 1:
+        raise ValueError("x, x_prev, g, g_prev must have one size")
+    o = torch.empty(2, device=t[0].device, dtype=torch.float32) if dots is None else dots
+    with torch.cuda.device(t[0].device):
+        _check(lib().pyro_bb_dots(*(_ptr(a) for a in t), t[0].numel(), _ptr(o), _stream(t[0])))
+    return o
+
+
+def pyro_bb_update(x, x_prev, g, g_prev, dots: Optional[torch.Tensor], alpha0: float, alpha_max: float, first: bool,
+                   alpha_out: Optional[torch.Tensor] = None):
+    """x_prev = x, g_prev = g, x -= alpha g with alpha chosen on the device."""
+    t = [_f32(a, n) for a, n in ((x, "x"), (x_prev, "x_prev"), (g, "g"), (g_prev, "g_prev"))]
+    if len({a.numel() for a in t}) != 1:
+        raise ValueError("x, x_prev, g, g_prev must have one size")
+    with torch.cuda.device(t[0].device):
+        _check(lib().pyro_bb_update(_ptr(t[0]), _ptr(t[1]), _ptr(t[2]), _ptr(t[3]), t[0].numel(), _ptr(dots),
+                                    float(alpha0), float(alpha_max), int(bool(first)), _ptr(alpha_out),
+                                    _stream(t[0])))
 
 
 # ------------------------------------------------------------ residual CNN --

@@ -134,6 +134,10 @@ cudaError_t launch_bp3d(const void *sino, void *vol, int batch, const BP3DParams
                         pyro_dtype vol_dt, cudaStream_t s);
 cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const BP3DParams &p, cudaStream_t s);
 
+cudaError_t launch_bb_dots(const float *x, const float *xp, const float *g, const float *gp, long n, float *dots,
+                           cudaStream_t s);
+cudaError_t launch_bb_update(float *x, float *xp, const float *g, float *gp, long n, const float *dots, float alpha0,
+                             float alpha_max, int first, float *alpha_out, cudaStream_t s);
 cudaError_t launch_weights_table(void *sino, int batch, const WeightParams &w, const float *table, pyro_dtype dt,
                                  cudaStream_t s);
 cudaError_t launch_redundancy_grad(const float *a, const float *g, float *out, int batch, int n_views, int nv, int nu,

@@ -102,7 +102,69 @@ __global__ void __launch_bounds__(kTVThreads) dot_kernel(const float *__restrict
     if (threadIdx.x == 0) atomicAdd(out, s);
 }
 
+// |x - x_prev|^2 and (x - x_prev).(g - g_prev) in one pass: the two scalars
+// of a Barzilai-Borwein step, without forming the differences
+__global__ void __launch_bounds__(kTVThreads) bb_dots_kernel(const float *__restrict__ x,
+                                                             const float *__restrict__ xp,
+                                                             const float *__restrict__ g,
+                                                             const float *__restrict__ gp, long n,
+                                                             float *__restrict__ dots)
+{
+    float ss = 0.0f, sy = 0.0f;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const float s = x[e] - xp[e];
+        ss = fmaf(s, s, ss);
+        sy = fmaf(s, g[e] - gp[e], sy);
+    }
+    ss = block_sum(ss);
+    __syncthreads();  // block_sum's shared array is reused
+    sy = block_sum(sy);
+    if (threadIdx.x == 0) {
+        atomicAdd(dots, ss);
+        atomicAdd(dots + 1, sy);
+    }
+}
+
+// alpha = first ? alpha0 : clamp(ss / sy, 0, alpha_max) (alpha0 when sy <= 0);
+// x_prev = x, g_prev = g, x -= alpha g
+__global__ void bb_update_kernel(float *__restrict__ x, float *__restrict__ xp, const float *__restrict__ g,
+                                 float *__restrict__ gp, long n, const float *__restrict__ dots, float alpha0,
+                                 float alpha_max, int first, float *__restrict__ alpha_out)
+{
+    float alpha = alpha0;
+    if (!first) {
+        const float ss = dots[0], sy = dots[1];
+        alpha = sy > 0.0f ? fminf(fmaxf(ss / sy, 0.0f), alpha_max) : alpha0;
+    }
+    if (alpha_out && blockIdx.x == 0 && threadIdx.x == 0) *alpha_out = alpha;
+    for (long e = blockIdx.x * (long)blockDim.x + threadIdx.x; e < n; e += (long)gridDim.x * blockDim.x) {
+        const float xe = x[e], ge = g[e];
+        xp[e] = xe;
+        gp[e] = ge;
+        x[e] = fmaf(-alpha, ge, xe);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_bb_dots(const float *x, const float *xp, const float *g, const float *gp, long n, float *dots,
+                           cudaStream_t s)
+{
+    cudaError_t e = cudaMemsetAsync(dots, 0, 2 * sizeof(float), s);
+    if (e != cudaSuccess) return e;
+    const long blocks = std::min<long>((n + kTVThreads - 1) / kTVThreads, (long)device_sm_count() * 8);
+    bb_dots_kernel<<<(unsigned)std::max<long>(blocks, 1), kTVThreads, 0, s>>>(x, xp, g, gp, n, dots);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bb_update(float *x, float *xp, const float *g, float *gp, long n, const float *dots, float alpha0,
+                             float alpha_max, int first, float *alpha_out, cudaStream_t s)
+{
+    const long blocks = std::min<long>((n + 255) / 256, (long)device_sm_count() * 16);
+    bb_update_kernel<<<(unsigned)std::max<long>(blocks, 1), 256, 0, s>>>(x, xp, g, gp, n, dots, alpha0, alpha_max,
+                                                                         first, alpha_out);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_tv(const float *x, float *grad, const float *base, float alpha, float lambda, float *value,
                       int batch, int nz, int ny, int nx, float eps, cudaStream_t s)

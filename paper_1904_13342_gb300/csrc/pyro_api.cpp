@@ -1176,6 +1176,33 @@ PYRO_API int pyro_dot(const float *a, const float *b, long n, float *out, void *
     return PYRO_OK;
 }
 
+PYRO_API int pyro_bb_dots(const float *x, const float *x_prev, const float *g, const float *g_prev, long n,
+                          float *dots, void *stream)
+{
+    PYRO_CHECK(n >= 0 && dots != nullptr, "bad arguments");
+    if (n > 0) PYRO_CHECK(x && x_prev && g && g_prev, "NULL pointer");
+    if (n == 0) {
+        PYRO_CUDA(cudaMemsetAsync(dots, 0, 2 * sizeof(float), as_stream(stream)));
+        return PYRO_OK;
+    }
+    PYRO_CUDA(launch_bb_dots(x, x_prev, g, g_prev, n, dots, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_bb_update(float *x, float *x_prev, const float *g, float *g_prev, long n, const float *dots,
+                            float alpha0, float alpha_max, int first, float *alpha_out, void *stream)
+{
+    PYRO_CHECK(n >= 0, "n must be >= 0");
+    PYRO_CHECK(std::isfinite(alpha0) && std::isfinite(alpha_max) && alpha0 >= 0 && alpha_max >= 0,
+               "step bounds must be finite and >= 0");
+    if (!first) PYRO_CHECK(dots != nullptr, "dots is NULL");
+    if (n > 0) PYRO_CHECK(x && x_prev && g && g_prev, "NULL pointer");
+    if (n == 0) return PYRO_OK;
+    PYRO_CUDA(launch_bb_update(x, x_prev, g, g_prev, n, dots, alpha0, alpha_max, first, alpha_out,
+                               as_stream(stream)));
+    return PYRO_OK;
+}
+
 static int conv_dims_ok(int batch, int nz, int ny, int nx, int cin, int cout)
 {
     PYRO_CHECK(batch >= 0 && nz > 0 && ny > 0 && nx > 0, "bad activation shape");

@@ -128,7 +128,7 @@ def choose_lambda(maker: PairMaker, seeds: Sequence[int], lams: Sequence[float],
     mask = fov_mask(maker.setup, maker.dev)
     out = {}
     for lam in lams:
-        vals = [psnr(tv_reconstruct(sino[i], maker.g, n_iter, lam, eps, L_est=L_est).x, truth[i], mask)
+        vals = [psnr(tv_reconstruct(sino[i], maker.g, n_iter, lam, eps, L_est=L_est, graph=True).x, truth[i], mask)
                 for i in range(len(seeds))]
         out[lam] = float(np.mean(vals))
     return out
@@ -192,14 +192,14 @@ def ab_test(maker: PairMaker, net: ResidualCNN, seeds: Sequence[int], lam: float
     def learned(k):
         fdk = maker.fdk(sino)
         init = torch.cat([net.forward(fdk[i:i + cnn_batch].contiguous()) for i in range(0, n, cnn_batch)])
-        xs = [tv_reconstruct(sino[i], maker.g, k, lam, eps, L_est=L_est, x0=init[i]).x for i in range(n)]
+        xs = [tv_reconstruct(sino[i], maker.g, k, lam, eps, L_est=L_est, x0=init[i], graph=True).x for i in range(n)]
         return fdk, init, xs
 
     (fdk, init, xs), res.seconds_learned = _sync_time(lambda: learned(short_iter))
     plain, res.seconds_plain = _sync_time(
-        lambda: [tv_reconstruct(sino[i], maker.g, long_iter, lam, eps, L_est=L_est).x for i in range(n)])
+        lambda: [tv_reconstruct(sino[i], maker.g, long_iter, lam, eps, L_est=L_est, graph=True).x for i in range(n)])
     short, res.seconds_short_tv = _sync_time(
-        lambda: [tv_reconstruct(sino[i], maker.g, short_iter, lam, eps, L_est=L_est).x for i in range(n)])
+        lambda: [tv_reconstruct(sino[i], maker.g, short_iter, lam, eps, L_est=L_est, graph=True).x for i in range(n)])
     for i in range(n):
         res.psnr_fdk.append(psnr(fdk[i], truth[i], mask))
         res.psnr_cnn.append(psnr(init[i], truth[i], mask))

@@ -10,8 +10,9 @@ specified.  Here it is gradient descent with Barzilai-Borwein steps:
   clamped to [0, 10 / L_est],
   x_{k+1} = x_k - alpha_k g_k.
 Every vector operation is a library kernel (FP, exact adjoint, pyro_tv,
-pyro_axpby, pyro_dot); only the two scalars of each BB step come back to
-the host.
+pyro_axpby, and the BB step pyro_bb_dots / pyro_bb_update, which chooses
+alpha on the device); an iteration reads nothing back to the host, so it can
+be captured in a CUDA graph and replayed.
 """
 from __future__ import annotations
 
@@ -67,45 +68,63 @@ def estimate_lipschitz(g, shape, device, iters: int = 20, seed: int = 0) -> floa
 
 def tv_reconstruct(p: torch.Tensor, g, n_iter: int, lam: float, eps: float, L_est: Optional[float] = None,
                    x0: Optional[torch.Tensor] = None, clamp: float = 10.0, track_objective: bool = False,
-                   callback=None) -> TVResult:
+                   callback=None, graph: bool = False) -> TVResult:
     """Minimise |A x - p|^2 + lam TV(x) (Eq. 7); p is one FP32 sinogram.
-    `callback(k, x)`, when given, sees the iterate after each step k."""
+
+    The step size is chosen on the device (pyro_bb_dots / pyro_bb_update), so
+    an iteration reads nothing back to the host unless `track_objective`
+    (objective and step per iteration) or `callback(k, x)` asks for it.  With
+    `graph=True` (and neither of those) one iteration is captured in a CUDA
+    graph after two eager ones and replayed for the rest."""
     A, AT = _ops(g)
     shape = tuple(g.volume_shape)
     dev = p.device
     if L_est is None:
         L_est = estimate_lipschitz(g, shape, dev)
     x = torch.zeros(shape, device=dev, dtype=torch.float32) if x0 is None else x0.clone().float()
-    x_prev = torch.empty_like(x)
-    g_prev = torch.empty_like(x)
+    x_prev = torch.zeros_like(x)
+    g_prev = torch.zeros_like(x)
     r = torch.empty_like(p)
+    dots = torch.zeros(2, device=dev, dtype=torch.float32)
+    alpha = torch.zeros(1, device=dev, dtype=torch.float32)
+    alpha0, alpha_max = 1.0 / L_est, clamp / L_est
     res = TVResult(x)
-    for k in range(n_iter):
-        r = A(x, out=r) if isinstance(g, ConeGeometry3D) else A(x)
-        B.pyro_axpby(p, r, -1.0, 1.0)  # r = A x - p
-        gd = AT(r)
+    cone = isinstance(g, ConeGeometry3D)
+
+    def step(first: bool):
+        rr = A(x, out=r) if cone else A(x)
+        B.pyro_axpby(p, rr, -1.0, 1.0)  # r = A x - p
+        gd = AT(rr)
         grad, tvv = B.pyro_tv(x, eps, lam, base=gd, alpha=2.0, want_value=track_objective)
         if track_objective:
-            res.objective.append(float(B.pyro_dot(r, r).item()) + lam * float(tvv.item()))
-        if k == 0:
-            alpha = 1.0 / L_est
-        else:
-            B.pyro_axpby(x, x_prev, 1.0, -1.0)  # s = x_k - x_{k-1}
-            B.pyro_axpby(grad, g_prev, 1.0, -1.0)  # dy = g_k - g_{k-1}
-            ss = float(B.pyro_dot(x_prev, x_prev).item())
-            sy = float(B.pyro_dot(x_prev, g_prev).item())
-            alpha = ss / sy if sy > 0 else 1.0 / L_est
-            alpha = min(max(alpha, 0.0), clamp / L_est)
-        res.steps.append(alpha)
-        B.pyro_axpby(x, x_prev, 1.0, 0.0)
-        B.pyro_axpby(grad, g_prev, 1.0, 0.0)
-        B.pyro_axpby(grad, x, -alpha, 1.0)
-        if callback is not None:
-            callback(k + 1, x)
+            res.objective.append(float(B.pyro_dot(rr, rr).item()) + lam * float(tvv.item()))
+        if not first:
+            B.pyro_bb_dots(x, x_prev, grad, g_prev, dots)
+        B.pyro_bb_update(x, x_prev, grad, g_prev, dots, alpha0, alpha_max, first, alpha)
+        if track_objective:
+            res.steps.append(float(alpha.item()))
+
+    if graph and n_iter > 2 and not track_objective and callback is None:
+        step(True)
+        side = torch.cuda.Stream(device=dev)
+        side.wait_stream(torch.cuda.current_stream(dev))
+        with torch.cuda.stream(side):
+            step(False)
+        torch.cuda.current_stream(dev).wait_stream(side)
+        cg = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(cg):
+            step(False)
+        for _ in range(n_iter - 2):
+            cg.replay()
+    else:
+        for k in range(n_iter):
+            step(k == 0)
+            if callback is not None:
+                callback(k + 1, x)
     if track_objective:
-        r = A(x, out=r) if isinstance(g, ConeGeometry3D) else A(x)
-        B.pyro_axpby(p, r, -1.0, 1.0)
+        rr = A(x, out=r) if cone else A(x)
+        B.pyro_axpby(p, rr, -1.0, 1.0)
         _, tvv = B.pyro_tv(x, eps, lam, want_grad=False)
-        res.objective.append(float(B.pyro_dot(r, r).item()) + lam * float(tvv.item()))
+        res.objective.append(float(B.pyro_dot(rr, rr).item()) + lam * float(tvv.item()))
     res.x = x
     return res
