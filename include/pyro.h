@@ -349,6 +349,11 @@ PYRO_API int pyro_fdk_noalloc(const void *sino, void *vol, int batch, const pyro
                               const float *custom_K, pyro_redund redund, pyro_dtype dtype, void *stream);
 
 /* thread-local message describing the last non-OK status of this thread */
+/* --- Waits for the stream and reports what happened on it: PYRO_OK, or
+ * PYRO_ECUDA with the CUDA error's text in pyro_last_error.  The library's
+ * kernels hold no device-side waits and keep no device status word, so the
+ * stream's own error state is all there is to drain. */
+PYRO_API int pyro_sync_status(void *stream);
 PYRO_API const char *pyro_last_error(void);
 /* library version string */
 PYRO_API const char *pyro_version(void);

@@ -58,6 +58,7 @@ _SIGS = {
     "pyro_cone_projection_matrices": [_G3, _VP],
     "pyro_weights3d_table": [_VP, _I, _G3, _VP, _I, _I, _VP],
     "pyro_bb_dots": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, _VP],
+    "pyro_sync_status": [_VP],
     "pyro_bb_update": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, ctypes.c_float, ctypes.c_float, _I, _VP, _VP],
     "pyro_redundancy_grad": [_VP, _VP, _VP, _I, _I, _I, _I, _VP],
     "pyro_fpT_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
@@ -519,6 +520,13 @@ def pyro_bb_update(x, x_prev, g, g_prev, dots: Optional[torch.Tensor], alpha0: f
         _check(lib().pyro_bb_update(_ptr(t[0]), _ptr(t[1]), _ptr(t[2]), _ptr(t[3]), t[0].numel(), _ptr(dots),
                                     float(alpha0), float(alpha_max), int(bool(first)), _ptr(alpha_out),
                                     _stream(t[0])))
+
+
+def pyro_sync_status(device=None) -> None:
+    """Wait for the current stream of `device`; raise PyroError if it faulted."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        _check(lib().pyro_sync_status(ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
 
 
 # ------------------------------------------------------------ residual CNN --

@@ -1295,6 +1295,15 @@ PYRO_API int pyro_cnn_adam(float *p, const float *g, float *m, float *v, void *p
     return PYRO_OK;
 }
 
+PYRO_API int pyro_sync_status(void *stream)
+{
+    // the kernels hold no device-side waits and set no status word, so the
+    // device state to drain is the stream's own: any fault surfaces here
+    PYRO_CUDA(cudaStreamSynchronize(as_stream(stream)));
+    PYRO_CUDA(cudaGetLastError());
+    return PYRO_OK;
+}
+
 PYRO_API const char *pyro_last_error(void)
 {
     return g_last_error.c_str();

@@ -13,7 +13,7 @@ from __future__ import annotations
 
 import ctypes
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 from typing import Optional, Sequence
 
 import numpy as np
@@ -78,6 +78,19 @@ class Geometry2D:
             return np.asarray(self.angles, dtype=np.float64)
         return np.arange(self.number_of_projections) * (self.angular_range / self.number_of_projections)
 
+    def central_ray_vectors(self) -> np.ndarray:
+        """[V, 2] unit central-ray direction c = (cos b, sin b) of every view
+        (the 2D trajectory as the paper describes it)."""
+        b = self.view_angles()
+        return np.stack([np.cos(b), np.sin(b)], axis=1)
+
+    def with_central_ray_vectors(self, vectors) -> "Geometry2D":
+        """The same geometry on a trajectory given by central-ray vectors [V, 2]."""
+        v = np.asarray(vectors, dtype=np.float64)
+        if v.ndim != 2 or v.shape[1] != 2 or not np.all(np.linalg.norm(v, axis=1) > 0):
+            raise ValueError("central ray vectors must be a nonzero [V, 2] array")
+        return replace(self, number_of_projections=v.shape[0], angles=np.arctan2(v[:, 1], v[:, 0]), _keep=[])
+
     def to_c(self) -> CGeom2D:
         ang = None if self.angles is None else np.ascontiguousarray(self.angles, dtype=np.float64)
         if ang is not None and ang.size != self.number_of_projections:
@@ -124,6 +137,14 @@ class ConeGeometry3D:
         if self.angles is not None:
             return np.asarray(self.angles, dtype=np.float64)
         return np.arange(self.number_of_projections) * (self.angular_range / self.number_of_projections)
+
+    def trajectory(self) -> np.ndarray:
+        """[V, 3, 4] projection matrices the library uses for this geometry:
+        the given ones normalised, or the circular trajectory's (computed by
+        the library from the geometry)."""
+        from .shard import projection_matrices
+
+        return projection_matrices(self)
 
     def to_c(self) -> CGeom3D:
         P = None

@@ -430,6 +430,11 @@ def test_many_views_are_chunked():
                oracle.bp_par2d(f32(y2), c2["shape"], c2["spacing"], c2["su"], ang2)) < 1e-5
 
 
+def test_sync_status_reports_a_clean_stream():
+    B.pyro_fp_cone3d(to_dev(ph.random_volume(CONE["shape"], 50)), cone_geom(CONE))
+    B.pyro_sync_status()  # raises PyroError if the stream faulted
+
+
 def test_invalid_call_enqueues_nothing():
     g = ParallelGeometry2D((8, 8), (1.0, 1.0), 9, 1.0, 4)
     with pytest.raises(ValueError):

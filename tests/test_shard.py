@@ -91,3 +91,18 @@ def _rank(rank, world, port, out_dir):
 def test_sharded_fp_bp_fdk_over_gloo_ranks(world, tmp_path):
     mp.spawn(_rank, args=(world, _free_port(), str(tmp_path)), nprocs=world, join=True)
     assert (tmp_path / "ok.npy").exists()
+
+
+def test_geometry_trajectory_helpers():
+    """Central-ray vectors (2D) round-trip through the angles; trajectory()
+    (3D) is the library's matrices, the circular ones when none are given."""
+    from paper_1904_13342_gb300.geometry import FanGeometry2D
+
+    g2 = FanGeometry2D((16, 16), (1.0, 1.0), 24, 1.2, 10, 2 * math.pi, 300.0, 500.0)
+    v = g2.central_ray_vectors()
+    assert np.allclose(np.linalg.norm(v, axis=1), 1.0)
+    g2b = g2.with_central_ray_vectors(3.0 * v[::-1])
+    assert g2b.number_of_projections == 10
+    assert np.allclose(g2b.central_ray_vectors(), v[::-1])
+    g = geometry()
+    assert np.array_equal(g.trajectory(), shard.projection_matrices(g))
