@@ -349,10 +349,11 @@ PYRO_API int pyro_fdk_noalloc(const void *sino, void *vol, int batch, const pyro
                               const float *custom_K, pyro_redund redund, pyro_dtype dtype, void *stream);
 
 /* thread-local message describing the last non-OK status of this thread */
-/* --- Waits for the stream and reports what happened on it: PYRO_OK, or
- * PYRO_ECUDA with the CUDA error's text in pyro_last_error.  The library's
- * kernels hold no device-side waits and keep no device status word, so the
- * stream's own error state is all there is to drain. */
+/* --- Waits for the stream and reports what happened on it: PYRO_OK,
+ * PYRO_ECUDA with the CUDA error's text in pyro_last_error, or PYRO_ETIMEOUT
+ * when a bounded device-side wait gave up (the TMA-staged cone BP waits on
+ * its copies with an iteration limit; a block that gives up sets a device
+ * status word, which this call reads and clears).  Synchronous. */
 PYRO_API int pyro_sync_status(void *stream);
 PYRO_API const char *pyro_last_error(void);
 /* library version string */

@@ -5,6 +5,7 @@
 // the library needs no device allocation of its own.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 #include <cstddef>
 #include <cstdint>
@@ -133,6 +134,14 @@ cudaError_t launch_bp2d_transpose(const void *vol, void *sino, int batch, const 
 cudaError_t launch_bp3d(const void *sino, void *vol, int batch, const BP3DParams &p, pyro_dtype sino_dt,
                         pyro_dtype vol_dt, cudaStream_t s);
 cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const BP3DParams &p, cudaStream_t s);
+// TMA-staged cone BP: the FP32 sinogram as a 3D tensor map [batch * views][nv][nu],
+// detector boxes of bu x bv floats (bu a multiple of 4)
+constexpr int kBPTmaStages = 3;
+int tma_stage_floats(int bu, int bv);
+cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv,
+                            pyro_dtype vol_dt, cudaStream_t s);
+// address of the device word a bounded wait sets when it gives up
+cudaError_t status_word(int **ptr);
 
 cudaError_t launch_bb_dots(const float *x, const float *xp, const float *g, const float *gp, long n, float *dots,
                            cudaStream_t s);

@@ -178,6 +178,188 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__
     }
 }
 
+// ---- TMA-staged cone BP (circular-type trajectories, FP32 sinogram) ------
+// Per view a block's 32 x 8 x ZB voxel tile projects onto a small detector
+// box; one thread copies the boxes of the next views into a ring of shared
+// memory stages with cp.async.bulk.tensor (completion counted on an
+// mbarrier), and every thread reads its four taps per voxel from shared
+// memory.  Out-of-range parts of a box are zero-filled by the copy, which is
+// the zero extension of the detector, so no tap needs masking.  Box sizes are
+// a host-computed bound; shared-memory indices are clamped to the stage.
+constexpr int kTmaStages = 3;
+constexpr long kTmaSpinLimit = 1L << 26;  // try_wait rounds before a wait gives up
+
+__device__ int g_status;  // set to 1 by a wait that gave up (read by pyro_sync_status)
+
+__device__ __forceinline__ unsigned smem_addr(const void *ptr)
+{
+    return (unsigned)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+// bounded wait: false when it gave up
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase)
+{
+    for (long n = 0; n < kTmaSpinLimit; ++n)
+        if (mbar_try_wait(bar, phase)) return true;
+    return false;
+}
+
+__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
+        ::"r"(smem_addr(dst)), "l"((unsigned long long)map), "r"(x), "r"(y), "r"(z), "r"(smem_addr(bar))
+        : "memory");
+}
+
+template <typename TV>
+__global__ void __launch_bounds__(kBPX *kBPY) bp3d_tma_kernel(const __grid_constant__ CUtensorMap map,
+                                                              TV *__restrict__ vol,
+                                                              const __grid_constant__ BP3DParams p, int bu, int bv,
+                                                              int stage_floats)
+{
+    extern __shared__ __align__(128) float stages[];
+    __shared__ __align__(8) uint64_t full[kTmaStages];
+    __shared__ int2 origin[kTmaStages];
+    __shared__ int gave_up;
+    const int t = threadIdx.y * kBPX + threadIdx.x;
+    const int lane = t & 31, warp = t >> 5;
+    const int i0 = blockIdx.x * kBPX, j0 = blockIdx.y * kBPY;
+    const int i = i0 + (warp & 3) * 8 + (lane & 7);
+    const int j = j0 + (warp >> 2) * 4 + (lane >> 3);
+    const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
+    const int b = blockIdx.z / zblocks;
+    const int z0 = (blockIdx.z % zblocks) * kBPZ;
+    const int i1 = min(i0 + kBPX - 1, p.nx - 1), j1 = min(j0 + kBPY - 1, p.ny - 1), z1 = min(z0 + kBPZ - 1, p.nz - 1);
+    const int vbase = b * p.views_total + p.view0;
+    const bool active = i < p.nx && j < p.ny;  // the others still take part in the barriers
+    const unsigned stage_bytes = (unsigned)(bu * bv * sizeof(float));
+    if (t == 0) {
+        for (int s = 0; s < kTmaStages; ++s) mbar_init(&full[s], 1);
+        gave_up = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+
+    // thread 0: the box of view v from the tile's eight corners (the
+    // projection is linear-fractional with a positive depth, so the corners
+    // bound it), then the copy into stage v % kTmaStages
+    auto issue = [&](int v) {
+        const int s = v % kTmaStages;
+        const float *P = p.P[v];
+        float umin = 3.0e38f, umax = -3.0e38f, lmin = 3.0e38f;
+        for (int c = 0; c < 4; ++c) {
+            const float fi = (float)((c & 1) ? i1 : i0), fj = (float)((c & 2) ? j1 : j0);
+            const float xb = fmaf(P[0], fi, fmaf(P[1], fj, P[3]));
+            const float yb = fmaf(P[4], fi, fmaf(P[5], fj, P[7]));
+            const float wb = fmaf(P[8], fi, fmaf(P[9], fj, P[11]));
+            const float rw = 1.0f / wb;
+            const float fu = fmaf(xb, rw, p.cu);
+            const float dl = P[6] * rw;
+            const float l0 = fmaf(yb, rw, p.cv);
+            umin = fminf(umin, fu);
+            umax = fmaxf(umax, fu);
+            lmin = fminf(lmin, fminf(fmaf((float)z0, dl, l0), fmaf((float)z1, dl, l0)));
+        }
+        // x of a tensor copy must be a multiple of 4 floats (16 bytes)
+        const int ux = ((int)floorf(fmaxf(umin, -1.0e8f) - 0.01f)) & ~3;
+        const int ly = (int)floorf(fmaxf(lmin, -1.0e8f) - 0.01f);
+        origin[s] = make_int2(ux, ly);
+        mbar_expect_tx(&full[s], stage_bytes);
+        tma_load_3d(stages + s * stage_floats, &map, ux, ly, vbase + v, &full[s]);
+    };
+    if (t == 0)
+        for (int v = 0; v < min(kTmaStages, p.n_views); ++v) issue(v);
+
+    float acc[kBPZ];
+#pragma unroll
+    for (int zz = 0; zz < kBPZ; ++zz) acc[zz] = 0.0f;
+    const float fi = (float)i, fj = (float)j;
+    const int last = stage_floats - bu - 2;  // highest first tap index of a 2 x 2 patch
+    int v = 0;
+    for (; v < p.n_views; ++v) {
+        const int s = v % kTmaStages;
+        if (!mbar_wait(&full[s], (unsigned)(v / kTmaStages) & 1u)) atomicExch(&gave_up, 1);
+        if (active) {
+            const float *S = stages + s * stage_floats;
+            const int2 o = origin[s];
+            const float *P = p.P[v];
+            const float xb = fmaf(P[0], fi, fmaf(P[1], fj, P[3]));
+            const float yb = fmaf(P[4], fi, fmaf(P[5], fj, P[7]));
+            const float wb = fmaf(P[8], fi, fmaf(P[9], fj, P[11]));
+            const float rw = 1.0f / wb;
+            const float om = weight_of(rw, p.wexp);
+            const float fu = fmaf(xb, rw, p.cu);
+            const float dl = P[6] * rw;
+            const float l0 = fmaf(yb, rw, p.cv);
+            const float tu = floor_magic(fu);
+            const float au = fu - magic_to_float(tu);
+            const float w1 = om * au, w0 = om - w1;
+            const int col = magic_to_int(tu) - o.x;
+#pragma unroll
+            for (int zz = 0; zz < kBPZ; ++zz) {
+                const float ll = fmaf((float)(z0 + zz), dl, l0);
+                const float tl = floor_magic(ll);
+                const float av = ll - magic_to_float(tl);
+                const int e = min(max((magic_to_int(tl) - o.y) * bu + col, 0), last);
+                const float t0 = fmaf(w0, S[e], w1 * S[e + 1]);
+                const float t1 = fmaf(w0, S[e + bu], w1 * S[e + bu + 1]);
+                acc[zz] += lerpf(t0, t1, av);
+            }
+        }
+        __syncthreads();  // stage s is free again; gave_up is visible
+        if (gave_up) break;
+        if (t == 0 && v + kTmaStages < p.n_views) issue(v + kTmaStages);
+    }
+    if (gave_up) {
+        // let the copies still in flight land (bounded) before the block ends
+        if (t == 0) {
+            atomicExch(&g_status, 1);
+            for (int w = v; w < min(v + kTmaStages, p.n_views); ++w)
+                mbar_wait(&full[w % kTmaStages], (unsigned)(w / kTmaStages) & 1u);
+        }
+        return;
+    }
+    if (!active) return;
+    const size_t sxy = (size_t)p.nx * p.ny;
+    TV *out = vol + (size_t)b * sxy * p.nz + (size_t)j * p.nx + i;
+#pragma unroll
+    for (int zz = 0; zz < kBPZ; ++zz) {
+        const int z = z0 + zz;
+        if (z < p.nz) {
+            float r = p.scale * acc[zz];
+            if (p.accumulate) r += to_float<TV>(out[z * sxy]);
+            out[z * sxy] = to_storage<TV>(r);
+        }
+    }
+}
+
 __global__ void __launch_bounds__(kBPX *kBPY) bp3d_transpose_kernel(const float *__restrict__ vol,
                                                                     float *__restrict__ sino,
                                                                     const __grid_constant__ BP3DParams p)
@@ -291,6 +473,38 @@ cudaError_t launch_bp3d(const void *sino, void *vol, int batch, const BP3DParams
     case PYRO_BF16: return bp3d_by_vol<__nv_bfloat16>(sino, vol, batch, p, vol_dt, s);
     }
     return cudaErrorInvalidValue;
+}
+
+int tma_stage_floats(int bu, int bv)
+{
+    return (bu * bv + 31) / 32 * 32;  // stages start on 128-byte boundaries
+}
+
+cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv,
+                            pyro_dtype vol_dt, cudaStream_t s)
+{
+    const int sf = tma_stage_floats(bu, bv);
+    const size_t smem = (size_t)kTmaStages * sf * sizeof(float);
+    dim3 block(kBPX, kBPY);
+    const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
+    dim3 grid((p.nx + kBPX - 1) / kBPX, (p.ny + kBPY - 1) / kBPY, (unsigned)(zblocks * batch));
+    switch (vol_dt) {
+    case PYRO_F32:
+        bp3d_tma_kernel<float><<<grid, block, smem, s>>>(map, (float *)vol, p, bu, bv, sf);
+        break;
+    case PYRO_F16:
+        bp3d_tma_kernel<__half><<<grid, block, smem, s>>>(map, (__half *)vol, p, bu, bv, sf);
+        break;
+    case PYRO_BF16:
+        bp3d_tma_kernel<__nv_bfloat16><<<grid, block, smem, s>>>(map, (__nv_bfloat16 *)vol, p, bu, bv, sf);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t status_word(int **ptr)
+{
+    return cudaGetSymbolAddress((void **)ptr, g_status);
 }
 
 cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const BP3DParams &p, cudaStream_t s)

@@ -740,6 +740,76 @@ int fp3d_adjoint_staged(const void *sino, void *vol, int batch, const pyro_geom3
     return PYRO_OK;
 }
 
+// Detector boxes of the TMA-staged BP: a bound, over every 32 x 8 x 8 voxel
+// tile and view of the chunk, on the extent of the tile's taps.  With the
+// centred, SID-scaled map of fill_bp3d, u - cu = x / w and l - cv = y / w;
+// along a segment inside the volume d(x/w) = (dx - (x/w) dw) / w, so the
+// extent is at most (|dx| + max|x/w| |dw|) / min w, and likewise for l.  The
+// extrema of x/w, y/w and w over the volume sit at its corners (linear-
+// fractional maps with a positive depth).  False when the TMA path does not
+// apply (non-circular maps, a depth <= 0, boxes too large).
+bool tma_boxes(const BP3DParams &p, int &bu, int &bv)
+{
+    if (!p.z_invariant) return false;
+    const double di = std::min(31, p.nx - 1), dj = std::min(7, p.ny - 1), dk = std::min(7, p.nz - 1);
+    double ext_u = 0.0, ext_l = 0.0;
+    for (int v = 0; v < p.n_views; ++v) {
+        const float *P = p.P[v];
+        double wmin = 1e300, xr = 0.0, yr = 0.0;
+        for (int c = 0; c < 8; ++c) {
+            const double i = (c & 1) ? p.nx - 1 : 0, j = (c & 2) ? p.ny - 1 : 0, k = (c & 4) ? p.nz - 1 : 0;
+            const double x = P[0] * i + P[1] * j + P[2] * k + P[3];
+            const double y = P[4] * i + P[5] * j + P[6] * k + P[7];
+            const double w = P[8] * i + P[9] * j + P[10] * k + P[11];
+            if (!(w > 0.0)) return false;
+            wmin = std::min(wmin, w);
+            xr = std::max(xr, std::fabs(x / w));
+            yr = std::max(yr, std::fabs(y / w));
+        }
+        const double dw = std::fabs(P[8]) * di + std::fabs(P[9]) * dj;
+        ext_u = std::max(ext_u, (std::fabs(P[0]) * di + std::fabs(P[1]) * dj + xr * dw) / wmin);
+        ext_l = std::max(ext_l, (std::fabs(P[4]) * di + std::fabs(P[5]) * dj + std::fabs(P[6]) * dk + yr * dw) / wmin);
+    }
+    if (!(ext_u < 240.0 && ext_l < 240.0)) return false;
+    // two taps, the 16-byte alignment of x (3) and rounding margins
+    bu = ((int)std::ceil(ext_u) + 7 + 3) / 4 * 4;
+    bv = (int)std::ceil(ext_l) + 4;
+    return bu <= 256 && bv <= 256 && (size_t)kBPTmaStages * tma_stage_floats(bu, bv) * sizeof(float) <= 48 * 1024;
+}
+
+using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_tiled()
+{
+    static EncodeTiledFn fn = [] {
+        void *f = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) !=
+                cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            f = nullptr;
+        return (EncodeTiledFn)f;
+    }();
+    return fn;
+}
+
+// FP32 sinogram [views][nv][nu] as a 3D tensor map with bu x bv x 1 boxes;
+// reads outside it return 0
+bool sino_tensor_map(const void *sino, int views, int nv, int nu, int bu, int bv, CUtensorMap &map)
+{
+    EncodeTiledFn fn = encode_tiled();
+    if (!fn || ((uintptr_t)sino & 15) || (nu % 4)) return false;
+    const cuuint64_t dims[3] = {(cuuint64_t)nu, (cuuint64_t)nv, (cuuint64_t)views};
+    const cuuint64_t strides[2] = {(cuuint64_t)nu * 4, (cuuint64_t)nu * nv * 4};
+    const cuuint32_t box[3] = {(cuuint32_t)bu, (cuuint32_t)bv, 1};
+    const cuuint32_t estr[3] = {1, 1, 1};
+    return fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(sino), dims, strides, box, estr,
+              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+              CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
+}
+
 int bp3d_impl(const void *sino, void *vol, int batch, const Geo3D &G, int wexp, float scale, pyro_dtype sino_dt,
               pyro_dtype vol_dt, void *stream)
 {
@@ -751,11 +821,17 @@ int bp3d_impl(const void *sino, void *vol, int batch, const Geo3D &G, int wexp, 
     for (int v0 = 0; v0 < V; v0 += kMaxViewsConeBP) {
         const int nvw = std::min(kMaxViewsConeBP, V - v0);
         fill_bp3d(G, v0, nvw, wexp, scale, v0 > 0, p);
+        int bu = 0, bv = 0;
+        const bool tma = sino_dt == PYRO_F32 && tma_boxes(p, bu, bv);
         for (int b0 = 0; b0 < batch; b0 += bstep) {
             const int nb = std::min(bstep, batch - b0);
             const char *si = (const char *)sino + b0 * V * det * elem_size(sino_dt);
             char *vo = (char *)vol + b0 * vox * elem_size(vol_dt);
-            PYRO_CUDA(launch_bp3d(si, vo, nb, p, sino_dt, vol_dt, as_stream(stream)));
+            CUtensorMap map;
+            if (tma && sino_tensor_map(si, nb * V, G.nv, G.nu, bu, bv, map))
+                PYRO_CUDA(launch_bp3d_tma(map, vo, nb, p, bu, bv, vol_dt, as_stream(stream)));
+            else
+                PYRO_CUDA(launch_bp3d(si, vo, nb, p, sino_dt, vol_dt, as_stream(stream)));
         }
     }
     return PYRO_OK;
@@ -1297,10 +1373,17 @@ PYRO_API int pyro_cnn_adam(float *p, const float *g, float *m, float *v, void *p
 
 PYRO_API int pyro_sync_status(void *stream)
 {
-    // the kernels hold no device-side waits and set no status word, so the
-    // device state to drain is the stream's own: any fault surfaces here
     PYRO_CUDA(cudaStreamSynchronize(as_stream(stream)));
     PYRO_CUDA(cudaGetLastError());
+    // the word a bounded device-side wait sets when it gives up (TMA-staged BP)
+    int *word = nullptr;
+    PYRO_CUDA(status_word(&word));
+    int flag = 0;
+    PYRO_CUDA(cudaMemcpy(&flag, word, sizeof(int), cudaMemcpyDeviceToHost));
+    if (flag) {
+        PYRO_CUDA(cudaMemset(word, 0, sizeof(int)));
+        return fail(PYRO_ETIMEOUT, "a device-side wait gave up; the results of that call are not valid");
+    }
     return PYRO_OK;
 }
 

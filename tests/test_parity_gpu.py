@@ -430,6 +430,28 @@ def test_many_views_are_chunked():
                oracle.bp_par2d(f32(y2), c2["shape"], c2["spacing"], c2["su"], ang2)) < 1e-5
 
 
+@pytest.mark.parametrize("weight", [0, 1, 2])
+def test_bp_cone_tma_staged(weight):
+    """A detector whose width is a multiple of 4 and an FP32 sinogram: the cone
+    BP of a circular trajectory stages its detector boxes with tensor copies.
+    Against the oracle, with more views than one parameter pack (chunks) and
+    voxels whose rays leave the detector (zero-filled boxes)."""
+    c = dict(CONE, det=(30, 44), dspacing=(1.2, 1.0), views=700)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang)
+    y = ph.random_sinogram((2, c["views"], *c["det"]), 51, smooth=2)
+    got = B.pyro_bp_cone3d(to_dev(y), cone_geom(c), weight=weight, scale=0.3)
+    ref = np.stack([oracle.bp_cone3d(f32(s), c["shape"], c["spacing"], P, c["sid"], weight, 0.3) for s in y])
+    assert rel(host(got), ref) < 1e-5
+    vol = ph.voxelize_ellipsoids(ph.random_ellipsoids(5, 18.0, seed=52), c["shape"], c["spacing"]).numpy()
+    p = f32(oracle.fp_cone3d(vol, c["spacing"], c["det"], P))
+    fdk = B.pyro_fdk(to_dev(p), cone_geom(c), kind=B.SHEPP_LOGAN, redund=B.REDUND_FULL)
+    ref = oracle.fdk(p, c["shape"], c["spacing"], c["dspacing"], ang, P, c["sid"], c["sdd"], c["range"] / c["views"],
+                     kind=oracle.SHEPP_LOGAN, redund=oracle.REDUND_FULL)
+    assert rel(host(fdk), ref) < 1e-5
+    B.pyro_sync_status()
+
+
 def test_sync_status_reports_a_clean_stream():
     B.pyro_fp_cone3d(to_dev(ph.random_volume(CONE["shape"], 50)), cone_geom(CONE))
     B.pyro_sync_status()  # raises PyroError if the stream faulted
