@@ -355,6 +355,12 @@ PYRO_API int pyro_fdk_noalloc(const void *sino, void *vol, int batch, const pyro
  * its copies with an iteration limit; a block that gives up sets a device
  * status word, which this call reads and clears).  Synchronous. */
 PYRO_API int pyro_sync_status(void *stream);
+/* --- Self-test of that path (no counterpart in the paper): enqueues a kernel
+ * whose single warp waits on a barrier that nothing completes, gives up after
+ * limit_ms (1..1000) milliseconds and sets the status word, so that the next
+ * pyro_sync_status returns PYRO_ETIMEOUT.  Nothing faults and nothing hangs;
+ * the context stays usable. */
+PYRO_API int pyro_selftest_wait_timeout(int limit_ms, void *stream);
 PYRO_API const char *pyro_last_error(void);
 /* library version string */
 PYRO_API const char *pyro_version(void);

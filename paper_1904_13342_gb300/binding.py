@@ -59,6 +59,7 @@ _SIGS = {
     "pyro_weights3d_table": [_VP, _I, _G3, _VP, _I, _I, _VP],
     "pyro_bb_dots": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, _VP],
     "pyro_sync_status": [_VP],
+    "pyro_selftest_wait_timeout": [_I, _VP],
     "pyro_bb_update": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, ctypes.c_float, ctypes.c_float, _I, _VP, _VP],
     "pyro_redundancy_grad": [_VP, _VP, _VP, _I, _I, _I, _I, _VP],
     "pyro_fpT_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
@@ -527,6 +528,14 @@ def pyro_sync_status(device=None) -> None:
     dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
     with torch.cuda.device(dev):
         _check(lib().pyro_sync_status(ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
+
+
+def pyro_selftest_wait_timeout(limit_ms: int = 20, device=None) -> None:
+    """Enqueue the bounded-wait self-test (see include/pyro.h)."""
+    dev = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+    with torch.cuda.device(dev):
+        _check(lib().pyro_selftest_wait_timeout(int(limit_ms),
+                                                ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
 
 
 # ------------------------------------------------------------ residual CNN --

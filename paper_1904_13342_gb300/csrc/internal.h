@@ -142,6 +142,7 @@ cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const 
                             pyro_dtype vol_dt, cudaStream_t s);
 // address of the device word a bounded wait sets when it gives up
 cudaError_t status_word(int **ptr);
+cudaError_t launch_wait_timeout_probe(unsigned long long limit_ns, cudaStream_t s);
 
 cudaError_t launch_bb_dots(const float *x, const float *xp, const float *g, const float *gp, long n, float *dots,
                            cudaStream_t s);

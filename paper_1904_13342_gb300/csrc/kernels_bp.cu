@@ -187,7 +187,7 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__
 // the zero extension of the detector, so no tap needs masking.  Box sizes are
 // a host-computed bound; shared-memory indices are clamped to the stage.
 constexpr int kTmaStages = 3;
-constexpr long kTmaSpinLimit = 1L << 26;  // try_wait rounds before a wait gives up
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a wait gives up after one second
 
 __device__ int g_status;  // set to 1 by a wait that gave up (read by pyro_sync_status)
 
@@ -222,12 +222,35 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
     return ok != 0;
 }
 
-// bounded wait: false when it gave up
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase)
+__device__ __forceinline__ unsigned long long global_ns()
 {
-    for (long n = 0; n < kTmaSpinLimit; ++n)
-        if (mbar_try_wait(bar, phase)) return true;
-    return false;
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait: false when it gave up after limit_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase, unsigned long long limit_ns = kWaitLimitNs)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int n = 0; n < 64; ++n)
+            if (mbar_try_wait(bar, phase)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
+}
+
+// Self-test of the wait-and-report path: one warp waits on an mbarrier that
+// nothing arrives at, gives up after limit_ns and sets the status word.
+__global__ void wait_timeout_probe_kernel(unsigned long long limit_ns)
+{
+    __shared__ __align__(8) uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncwarp();
+    if (!mbar_wait(&bar, 0, limit_ns) && threadIdx.x == 0) atomicExch(&g_status, 1);
 }
 
 __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
@@ -499,6 +522,12 @@ cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const 
         bp3d_tma_kernel<__nv_bfloat16><<<grid, block, smem, s>>>(map, (__nv_bfloat16 *)vol, p, bu, bv, sf);
         break;
     }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_wait_timeout_probe(unsigned long long limit_ns, cudaStream_t s)
+{
+    wait_timeout_probe_kernel<<<1, 32, 0, s>>>(limit_ns);
     return cudaGetLastError();
 }
 

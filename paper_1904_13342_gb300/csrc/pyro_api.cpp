@@ -1387,6 +1387,13 @@ PYRO_API int pyro_sync_status(void *stream)
     return PYRO_OK;
 }
 
+PYRO_API int pyro_selftest_wait_timeout(int limit_ms, void *stream)
+{
+    PYRO_CHECK(limit_ms >= 1 && limit_ms <= 1000, "limit_ms=%d outside [1, 1000]", limit_ms);
+    PYRO_CUDA(launch_wait_timeout_probe((unsigned long long)limit_ms * 1000000ull, as_stream(stream)));
+    return PYRO_OK;
+}
+
 PYRO_API const char *pyro_last_error(void)
 {
     return g_last_error.c_str();

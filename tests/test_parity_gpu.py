@@ -457,6 +457,22 @@ def test_sync_status_reports_a_clean_stream():
     B.pyro_sync_status()  # raises PyroError if the stream faulted
 
 
+def test_a_wait_that_runs_out_is_reported_and_the_context_survives():
+    """A bounded device-side wait on a barrier nothing completes gives up
+    after 20 ms and sets the status word: pyro_sync_status reports
+    PYRO_ETIMEOUT once, clears it, and the context keeps working."""
+    B.pyro_selftest_wait_timeout(20)
+    with pytest.raises(B.PyroError) as e:
+        B.pyro_sync_status()
+    assert e.value.status == 3
+    B.pyro_sync_status()  # cleared
+    c = CONE
+    vol = ph.random_volume(c["shape"], 53)
+    P = cone_pmats(c, oracle.uniform_angles(c["views"], c["range"]))
+    got = B.pyro_fp_cone3d(to_dev(vol), cone_geom(c))
+    assert rel(host(got), oracle.fp_cone3d(f32(vol), c["spacing"], c["det"], P)) < 1e-5
+
+
 def test_invalid_call_enqueues_nothing():
     g = ParallelGeometry2D((8, 8), (1.0, 1.0), 9, 1.0, 4)
     with pytest.raises(ValueError):
