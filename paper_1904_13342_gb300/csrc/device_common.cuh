@@ -10,6 +10,8 @@
 #include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
+#include <cstdint>
+
 namespace pyro {
 
 template <typename T>
@@ -165,6 +167,58 @@ __device__ __forceinline__ float trilerp_interior(const T *vol, int stx, int sty
     const float v10 = lerpf(ld(b + stx), ld(b + stx + stz), az);
     const float v11 = lerpf(ld(b + stx + sty), ld(b + stx + sty + stz), az);
     return lerpf(lerpf(v00, v01, ay), lerpf(v10, v11, ay), ax);
+}
+
+// ---- mbarrier waits with a time limit (shared by the TMA and tcgen05 kernels)
+constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a wait gives up after one second
+
+__device__ __forceinline__ unsigned smem_addr(const void *ptr)
+{
+    return (unsigned)__cvta_generic_to_shared(ptr);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
+{
+    unsigned ok;
+    asm volatile(
+        "{\n"
+        " .reg .pred p;\n"
+        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n"
+        "}\n"
+        : "=r"(ok)
+        : "r"(smem_addr(bar)), "r"(phase)
+        : "memory");
+    return ok != 0;
+}
+
+__device__ __forceinline__ unsigned long long global_ns()
+{
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+// bounded wait: false when it gave up after limit_ns
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase, unsigned long long limit_ns = kWaitLimitNs)
+{
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        for (int n = 0; n < 64; ++n)
+            if (mbar_try_wait(bar, phase)) return true;
+        if (global_ns() - t0 > limit_ns) return false;
+    }
 }
 
 // floor(x) for |x| < 2^22 on the FMA pipe: x + 1.5 * 2^23 rounded toward

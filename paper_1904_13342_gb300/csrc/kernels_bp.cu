@@ -187,58 +187,8 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__
 // the zero extension of the detector, so no tap needs masking.  Box sizes are
 // a host-computed bound; shared-memory indices are clamped to the stage.
 constexpr int kTmaStages = 3;
-constexpr unsigned long long kWaitLimitNs = 1000000000ull;  // a wait gives up after one second
 
 __device__ int g_status;  // set to 1 by a wait that gave up (read by pyro_sync_status)
-
-__device__ __forceinline__ unsigned smem_addr(const void *ptr)
-{
-    return (unsigned)__cvta_generic_to_shared(ptr);
-}
-
-__device__ __forceinline__ void mbar_init(uint64_t *bar, unsigned count)
-{
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count) : "memory");
-}
-
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, unsigned bytes)
-{
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)), "r"(bytes)
-                 : "memory");
-}
-
-__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, unsigned phase)
-{
-    unsigned ok;
-    asm volatile(
-        "{\n"
-        " .reg .pred p;\n"
-        " mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
-        " selp.u32 %0, 1, 0, p;\n"
-        "}\n"
-        : "=r"(ok)
-        : "r"(smem_addr(bar)), "r"(phase)
-        : "memory");
-    return ok != 0;
-}
-
-__device__ __forceinline__ unsigned long long global_ns()
-{
-    unsigned long long t;
-    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-    return t;
-}
-
-// bounded wait: false when it gave up after limit_ns
-__device__ __forceinline__ bool mbar_wait(uint64_t *bar, unsigned phase, unsigned long long limit_ns = kWaitLimitNs)
-{
-    const unsigned long long t0 = global_ns();
-    for (;;) {
-        for (int n = 0; n < 64; ++n)
-            if (mbar_try_wait(bar, phase)) return true;
-        if (global_ns() - t0 > limit_ns) return false;
-    }
-}
 
 // Self-test of the wait-and-report path: one warp waits on an mbarrier that
 // nothing arrives at, gives up after limit_ns and sets the status word.

@@ -6,17 +6,14 @@
 // [27][Cout][Cin] bf16 (tap = (dz*3 + dy)*3 + dx, taps of a 3x3x3 window,
 // stride 1, zero padding 1); master weights and gradients are FP32.
 //
-// conv3d_mma_kernel: implicit GEMM on the tensor cores with
-// mma.sync.m16n8k16 (bf16 in, fp32 accumulate).  A block computes 128 output
-// voxels (a TX x TY x TZ box) x Cout; its input halo ((TZ+2) x (TY+2) x
-// (TX+2) voxels x Cin) is staged in shared memory with each voxel's channel
-// vector padded by 8 so that the A-fragment loads of the 8 row groups fall
-// in distinct banks.  The same kernel computes the data gradient with the
-// spatially flipped, channel-transposed weights.
+// conv3d_tc_kernel: implicit GEMM on the 5th-generation tensor cores
+// (tcgen05.mma, bf16 in, FP32 accumulate in tensor memory); a block computes
+// 128 output voxels (a TX x TY x TZ box) x Cout.  The same kernel computes the
+// data gradient with the spatially flipped, channel-transposed weights.
 // conv3d_wgrad_mma_kernel: dW[tap][co][ci] = sum_v dY[v][co] X[v+tap][ci] as a
-// GEMM with M = Cout, N = taps x Cin, K = voxels: a block owns a group of
-// taps, walks a strided set of voxel tiles accumulating in registers, and
-// adds its partial sums to dW with FP32 atomics once at the end.
+// GEMM with M = Cout, N = taps x Cin, K = voxels on mma.sync.m16n8k16: a
+// block owns a group of taps, walks a strided set of voxel tiles accumulating
+// in registers, and adds its partial sums to dW with FP32 atomics at the end.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -61,85 +58,151 @@ __host__ __device__ inline Tile conv_tile(int W, int H)
     return t;
 }
 
-template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) conv3d_mma_kernel(const bf16 *__restrict__ X,
-                                                                  const bf16 *__restrict__ Wt,
-                                                                  const float *__restrict__ bias,
-                                                                  bf16 *__restrict__ Y, int D, int H, int Wd,
-                                                                  int relu)
+// ---- conv3d_tc_kernel: the same implicit GEMM on the 5th-generation tensor
+// cores.  A block of 128 threads owns 128 output voxels (row m = thread m)
+// and a [128 x Cout] FP32 accumulator in tensor memory.  Per tap of the 3x3x3
+// window every thread gathers its voxel's shifted input row (Cin bf16, 16-byte
+// loads; zero outside the volume) and the block gathers the tap's [Cout x Cin]
+// weights, both into a double-buffered shared-memory stage in the canonical
+// K-major layout of the MMA (8 x 8 core matrices of 128 contiguous bytes);
+// one thread issues Cin / 16 tcgen05.mma (M = 128, N = Cout, K = 16) and
+// commits them to the stage's mbarrier, so the gather of tap t + 1 overlaps
+// the MMAs of tap t.  The epilogue reads the accumulator with tcgen05.ld and
+// adds the bias and the ReLU.  Waits are time-bounded; a block whose wait
+// gives up writes nothing and sets the status word.
+__device__ __forceinline__ uint64_t umma_desc(const void *smem, unsigned lbo, unsigned sbo)
 {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    bf16 *halo = reinterpret_cast<bf16 *>(smem_raw);
-    constexpr int CP = CIN + 8;
+    uint64_t d = (uint64_t)((smem_addr(smem) >> 4) & 0x3FFF);
+    d |= (uint64_t)((lbo >> 4) & 0x3FFF) << 16;  // next core matrix along K
+    d |= (uint64_t)((sbo >> 4) & 0x3FFF) << 32;  // next group of 8 rows
+    d |= (uint64_t)1 << 46;                      // descriptor version; no swizzle, base offset 0
+    return d;
+}
+
+template <int CIN, int COUT>
+__global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
+                                                        const float *__restrict__ bias, bf16 *__restrict__ Y, int D,
+                                                        int H, int Wd, int relu, int *status)
+{
+    constexpr int KCH = CIN / 8;  // 16-byte chunks of a row
+    constexpr int A_EL = 128 * CIN, B_EL = COUT * CIN;
+    constexpr unsigned TCOLS = COUT < 32 ? 32 : COUT;  // tensor-memory columns (a power of two >= 32)
+    extern __shared__ __align__(128) unsigned char conv_smem[];
+    bf16 *sA = reinterpret_cast<bf16 *>(conv_smem);  // [2][128 x Cin]
+    bf16 *sB = sA + 2 * A_EL;                         // [2][Cout x Cin]
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ unsigned tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5;
     const Tile tl = conv_tile(Wd, H);
-    const int TX = tl.TX, TY = tl.TY, TZ = tl.TZ, HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
-    const int tiles_x = Wd / TX, tiles_y = H / TY, tiles_z = D / TZ;
-    int t = blockIdx.x;
-    const int tx0 = (t % tiles_x) * TX;
-    t /= tiles_x;
-    const int ty0 = (t % tiles_y) * TY;
-    t /= tiles_y;
-    const int tz0 = (t % tiles_z) * TZ;
-    const int b = t / tiles_z;
-    constexpr int CH = CIN / 8;  // 16-byte chunks per voxel
-    const int nvox = HZ * HY * HX;
-    for (int e = threadIdx.x; e < nvox * CH; e += kConvThreads) {
-        const int vox = e / CH, ch = e - vox * CH;
-        const int hx = vox % HX, r = vox / HX;
-        const int hy = r % HY, hz = r / HY;
-        const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
-        uint4 val = make_uint4(0u, 0u, 0u, 0u);
-        if ((unsigned)gx < (unsigned)Wd && (unsigned)gy < (unsigned)H && (unsigned)gz < (unsigned)D)
-            val = __ldg(reinterpret_cast<const uint4 *>(X + ((((size_t)b * D + gz) * H + gy) * Wd + gx) * CIN) + ch);
-        *reinterpret_cast<uint4 *>(halo + (size_t)vox * CP + ch * 8) = val;
+    const int TX = tl.TX, TY = tl.TY;
+    const int tiles_x = Wd / TX, tiles_y = H / TY, tiles_z = D / tl.TZ;
+    int blk = blockIdx.x;
+    const int tx0 = (blk % tiles_x) * TX;
+    blk /= tiles_x;
+    const int ty0 = (blk % tiles_y) * TY;
+    blk /= tiles_y;
+    const int tz0 = (blk % tiles_z) * tl.TZ;
+    const int b = blk / tiles_z;
+    const int vz = tz0 + t / (TX * TY), vy = ty0 + (t / TX) % TY, vx = tx0 + t % TX;
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
     }
     __syncthreads();
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
-    const int m0 = warp * 16 + g, m1 = m0 + 8;  // the two output voxels (rows) of this thread
-    const int lz0 = m0 / (TX * TY), lz1 = m1 / (TX * TY);
-    const int ly0 = (m0 / TX) % TY, lx0 = m0 % TX, ly1 = (m1 / TX) % TY, lx1 = m1 % TX;
-    float acc[COUT / 8][4];
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_slot;
+    // f32 accumulate, bf16 A and B, both K-major, N = Cout, M = 128
+    constexpr unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COUT >> 3) << 17) | (8u << 24);
+    bool ok = true;
+    for (int tap = 0; tap < 27; ++tap) {
+        const int buf = tap & 1;
+        // the MMAs of tap - 2 read this stage
+        if (tap >= 2 && !mbar_wait(&bar[buf], (unsigned)((tap - 2) >> 1) & 1u)) ok = false;
+        const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+        const int gz = vz + dz - 1, gy = vy + dy - 1, gx = vx + dx - 1;
+        const bool in = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < Wd;
+        const uint4 *src = reinterpret_cast<const uint4 *>(X + ((((size_t)b * D + gz) * H + gy) * Wd + gx) * CIN);
+        bf16 *A = sA + buf * A_EL;
 #pragma unroll
-    for (int n = 0; n < COUT / 8; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.0f;
-    for (int dz = 0; dz < 3; ++dz)
-        for (int dy = 0; dy < 3; ++dy)
-            for (int dx = 0; dx < 3; ++dx) {
-                const int tap = (dz * 3 + dy) * 3 + dx;
-                const bf16 *r0 = halo + (((lz0 + dz) * HY + ly0 + dy) * HX + lx0 + dx) * CP;
-                const bf16 *r1 = halo + (((lz1 + dz) * HY + ly1 + dy) * HX + lx1 + dx) * CP;
-                const bf16 *wt = Wt + (size_t)tap * COUT * CIN;
-#pragma unroll
-                for (int kc = 0; kc < CIN / 16; ++kc) {
-                    const int c0 = kc * 16 + 2 * tg;
-                    const unsigned a0 = *reinterpret_cast<const unsigned *>(r0 + c0);
-                    const unsigned a1 = *reinterpret_cast<const unsigned *>(r1 + c0);
-                    const unsigned a2 = *reinterpret_cast<const unsigned *>(r0 + c0 + 8);
-                    const unsigned a3 = *reinterpret_cast<const unsigned *>(r1 + c0 + 8);
-#pragma unroll
-                    for (int n = 0; n < COUT / 8; ++n) {
-                        const bf16 *wr = wt + (size_t)(n * 8 + g) * CIN + c0;
-                        const unsigned b0 = __ldg(reinterpret_cast<const unsigned *>(wr));
-                        const unsigned b1 = __ldg(reinterpret_cast<const unsigned *>(wr + 8));
-                        mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
-                    }
-                }
-            }
-    const size_t o0 = ((((size_t)b * D + tz0 + lz0) * H + ty0 + ly0) * Wd + tx0 + lx0) * COUT;
-    const size_t o1 = ((((size_t)b * D + tz0 + lz1) * H + ty0 + ly1) * Wd + tx0 + lx1) * COUT;
-#pragma unroll
-    for (int n = 0; n < COUT / 8; ++n) {
-        const int co = n * 8 + 2 * tg;
-        const float b0 = bias ? bias[co] : 0.0f, b1 = bias ? bias[co + 1] : 0.0f;
-        float v0 = acc[n][0] + b0, v1 = acc[n][1] + b1, v2 = acc[n][2] + b0, v3 = acc[n][3] + b1;
-        if (relu) {
-            v0 = fmaxf(v0, 0.0f);
-            v1 = fmaxf(v1, 0.0f);
-            v2 = fmaxf(v2, 0.0f);
-            v3 = fmaxf(v3, 0.0f);
+        for (int c = 0; c < KCH; ++c) {
+            const uint4 v = in ? __ldg(src + c) : make_uint4(0u, 0u, 0u, 0u);
+            *reinterpret_cast<uint4 *>(A + ((t >> 3) * KCH + c) * 64 + (t & 7) * 8) = v;
         }
-        *reinterpret_cast<unsigned *>(Y + o0 + co) = pack_bf16(__float2bfloat16_rn(v0), __float2bfloat16_rn(v1));
-        *reinterpret_cast<unsigned *>(Y + o1 + co) = pack_bf16(__float2bfloat16_rn(v2), __float2bfloat16_rn(v3));
+        bf16 *Bs = sB + buf * B_EL;
+        const uint4 *wsrc = reinterpret_cast<const uint4 *>(Wt + (size_t)tap * COUT * CIN);
+        for (int q = t; q < COUT * KCH; q += 128) {
+            const int n = q / KCH, c = q - n * KCH;
+            *reinterpret_cast<uint4 *>(Bs + ((n >> 3) * KCH + c) * 64 + (n & 7) * 8) = __ldg(wsrc + q);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+#pragma unroll
+            for (int kk = 0; kk < CIN / 16; ++kk) {
+                const uint64_t ad = umma_desc(A + kk * 128, 128, CIN * 16);
+                const uint64_t bd = umma_desc(Bs + kk * 128, 128, CIN * 16);
+                const unsigned accumulate = (tap > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n"
+                    " .reg .pred p;\n"
+                    " setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                    "}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&bar[buf]))
+                         : "memory");
+        }
     }
+    // the last commit tracks every MMA issued before it
+    if (!mbar_wait(&bar[26 & 1], (26 >> 1) & 1u)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int all_ok = __syncthreads_and(ok ? 1 : 0);
+    if (all_ok) {
+        bf16 *out = Y + ((((size_t)b * D + vz) * H + vy) * Wd + vx) * COUT;
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            unsigned r[16];
+            const unsigned addr = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            unsigned pk[8];
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                float a = __uint_as_float(r[c]), d = __uint_as_float(r[c + 1]);
+                if (bias) {
+                    a += bias[c0 + c];
+                    d += bias[c0 + c + 1];
+                }
+                if (relu) {
+                    a = fmaxf(a, 0.0f);
+                    d = fmaxf(d, 0.0f);
+                }
+                pk[c / 2] = pack_bf16(__float2bfloat16(a), __float2bfloat16(d));
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(out + c0);
+            o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+    } else if (t == 0) {
+        atomicExch(status, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // taps per wgrad block: enough to keep COUT x CIN x TP accumulators <= 64 per thread
@@ -508,16 +571,19 @@ long grid_for(long n)
 }
 
 template <int CIN, int COUT>
-cudaError_t conv_mma_launch(const bf16 *X, const bf16 *W, const float *bias, bf16 *Y, int B, int D, int H, int Wd,
-                            int relu, cudaStream_t s)
+cudaError_t conv_tc_launch(const bf16 *X, const bf16 *W, const float *bias, bf16 *Y, int B, int D, int H, int Wd,
+                           int relu, cudaStream_t s)
 {
     const Tile tl = conv_tile(Wd, H);
-    const size_t smem = (size_t)(tl.TZ + 2) * (tl.TY + 2) * (tl.TX + 2) * (CIN + 8) * sizeof(bf16);
-    auto k = conv3d_mma_kernel<CIN, COUT>;
+    const size_t smem = (size_t)2 * (128 * CIN + COUT * CIN) * sizeof(bf16);
+    auto k = conv3d_tc_kernel<CIN, COUT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
+    int *status = nullptr;
+    e = status_word(&status);
+    if (e != cudaSuccess) return e;
     const long blocks = (long)B * (D / tl.TZ) * (H / tl.TY) * (Wd / tl.TX);
-    k<<<(unsigned)blocks, kConvThreads, smem, s>>>(X, W, bias, Y, D, H, Wd, relu);
+    k<<<(unsigned)blocks, 128, smem, s>>>(X, W, bias, Y, D, H, Wd, relu, status);
     return cudaGetLastError();
 }
 
@@ -563,7 +629,7 @@ cudaError_t launch_conv3d(const void *X, const void *W, const float *bias, void 
     const bf16 *x = (const bf16 *)X, *w = (const bf16 *)W;
     bf16 *y = (bf16 *)Y;
 #define PYRO_CONV_CASE(ci, co)                                                      \
-    if (cin == ci && cout == co) return conv_mma_launch<ci, co>(x, w, bias, y, B, D, H, Wd, relu, s);
+    if (cin == ci && cout == co) return conv_tc_launch<ci, co>(x, w, bias, y, B, D, H, Wd, relu, s);
     PYRO_CONV_CASE(16, 16)
     PYRO_CONV_CASE(16, 32)
     PYRO_CONV_CASE(16, 64)
