@@ -117,3 +117,18 @@ def test_tensor_wrappers_refuse_cpu_tensors():
     g = ParallelGeometry2D((8, 8), (1.0, 1.0), 9, 1.0, 4)
     with pytest.raises(TypeError):
         B.pyro_fp_par2d(torch.zeros(8, 8), g)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """No library and no way to build it: the binding raises (there is no
+    CPU fallback to fall into)."""
+    monkeypatch.setattr(B, "_lib", None)
+
+    def no_compiler():
+        raise RuntimeError("nvcc not found")
+
+    monkeypatch.setattr(B._build, "build", no_compiler)
+    with pytest.raises(RuntimeError):
+        B.lib()
+    with pytest.raises(RuntimeError):
+        B.pyro_filter_pad_length(100)
