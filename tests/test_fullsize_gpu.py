@@ -7,7 +7,9 @@ configuration the benchmark times, on outputs the oracle computes one by one
     SID 750 mm, SDD 1200 mm, Parker weights, Shepp-Logan filter;
   * 2D fan-beam batch: 16 random-ellipse phantoms 512^2 (0.5 mm), 360 views
     over 2 pi, 1024 bins (1.0 mm), SID 750 mm, SDD 1200 mm;
-  * 2D parallel beam: 128^2 (1.0 mm), 180 views over pi, 183 bins, whole.
+  * 2D parallel beam: 128^2 (1.0 mm), 180 views over pi, 183 bins, whole;
+  * the 512^3 iterative workload's FP, BP and exact adjoint;
+  * the learned initialiser's batch of 32 FDKs at 128^3.
 """
 import math
 
@@ -147,3 +149,54 @@ def test_parallel_full_problem():
     rec = B.pyro_fbp_par2d(y.to(DEV), g, kind=B.RAMLAK)
     rref = oracle.fbp_par2d(y.double().numpy(), (n, n), (1.0, 1.0), 1.0, ang, oracle.RAMLAK)
     assert rel(rec.double().cpu().numpy(), rref) < 1e-5
+
+
+def test_tv512_geometry_full_size():
+    """The 512^3 iterative workload's operators at full size (0.5 mm, 496
+    views over 2 pi, 1240 x 960 detector at 0.308 mm): staged FP on sampled
+    rays and BP on sampled voxels against the oracle; the staged exact
+    adjoint through <A x, y> = <x, A^T y> on the whole problem."""
+    n = 512
+    g = ConeGeometry3D((n, n, n), (0.5,) * 3, (960, 1240), (0.308, 0.308), 496, 2 * math.pi, 750.0, 1200.0)
+    vol = ph.voxelize_ellipsoids(ph.random_ellipsoids(20, n * 0.5 / 2, seed=0), g.volume_shape, g.volume_spacing,
+                                 device=DEV, dtype=torch.float32)
+    sino = B.pyro_fp_cone3d_ws(vol, g)
+    torch.cuda.synchronize()
+    P = oracle.circular_pmats(g.view_angles(), g.sid, g.sdd, g.detector_shape, g.detector_spacing)
+    rng = np.random.default_rng(11)
+    views, ks, ls = rng.integers(0, 496, 150), rng.integers(0, 1240, 150), rng.integers(0, 960, 150)
+    views, ks, ls = np.r_[views, 0, 495], np.r_[ks, 0, 1239], np.r_[ls, 0, 959]
+    ref = oracle.fp_cone3d_rays(vol.double().cpu().numpy(), g.volume_spacing, P, views, ks, ls)
+    assert rel(sino[views, ls, ks].double().cpu().numpy(), ref) < 1e-5
+    y = sino.contiguous()
+    bp = B.pyro_bp_cone3d(y, g, weight=B.W_INV_L2, scale=0.01)
+    torch.cuda.synchronize()
+    ii, jj, kk = rng.integers(0, n, 60), rng.integers(0, n, 60), rng.integers(0, n, 60)
+    refv = oracle.bp_cone3d_voxels(y.double().cpu().numpy(), g.volume_shape, g.volume_spacing, P, g.sid, ii, jj, kk,
+                                   weight=2, scale=0.01)
+    assert rel(bp[kk, jj, ii].double().cpu().numpy(), refv) < 1e-5
+    w = torch.from_numpy(ph.random_sinogram((496, 960, 1240), 12)).float().to(DEV)
+    atw = B.pyro_fpT_cone3d_ws(w, g)
+    lhs = torch.sum(sino.double() * w.double()).item()
+    rhs = torch.sum(vol.double() * atw.double()).item()
+    assert abs(lhs - rhs) < 1e-5 * abs(lhs)
+
+
+def test_learned_init_batch_full_size():
+    """The learned-initialiser workload's FDK on its batch of 32 128^3
+    phantoms (60 views over 2 pi, 256 x 200 at 1 mm): sampled voxels of the
+    first and last volume against the oracle."""
+    g = ConeGeometry3D((128,) * 3, (1.0,) * 3, (200, 256), (1.0, 1.0), 60, 2 * math.pi, 750.0, 1200.0)
+    vols = torch.stack([ph.voxelize_ellipsoids(ph.random_ellipsoids(12, 64.0, seed=s), g.volume_shape,
+                                               g.volume_spacing, device=DEV, dtype=torch.float32) for s in range(32)])
+    sino = B.pyro_fp_cone3d_ws(vols, g)
+    rec = B.pyro_fdk(sino, g, kind=B.SHEPP_LOGAN, redund=B.REDUND_FULL)
+    torch.cuda.synchronize()
+    P = oracle.circular_pmats(g.view_angles(), g.sid, g.sdd, g.detector_shape, g.detector_spacing)
+    rng = np.random.default_rng(13)
+    ii, jj, kk = rng.integers(0, 128, 300), rng.integers(0, 128, 300), rng.integers(0, 128, 300)
+    for b in (0, 31):
+        ref = oracle.fdk_voxels(sino[b].double().cpu().numpy(), g.volume_shape, g.volume_spacing, g.detector_spacing,
+                                g.view_angles(), P, g.sid, g.sdd, 2 * math.pi / 60, ii, jj, kk,
+                                kind=oracle.SHEPP_LOGAN, redund=oracle.REDUND_FULL)
+        assert rel(rec[b][kk, jj, ii].double().cpu().numpy(), ref) < 1e-5
