@@ -224,6 +224,10 @@ def run_gpu(args):
         e2e_ms = float(t.item())
     e2e = world * E * units_per_step() / (e2e_ms * 1e-3) / 1e9
 
+    # the gather-bound view: achievable random 16-byte gather bandwidth from an
+    # L2-resident 64 MB buffer (the project's probe), against the tap bytes the
+    # FP (8 FP32 taps per sample) and the BP (4 taps per update) consume
+    gather_gbs = gather_peak(dev, stream)
     peaks = {}
     pf = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(pf):
@@ -250,6 +254,12 @@ def run_gpu(args):
                      "traffic": traffic,
                      "note": f"{samples:.4g} samples x {FLOPS_PER_SAMPLE} flop; peak = {props.multi_processor_count}"
                              f" SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
+        "gather_roofline": {
+            "peak_GBps": round(gather_gbs, 1), "what": "random 16-byte gathers from a 64 MB L2-resident buffer",
+            "fp_taps_GBps": round(samples * 32 / (fp_avg_ms * 1e-3) / 1e9, 1),
+            "fp_frac": round(samples * 32 / (fp_avg_ms * 1e-3) / 1e9 / gather_gbs, 3),
+            "bp_taps_GBps": round(N ** 3 * VIEWS * 16 / (tk["bp"] * 1e-3) / 1e9, 1),
+            "bp_frac": round(N ** 3 * VIEWS * 16 / (tk["bp"] * 1e-3) / 1e9 / gather_gbs, 3)},
         "breakdown_ms": {"fp": round(fp_avg_ms, 4), "fdk": round(statistics.mean(fdk_ms), 4),
                          "bp_alone": round(tk["bp"], 4), "filter_alone": round(tk["filter"], 4)},
         "kernel_gups": {"fp": round(N ** 3 * VIEWS / (fp_avg_ms * 1e-3) / 1e9, 2),
@@ -265,6 +275,27 @@ def run_gpu(args):
 
 
 FLOPS_PER_SAMPLE = 28  # 3 position FMA (6) + 7 lerps (3 each) + 1 accumulate
+
+
+def gather_peak(dev, stream) -> float:
+    """GB/s of the library's random 16-byte gather probe over a 64 MB buffer
+    (L2-resident after a warm-up), median of 5 runs."""
+    from paper_1904_13342_gb300 import binding as B
+
+    buf = torch.zeros(64 << 20, dtype=torch.uint8, device=dev)
+    sink = torch.zeros(1024, dtype=torch.int32, device=dev)
+    threads = torch.cuda.get_device_properties(dev).multi_processor_count * 2048
+    loads = 256
+    B.pyro_probe_gather(buf, loads, threads, sink)
+    ts = []
+    for _ in range(5):
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        B.pyro_probe_gather(buf, loads, threads, sink)
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ts.append(a.elapsed_time(b))
+    return 16.0 * threads * loads / (statistics.median(ts) * 1e-3) / 1e9
 
 
 def fp_traffic_per_launch():

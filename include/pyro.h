@@ -361,6 +361,16 @@ PYRO_API int pyro_sync_status(void *stream);
  * pyro_sync_status returns PYRO_ETIMEOUT.  Nothing faults and nothing hangs;
  * the context stays usable. */
 PYRO_API int pyro_selftest_wait_timeout(int limit_ms, void *stream);
+
+/* --- Gather-bandwidth probe (no counterpart in the paper; the roofline
+ * denominator for gather-bound kernels): `threads` threads each read
+ * loads_per_thread 16-byte chunks at pseudo-random positions of the DEVICE
+ * buffer `buf` (bytes, 16-byte aligned; a buffer smaller than L2 measures
+ * L2 gathers).  sink: DEVICE array of 1024 unsigned, written only to keep
+ * the loads alive.  Time it with events on `stream`: bandwidth =
+ * 16 * threads * loads_per_thread / time. */
+PYRO_API int pyro_probe_gather(const void *buf, size_t bytes, int loads_per_thread, long threads, unsigned *sink,
+                               void *stream);
 PYRO_API const char *pyro_last_error(void);
 /* library version string */
 PYRO_API const char *pyro_version(void);

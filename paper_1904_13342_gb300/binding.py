@@ -60,6 +60,7 @@ _SIGS = {
     "pyro_bb_dots": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, _VP],
     "pyro_sync_status": [_VP],
     "pyro_selftest_wait_timeout": [_I, _VP],
+    "pyro_probe_gather": [_VP, _SZ, _I, ctypes.c_long, _VP, _VP],
     "pyro_bb_update": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, ctypes.c_float, ctypes.c_float, _I, _VP, _VP],
     "pyro_redundancy_grad": [_VP, _VP, _VP, _I, _I, _I, _I, _VP],
     "pyro_fpT_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
@@ -536,6 +537,20 @@ def pyro_selftest_wait_timeout(limit_ms: int = 20, device=None) -> None:
     with torch.cuda.device(dev):
         _check(lib().pyro_selftest_wait_timeout(int(limit_ms),
                                                 ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)))
+
+
+def pyro_probe_gather(buf: torch.Tensor, loads_per_thread: int, threads: int, sink: torch.Tensor) -> None:
+    """Enqueue the 16-byte random-gather probe over the bytes of `buf`."""
+    b = _dev_any(buf, "buf")
+    with torch.cuda.device(b.device):
+        _check(lib().pyro_probe_gather(_ptr(b), b.numel() * b.element_size(), int(loads_per_thread), int(threads),
+                                       _ptr(sink), _stream(b)))
+
+
+def _dev_any(t: torch.Tensor, name: str) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor) or not t.is_cuda or not t.is_contiguous():
+        raise TypeError(f"{name} must be a contiguous CUDA tensor")
+    return t
 
 
 # ------------------------------------------------------------ residual CNN --

@@ -144,6 +144,8 @@ cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const 
 cudaError_t status_word(int **ptr);
 cudaError_t launch_wait_timeout_probe(unsigned long long limit_ns, cudaStream_t s);
 
+cudaError_t launch_gather_probe(const void *buf, unsigned n16, int loads, unsigned *sink, long threads,
+                                cudaStream_t s);
 cudaError_t launch_bb_dots(const float *x, const float *xp, const float *g, const float *gp, long n, float *dots,
                            cudaStream_t s);
 cudaError_t launch_bb_update(float *x, float *xp, const float *g, float *gp, long n, const float *dots, float alpha0,

@@ -145,7 +145,34 @@ __global__ void bb_update_kernel(float *__restrict__ x, float *__restrict__ xp, 
     }
 }
 
+// Gather-bandwidth probe: every thread reads `loads` 16-byte chunks at
+// pseudo-random positions of a buffer of n16 chunks (a linear congruential
+// walk scaled to the buffer by a high multiply: three integer instructions
+// per load) and folds them into one word, written once so that no load is
+// dead.
+__global__ void __launch_bounds__(256) gather_probe_kernel(const uint4 *__restrict__ buf, unsigned n16, int loads,
+                                                           unsigned *__restrict__ sink)
+{
+    const unsigned tid = blockIdx.x * blockDim.x + threadIdx.x;
+    unsigned h = tid * 2654435761u + 12345u;
+    unsigned acc = 0u;
+#pragma unroll 8
+    for (int i = 0; i < loads; ++i) {
+        h = h * 1664525u + 1013904223u;
+        const uint4 v = __ldg(buf + __umulhi(h, n16));  // h / 2^32 scaled to [0, n16): one instruction
+        acc ^= v.x ^ v.y ^ v.z ^ v.w;
+    }
+    if (acc == 0x9e3779b9u) sink[tid & 1023] = acc;  // practically never: keeps the loads alive
+}
+
 }  // namespace
+
+cudaError_t launch_gather_probe(const void *buf, unsigned n16, int loads, unsigned *sink, long threads,
+                                cudaStream_t s)
+{
+    gather_probe_kernel<<<(unsigned)((threads + 255) / 256), 256, 0, s>>>((const uint4 *)buf, n16, loads, sink);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_bb_dots(const float *x, const float *xp, const float *g, const float *gp, long n, float *dots,
                            cudaStream_t s)

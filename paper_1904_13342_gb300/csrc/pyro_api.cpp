@@ -1387,6 +1387,16 @@ PYRO_API int pyro_sync_status(void *stream)
     return PYRO_OK;
 }
 
+PYRO_API int pyro_probe_gather(const void *buf, size_t bytes, int loads_per_thread, long threads, unsigned *sink,
+                               void *stream)
+{
+    PYRO_CHECK(buf != nullptr && sink != nullptr, "NULL pointer");
+    PYRO_CHECK(aligned16(buf) && bytes >= 16 && bytes / 16 <= 0xFFFFFFFFull, "buffer must be 16-byte aligned, 16 B .. 64 GiB");
+    PYRO_CHECK(loads_per_thread > 0 && threads > 0 && threads <= (1L << 31), "bad probe size");
+    PYRO_CUDA(launch_gather_probe(buf, (unsigned)(bytes / 16), loads_per_thread, sink, threads, as_stream(stream)));
+    return PYRO_OK;
+}
+
 PYRO_API int pyro_selftest_wait_timeout(int limit_ms, void *stream)
 {
     PYRO_CHECK(limit_ms >= 1 && limit_ms <= 1000, "limit_ms=%d outside [1, 1000]", limit_ms);
