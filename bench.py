@@ -605,7 +605,10 @@ def run_configs(args):
     ang = gp.view_angles()
     i64, s64 = img.double().cpu().numpy(), sino.double().cpu().numpy()
     ns, nb = samples2d(gp, 1), 128 * 128 * 180
-    t = {"fp": gpu_ms(lambda: B.pyro_fp_par2d(img, gp)), "bp": gpu_ms(lambda: B.pyro_bp_par2d(sino, gp)),
+    wsp = torch.empty(B.fp2d_workspace_bytes(gp, 1), dtype=torch.uint8, device=dev)
+    t = {"fp": gpu_ms(lambda: B.pyro_fp_par2d(img, gp)),
+         "fp_staged": gpu_ms(lambda: B.pyro_fp_par2d_ws(img, gp, workspace=wsp)),
+         "bp": gpu_ms(lambda: B.pyro_bp_par2d(sino, gp)),
          "fbp": gpu_ms(lambda: B.pyro_fbp_par2d(sino, gp, kind=B.RAMLAK))}
     c = {"fp": cpu_s(lambda: oracle.fp_par2d(i64, (1.0, 1.0), 183, 1.0, ang)),
          "bp": cpu_s(lambda: oracle.bp_par2d(s64, (128, 128), (1.0, 1.0), 1.0, ang)),
@@ -625,14 +628,20 @@ def run_configs(args):
     angf = gf.view_angles()
     i0, s0 = imgs[0].double().cpu().numpy(), sf[0].double().cpu().numpy()
     ns, nb = samples2d(gf, 16), 16 * 512 * 512 * 360
-    t = {"fp": gpu_ms(lambda: B.pyro_fp_fan2d(imgs, gf)), "fpT": gpu_ms(lambda: B.pyro_fpT_fan2d(sf, gf)),
+    wsf = torch.empty(B.fp2d_workspace_bytes(gf, 16), dtype=torch.uint8, device=dev)
+    t = {"fp": gpu_ms(lambda: B.pyro_fp_fan2d(imgs, gf)),
+         "fp_staged": gpu_ms(lambda: B.pyro_fp_fan2d_ws(imgs, gf, workspace=wsf)),
+         "fpT": gpu_ms(lambda: B.pyro_fpT_fan2d(sf, gf)),
+         "fpT_staged": gpu_ms(lambda: B.pyro_fpT_fan2d_ws(sf, gf, workspace=wsf)),
          "bp": gpu_ms(lambda: B.pyro_bp_fan2d(sf, gf, weight=B.W_INV_L2, scale=1.0))}
     c = {"fp": cpu_s(lambda: oracle.fp_fan2d(i0, (0.5, 0.5), 1024, 1.0, angf, 750.0, 1200.0, step=0.25)),
          "fpT": cpu_s(lambda: oracle.fpT_fan2d(s0, (512, 512), (0.5, 0.5), 1.0, angf, 750.0, 1200.0, step=0.25)),
          "bp": cpu_s(lambda: oracle.bp_fan2d(s0, (512, 512), (0.5, 0.5), 1.0, angf, 750.0, 1200.0, 2, 1.0))}
     out["fan2d_16x512"] = {"gpu_ms": {k: round(v, 4) for k, v in t.items()},
                            "fp_gsamples_per_s": round(ns / (t["fp"] * 1e-3) / 1e9, 2),
+                           "fp_staged_gsamples_per_s": round(ns / (t["fp_staged"] * 1e-3) / 1e9, 2),
                            "fpT_gsamples_per_s": round(ns / (t["fpT"] * 1e-3) / 1e9, 2),
+                           "fpT_staged_gsamples_per_s": round(ns / (t["fpT_staged"] * 1e-3) / 1e9, 2),
                            "bp_gups": round(nb / (t["bp"] * 1e-3) / 1e9, 2),
                            "cpu_baseline": {"kind": "oracle", "cores": oracle.num_threads(),
                                             "sample": "one of the 16 phantoms",

@@ -117,6 +117,27 @@ PYRO_API int pyro_fp_fan2d(const void *vol, void *sino, int batch, const pyro_ge
 PYRO_API int pyro_fp_cone3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtype dtype,
                             void *stream);
 
+/* --- The same 2D forward projections, also reading a transposed copy of
+ * the batch kept in `workspace` (device, at least pyro_fp2d_workspace_bytes
+ * bytes: batch images of `dtype`; PYRO_EWORKSPACE otherwise): a warp's lanes
+ * take consecutive detector bins, and for views whose rays run closer to x
+ * than to y the bins' taps are contiguous in the transposed copy.  Results
+ * equal pyro_fp_par2d / pyro_fp_fan2d up to FP32 rounding order. */
+PYRO_API size_t pyro_fp2d_workspace_bytes(const pyro_geom2d *g, int batch, pyro_dtype dtype);
+PYRO_API int pyro_fp_par2d_ws(const void *vol, void *sino, int batch, const pyro_geom2d *g, void *workspace,
+                              size_t workspace_bytes, pyro_dtype dtype, void *stream);
+PYRO_API int pyro_fp_fan2d_ws(const void *vol, void *sino, int batch, const pyro_geom2d *g, void *workspace,
+                              size_t workspace_bytes, pyro_dtype dtype, void *stream);
+/* The exact adjoints of the 2D projections with a transposed FP32
+ * accumulator in `workspace` (pyro_fp2d_workspace_bytes(g, batch, PYRO_F32)
+ * bytes at least) for the views whose rays run closer to x, added back into
+ * vol at the end.  Equal to pyro_fpT_par2d / pyro_fpT_fan2d up to FP32
+ * summation order.  PYRO_F32 only. */
+PYRO_API int pyro_fpT_par2d_ws(const void *sino, void *vol, int batch, const pyro_geom2d *g, void *workspace,
+                               size_t workspace_bytes, pyro_dtype dtype, void *stream);
+PYRO_API int pyro_fpT_fan2d_ws(const void *sino, void *vol, int batch, const pyro_geom2d *g, void *workspace,
+                               size_t workspace_bytes, pyro_dtype dtype, void *stream);
+
 /* --- The projection matrices the cone-beam calls use for geometry `g`
  * (the circular trajectory's when g->proj_mats is NULL, else the given
  * ones), normalised as the calls normalise them: third row (the depth) of

@@ -55,6 +55,11 @@ _SIGS = {
     "pyro_fpT_fan2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fpT_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
     "pyro_fpT_cone3d_workspace_bytes": [_G3],
+    "pyro_fp2d_workspace_bytes": [_G2, _I, _I],
+    "pyro_fp_par2d_ws": [_VP, _VP, _I, _G2, _VP, _SZ, _I, _VP],
+    "pyro_fp_fan2d_ws": [_VP, _VP, _I, _G2, _VP, _SZ, _I, _VP],
+    "pyro_fpT_par2d_ws": [_VP, _VP, _I, _G2, _VP, _SZ, _I, _VP],
+    "pyro_fpT_fan2d_ws": [_VP, _VP, _I, _G2, _VP, _SZ, _I, _VP],
     "pyro_cone_projection_matrices": [_G3, _VP],
     "pyro_weights3d_table": [_VP, _I, _G3, _VP, _I, _I, _VP],
     "pyro_bb_dots": [_VP, _VP, _VP, _VP, ctypes.c_long, _VP, _VP],
@@ -113,6 +118,7 @@ def lib():
             L.pyro_fdk_workspace_bytes.restype = _SZ
             L.pyro_fp_cone3d_workspace_bytes.restype = _SZ
             L.pyro_fpT_cone3d_workspace_bytes.restype = _SZ
+            L.pyro_fp2d_workspace_bytes.restype = _SZ
             L.pyro_fbp2d_workspace_bytes.restype = _SZ
             _lib = L
     return _lib
@@ -212,6 +218,62 @@ def pyro_fp_par2d(vol: torch.Tensor, g: Geometry2D) -> torch.Tensor:
 
 def pyro_fp_fan2d(vol: torch.Tensor, g: Geometry2D) -> torch.Tensor:
     return _fp(lib().pyro_fp_fan2d, vol, g, g.volume_shape, g.sinogram_shape)
+
+
+def _fp2d_ws(fn, vol, g, workspace, out):
+    v, squeeze = _batched(_dev(vol, "volume"), 2, "volume")
+    _shape_check(v, g.volume_shape, "volume")
+    cg = g.to_c()
+    need = lib().pyro_fp2d_workspace_bytes(ctypes.byref(cg), v.shape[0], _DTYPES[v.dtype])
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=v.device)
+    o = _out(v, g.sinogram_shape) if out is None else _dev(out, "out")
+    with torch.cuda.device(v.device):
+        _check(fn(_ptr(v), _ptr(o), v.shape[0], ctypes.byref(cg), _ptr(workspace),
+                  workspace.numel() * workspace.element_size(), _DTYPES[v.dtype], _stream(v)))
+    return o[0] if squeeze and out is None else o
+
+
+def pyro_fp_par2d_ws(vol: torch.Tensor, g: Geometry2D, workspace: Optional[torch.Tensor] = None,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Parallel-beam FP that also reads a transposed copy of the batch kept in
+    `workspace` (allocated here when not given)."""
+    return _fp2d_ws(lib().pyro_fp_par2d_ws, vol, g, workspace, out)
+
+
+def pyro_fp_fan2d_ws(vol: torch.Tensor, g: Geometry2D, workspace: Optional[torch.Tensor] = None,
+                     out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Fan-beam FP that also reads a transposed copy of the batch."""
+    return _fp2d_ws(lib().pyro_fp_fan2d_ws, vol, g, workspace, out)
+
+
+def _fpT2d_ws(fn, sino, g, workspace):
+    s, squeeze = _batched(_dev(sino, "sinogram"), 2, "sinogram")
+    _shape_check(s, g.sinogram_shape, "sinogram")
+    cg = g.to_c()
+    need = lib().pyro_fp2d_workspace_bytes(ctypes.byref(cg), s.shape[0], PYRO_F32)
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=s.device)
+    out = _out(s, g.volume_shape)
+    with torch.cuda.device(s.device):
+        _check(fn(_ptr(s), _ptr(out), s.shape[0], ctypes.byref(cg), _ptr(workspace),
+                  workspace.numel() * workspace.element_size(), _DTYPES[s.dtype], _stream(s)))
+    return out[0] if squeeze else out
+
+
+def pyro_fpT_par2d_ws(sino: torch.Tensor, g: Geometry2D, workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Exact adjoint of the parallel-beam FP with a transposed accumulator."""
+    return _fpT2d_ws(lib().pyro_fpT_par2d_ws, sino, g, workspace)
+
+
+def pyro_fpT_fan2d_ws(sino: torch.Tensor, g: Geometry2D, workspace: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Exact adjoint of the fan-beam FP with a transposed accumulator."""
+    return _fpT2d_ws(lib().pyro_fpT_fan2d_ws, sino, g, workspace)
+
+
+def fp2d_workspace_bytes(g: Geometry2D, batch: int, dtype=torch.float32) -> int:
+    cg = g.to_c()
+    return int(lib().pyro_fp2d_workspace_bytes(ctypes.byref(cg), int(batch), _DTYPES[dtype]))
 
 
 def pyro_fp_cone3d(vol: torch.Tensor, g: ConeGeometry3D) -> torch.Tensor:

@@ -110,9 +110,12 @@ struct FilterParams {
 
 // --------------------------------------------------------------- launchers --
 // All launchers return cudaSuccess or the launch error; T is the storage type.
-cudaError_t launch_fp2d(const void *vol, void *sino, int batch, const FP2DParams &p, pyro_dtype dt,
+cudaError_t launch_fp2d(const void *vol, const void *volT, void *sino, int batch, const FP2DParams &p, pyro_dtype dt,
                         cudaStream_t s);
-cudaError_t launch_fp2d_adjoint(const void *sino, void *vol, int batch, const FP2DParams &p, cudaStream_t s);
+cudaError_t launch_transpose2d(const void *in, void *out, int batch, int nx, int ny, pyro_dtype dt, cudaStream_t s);
+cudaError_t launch_fp2d_adjoint(const void *sino, void *vol, void *volT, int batch, const FP2DParams &p,
+                                cudaStream_t s);
+cudaError_t launch_add_transposed(const void *accT, void *vol, int batch, int nx, int ny, cudaStream_t s);
 cudaError_t launch_fp3d(const void *vol, void *sino, int batch, const FP3DParams &p, pyro_dtype dt,
                         cudaStream_t s);
 cudaError_t launch_fp3d_adjoint(const void *sino, void *vol, int batch, const FP3DParams &p, cudaStream_t s);

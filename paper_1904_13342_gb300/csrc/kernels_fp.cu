@@ -64,22 +64,38 @@ __device__ __forceinline__ void range2d(const Ray2 &r, const FP2DParams &p, int 
     m1 = min(p.M, (int)ceilf(hi));
 }
 
+// volT (may be NULL): the batch transposed, [b][x][y].  The lanes of a warp
+// take consecutive detector bins, which for a given sample lie along e_u:
+// when the rays run closer to x than to y (|c_x| > |c_y|) the bins spread
+// along y, so their taps are contiguous in the transposed copy; the kernel
+// then reads that copy with the roles of x and y swapped.
 template <typename T>
-__global__ void __launch_bounds__(128) fp2d_kernel(const T *__restrict__ vol, T *__restrict__ sino,
-                                                   const __grid_constant__ FP2DParams p)
+__global__ void __launch_bounds__(128) fp2d_kernel(const T *__restrict__ vol, const T *__restrict__ volT,
+                                                   T *__restrict__ sino, const __grid_constant__ FP2DParams p)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
     const int v = blockIdx.y;
     const int b = blockIdx.z;
     if (k >= p.nu) return;
-    const Ray2 r = ray2d(p, v, k);
+    Ray2 r = ray2d(p, v, k);
     int m0, m1;
     range2d(r, p, m0, m1);
     const T *img = vol + (size_t)b * p.nx * p.ny;
+    int nx = p.nx, ny = p.ny;
+    if (volT && fabsf(p.dir[v].x) > fabsf(p.dir[v].y)) {  // the whole block: one view
+        img = volT + (size_t)b * p.nx * p.ny;
+        nx = p.ny;
+        ny = p.nx;
+        const float t0 = r.px, t1 = r.qx;
+        r.px = r.py;
+        r.qx = r.qy;
+        r.py = t0;
+        r.qy = t1;
+    }
     // samples whose four taps are all inside the image take the unmasked path
     float lo = (float)m0, hi = (float)m1;
-    clip_axis_interior(r.px, r.qx, p.nx, lo, hi);
-    clip_axis_interior(r.py, r.qy, p.ny, lo, hi);
+    clip_axis_interior(r.px, r.qx, nx, lo, hi);
+    clip_axis_interior(r.py, r.qy, ny, lo, hi);
     int i0 = max(m0, (int)ceilf(lo)), i1 = min(m1, (int)floorf(hi));
     if (i0 > i1) {  // no interior sample
         i0 = m1 + 1;
@@ -88,7 +104,7 @@ __global__ void __launch_bounds__(128) fp2d_kernel(const T *__restrict__ vol, T 
     float acc = 0.0f;
     for (int m = m0; m < i0; ++m) {
         const float fm = (float)m;
-        acc += bilerp_zero(img, p.nx, p.ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
+        acc += bilerp_zero(img, nx, ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
     }
     // two samples per iteration with separate partial sums (unrolled twice
     // more by the compiler), so that several samples' loads are in flight
@@ -97,19 +113,24 @@ __global__ void __launch_bounds__(128) fp2d_kernel(const T *__restrict__ vol, T 
 #pragma unroll 2
     for (; m + 1 <= i1; m += 2) {
         const float fa = (float)m, fb = (float)(m + 1);
-        acc += bilerp_interior(img, 1, p.nx, fmaf(fa, r.qx, r.px), fmaf(fa, r.qy, r.py));
-        acc2 += bilerp_interior(img, 1, p.nx, fmaf(fb, r.qx, r.px), fmaf(fb, r.qy, r.py));
+        acc += bilerp_interior(img, 1, nx, fmaf(fa, r.qx, r.px), fmaf(fa, r.qy, r.py));
+        acc2 += bilerp_interior(img, 1, nx, fmaf(fb, r.qx, r.px), fmaf(fb, r.qy, r.py));
     }
-    if (m <= i1) acc += bilerp_interior(img, 1, p.nx, fmaf((float)m, r.qx, r.px), fmaf((float)m, r.qy, r.py));
+    if (m <= i1) acc += bilerp_interior(img, 1, nx, fmaf((float)m, r.qx, r.px), fmaf((float)m, r.qy, r.py));
     acc += acc2;
     for (int m = max(i1 + 1, i0); m <= m1; ++m) {
         const float fm = (float)m;
-        acc += bilerp_zero(img, p.nx, p.ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
+        acc += bilerp_zero(img, nx, ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
     }
     sino[((size_t)b * p.views_total + p.view0 + v) * p.nu + k] = to_storage<T>(r.w * acc);
 }
 
+// volT (may be NULL): a zeroed transposed accumulator [b][x][y] that takes
+// the views whose rays run closer to x than to y (their detector bins spread
+// along y, so the warp's atomics are contiguous there); the caller adds it
+// back, transposed, into vol.
 __global__ void __launch_bounds__(128) fp2d_adjoint_kernel(const float *__restrict__ sino, float *__restrict__ vol,
+                                                           float *__restrict__ volT,
                                                            const __grid_constant__ FP2DParams p)
 {
     const int k = blockIdx.x * blockDim.x + threadIdx.x;
@@ -118,17 +139,28 @@ __global__ void __launch_bounds__(128) fp2d_adjoint_kernel(const float *__restri
     if (k >= p.nu) return;
     const float y0s = sino[((size_t)b * p.views_total + p.view0 + v) * p.nu + k];
     if (y0s == 0.0f) return;
-    const Ray2 r = ray2d(p, v, k);
+    Ray2 r = ray2d(p, v, k);
     const float y = r.w * y0s;
     int m0, m1;
     range2d(r, p, m0, m1);
     float *img = vol + (size_t)b * p.nx * p.ny;
+    int nx = p.nx, ny = p.ny;
+    if (volT && fabsf(p.dir[v].x) > fabsf(p.dir[v].y)) {  // the whole block: one view
+        img = volT + (size_t)b * p.nx * p.ny;
+        nx = p.ny;
+        ny = p.nx;
+        const float t0 = r.px, t1 = r.qx;
+        r.px = r.py;
+        r.qx = r.qy;
+        r.py = t0;
+        r.qy = t1;
+    }
     for (int m = m0; m <= m1; ++m) {
         const float fm = (float)m;
-        const Axis ax = axis_taps(fmaf(fm, r.qx, r.px), p.nx);
-        const Axis ay = axis_taps(fmaf(fm, r.qy, r.py), p.ny);
-        float *r0 = img + (size_t)ay.i0 * p.nx;
-        float *r1 = img + (size_t)ay.i1 * p.nx;
+        const Axis ax = axis_taps(fmaf(fm, r.qx, r.px), nx);
+        const Axis ay = axis_taps(fmaf(fm, r.qy, r.py), ny);
+        float *r0 = img + (size_t)ay.i0 * nx;
+        float *r1 = img + (size_t)ay.i1 * nx;
         const float y0 = y * ay.w0, y1 = y * ay.w1;
         if (y0 * ax.w0 != 0.0f) atomicAdd(r0 + ax.i0, y0 * ax.w0);
         if (y0 * ax.w1 != 0.0f) atomicAdd(r0 + ax.i1, y0 * ax.w1);
@@ -670,29 +702,93 @@ __global__ void __launch_bounds__(kFP3DBlockX *kFP3DBlockY) fp3d_adjoint_kernel(
 
 }  // namespace
 
-cudaError_t launch_fp2d(const void *vol, void *sino, int batch, const FP2DParams &p, pyro_dtype dt, cudaStream_t s)
+cudaError_t launch_fp2d(const void *vol, const void *volT, void *sino, int batch, const FP2DParams &p, pyro_dtype dt,
+                        cudaStream_t s)
 {
     dim3 block(128);
     dim3 grid((p.nu + 127) / 128, p.n_views, batch);
     switch (dt) {
     case PYRO_F32:
-        fp2d_kernel<float><<<grid, block, 0, s>>>((const float *)vol, (float *)sino, p);
+        fp2d_kernel<float><<<grid, block, 0, s>>>((const float *)vol, (const float *)volT, (float *)sino, p);
         break;
     case PYRO_F16:
-        fp2d_kernel<__half><<<grid, block, 0, s>>>((const __half *)vol, (__half *)sino, p);
+        fp2d_kernel<__half><<<grid, block, 0, s>>>((const __half *)vol, (const __half *)volT, (__half *)sino, p);
         break;
     case PYRO_BF16:
-        fp2d_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16 *)vol, (__nv_bfloat16 *)sino, p);
+        fp2d_kernel<__nv_bfloat16><<<grid, block, 0, s>>>((const __nv_bfloat16 *)vol, (const __nv_bfloat16 *)volT,
+                                                          (__nv_bfloat16 *)sino, p);
         break;
     }
     return cudaGetLastError();
 }
 
-cudaError_t launch_fp2d_adjoint(const void *sino, void *vol, int batch, const FP2DParams &p, cudaStream_t s)
+// [b][y][x] -> [b][x][y], 32 x 32 tiles through shared memory
+template <typename T>
+__global__ void __launch_bounds__(256) transpose2d_kernel(const T *__restrict__ in, T *__restrict__ out, int nx, int ny)
+{
+    __shared__ T tile[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const size_t off = (size_t)blockIdx.z * nx * ny;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int y = y0 + i, x = x0 + threadIdx.x;
+        if (y < ny && x < nx) tile[i][threadIdx.x] = in[off + (size_t)y * nx + x];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int x = x0 + i, y = y0 + threadIdx.x;
+        if (y < ny && x < nx) out[off + (size_t)x * ny + y] = tile[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_transpose2d(const void *in, void *out, int batch, int nx, int ny, pyro_dtype dt, cudaStream_t s)
+{
+    dim3 block(32, 8), grid((nx + 31) / 32, (ny + 31) / 32, batch);
+    switch (dt) {
+    case PYRO_F32:
+        transpose2d_kernel<float><<<grid, block, 0, s>>>((const float *)in, (float *)out, nx, ny);
+        break;
+    case PYRO_F16:
+        transpose2d_kernel<__half><<<grid, block, 0, s>>>((const __half *)in, (__half *)out, nx, ny);
+        break;
+    case PYRO_BF16:
+        transpose2d_kernel<__nv_bfloat16>
+            <<<grid, block, 0, s>>>((const __nv_bfloat16 *)in, (__nv_bfloat16 *)out, nx, ny);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp2d_adjoint(const void *sino, void *vol, void *volT, int batch, const FP2DParams &p,
+                                cudaStream_t s)
 {
     dim3 block(128);
     dim3 grid((p.nu + 127) / 128, p.n_views, batch);
-    fp2d_adjoint_kernel<<<grid, block, 0, s>>>((const float *)sino, (float *)vol, p);
+    fp2d_adjoint_kernel<<<grid, block, 0, s>>>((const float *)sino, (float *)vol, (float *)volT, p);
+    return cudaGetLastError();
+}
+
+// vol[b][y][x] += accT[b][x][y], 32 x 32 tiles through shared memory
+__global__ void __launch_bounds__(256) add_transposed_kernel(const float *__restrict__ accT, float *__restrict__ vol,
+                                                             int nx, int ny)
+{
+    __shared__ float tile[32][33];
+    const int x0 = blockIdx.x * 32, y0 = blockIdx.y * 32;
+    const size_t off = (size_t)blockIdx.z * nx * ny;
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int x = x0 + i, y = y0 + threadIdx.x;
+        if (x < nx && y < ny) tile[i][threadIdx.x] = accT[off + (size_t)x * ny + y];
+    }
+    __syncthreads();
+    for (int i = threadIdx.y; i < 32; i += 8) {
+        const int y = y0 + i, x = x0 + threadIdx.x;
+        if (x < nx && y < ny) vol[off + (size_t)y * nx + x] += tile[threadIdx.x][i];
+    }
+}
+
+cudaError_t launch_add_transposed(const void *accT, void *vol, int batch, int nx, int ny, cudaStream_t s)
+{
+    dim3 block(32, 8), grid((nx + 31) / 32, (ny + 31) / 32, batch);
+    add_transposed_kernel<<<grid, block, 0, s>>>((const float *)accT, (float *)vol, nx, ny);
     return cudaGetLastError();
 }
 

@@ -522,12 +522,24 @@ cudaStream_t as_stream(void *s)
 }
 
 // -------------------------------------------------------- operations ----
-int fp2d(bool fan, const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dt, void *stream)
+// work (may be NULL): a transposed copy of the batch for the staged form
+int fp2d(bool fan, const void *vol, void *sino, int batch, const pyro_geom2d *g, pyro_dtype dt, void *stream,
+         void *work = nullptr, size_t work_bytes = 0)
 {
     if (int e = check_io(vol, sino, batch, dt)) return e;
     Geo2D G;
     if (int e = prep2d(g, fan, G)) return e;
+    const size_t img = (size_t)G.nx * G.ny * elem_size(dt);
+    if (work) {
+        const size_t need = img * (size_t)std::max(batch, 1);
+        if (work_bytes < need || !aligned16(work))
+            return fail(PYRO_EWORKSPACE, "the staged 2D projector needs a 16-byte aligned workspace of %zu bytes "
+                                         "(got %zu)", need, work_bytes);
+    }
     if (batch == 0) return PYRO_OK;
+    for (int b0 = 0; work && b0 < batch; b0 += 65535)
+        PYRO_CUDA(launch_transpose2d((const char *)vol + b0 * img, (char *)work + b0 * img,
+                                     std::min(65535, batch - b0), G.nx, G.ny, dt, as_stream(stream)));
     const int V = (int)G.beta.size();
     static thread_local FP2DParams p;
     for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
@@ -535,23 +547,34 @@ int fp2d(bool fan, const void *vol, void *sino, int batch, const pyro_geom2d *g,
         fill_fp2d(G, v0, nvw, p);
         for (int b0 = 0; b0 < batch; b0 += 65535) {
             const int nb = std::min(65535, batch - b0);
-            const char *vi = (const char *)vol + (size_t)b0 * G.nx * G.ny * elem_size(dt);
+            const char *vi = (const char *)vol + (size_t)b0 * img;
+            const char *vt = work ? (const char *)work + (size_t)b0 * img : nullptr;
             char *so = (char *)sino + (size_t)b0 * V * G.nu * elem_size(dt);
-            PYRO_CUDA(launch_fp2d(vi, so, nb, p, dt, as_stream(stream)));
+            PYRO_CUDA(launch_fp2d(vi, vt, so, nb, p, dt, as_stream(stream)));
         }
     }
     return PYRO_OK;
 }
 
-int fp2d_adjoint(bool fan, const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dt, void *stream)
+// work (may be NULL): a transposed FP32 accumulator for the staged form
+int fp2d_adjoint(bool fan, const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dt, void *stream,
+                 void *work = nullptr, size_t work_bytes = 0)
 {
     if (int e = check_io(sino, vol, batch, dt)) return e;
     if (dt != PYRO_F32) return fail(PYRO_EUNSUPPORTED, "the FP adjoint supports PYRO_F32 only");
     Geo2D G;
     if (int e = prep2d(g, fan, G)) return e;
+    const size_t vox_bytes = sizeof(float) * (size_t)G.nx * G.ny;
+    if (work) {
+        const size_t need = vox_bytes * (size_t)std::max(batch, 1);
+        if (work_bytes < need || !aligned16(work))
+            return fail(PYRO_EWORKSPACE, "the staged 2D adjoint needs a 16-byte aligned workspace of %zu bytes "
+                                         "(got %zu)", need, work_bytes);
+    }
     if (batch == 0) return PYRO_OK;
     const int V = (int)G.beta.size();
-    PYRO_CUDA(cudaMemsetAsync(vol, 0, sizeof(float) * (size_t)batch * G.nx * G.ny, as_stream(stream)));
+    PYRO_CUDA(cudaMemsetAsync(vol, 0, vox_bytes * batch, as_stream(stream)));
+    if (work) PYRO_CUDA(cudaMemsetAsync(work, 0, vox_bytes * batch, as_stream(stream)));
     static thread_local FP2DParams p;
     for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
         const int nvw = std::min(kMaxViews2D, V - v0);
@@ -560,9 +583,14 @@ int fp2d_adjoint(bool fan, const void *sino, void *vol, int batch, const pyro_ge
             const int nb = std::min(65535, batch - b0);
             const float *si = (const float *)sino + (size_t)b0 * V * G.nu;
             float *vo = (float *)vol + (size_t)b0 * G.nx * G.ny;
-            PYRO_CUDA(launch_fp2d_adjoint(si, vo, nb, p, as_stream(stream)));
+            float *vt = work ? (float *)work + (size_t)b0 * G.nx * G.ny : nullptr;
+            PYRO_CUDA(launch_fp2d_adjoint(si, vo, vt, nb, p, as_stream(stream)));
         }
     }
+    for (int b0 = 0; work && b0 < batch; b0 += 65535)
+        PYRO_CUDA(launch_add_transposed((const float *)work + (size_t)b0 * G.nx * G.ny,
+                                        (float *)vol + (size_t)b0 * G.nx * G.ny, std::min(65535, batch - b0), G.nx,
+                                        G.ny, as_stream(stream)));
     return PYRO_OK;
 }
 
@@ -951,6 +979,40 @@ PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyr
                                size_t workspace_bytes, pyro_dtype dtype, void *stream)
 {
     return fp3d_staged(vol, sino, batch, g, workspace, workspace_bytes, dtype, stream);
+}
+
+PYRO_API size_t pyro_fp2d_workspace_bytes(const pyro_geom2d *g, int batch, pyro_dtype dtype)
+{
+    if (!g || g->nx <= 0 || g->ny <= 0 || batch < 0 || !valid_dtype(dtype)) return 0;
+    return (size_t)g->nx * g->ny * elem_size(dtype) * (size_t)std::max(batch, 1);
+}
+
+PYRO_API int pyro_fp_par2d_ws(const void *vol, void *sino, int batch, const pyro_geom2d *g, void *workspace,
+                              size_t workspace_bytes, pyro_dtype dtype, void *stream)
+{
+    PYRO_CHECK(workspace != nullptr, "workspace is NULL");
+    return fp2d(false, vol, sino, batch, g, dtype, stream, workspace, workspace_bytes);
+}
+
+PYRO_API int pyro_fp_fan2d_ws(const void *vol, void *sino, int batch, const pyro_geom2d *g, void *workspace,
+                              size_t workspace_bytes, pyro_dtype dtype, void *stream)
+{
+    PYRO_CHECK(workspace != nullptr, "workspace is NULL");
+    return fp2d(true, vol, sino, batch, g, dtype, stream, workspace, workspace_bytes);
+}
+
+PYRO_API int pyro_fpT_par2d_ws(const void *sino, void *vol, int batch, const pyro_geom2d *g, void *workspace,
+                               size_t workspace_bytes, pyro_dtype dtype, void *stream)
+{
+    PYRO_CHECK(workspace != nullptr, "workspace is NULL");
+    return fp2d_adjoint(false, sino, vol, batch, g, dtype, stream, workspace, workspace_bytes);
+}
+
+PYRO_API int pyro_fpT_fan2d_ws(const void *sino, void *vol, int batch, const pyro_geom2d *g, void *workspace,
+                               size_t workspace_bytes, pyro_dtype dtype, void *stream)
+{
+    PYRO_CHECK(workspace != nullptr, "workspace is NULL");
+    return fp2d_adjoint(true, sino, vol, batch, g, dtype, stream, workspace, workspace_bytes);
 }
 
 PYRO_API int pyro_fpT_par2d(const void *sino, void *vol, int batch, const pyro_geom2d *g, pyro_dtype dtype,

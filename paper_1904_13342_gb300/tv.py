@@ -47,9 +47,15 @@ def _ops(g):
             return B.pyro_fpT_cone3d_ws(y, g, workspace=ws["wT"])
 
         return A, AT
-    if g.fan:
-        return (lambda x, out=None: B.pyro_fp_fan2d(x, g)), (lambda y: B.pyro_fpT_fan2d(y, g))
-    return (lambda x, out=None: B.pyro_fp_par2d(x, g)), (lambda y: B.pyro_fpT_par2d(y, g))
+    fp, fpT = (B.pyro_fp_fan2d_ws, B.pyro_fpT_fan2d_ws) if g.fan else (B.pyro_fp_par2d_ws, B.pyro_fpT_par2d_ws)
+    ws = {}
+
+    def work(t):  # one FP32 image: the transposed copy (FP) and accumulator (adjoint)
+        if "w" not in ws:
+            ws["w"] = torch.empty(B.fp2d_workspace_bytes(g, 1), dtype=torch.uint8, device=t.device)
+        return ws["w"]
+
+    return (lambda x, out=None: fp(x, g, workspace=work(x), out=out)), (lambda y: fpT(y, g, workspace=work(y)))
 
 
 def estimate_lipschitz(g, shape, device, iters: int = 20, seed: int = 0) -> float:

@@ -98,6 +98,34 @@ def test_fp_2d(geom, dtype):
     assert rel(host(got), np.stack(ref)) < TOL[dtype]
 
 
+@pytest.mark.parametrize("dtype", [torch.float32, torch.float16, torch.bfloat16])
+@pytest.mark.parametrize("geom", ["par", "fan"])
+def test_fp_2d_staged(geom, dtype):
+    """The staged 2D projector (a transposed copy for the views whose rays run
+    closer to x) against the oracle and the plain call; views all round."""
+    c = dict(PAR if geom == "par" else FAN, views=37, range=2 * math.pi)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    vol = np.stack([ph.voxelize_ellipses(ph.random_ellipses(6, 25.0, seed=60 + k), c["shape"], c["spacing"]).numpy()
+                    for k in range(3)])
+    if geom == "par":
+        g = par_geom(c)
+        ref = np.stack([oracle.fp_par2d(f32(v), c["spacing"], c["nu"], c["su"], ang) for v in vol])
+        got = B.pyro_fp_par2d_ws(to_dev(vol, dtype), g)
+        plain = B.pyro_fp_par2d(to_dev(vol, dtype), g)
+    else:
+        g = fan_geom(c)
+        ref = np.stack([oracle.fp_fan2d(f32(v), c["spacing"], c["nu"], c["su"], ang, c["sid"], c["sdd"]) for v in vol])
+        got = B.pyro_fp_fan2d_ws(to_dev(vol, dtype), g)
+        plain = B.pyro_fp_fan2d(to_dev(vol, dtype), g)
+    assert rel(host(got), ref) < TOL[dtype]
+    assert rel(host(got), host(plain)) < TOL[dtype]
+    small = torch.empty(16, dtype=torch.uint8, device=DEV)
+    with pytest.raises(B.PyroError) as e:
+        B.pyro_fp_par2d_ws(to_dev(vol), par_geom(c), workspace=small) if geom == "par" else \
+            B.pyro_fp_fan2d_ws(to_dev(vol), fan_geom(c), workspace=small)
+    assert e.value.status == 5
+
+
 @pytest.mark.parametrize("geom", ["par", "fan"])
 def test_fp_adjoint_2d(geom):
     c = PAR if geom == "par" else FAN
@@ -105,11 +133,21 @@ def test_fp_adjoint_2d(geom):
     ang = np.random.default_rng(4).uniform(0, 2 * np.pi, c["views"])  # explicit, unordered angles
     if geom == "par":
         got = B.pyro_fpT_par2d(to_dev(y), par_geom(c, angles=ang))
+        staged = B.pyro_fpT_par2d_ws(to_dev(y), par_geom(c, angles=ang))
         ref = [oracle.fpT_par2d(f32(s), c["shape"], c["spacing"], c["su"], ang) for s in y]
     else:
         got = B.pyro_fpT_fan2d(to_dev(y), fan_geom(c, angles=ang))
+        staged = B.pyro_fpT_fan2d_ws(to_dev(y), fan_geom(c, angles=ang))
         ref = [oracle.fpT_fan2d(f32(s), c["shape"], c["spacing"], c["su"], ang, c["sid"], c["sdd"]) for s in y]
     assert rel(host(got), np.stack(ref)) < 1e-5
+    # the transposed accumulator: views of both kinds (the angles cover the circle)
+    assert rel(host(staged), np.stack(ref)) < 1e-5
+    assert rel(host(staged), host(got)) < 1e-5
+    small = torch.empty(16, dtype=torch.uint8, device=DEV)
+    with pytest.raises(B.PyroError) as e:
+        B.pyro_fpT_par2d_ws(to_dev(y), par_geom(c, angles=ang), workspace=small) if geom == "par" else \
+            B.pyro_fpT_fan2d_ws(to_dev(y), fan_geom(c, angles=ang), workspace=small)
+    assert e.value.status == 5
 
 
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
