@@ -70,16 +70,17 @@ def _load():
                                             _PI, _PI, _PI, _PD],
                 "oracle_bpT_cone3d": [_PD, _I, _I, _I, _D, _D, _D, _I, _I, _I, _PD, _D, _I, _D, _PD],
                 "oracle_parker_weight": [_D, _D, _D],
-                "oracle_weights": [_PD, _I, _I, _I, _D, _D, _PD, _D, _I, _I],
+                "oracle_scan_weight": [_D, _D, _D],
+                "oracle_weights": [_PD, _I, _I, _I, _D, _D, _PD, _D, _I, _I, _D],
                 "oracle_pad_length": [_I],
                 "oracle_filter_rows": [_PD, _PD, _L, _I, _D, _I, _PD],
                 "oracle_filter_grad_K": [_PD, _PD, _L, _I, _PD],
                 "oracle_fbp_par2d": [_PD, _I, _I, _D, _D, _I, _D, _I, _PD, _I, _PD, _PD],
-                "oracle_fbp_fan2d": [_PD, _I, _I, _D, _D, _I, _D, _I, _PD, _D, _D, _D, _I, _PD, _I, _PD],
+                "oracle_fbp_fan2d": [_PD, _I, _I, _D, _D, _I, _D, _I, _PD, _D, _D, _D, _I, _PD, _I, _D, _PD],
                 "oracle_fdk": [_PD, _I, _I, _I, _D, _D, _D, _I, _I, _D, _D, _I, _PD, _PD, _D, _D, _D, _I, _PD,
-                               _I, _PD],
+                               _I, _D, _PD],
                 "oracle_fdk_voxels": [_PD, _I, _I, _I, _D, _D, _D, _I, _I, _D, _D, _I, _PD, _PD, _D, _D, _D, _I,
-                                      _PD, _I, _I, _PI, _PI, _PI, _PD],
+                                      _PD, _I, _D, _I, _PI, _PI, _PI, _PD],
                 "oracle_tv_value": [_PD, _I, _I, _I, _D],
                 "oracle_tv_grad": [_PD, _I, _I, _I, _D, _PD],
                 "oracle_num_threads": [],
@@ -89,6 +90,7 @@ def _load():
                 fn.argtypes = args
                 fn.restype = None
             lib.oracle_parker_weight.restype = _D
+            lib.oracle_scan_weight.restype = _D
             lib.oracle_pad_length.restype = _I
             lib.oracle_tv_value.restype = _D
             lib.oracle_num_threads.restype = _I
@@ -114,7 +116,7 @@ def _p(a: np.ndarray):
 
 # filter kinds and redundancy modes, same numbering as the product API
 RAMLAK, RAMP, SHEPP_LOGAN, CUSTOM = 0, 1, 2, 3
-REDUND_FULL, REDUND_PARKER, REDUND_NONE = 0, 1, 2
+REDUND_FULL, REDUND_PARKER, REDUND_NONE, REDUND_SCAN = 0, 1, 2, 3
 
 
 def uniform_angles(n_views: int, angular_range: float) -> np.ndarray:
@@ -305,8 +307,20 @@ def parker_weight(beta, gamma, delta) -> float:
     return float(_load().oracle_parker_weight(beta, gamma, delta))
 
 
-def weights(sino, det_spacing, angles, sdd, cosine=True, redund=REDUND_NONE):
-    """W_red W_cos p for a [V, Nu] (fan) or [V, Nv, Nu] (cone) sinogram."""
+def scan_weight(beta, gamma, scan_range) -> float:
+    """Redundancy weight of ray (beta, gamma) in a scan over [0, scan_range]."""
+    return float(_load().oracle_scan_weight(beta, gamma, scan_range))
+
+
+def _scan(redund, scan_range):
+    if redund == REDUND_SCAN and not (scan_range and 0.0 < scan_range <= 2 * np.pi + 1e-12):
+        raise ValueError("REDUND_SCAN needs 0 < scan_range <= 2 pi")
+    return float(scan_range or 0.0)
+
+
+def weights(sino, det_spacing, angles, sdd, cosine=True, redund=REDUND_NONE, scan_range=None):
+    """W_red W_cos p for a [V, Nu] (fan) or [V, Nv, Nu] (cone) sinogram;
+    scan_range is the scan's angular range for REDUND_SCAN."""
     s = _f64(sino).copy()
     if s.ndim == 2:
         nvw, nu = s.shape
@@ -316,7 +330,8 @@ def weights(sino, det_spacing, angles, sdd, cosine=True, redund=REDUND_NONE):
         nvw, nv, nu = s.shape
         sv, su = det_spacing
     ang = _f64(angles)
-    _load().oracle_weights(_p(s), nvw, nv, nu, su, sv, _p(ang), sdd, int(bool(cosine)), redund)
+    _load().oracle_weights(_p(s), nvw, nv, nu, su, sv, _p(ang), sdd, int(bool(cosine)), redund,
+                           _scan(redund, scan_range))
     return s
 
 
@@ -356,7 +371,8 @@ def fbp_par2d(sino, shape, spacing, su, angles, kind=RAMLAK, K=None):
     return out
 
 
-def fbp_fan2d(sino, shape, spacing, su, angles, sid, sdd, dbeta, kind=RAMLAK, redund=REDUND_FULL, K=None):
+def fbp_fan2d(sino, shape, spacing, su, angles, sid, sdd, dbeta, kind=RAMLAK, redund=REDUND_FULL, K=None,
+              scan_range=None):
     sino = _f64(sino)
     ny, nx = shape
     sy, sx = spacing
@@ -364,12 +380,12 @@ def fbp_fan2d(sino, shape, spacing, su, angles, sid, sdd, dbeta, kind=RAMLAK, re
     Kc = None if K is None else _f64(K)
     out = np.empty((ny, nx))
     _load().oracle_fbp_fan2d(_p(sino), nx, ny, sx, sy, sino.shape[1], su, ang.size, _p(ang), dbeta, sid, sdd, kind,
-                             _p(Kc), redund, _p(out))
+                             _p(Kc), redund, _scan(redund, scan_range), _p(out))
     return out
 
 
 def fdk(sino, shape, spacing, det_spacing, angles, pmats, sid, sdd, dbeta, kind=SHEPP_LOGAN, redund=REDUND_PARKER,
-        K=None):
+        K=None, scan_range=None):
     sino = _f64(sino)
     nz, ny, nx = shape
     sz, sy, sx = spacing
@@ -380,12 +396,12 @@ def fdk(sino, shape, spacing, det_spacing, angles, pmats, sid, sdd, dbeta, kind=
     Kc = None if K is None else _f64(K)
     out = np.empty((nz, ny, nx))
     _load().oracle_fdk(_p(sino), nx, ny, nz, sx, sy, sz, nu, nv, su, sv, ang.size, _p(P), _p(ang), dbeta, sid, sdd,
-                       kind, _p(Kc), redund, _p(out))
+                       kind, _p(Kc), redund, _scan(redund, scan_range), _p(out))
     return out
 
 
 def fdk_voxels(sino, shape, spacing, det_spacing, angles, pmats, sid, sdd, dbeta, ii, jj, kk, kind=SHEPP_LOGAN,
-               redund=REDUND_PARKER, K=None):
+               redund=REDUND_PARKER, K=None, scan_range=None):
     sino = _f64(sino)
     nz, ny, nx = shape
     sz, sy, sx = spacing
@@ -397,7 +413,8 @@ def fdk_voxels(sino, shape, spacing, det_spacing, angles, pmats, sid, sdd, dbeta
     i, j, k = _i32(ii), _i32(jj), _i32(kk)
     out = np.empty(i.size)
     _load().oracle_fdk_voxels(_p(sino), nx, ny, nz, sx, sy, sz, nu, nv, su, sv, ang.size, _p(P), _p(ang), dbeta, sid,
-                              sdd, kind, _p(Kc), redund, i.size, _p(i), _p(j), _p(k), _p(out))
+                              sdd, kind, _p(Kc), redund, _scan(redund, scan_range), i.size, _p(i), _p(j), _p(k),
+                              _p(out))
     return out
 
 

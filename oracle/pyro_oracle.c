@@ -589,10 +589,48 @@ double oracle_parker_weight(double beta, double gamma, double delta)
     return 0.0;
 }
 
+/* Redundancy weight for a scan over [0, range], 0 < range <= 2 pi (short,
+ * super-short and over-scans; Section "Geometric Correction Weights" names
+ * short and super-short scans).  With the volume's conventions the line of
+ * ray (beta, gamma) is measured again by the ray (beta + pi + 2 gamma, -gamma)
+ * (a later partner) or (beta - pi + 2 gamma, -gamma) (an earlier one).  A ray
+ * with no partner inside the scan keeps weight 1.  A ray with a later partner
+ * lies in the overlap at the scan start, beta in [0, range - pi - 2 gamma];
+ * it takes sin^2 of a quarter period scaled to that overlap, and its partner,
+ * in the overlap at the scan end, the complementary cos^2, so each line's
+ * weights add to 1.  For range = pi + 2 delta this is Parker's weighting. */
+double oracle_scan_weight(double beta, double gamma, double range)
+{
+    if (beta < 0.0 || beta > range) return 0.0;
+    double later = beta + M_PI + 2.0 * gamma, earlier = beta - M_PI + 2.0 * gamma;
+    double lead = range - M_PI - 2.0 * gamma;   /* overlap length at the start for this gamma */
+    double trail = range - M_PI + 2.0 * gamma;  /* overlap length at the end */
+    if (later <= range && lead > 0.0) {
+        double s = sin(0.5 * M_PI * beta / lead);
+        return s * s;
+    }
+    if (earlier >= 0.0 && trail > 0.0) {
+        double s = sin(0.5 * M_PI * (range - beta) / trail);
+        return s * s;
+    }
+    return 1.0;
+}
+
+static double redundancy_weight(int redund, double beta, double gamma, double delta, double range)
+{
+    switch (redund) {
+    case 0: return 0.5;
+    case 1: return oracle_parker_weight(beta, gamma, delta);
+    case 3: return oracle_scan_weight(beta, gamma, range);
+    default: return 1.0;
+    }
+}
+
 /* p <- W_red W_cos p over a [n_views][nv][nu] sinogram (nv = 1 for fan beam).
- * cosine: apply W_cos; redund: 0 full scan (1/2), 1 Parker, 2 none (1). */
+ * cosine: apply W_cos; redund: 0 full scan (1/2), 1 Parker, 2 none (1),
+ * 3 the weighting for a scan over [0, range] (oracle_scan_weight). */
 void oracle_weights(double *sino, int n_views, int nv, int nu, double su, double sv, const double *angles,
-                    double sdd, int cosine, int redund)
+                    double sdd, int cosine, int redund, double range)
 {
     double delta = atan(0.5 * nu * su / sdd);
 #pragma omp parallel for schedule(static)
@@ -603,8 +641,7 @@ void oracle_weights(double *sino, int n_views, int nv, int nu, double su, double
                 double v = (l - 0.5 * (nv - 1)) * sv;
                 double w = 1.0;
                 if (cosine) w *= cosine_weight(sdd, u, v);
-                if (redund == 0) w *= 0.5;
-                if (redund == 1) w *= oracle_parker_weight(angles[j] - angles[0], atan(u / sdd), delta);
+                w *= redundancy_weight(redund, angles[j] - angles[0], atan(u / sdd), delta, range);
                 sino[IDX3(j, l, k, nv, nu)] *= w;
             }
 }
@@ -755,12 +792,12 @@ void oracle_fbp_par2d(const double *sino, int nx, int ny, double sx, double sy, 
  * detector spacing su*SID/SDD, then x = dbeta * sum_j (SID/L)^2 L(q_j; k_j). */
 void oracle_fbp_fan2d(const double *sino, int nx, int ny, double sx, double sy, int nu, double su, int n_views,
                       const double *angles, double dbeta, double sid, double sdd, int kind, const double *Kc,
-                      int redund, double *img)
+                      int redund, double range, double *img)
 {
     size_t n = (size_t)n_views * nu;
     double *w = (double *)malloc(sizeof(double) * n), *q = (double *)malloc(sizeof(double) * n);
     memcpy(w, sino, sizeof(double) * n);
-    oracle_weights(w, n_views, 1, nu, su, 0.0, angles, sdd, 1, redund);
+    oracle_weights(w, n_views, 1, nu, su, 0.0, angles, sdd, 1, redund, range);
     oracle_filter_rows(w, q, n_views, nu, su * sid / sdd, kind, Kc);
     oracle_bp_fan2d(q, nx, ny, sx, sy, nu, su, n_views, angles, sid, sdd, 2, dbeta, img);
     free(w);
@@ -770,12 +807,12 @@ void oracle_fbp_fan2d(const double *sino, int nx, int ny, double sx, double sy, 
 /* Cone-beam FDK (Eq. 5) with projection matrices. */
 void oracle_fdk(const double *sino, int nx, int ny, int nz, double sx, double sy, double sz, int nu, int nv,
                 double su, double sv, int n_views, const double *pmats, const double *angles, double dbeta,
-                double sid, double sdd, int kind, const double *Kc, int redund, double *vol)
+                double sid, double sdd, int kind, const double *Kc, int redund, double range, double *vol)
 {
     size_t n = (size_t)n_views * nu * nv;
     double *w = (double *)malloc(sizeof(double) * n), *q = (double *)malloc(sizeof(double) * n);
     memcpy(w, sino, sizeof(double) * n);
-    oracle_weights(w, n_views, nv, nu, su, sv, angles, sdd, 1, redund);
+    oracle_weights(w, n_views, nv, nu, su, sv, angles, sdd, 1, redund, range);
     oracle_filter_rows(w, q, (long)n_views * nv, nu, su * sid / sdd, kind, Kc);
     oracle_bp_cone3d(q, nx, ny, nz, sx, sy, sz, nu, nv, n_views, pmats, sid, 2, dbeta, vol);
     free(w);
@@ -786,7 +823,8 @@ void oracle_fdk(const double *sino, int nx, int ny, int nz, double sx, double sy
  * filtering done just for the detector rows those voxels project onto. */
 void oracle_fdk_voxels(const double *sino, int nx, int ny, int nz, double sx, double sy, double sz, int nu, int nv,
                        double su, double sv, int n_views, const double *pmats, const double *angles, double dbeta,
-                       double sid, double sdd, int kind, const double *Kc, int redund, int n_vox, const int *ii,
+                       double sid, double sdd, int kind, const double *Kc, int redund, double range, int n_vox,
+                       const int *ii,
                        const int *jj, const int *kk, double *out)
 {
     size_t n = (size_t)n_views * nu * nv;
@@ -814,8 +852,7 @@ void oracle_fdk_voxels(const double *sino, int nx, int ny, int nz, double sx, do
             for (int k = 0; k < nu; ++k) {
                 double u = (k - 0.5 * (nu - 1)) * su, vv = (l - 0.5 * (nv - 1)) * sv;
                 double w = cosine_weight(sdd, u, vv);
-                if (redund == 0) w *= 0.5;
-                if (redund == 1) w *= oracle_parker_weight(angles[v] - angles[0], atan(u / sdd), delta);
+                w *= redundancy_weight(redund, angles[v] - angles[0], atan(u / sdd), delta, range);
                 row[k] *= w;
             }
             oracle_filter_rows(row, q + IDX3(v, l, 0, nv, nu), 1, nu, su * sid / sdd, kind, Kc);

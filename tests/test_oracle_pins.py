@@ -364,6 +364,62 @@ def test_parker_conjugate_rays_sum_to_one():
             assert abs(a - b) < 1e-7
 
 
+def _same_line(a1, d1, a2, d2, tol=1e-9):
+    """two 2D rays (origin, unit direction) lie on one line"""
+    cross = d1[0] * d2[1] - d1[1] * d2[0]
+    off = (a2[0] - a1[0]) * d1[1] - (a2[1] - a1[1]) * d1[0]
+    return abs(cross) < tol and abs(off) < tol * 1e3
+
+
+def test_conjugate_ray_convention_matches_the_fan_geometry():
+    """The partner (beta + pi + 2 gamma, -gamma) the scan weights assume is
+    the same line as (beta, gamma), built from the source and detector
+    positions of the geometry (a symmetric detector: bin nu-1-k has -gamma)."""
+    nu, su, sid, sdd = 65, 1.3, 400.0, 700.0
+    rng = np.random.default_rng(41)
+    for _ in range(50):
+        b, k = rng.uniform(0, 2 * np.pi), int(rng.integers(nu))
+        g = np.arctan((k - 0.5 * (nu - 1)) * su / sdd)
+        a1, d1 = an.fan_rays([b], nu, su, sid, sdd)
+        a2, d2 = an.fan_rays([b + np.pi + 2 * g], nu, su, sid, sdd)
+        assert _same_line(a1[k], d1[k], a2[nu - 1 - k], d2[nu - 1 - k])
+        # and not the other sign
+        a3, d3 = an.fan_rays([b + np.pi - 2 * g], nu, su, sid, sdd)
+        if abs(g) > 1e-3:
+            assert not _same_line(a1[k], d1[k], a3[nu - 1 - k], d3[nu - 1 - k])
+
+
+@pytest.mark.parametrize("frac", [-0.6, 0.0, 0.4, 1.0, 1.7, None])
+def test_scan_weights_partition_every_line(frac):
+    """Scan over [0, R] for R from below pi to 2 pi: every ray's line, summed
+    over all its measurements inside the scan (brute-force enumeration of
+    the partners at beta +- pi + 2 gamma, with their 2 pi images), has total
+    weight 1; 0 <= w <= 1; and R = pi + 2 delta gives Parker's weights."""
+    delta = np.arctan(0.5 * 620 * 0.616 / 1200.0)
+    R = 2 * np.pi if frac is None else np.pi + 2 * frac * delta
+    rng = np.random.default_rng(42)
+    for _ in range(3000):
+        g = rng.uniform(-delta, delta)
+        b = rng.uniform(0, R)
+        w = oracle.scan_weight(b, g, R)
+        assert 0.0 <= w <= 1.0
+        total, seen = w, []
+        for b2 in [b + np.pi + 2 * g + 2 * np.pi * m for m in (-2, -1, 0, 1)]:
+            if 0.0 <= b2 <= R and all(abs(b2 - x) > 1e-9 for x in seen):
+                seen.append(b2)
+                total += oracle.scan_weight(b2, -g, R)
+        assert abs(total - 1.0) < 1e-12, (b, g, R, w, total)
+        if frac == 1.0:
+            assert abs(w - oracle.parker_weight(b, g, delta)) < 1e-12
+    # outside the scan: 0; inside, continuous across the overlap borders
+    assert oracle.scan_weight(-1e-9, 0.01, R) == 0.0 and oracle.scan_weight(R + 1e-9, 0.01, R) == 0.0
+    for g in (-0.1, 0.0, 0.07):
+        for edge in (R - np.pi - 2 * g, np.pi - 2 * g):
+            if 1e-6 < edge < R - 1e-6:
+                lo, hi = oracle.scan_weight(edge - 1e-9, g, R), oracle.scan_weight(edge + 1e-9, g, R)
+                assert abs(lo - hi) < 1e-6
+
+
 def test_filter_rows_equals_fft_circular_convolution():
     """Linear convolution with the Ram-Lak / Shepp-Logan taps equals F^H K F
     on the zero-padded row (numpy FFT), K the DFT of the truncated taps."""
@@ -452,34 +508,47 @@ def test_fbp_par2d_uniform_disk():
     assert abs(np.mean(ramp[inside]) - mu) > 0.005 * mu
 
 
-@pytest.mark.parametrize("redund", [oracle.REDUND_FULL, oracle.REDUND_PARKER])
+@pytest.mark.parametrize("redund", [oracle.REDUND_FULL, oracle.REDUND_PARKER, oracle.REDUND_SCAN])
 def test_fbp_fan2d_uniform_disk(redund):
+    """REDUND_SCAN runs a super-short scan: pi plus twice the disk's own half
+    fan angle (6.1 deg) and a margin, shorter than pi + 2 delta (delta 12.4 deg)."""
     N, s, nu, su, sid, sdd = 128, 1.0, 256, 1.2, 400.0, 700.0
     r, mu, c = 25.0, 1.0, (-14.0, 10.0)
     delta = np.arctan(0.5 * nu * su / sdd)
-    rng_ = 2 * np.pi if redund == oracle.REDUND_FULL else np.pi + 2 * delta
+    rng_ = {oracle.REDUND_FULL: 2 * np.pi, oracle.REDUND_PARKER: np.pi + 2 * delta,
+            oracle.REDUND_SCAN: np.pi + 2 * np.radians(7.5)}[redund]
     nviews = 360 if redund == oracle.REDUND_FULL else 220
     ang = oracle.uniform_angles(nviews, rng_)
     a, d = an.fan_rays(ang, nu, su, sid, sdd)
     disk = ph.Ellipses(np.array([c]), np.array([[r, r]]), np.array([0.0]), np.array([mu]))
     sino = an.ellipse_line_integrals(disk, a, d).reshape(nviews, nu)
-    img = oracle.fbp_fan2d(sino, (N, N), (s, s), su, ang, sid, sdd, rng_ / nviews, kind=oracle.RAMLAK, redund=redund)
+    img = oracle.fbp_fan2d(sino, (N, N), (s, s), su, ang, sid, sdd, rng_ / nviews, kind=oracle.RAMLAK, redund=redund,
+                           scan_range=rng_)
+    if redund == oracle.REDUND_SCAN:
+        # control: Parker's weights for the full detector fan on this shorter scan miss the lines' late halves
+        bad = oracle.fbp_fan2d(sino, (N, N), (s, s), su, ang, sid, sdd, rng_ / nviews, kind=oracle.RAMLAK,
+                               redund=oracle.REDUND_PARKER)
     x = (np.arange(N) - 0.5 * (N - 1)) * s
     X, Y = np.meshgrid(x, x)
     dist = np.hypot(X - c[0], Y - c[1])
     assert np.max(np.abs(img[dist < 0.8 * r] - mu)) < 0.015 * mu
     assert abs(np.mean(img[dist > 1.2 * r])) < 0.01 * mu
+    if redund == oracle.REDUND_SCAN:
+        assert np.max(np.abs(bad[dist < 0.8 * r] - mu)) > 0.015 * mu  # fails the gate the scan weights pass
 
 
-@pytest.mark.parametrize("redund", [oracle.REDUND_FULL, oracle.REDUND_PARKER])
+@pytest.mark.parametrize("redund", [oracle.REDUND_FULL, oracle.REDUND_PARKER, oracle.REDUND_SCAN])
 def test_fdk_uniform_sphere(redund):
     """FDK (Eq. 5) of the analytic cone projections of an off-centre sphere:
-    the mid-plane through the sphere reconstructs its density within 2 %."""
+    the mid-plane through the sphere reconstructs its density within 2 %.
+    REDUND_SCAN: a super-short scan of pi + 2 x 5.5 deg (the sphere's half fan
+    angle is 4.2 deg, the detector's 7.3 deg)."""
     n, s = 64, 1.0
     nu, nv, su, sv, sid, sdd = 128, 96, 1.0, 1.0, 300.0, 500.0
     r, mu, c = 12.0, 1.0, np.array([8.0, -6.0, 2.0])
     delta = np.arctan(0.5 * nu * su / sdd)
-    rng_ = 2 * np.pi if redund == oracle.REDUND_FULL else np.pi + 2 * delta
+    rng_ = {oracle.REDUND_FULL: 2 * np.pi, oracle.REDUND_PARKER: np.pi + 2 * delta,
+            oracle.REDUND_SCAN: np.pi + 2 * np.radians(5.5)}[redund]
     nviews = 180 if redund == oracle.REDUND_FULL else 120
     ang = oracle.uniform_angles(nviews, rng_)
     P = oracle.circular_pmats(ang, sid, sdd, (nv, nu), (sv, su))
@@ -491,7 +560,8 @@ def test_fdk_uniform_sphere(redund):
     x = (np.arange(n) - 0.5 * (n - 1)) * s
     jj, ii = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
     vals = oracle.fdk_voxels(sino, (n, n, n), (s, s, s), (sv, su), ang, P, sid, sdd, rng_ / nviews,
-                             ii.ravel(), jj.ravel(), np.full(ii.size, kz), kind=oracle.RAMLAK, redund=redund)
+                             ii.ravel(), jj.ravel(), np.full(ii.size, kz), kind=oracle.RAMLAK, redund=redund,
+                             scan_range=rng_)
     img = vals.reshape(n, n)
     X, Y = np.meshgrid(x, x)
     zc = (kz - 0.5 * (n - 1)) * s - c[2]
