@@ -67,8 +67,19 @@ typedef enum { PYRO_W_NONE = 0, PYRO_W_INV_L = 1, PYRO_W_INV_L2 = 2 } pyro_bp_we
 
 typedef enum { PYRO_RAMLAK = 0, PYRO_RAMP = 1, PYRO_SHEPP_LOGAN = 2, PYRO_FILTER_CUSTOM = 3 } pyro_filter;
 
-/* redundancy weight W_red: 1/2 (full 360 degree scan), Parker short scan, or 1 */
-typedef enum { PYRO_REDUND_FULL = 0, PYRO_REDUND_PARKER = 1, PYRO_REDUND_NONE = 2 } pyro_redund;
+/* redundancy weight W_red: 1/2 (full 360 degree scan), Parker short scan
+ * (pi + 2 delta), 1, or PYRO_REDUND_SCAN: the weighting for a scan over the
+ * geometry's `range` R, 0 < R <= 2 pi (super-short scans, R < pi + 2 delta,
+ * named in Section "Geometric Correction Weights", as well as short and
+ * over-scans): Parker's form with delta replaced by (R - pi) / 2.  The rays
+ * whose line the scan measures twice get smooth weights that add to 1 over
+ * the two measurements, the rays measured once get 1. */
+typedef enum {
+    PYRO_REDUND_FULL = 0,
+    PYRO_REDUND_PARKER = 1,
+    PYRO_REDUND_NONE = 2,
+    PYRO_REDUND_SCAN = 3
+} pyro_redund;
 
 /* 2D parallel / fan geometry (Section "Reconstruction & Geometry": volume
  * shape and spacing, detector shape and spacing, number of projections,

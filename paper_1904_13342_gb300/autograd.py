@@ -192,13 +192,19 @@ class FDK(torch.nn.Module):
         return _FDK.apply(p, self.K, self.g, self.redund)
 
 
-def parker_table(g: ConeGeometry3D, device) -> torch.Tensor:
-    """[V, nu] Parker weights of the geometry (computed by the library)."""
+def redundancy_table(g: ConeGeometry3D, device, redund: int = B.REDUND_PARKER) -> torch.Tensor:
+    """[V, nu] redundancy weights of the geometry (computed by the library):
+    Parker's for the short scan, or REDUND_SCAN's for the geometry's range."""
     from dataclasses import replace
 
     g1 = replace(g, detector_shape=(1, g.detector_shape[1]), _keep=[])
     ones = torch.ones((g.number_of_projections, 1, g.detector_shape[1]), device=device, dtype=torch.float32)
-    return B.pyro_weights3d(ones, g1, cosine=False, redund=B.REDUND_PARKER)[:, 0].contiguous()
+    return B.pyro_weights3d(ones, g1, cosine=False, redund=redund)[:, 0].contiguous()
+
+
+def parker_table(g: ConeGeometry3D, device) -> torch.Tensor:
+    """[V, nu] Parker weights of the geometry (computed by the library)."""
+    return redundancy_table(g, device, B.REDUND_PARKER)
 
 
 class _FDKTable(torch.autograd.Function):
@@ -241,7 +247,8 @@ class _FDKTable(torch.autograd.Function):
 class RedundancyFDK(torch.nn.Module):
     """FDK (Eq. 5) whose redundancy weights W_red are a learnable [V, nu]
     table; the filter K is fixed unless `learnable_filter`.  `init`:
-    "parker", "full" (1/2 everywhere) or a [V, nu] tensor."""
+    "parker", "scan" (the weighting for the geometry's own scan range, any
+    range up to 2 pi), "full" (1/2 everywhere) or a [V, nu] tensor."""
 
     def __init__(self, g: ConeGeometry3D, kind: int = B.SHEPP_LOGAN, init="parker", learnable_filter: bool = False,
                  device="cuda"):
@@ -252,10 +259,12 @@ class RedundancyFDK(torch.nn.Module):
             t = init.to(device=device, dtype=torch.float32)
         elif init == "parker":
             t = parker_table(g, device)
+        elif init == "scan":
+            t = redundancy_table(g, device, B.REDUND_SCAN)
         elif init == "full":
             t = torch.full((g.number_of_projections, g.detector_shape[1]), 0.5, device=device)
         else:
-            raise ValueError("init must be 'parker', 'full' or a tensor")
+            raise ValueError("init must be 'parker', 'scan', 'full' or a tensor")
         self.table = torch.nn.Parameter(t.clone())
         self.K = torch.nn.Parameter(filter_taps(kind, g.detector_shape[1], tau, device),
                                     requires_grad=learnable_filter)

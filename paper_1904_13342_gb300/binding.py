@@ -24,7 +24,7 @@ _lib = None
 PYRO_F32, PYRO_F16, PYRO_BF16 = 0, 1, 2
 W_NONE, W_INV_L, W_INV_L2 = 0, 1, 2
 RAMLAK, RAMP, SHEPP_LOGAN, FILTER_CUSTOM = 0, 1, 2, 3
-REDUND_FULL, REDUND_PARKER, REDUND_NONE = 0, 1, 2
+REDUND_FULL, REDUND_PARKER, REDUND_NONE, REDUND_SCAN = 0, 1, 2, 3
 
 _DTYPES = {torch.float32: PYRO_F32, torch.float16: PYRO_F16, torch.bfloat16: PYRO_BF16}
 _STATUS = {1: "EINVAL", 2: "ECUDA", 3: "ETIMEOUT", 4: "EUNSUPPORTED", 5: "EWORKSPACE"}

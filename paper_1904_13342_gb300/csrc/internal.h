@@ -91,7 +91,7 @@ struct WeightParams {
     int nu, nv, n_views;
     int cosine, redund;        // pyro_redund
     float su, sv, cu, cv, sdd;
-    float delta;               // Parker half fan angle
+    float delta;               // Parker half fan angle, or (range - pi) / 2 for PYRO_REDUND_SCAN
 };
 
 struct BetaTable {             // b_j - b_0 per view, for Parker weights

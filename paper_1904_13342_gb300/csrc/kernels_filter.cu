@@ -24,11 +24,16 @@ __device__ __forceinline__ float cosine_weight(const WeightParams &w, float u, f
 
 // Parker short-scan weight: beta from the first view, gamma the fan angle of
 // the bin, delta the half fan angle (regions of the short scan pi + 2 delta).
+// A scan over any range R <= 2 pi takes the same form with delta = (R - pi) / 2:
+// the overlap at the start, beta <= R - pi - 2 gamma, holds exactly the rays
+// whose line is measured again before R, and the overlap at the end their
+// partners; every other ray is measured once (weight 1).  For those delta the
+// start overlap can be empty (delta <= gamma), hence the first guard.
 __device__ __forceinline__ float parker_weight(float beta, float gamma, float delta)
 {
     const float pi = 3.14159265358979323846f;
     if (beta < 0.0f) return 0.0f;
-    if (beta <= 2.0f * (delta - gamma)) {
+    if (delta - gamma > 0.0f && beta <= 2.0f * (delta - gamma)) {
         const float s = sinpif(0.25f * beta / (delta - gamma));
         return s * s;
     }
@@ -46,7 +51,8 @@ __device__ __forceinline__ float total_weight(const WeightParams &w, const BetaT
     const float v = ((float)l - w.cv) * w.sv;
     float r = w.cosine ? cosine_weight(w, u, v) : 1.0f;
     if (w.redund == PYRO_REDUND_FULL) r *= 0.5f;
-    if (w.redund == PYRO_REDUND_PARKER) r *= parker_weight(bt.beta[view], atanf(u / w.sdd), w.delta);
+    if (w.redund == PYRO_REDUND_PARKER || w.redund == PYRO_REDUND_SCAN)
+        r *= parker_weight(bt.beta[view], atanf(u / w.sdd), w.delta);
     return r;
 }
 
@@ -311,8 +317,8 @@ __global__ void __launch_bounds__(kFilterThreads) filter_stockham_kernel(const T
     const long first = (long)blockIdx.x * per_cta, last = min(n_pairs, first + per_cta);
     for (long pr0 = first; pr0 < last; pr0 += ppc) {
         const int groups = (int)min((long)ppc, last - pr0);
-        if (p.apply_weights && p.w.redund == PYRO_REDUND_PARKER) {
-            // Parker weight depends on (view, u) only: one row per view, cached
+        if (p.apply_weights && (p.w.redund == PYRO_REDUND_PARKER || p.w.redund == PYRO_REDUND_SCAN)) {
+            // the scan weight depends on (view, u) only: one row per view, cached
             const int view = (int)(((2 * pr0) / p.rows_per_view) % p.n_views);
             const int view_end = (int)(((2 * (pr0 + groups) - 1) / p.rows_per_view) % p.n_views);
             if (view == view_end && view != cached_view) {

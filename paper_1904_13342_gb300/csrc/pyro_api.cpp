@@ -480,15 +480,21 @@ int fill_filter(long n_rows, int nu, double tau, pyro_filter kind, const float *
     return PYRO_OK;
 }
 
-int fill_weights(int nu, int nv, double su, double sv, double sdd, const std::vector<double> &beta, int cosine,
-                 pyro_redund redund, WeightParams &w, BetaTable &bt)
+constexpr double kPi = 3.14159265358979323846;
+
+int fill_weights(int nu, int nv, double su, double sv, double sdd, const std::vector<double> &beta, double range,
+                 int cosine, pyro_redund redund, WeightParams &w, BetaTable &bt)
 {
-    PYRO_CHECK(redund == PYRO_REDUND_FULL || redund == PYRO_REDUND_PARKER || redund == PYRO_REDUND_NONE,
+    PYRO_CHECK(redund == PYRO_REDUND_FULL || redund == PYRO_REDUND_PARKER || redund == PYRO_REDUND_NONE ||
+                   redund == PYRO_REDUND_SCAN,
                "unknown redundancy mode %d", (int)redund);
     PYRO_CHECK(pos_finite(sdd), "weights need SDD > 0");
     const int V = (int)beta.size();
-    if (redund == PYRO_REDUND_PARKER)
-        PYRO_CHECK(V <= kMaxViews2D, "Parker weights support at most %d views", kMaxViews2D);
+    const bool by_view = redund == PYRO_REDUND_PARKER || redund == PYRO_REDUND_SCAN;
+    if (by_view) PYRO_CHECK(V <= kMaxViews2D, "scan weights support at most %d views", kMaxViews2D);
+    if (redund == PYRO_REDUND_SCAN)
+        PYRO_CHECK(std::isfinite(range) && range > 0.0 && range <= 2.0 * kPi * (1.0 + 1e-12),
+                   "PYRO_REDUND_SCAN needs 0 < range <= 2 pi (got %g)", range);
     w.nu = nu;
     w.nv = nv;
     w.n_views = V;
@@ -499,9 +505,9 @@ int fill_weights(int nu, int nv, double su, double sv, double sdd, const std::ve
     w.cu = (float)(0.5 * (nu - 1));
     w.cv = (float)(0.5 * (nv - 1));
     w.sdd = (float)sdd;
-    w.delta = (float)std::atan(0.5 * nu * su / sdd);
+    w.delta = redund == PYRO_REDUND_SCAN ? (float)(0.5 * (range - kPi)) : (float)std::atan(0.5 * nu * su / sdd);
     std::memset(&bt, 0, sizeof(bt));
-    if (redund == PYRO_REDUND_PARKER)
+    if (by_view)
         for (int j = 0; j < V; ++j) bt.beta[j] = (float)(beta[j] - beta[0]);
     return PYRO_OK;
 }
@@ -1089,7 +1095,7 @@ PYRO_API int pyro_weights2d(void *sino, int batch, const pyro_geom2d *g, int cos
     if (int e = prep2d(g, false, G)) return e;
     WeightParams w;
     static thread_local BetaTable bt;
-    if (int e = fill_weights(G.nu, 1, G.su, 0.0, g->sdd, G.beta, cosine, redund, w, bt)) return e;
+    if (int e = fill_weights(G.nu, 1, G.su, 0.0, g->sdd, G.beta, G.range, cosine, redund, w, bt)) return e;
     if (batch == 0) return PYRO_OK;
     PYRO_CUDA(launch_weights(sino, batch, w, bt, dtype, as_stream(stream)));
     return PYRO_OK;
@@ -1103,7 +1109,7 @@ PYRO_API int pyro_weights3d(void *sino, int batch, const pyro_geom3d *g, int cos
     if (int e = prep3d(g, G)) return e;
     WeightParams w;
     static thread_local BetaTable bt;
-    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, cosine, redund, w, bt)) return e;
+    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, G.range, cosine, redund, w, bt)) return e;
     if (batch == 0) return PYRO_OK;
     PYRO_CUDA(launch_weights(sino, batch, w, bt, dtype, as_stream(stream)));
     return PYRO_OK;
@@ -1118,7 +1124,7 @@ PYRO_API int pyro_weights3d_table(void *sino, int batch, const pyro_geom3d *g, c
     if (batch > 0) PYRO_CHECK(table != nullptr, "table is NULL");
     WeightParams w;
     static thread_local BetaTable bt;
-    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, cosine, PYRO_REDUND_NONE, w, bt)) return e;
+    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, G.range, cosine, PYRO_REDUND_NONE, w, bt)) return e;
     if (batch == 0) return PYRO_OK;
     PYRO_CUDA(launch_weights_table(sino, batch, w, table, dtype, as_stream(stream)));
     return PYRO_OK;
@@ -1206,7 +1212,7 @@ PYRO_API int pyro_fdk(const void *sino, void *vol, int batch, const pyro_geom3d 
     static thread_local FilterParams p;
     static thread_local BetaTable bt;
     if (int e = fill_filter((long)batch * V * G.nv, G.nu, G.su * G.sid / G.sdd, kind, custom_K, p)) return e;
-    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, 1, redund, p.w, bt)) return e;
+    if (int e = fill_weights(G.nu, G.nv, G.su, G.sv, G.sdd, G.beta, G.range, 1, redund, p.w, bt)) return e;
     p.apply_weights = 1;
     p.rows_per_view = G.nv;
     p.n_views = V;
@@ -1240,7 +1246,7 @@ static int fbp2d(bool fan, const void *sino, void *vol, int batch, const pyro_ge
     if (int e = fill_filter((long)batch * V, G.nu, tau, kind, custom_K, p)) return e;
     if (fan) {
         PYRO_CHECK(std::isfinite(G.range) && G.range != 0.0, "fan FBP needs the angular range");
-        if (int e = fill_weights(G.nu, 1, G.su, 0.0, G.sdd, G.beta, 1, redund, p.w, bt)) return e;
+        if (int e = fill_weights(G.nu, 1, G.su, 0.0, G.sdd, G.beta, G.range, 1, redund, p.w, bt)) return e;
         p.apply_weights = 1;
         p.rows_per_view = 1;
         p.n_views = V;

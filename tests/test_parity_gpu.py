@@ -338,15 +338,36 @@ def test_bp_transpose_cone():
 
 
 # ---------------------------------------------------- weights / filters ---
-@pytest.mark.parametrize("redund", [B.REDUND_FULL, B.REDUND_PARKER, B.REDUND_NONE])
-def test_weights_cone(redund):
+# scan ranges for REDUND_SCAN: super-short (pi + 2 x 2 deg, the detector's half
+# fan angle is 3.9 deg), below pi (every ray measured once) and an over-scan
+SCAN_RANGES = [math.pi + math.radians(4.0), 0.9 * math.pi, 1.4 * math.pi]
+
+
+@pytest.mark.parametrize("redund,scan", [(B.REDUND_FULL, None), (B.REDUND_PARKER, None), (B.REDUND_NONE, None)] +
+                         [(B.REDUND_SCAN, r) for r in SCAN_RANGES])
+def test_weights_cone(redund, scan):
     c = dict(CONE)
     c["range"] = short_scan_range(c["det"][1] * c["dspacing"][1], c["sdd"]) if redund == B.REDUND_PARKER else 2 * math.pi
+    if scan:
+        c["range"] = scan
     y = ph.random_sinogram((2, c["views"], *c["det"]), 12)
     ang = oracle.uniform_angles(c["views"], c["range"])
     got = B.pyro_weights3d(to_dev(y), cone_geom(c), cosine=True, redund=redund)
-    ref = np.stack([oracle.weights(f32(s), c["dspacing"], ang, c["sdd"], True, redund) for s in y])
+    ref = np.stack([oracle.weights(f32(s), c["dspacing"], ang, c["sdd"], True, redund, scan_range=c["range"])
+                    for s in y])
     assert rel(host(got), ref) < 1e-6
+
+
+@pytest.mark.parametrize("scan", SCAN_RANGES)
+def test_weights_fan_scan(scan):
+    c = dict(FAN, range=scan)
+    y = ph.random_sinogram((2, c["views"], c["nu"]), 12)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    got = B.pyro_weights2d(to_dev(y), fan_geom(c), cosine=True, redund=B.REDUND_SCAN)
+    ref = np.stack([oracle.weights(f32(s), c["su"], ang, c["sdd"], True, B.REDUND_SCAN, scan_range=scan) for s in y])
+    assert rel(host(got), ref) < 1e-6
+    with pytest.raises(B.PyroError):  # outside (0, 2 pi]
+        B.pyro_weights2d(to_dev(y), fan_geom(dict(c, range=7.0)), cosine=True, redund=B.REDUND_SCAN)
 
 
 @pytest.mark.parametrize("nu", [1, 37, 183, 620, 1240])
@@ -386,10 +407,13 @@ NOISE_TOL = 1e-4  # filtered noise: FP32 detector-coordinate rounding, amplified
 
 @pytest.mark.parametrize("data", ["phantom", "noise"])
 @pytest.mark.parametrize("dtype", [torch.float32, torch.float16])
-@pytest.mark.parametrize("redund,kind", [(B.REDUND_PARKER, B.SHEPP_LOGAN), (B.REDUND_FULL, B.RAMLAK)])
+@pytest.mark.parametrize("redund,kind", [(B.REDUND_PARKER, B.SHEPP_LOGAN), (B.REDUND_FULL, B.RAMLAK),
+                                         (B.REDUND_SCAN, B.SHEPP_LOGAN)])
 def test_fdk(redund, kind, dtype, data):
     c = dict(CONE)
     c["range"] = short_scan_range(c["det"][1] * c["dspacing"][1], c["sdd"]) if redund == B.REDUND_PARKER else 2 * math.pi
+    if redund == B.REDUND_SCAN:
+        c["range"] = SCAN_RANGES[0]
     ang = oracle.uniform_angles(c["views"], c["range"])
     P = cone_pmats(c, ang)
     if data == "phantom":
@@ -399,17 +423,19 @@ def test_fdk(redund, kind, dtype, data):
         y = ph.random_sinogram((2, c["views"], *c["det"]), 18, smooth=3)
     got = B.pyro_fdk(to_dev(y, dtype), cone_geom(c), kind=kind, redund=redund)
     ref = np.stack([oracle.fdk(f32(s), c["shape"], c["spacing"], c["dspacing"], ang, P, c["sid"], c["sdd"],
-                               c["range"] / c["views"], kind, redund) for s in y])
+                               c["range"] / c["views"], kind, redund, scan_range=c["range"]) for s in y])
     tol = TOL[dtype] if (data == "phantom" or dtype != torch.float32) else NOISE_TOL
     assert rel(host(got), ref) < tol
 
 
 @pytest.mark.parametrize("data", ["phantom", "noise"])
-@pytest.mark.parametrize("geom", ["par", "fan_full", "fan_parker"])
+@pytest.mark.parametrize("geom", ["par", "fan_full", "fan_parker", "fan_scan"])
 def test_fbp_2d(geom, data):
     c = dict(PAR if geom == "par" else FAN)
     if geom == "fan_parker":
         c["range"] = short_scan_range(c["nu"] * c["su"], c["sdd"])
+    if geom == "fan_scan":  # super-short: pi + 2 x 6 deg, the detector's half fan angle is 6.8 deg
+        c["range"] = math.pi + math.radians(12.0)
     ang = oracle.uniform_angles(c["views"], c["range"])
     if data == "phantom":
         es = [ph.random_ellipses(6, 30.0, seed=s) for s in (40, 41)]
@@ -423,10 +449,10 @@ def test_fbp_2d(geom, data):
         got = B.pyro_fbp_par2d(to_dev(y), par_geom(c), kind=B.RAMLAK)
         ref = [oracle.fbp_par2d(f32(s), c["shape"], c["spacing"], c["su"], ang, B.RAMLAK) for s in y]
     else:
-        red = B.REDUND_FULL if geom == "fan_full" else B.REDUND_PARKER
+        red = {"fan_full": B.REDUND_FULL, "fan_parker": B.REDUND_PARKER, "fan_scan": B.REDUND_SCAN}[geom]
         got = B.pyro_fbp_fan2d(to_dev(y), fan_geom(c), kind=B.SHEPP_LOGAN, redund=red)
         ref = [oracle.fbp_fan2d(f32(s), c["shape"], c["spacing"], c["su"], ang, c["sid"], c["sdd"],
-                                c["range"] / c["views"], B.SHEPP_LOGAN, red) for s in y]
+                                c["range"] / c["views"], B.SHEPP_LOGAN, red, scan_range=c["range"]) for s in y]
     assert rel(host(got), np.stack(ref)) < (1e-5 if data == "phantom" else NOISE_TOL)
 
 

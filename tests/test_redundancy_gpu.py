@@ -134,3 +134,42 @@ def test_learned_table_from_the_full_scan_start():
     # a least-squares fit on these phantoms: the Parker table is one feasible point
     assert learned <= parker
     assert dist1 < 0.8 * dist0
+
+
+def test_learned_table_on_a_super_short_scan():
+    """A super-short scan (pi + 2 x 3.5 deg; the detector's half fan angle is
+    4.25 deg): the table initialised with REDUND_SCAN's weights reproduces the
+    fused FDK with those weights, and a table fitted from 1/2 everywhere
+    (the paper's 'weights learned for arbitrary short-scan angles') ends at
+    most at the scan weights' error."""
+    rng_ = math.pi + math.radians(7.0)
+    g = ConeGeometry3D((16, 32, 32), (1.0, 1.0, 1.0), (20, 48), (1.4, 1.3), 40, rng_, 250.0, 420.0)
+    truth = torch.stack([ph.voxelize_ellipsoids(ph.random_ellipsoids(6, 12.0, seed=s), g.volume_shape,
+                                                g.volume_spacing, device=DEV, dtype=torch.float32)
+                         for s in range(1000, 1008)])
+    p = B.pyro_fp_cone3d(truth, g)
+    scan = AG.RedundancyFDK(g, init="scan", device=DEV)
+    fused = B.pyro_fdk(p, g, kind=B.SHEPP_LOGAN, redund=B.REDUND_SCAN)
+    with torch.no_grad():
+        assert rel(scan(p).cpu().numpy(), fused.cpu().numpy()) < 1e-5
+    m = AG.RedundancyFDK(g, init="full", device=DEV)
+    opt = torch.optim.LBFGS([m.table], lr=1.0, max_iter=40, history_size=20, line_search_fn="strong_wolfe")
+    losses = []
+
+    def closure():
+        opt.zero_grad()
+        loss = ((m(p) - truth) ** 2).mean()
+        loss.backward()
+        losses.append(float(loss.item()))
+        return loss
+
+    opt.step(closure)
+    with torch.no_grad():
+        learned = float(((m(p) - truth) ** 2).mean())
+        ref = float(((fused - truth) ** 2).mean())
+        parker = float(((B.pyro_fdk(p, g, kind=B.SHEPP_LOGAN, redund=B.REDUND_PARKER) - truth) ** 2).mean())
+    print(f"\nsuper-short MSE start {losses[0]:.4e} learned {learned:.4e} scan weights {ref:.4e} "
+          f"parker (detector fan) {parker:.4e}")
+    assert learned < 0.5 * losses[0]
+    assert learned <= ref
+    assert ref < parker  # Parker's weights assume the longer scan pi + 2 delta
