@@ -186,9 +186,7 @@ def run_gpu(args):
     # separate per-kernel timings (outside the timed region): BP and filter alone
     sino = B.pyro_fp_cone3d_ws(vol, g, workspace=ws_fp)
     filt = torch.empty_like(sino)
-    tk = {}
-    for name, fn in (("bp", lambda: B.pyro_bp_cone3d(sino, g, weight=B.W_INV_L2, scale=1.0)),
-                     ("filter", lambda: B.pyro_filter_rows(sino, SU * SID / SDD, B.SHEPP_LOGAN, out=filt))):
+    def alone(fn):
         fn()
         ts = []
         for _ in range(3):
@@ -199,7 +197,32 @@ def run_gpu(args):
             b.record(stream)
             torch.cuda.synchronize(dev)
             ts.append(a.elapsed_time(b))
-        tk[name] = statistics.median(ts)
+        return statistics.median(ts)
+
+    tk = {"bp": alone(lambda: B.pyro_bp_cone3d(sino, g, weight=B.W_INV_L2, scale=1.0)),
+          "filter": alone(lambda: B.pyro_filter_rows(sino, SU * SID / SDD, B.SHEPP_LOGAN, out=filt))}
+
+    # texture mode (the paper's fast FP mode): the volume copied into a CUDA
+    # array and read with hardware trilinear filtering (8-bit weights)
+    def rel_l2(a, b):
+        return float(f"{float(torch.linalg.norm((a - b).double()) / torch.linalg.norm(b.double())):.3g}")
+
+    texture = {}
+    bp_soft = B.pyro_bp_cone3d(sino, g, weight=B.W_INV_L2, scale=1.0)
+    for name, dt in (("f32", torch.float32), ("f16", torch.float16)):
+        tv = B.Texture(g.volume_shape, dt, dev)
+        ts = B.Texture(g.sinogram_shape, dt, dev, kind="sinogram")
+        vd, sd = vol.to(dt), sino.to(dt)
+        up_v, up_s = alone(lambda: tv.upload(vd)), alone(lambda: ts.upload(sd))
+        fp_tex, bp_tex = torch.empty_like(sino), torch.empty_like(vol)
+        fp_t = alone(lambda: B.pyro_fp_cone3d_tex(tv, g, out=fp_tex))
+        bp_t = alone(lambda: B.pyro_bp_cone3d_tex(ts, g, weight=B.W_INV_L2, scale=1.0, out=bp_tex))
+        texture[name] = {"fp_ms": round(fp_t, 4), "bp_ms": round(bp_t, 4), "upload_volume_ms": round(up_v, 4),
+                         "upload_sinogram_ms": round(up_s, 4),
+                         "arrays_MB": round((vd.numel() + sd.numel()) * vd.element_size() / 1e6, 1),
+                         "fp_rel_l2_vs_software": rel_l2(fp_tex, sino), "bp_rel_l2_vs_software": rel_l2(bp_tex, bp_soft)}
+        tv.close()
+        ts.close()
 
     # end to end through the public API from pinned host memory
     host_vol = vol.cpu().pin_memory()
@@ -262,6 +285,8 @@ def run_gpu(args):
             "bp_frac": round(N ** 3 * VIEWS * 16 / (tk["bp"] * 1e-3) / 1e9 / gather_gbs, 3)},
         "breakdown_ms": {"fp": round(fp_avg_ms, 4), "fdk": round(statistics.mean(fdk_ms), 4),
                          "bp_alone": round(tk["bp"], 4), "filter_alone": round(tk["filter"], 4)},
+        "texture_mode": dict(texture, what="FP / BP through texture copies (hardware trilinear / bilinear "
+                                           "filtering, 8-bit weights), timed alone"),
         "kernel_gups": {"fp": round(N ** 3 * VIEWS / (fp_avg_ms * 1e-3) / 1e9, 2),
                         "bp": round(N ** 3 * VIEWS / (tk["bp"] * 1e-3) / 1e9, 2)},
         "clocks": clocks,

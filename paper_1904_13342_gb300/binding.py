@@ -58,6 +58,12 @@ _SIGS = {
     "pyro_fp2d_workspace_bytes": [_G2, _I, _I],
     "pyro_fp_par2d_ws": [_VP, _VP, _I, _G2, _VP, _SZ, _I, _VP],
     "pyro_fp_fan2d_ws": [_VP, _VP, _I, _G2, _VP, _SZ, _I, _VP],
+    "pyro_texture_volume_create": [_I, _I, _I, _I, ctypes.POINTER(_VP)],
+    "pyro_texture_sinogram_create": [_I, _I, _I, _I, ctypes.POINTER(_VP)],
+    "pyro_texture_upload": [_VP, _VP, _VP],
+    "pyro_texture_destroy": [_VP],
+    "pyro_fp_cone3d_tex": [_VP, _VP, _G3, _I, _VP],
+    "pyro_bp_cone3d_tex": [_VP, _VP, _G3, _I, _F, _I, _VP],
     "pyro_fpT_par2d_ws": [_VP, _VP, _I, _G2, _VP, _SZ, _I, _VP],
     "pyro_fpT_fan2d_ws": [_VP, _VP, _I, _G2, _VP, _SZ, _I, _VP],
     "pyro_cone_projection_matrices": [_G3, _VP],
@@ -284,6 +290,79 @@ def fp_cone3d_workspace_bytes(g: ConeGeometry3D, dtype=torch.float32) -> int:
     """Workspace pyro_fp_cone3d_ws needs for one volume of `dtype`."""
     cg = g.to_c()
     return int(lib().pyro_fp_cone3d_workspace_bytes(ctypes.byref(cg), _DTYPES[dtype]))
+
+
+class Texture:
+    """Data in a CUDA array read with hardware filtering (the paper's
+    texture mode): a [nz, ny, nx] volume (`kind="volume"`, trilinear) or a
+    [n_views, nv, nu] sinogram (`kind="sinogram"`, one layer per view,
+    bilinear).  The library allocates it; `close()` (or garbage collection)
+    releases it.  `upload(t)` copies a device tensor of the texture's shape
+    and dtype (float32 or float16) into it."""
+
+    def __init__(self, shape, dtype=torch.float32, device=None, kind="volume"):
+        self.shape = tuple(int(n) for n in shape)
+        self.dtype = dtype
+        self.kind = kind
+        self.device = torch.device("cuda", torch.cuda.current_device()) if device is None else torch.device(device)
+        if kind not in ("volume", "sinogram"):
+            raise ValueError("kind must be 'volume' or 'sinogram'")
+        if dtype not in (torch.float32, torch.float16):
+            raise PyroError(4, "textures hold float32 or float16 values")
+        a, b_, c = self.shape
+        h = _VP()
+        create = lib().pyro_texture_volume_create if kind == "volume" else lib().pyro_texture_sinogram_create
+        with torch.cuda.device(self.device):
+            _check(create(c, b_, a, _DTYPES[dtype], ctypes.byref(h)))
+        self._h = h
+
+    def upload(self, t: torch.Tensor) -> "Texture":
+        v = _dev(t, self.kind)
+        if tuple(v.shape) != self.shape or v.dtype != self.dtype or v.device != self.device:
+            raise ValueError(f"{self.kind} {tuple(v.shape)} {v.dtype} on {v.device} does not match the texture "
+                             f"{self.shape} {self.dtype} on {self.device}")
+        with torch.cuda.device(v.device):
+            _check(lib().pyro_texture_upload(self._h, _ptr(v), _stream(v)))
+        return self
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            with torch.cuda.device(self.device):
+                torch.cuda.current_stream().synchronize()
+                _check(lib().pyro_texture_destroy(self._h))
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def pyro_fp_cone3d_tex(tex: Texture, g: ConeGeometry3D, dtype=torch.float32,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Cone-beam FP of a volume texture (hardware trilinear filtering)."""
+    if tex.kind != "volume" or tuple(g.volume_shape) != tex.shape:
+        raise ValueError(f"geometry volume {tuple(g.volume_shape)} does not match the {tex.kind} texture {tex.shape}")
+    o = torch.empty(g.sinogram_shape, dtype=dtype, device=tex.device) if out is None else _dev(out, "out")
+    cg = g.to_c()
+    with torch.cuda.device(tex.device):
+        _check(lib().pyro_fp_cone3d_tex(tex._h, _ptr(o), ctypes.byref(cg), _DTYPES[o.dtype], _stream(o)))
+    return o
+
+
+def pyro_bp_cone3d_tex(tex: Texture, g: ConeGeometry3D, weight=W_INV_L2, scale=1.0, dtype=torch.float32,
+                       out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Voxel-driven cone-beam BP of a sinogram texture (hardware bilinear filtering)."""
+    if tex.kind != "sinogram" or tuple(g.sinogram_shape) != tex.shape:
+        raise ValueError(f"geometry sinogram {tuple(g.sinogram_shape)} does not match the {tex.kind} texture "
+                         f"{tex.shape}")
+    o = torch.empty(g.volume_shape, dtype=dtype, device=tex.device) if out is None else _dev(out, "out")
+    cg = g.to_c()
+    with torch.cuda.device(tex.device):
+        _check(lib().pyro_bp_cone3d_tex(tex._h, _ptr(o), ctypes.byref(cg), int(weight), float(scale),
+                                        _DTYPES[o.dtype], _stream(o)))
+    return o
 
 
 def pyro_fp_cone3d_ws(vol: torch.Tensor, g: ConeGeometry3D, workspace: Optional[torch.Tensor] = None,

@@ -113,6 +113,8 @@ struct FilterParams {
 cudaError_t launch_fp2d(const void *vol, const void *volT, void *sino, int batch, const FP2DParams &p, pyro_dtype dt,
                         cudaStream_t s);
 cudaError_t launch_transpose2d(const void *in, void *out, int batch, int nx, int ny, pyro_dtype dt, cudaStream_t s);
+cudaError_t launch_bp3d_tex(cudaTextureObject_t tex, void *vol, const BP3DParams &p, pyro_dtype vol_dt, cudaStream_t s);
+cudaError_t launch_fp3d_tex(cudaTextureObject_t tex, void *sino, const FP3DParams &p, pyro_dtype dt, cudaStream_t s);
 cudaError_t launch_fp2d_adjoint(const void *sino, void *vol, void *volT, int batch, const FP2DParams &p,
                                 cudaStream_t s);
 cudaError_t launch_add_transposed(const void *accT, void *vol, int batch, int nx, int ny, cudaStream_t s);

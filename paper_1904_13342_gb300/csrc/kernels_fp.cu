@@ -262,6 +262,44 @@ __global__ void __launch_bounds__(kFP3DBlockX *kFP3DBlockY) fp3d_kernel(const T 
     sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(r.w * acc);
 }
 
+// Texture-mode forward projection, the paper's fast mode (Section "The
+// Operator as a Layer"): the volume sits in a 3D CUDA array, read through a
+// texture object with hardware trilinear filtering and a zero border (the
+// zero extension of the software path), so one fetch replaces eight taps and
+// seven lerps.  The price is the second copy of the volume and the hardware's
+// fixed-point interpolation weights (8 fractional bits), which put the result
+// about 1e-4 .. 1e-3 from the FP32 software path.  Same rays, sample grid and
+// clipping as fp3d_kernel.  A warp covers 8 detector columns x 4 rows, a
+// compact footprint for the texture cache.
+constexpr int kFPTexX = 8, kFPTexY = 16;
+
+template <typename T>
+__global__ void __launch_bounds__(kFPTexX *kFPTexY) fp3d_tex_kernel(cudaTextureObject_t tex, T *__restrict__ sino,
+                                                                    const __grid_constant__ FP3DParams p)
+{
+    const int k = blockIdx.x * kFPTexX + threadIdx.x;
+    const int l = blockIdx.y * kFPTexY + threadIdx.y;
+    const int v = blockIdx.z;
+    if (k >= p.nu || l >= p.nv) return;
+    const Ray3 r = ray3d(p, v, k, l);
+    int m0, m1;
+    range3d(r, p, m0, m1);
+    // texel i's centre is at texture coordinate i + 0.5
+    const float px = r.px + 0.5f, py = r.py + 0.5f, pz = r.pz + 0.5f;
+    float acc0 = 0.0f, acc1 = 0.0f;
+    int m = m0;
+    for (; m + 1 <= m1; m += 2) {
+        const float f0 = (float)m, f1 = (float)(m + 1);
+        acc0 += tex3D<float>(tex, fmaf(f0, r.qx, px), fmaf(f0, r.qy, py), fmaf(f0, r.qz, pz));
+        acc1 += tex3D<float>(tex, fmaf(f1, r.qx, px), fmaf(f1, r.qy, py), fmaf(f1, r.qz, pz));
+    }
+    if (m <= m1) {
+        const float f0 = (float)m;
+        acc0 += tex3D<float>(tex, fmaf(f0, r.qx, px), fmaf(f0, r.qy, py), fmaf(f0, r.qz, pz));
+    }
+    sino[((size_t)(p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(r.w * (acc0 + acc1));
+}
+
 // Staged forward projection: the volume has been re-laid out z-fastest
 // ([y][x][z]) and each warp's 32 lanes take 32 consecutive detector rows l of
 // one column k.  Those rays differ only in elevation, so at every sample
@@ -966,6 +1004,24 @@ cudaError_t launch_fp3d_adjoint(const void *sino, void *vol, int batch, const FP
     dim3 grid((p.nu + kFP3DBlockX - 1) / kFP3DBlockX, (p.nv + kFP3DBlockY - 1) / kFP3DBlockY,
               (unsigned)(p.n_views * batch));
     fp3d_adjoint_kernel<<<grid, block, 0, s>>>((const float *)sino, (float *)vol, p);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_fp3d_tex(cudaTextureObject_t tex, void *sino, const FP3DParams &p, pyro_dtype dt, cudaStream_t s)
+{
+    dim3 block(kFPTexX, kFPTexY);
+    dim3 grid((p.nu + kFPTexX - 1) / kFPTexX, (p.nv + kFPTexY - 1) / kFPTexY, (unsigned)p.n_views);
+    switch (dt) {
+    case PYRO_F32:
+        fp3d_tex_kernel<float><<<grid, block, 0, s>>>(tex, (float *)sino, p);
+        break;
+    case PYRO_F16:
+        fp3d_tex_kernel<__half><<<grid, block, 0, s>>>(tex, (__half *)sino, p);
+        break;
+    case PYRO_BF16:
+        fp3d_tex_kernel<__nv_bfloat16><<<grid, block, 0, s>>>(tex, (__nv_bfloat16 *)sino, p);
+        break;
+    }
     return cudaGetLastError();
 }
 

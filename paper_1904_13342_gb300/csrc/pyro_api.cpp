@@ -981,6 +981,142 @@ PYRO_API size_t pyro_fp_cone3d_workspace_bytes(const pyro_geom3d *g, pyro_dtype 
     return (size_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2) * elem_size(dtype);
 }
 
+// ---- texture mode (the paper's fast mode, with its second copy) ----------
+struct pyro_texture_s {
+    int nx, ny, nz;  // array extent: (nx, ny, nz) of a volume, (nu, nv, n_views) of a layered sinogram
+    bool layered;
+    pyro_dtype dtype;
+    cudaArray_t array;
+    cudaTextureObject_t tex;
+};
+
+int texture_create(int nx, int ny, int nz, bool layered, pyro_dtype dtype, pyro_texture *out)
+{
+    PYRO_CHECK(out != nullptr, "out is NULL");
+    *out = nullptr;
+    PYRO_CHECK(nx > 0 && ny > 0 && nz > 0, "texture extent must be positive (%d x %d x %d)", nx, ny, nz);
+    if (dtype != PYRO_F32 && dtype != PYRO_F16)
+        return fail(PYRO_EUNSUPPORTED, "textures hold PYRO_F32 or PYRO_F16 values");
+    int dev = 0, w = 0, h = 0, d = 0;
+    PYRO_CUDA(cudaGetDevice(&dev));
+    if (layered) {
+        PYRO_CUDA(cudaDeviceGetAttribute(&w, cudaDevAttrMaxTexture2DLayeredWidth, dev));
+        PYRO_CUDA(cudaDeviceGetAttribute(&h, cudaDevAttrMaxTexture2DLayeredHeight, dev));
+        PYRO_CUDA(cudaDeviceGetAttribute(&d, cudaDevAttrMaxTexture2DLayeredLayers, dev));
+    } else {
+        PYRO_CUDA(cudaDeviceGetAttribute(&w, cudaDevAttrMaxTexture3DWidth, dev));
+        PYRO_CUDA(cudaDeviceGetAttribute(&h, cudaDevAttrMaxTexture3DHeight, dev));
+        PYRO_CUDA(cudaDeviceGetAttribute(&d, cudaDevAttrMaxTexture3DDepth, dev));
+    }
+    PYRO_CHECK(nx <= w && ny <= h && nz <= d, "extent %d x %d x %d exceeds the device's %s texture limits %d x %d x %d",
+               nx, ny, nz, layered ? "layered 2D" : "3D", w, h, d);
+    const cudaChannelFormatDesc fd =
+        cudaCreateChannelDesc(dtype == PYRO_F32 ? 32 : 16, 0, 0, 0, cudaChannelFormatKindFloat);
+    auto *t = new pyro_texture_s{nx, ny, nz, layered, dtype, nullptr, 0};
+    cudaError_t e = cudaMalloc3DArray(&t->array, &fd, make_cudaExtent(nx, ny, nz), layered ? cudaArrayLayered : 0);
+    if (e != cudaSuccess) {
+        delete t;
+        return fail(PYRO_ECUDA, "cudaMalloc3DArray: %s", cudaGetErrorString(e));
+    }
+    cudaResourceDesc rd;
+    std::memset(&rd, 0, sizeof(rd));
+    rd.resType = cudaResourceTypeArray;
+    rd.res.array.array = t->array;
+    cudaTextureDesc td;
+    std::memset(&td, 0, sizeof(td));  // border colour 0: the zero extension
+    for (int a = 0; a < 3; ++a) td.addressMode[a] = cudaAddressModeBorder;
+    td.filterMode = cudaFilterModeLinear;
+    td.readMode = cudaReadModeElementType;
+    td.normalizedCoords = 0;
+    e = cudaCreateTextureObject(&t->tex, &rd, &td, nullptr);
+    if (e != cudaSuccess) {
+        cudaFreeArray(t->array);
+        delete t;
+        return fail(PYRO_ECUDA, "cudaCreateTextureObject: %s", cudaGetErrorString(e));
+    }
+    *out = t;
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_texture_volume_create(int nx, int ny, int nz, pyro_dtype dtype, pyro_texture *out)
+{
+    return texture_create(nx, ny, nz, false, dtype, out);
+}
+
+PYRO_API int pyro_texture_sinogram_create(int nu, int nv, int n_views, pyro_dtype dtype, pyro_texture *out)
+{
+    return texture_create(nu, nv, n_views, true, dtype, out);
+}
+
+PYRO_API int pyro_texture_upload(pyro_texture t, const void *src, void *stream)
+{
+    PYRO_CHECK(t != nullptr && src != nullptr, "texture or source is NULL");
+    const size_t es = elem_size(t->dtype);
+    cudaMemcpy3DParms cp;
+    std::memset(&cp, 0, sizeof(cp));
+    cp.srcPtr = make_cudaPitchedPtr(const_cast<void *>(src), (size_t)t->nx * es, (size_t)t->nx, (size_t)t->ny);
+    cp.dstArray = t->array;
+    cp.extent = make_cudaExtent((size_t)t->nx, (size_t)t->ny, (size_t)t->nz);
+    cp.kind = cudaMemcpyDeviceToDevice;
+    PYRO_CUDA(cudaMemcpy3DAsync(&cp, as_stream(stream)));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_texture_destroy(pyro_texture t)
+{
+    if (t == nullptr) return PYRO_OK;
+    const cudaError_t e1 = cudaDestroyTextureObject(t->tex);
+    const cudaError_t e2 = cudaFreeArray(t->array);
+    delete t;
+    if (e1 != cudaSuccess || e2 != cudaSuccess)
+        return fail(PYRO_ECUDA, "releasing a texture: %s", cudaGetErrorString(e1 != cudaSuccess ? e1 : e2));
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_fp_cone3d_tex(pyro_texture t, void *sino, const pyro_geom3d *g, pyro_dtype dtype, void *stream)
+{
+    PYRO_CHECK(t != nullptr && !t->layered, "not a volume texture");
+    PYRO_CHECK(sino != nullptr && aligned16(sino), "sinogram pointer is NULL or not 16-byte aligned");
+    PYRO_CHECK(valid_dtype(dtype), "unknown dtype %d", (int)dtype);
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    PYRO_CHECK(G.nx == t->nx && G.ny == t->ny && G.nz == t->nz,
+               "geometry volume %d x %d x %d differs from the texture's %d x %d x %d", G.nx, G.ny, G.nz, t->nx, t->ny,
+               t->nz);
+    const int V = (int)G.beta.size();
+    static thread_local FP3DParams p;
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
+        const int nvw = std::min(kMaxViewsConeFP, V - v0);
+        if (int e = fill_fp3d(G, v0, nvw, p)) return e;
+        PYRO_CUDA(launch_fp3d_tex(t->tex, sino, p, dtype, as_stream(stream)));
+    }
+    return PYRO_OK;
+}
+
+PYRO_API int pyro_bp_cone3d_tex(pyro_texture t, void *vol, const pyro_geom3d *g, pyro_bp_weight w, float scale,
+                                pyro_dtype dtype, void *stream)
+{
+    PYRO_CHECK(t != nullptr && t->layered, "not a sinogram texture");
+    PYRO_CHECK(vol != nullptr && aligned16(vol), "volume pointer is NULL or not 16-byte aligned");
+    PYRO_CHECK(valid_dtype(dtype), "unknown dtype %d", (int)dtype);
+    const int wexp = bp_weight_exp(w);
+    PYRO_CHECK(wexp >= 0, "unknown back-projection weight %d", (int)w);
+    PYRO_CHECK(std::isfinite(scale), "scale is not finite");
+    if (wexp > 0) PYRO_CHECK(pos_finite(g ? g->sid : 0.0), "distance weights need SID > 0");
+    Geo3D G;
+    if (int e = prep3d(g, G)) return e;
+    const int V = (int)G.beta.size();
+    PYRO_CHECK(G.nu == t->nx && G.nv == t->ny && V == t->nz,
+               "geometry sinogram %d views x %d x %d differs from the texture's %d x %d x %d", V, G.nv, G.nu, t->nz,
+               t->ny, t->nx);
+    static thread_local BP3DParams p;
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsConeBP) {
+        fill_bp3d(G, v0, std::min(kMaxViewsConeBP, V - v0), wexp, scale, v0 > 0, p);
+        PYRO_CUDA(launch_bp3d_tex(t->tex, vol, p, dtype, as_stream(stream)));
+    }
+    return PYRO_OK;
+}
+
 PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
                                size_t workspace_bytes, pyro_dtype dtype, void *stream)
 {
