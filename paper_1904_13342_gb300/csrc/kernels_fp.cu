@@ -480,8 +480,11 @@ template <typename T, int R, bool CHECK, bool ADJ>
 __device__ __forceinline__ void column_planes(ColumnWindow (&W)[R], int m0, int m1, const Ray3 &rc, int lane, T *vp,
                                               int nz, int sxp, int syp, float *runs, int zs0, int zs1)
 {
+    // unrolled by 4 on the forward path (measured 1 % faster than 2, while
+    // 1, 6 and 8 were slower) and by 2 on the adjoint's
+    constexpr int kUnroll = ADJ ? 2 : 4;
     float fm = (float)m0;
-#pragma unroll 2
+#pragma unroll kUnroll
     for (int m = m0; m <= m1; ++m, fm += 1.0f) {
         const PlaneXY q = plane_xy(fm, rc, sxp, syp);
         T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
