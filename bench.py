@@ -436,10 +436,20 @@ class CpuSample:
 
 
 def cpu_baseline(seconds: float, vol=None):
-    """About `seconds` of oracle work (36 views + 48 slices take ~15 s on 16 Arm cores)."""
+    """About `seconds` of oracle work on all host cores (36 views + 48 slices
+    take ~15 s on 16 Arm cores), then a smaller sample on one thread."""
+    import oracle
+
     scale = max(seconds / 15.0, 0.1)
-    v, info = CpuSample(vol).run(max(1, round(36 * scale)), max(2, round(48 * scale)))
-    return {"value": round(v, 6), "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"]}
+    sample = CpuSample(vol)
+    v, info = sample.run(max(1, round(36 * scale)), max(2, round(48 * scale)))
+    prev = oracle.set_num_threads(1)
+    try:
+        v1, info1 = sample.run(1, 2)
+    finally:
+        oracle.set_num_threads(prev)
+    return {"value": round(v, 6), "unit": UNIT, "cores": info["cores"], "kind": "oracle", "sample": info["sample"],
+            "single_thread": {"value": round(v1, 6), "unit": UNIT, "cores": info1["cores"], "sample": info1["sample"]}}
 
 
 def run_reference(args):

@@ -84,6 +84,7 @@ def _load():
                 "oracle_tv_value": [_PD, _I, _I, _I, _D],
                 "oracle_tv_grad": [_PD, _I, _I, _I, _D, _PD],
                 "oracle_num_threads": [],
+                "oracle_set_num_threads": [_I],
             }
             for name, args in sig.items():
                 fn = getattr(lib, name)
@@ -94,6 +95,7 @@ def _load():
             lib.oracle_pad_length.restype = _I
             lib.oracle_tv_value.restype = _D
             lib.oracle_num_threads.restype = _I
+            lib.oracle_set_num_threads.restype = _I
             _lib = lib
     return _lib
 
@@ -126,6 +128,11 @@ def uniform_angles(n_views: int, angular_range: float) -> np.ndarray:
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> int:
+    """OpenMP threads for later oracle calls; returns the previous count."""
+    return int(_load().oracle_set_num_threads(int(n)))
 
 
 def circular_pmats(angles, sid, sdd, det_shape, det_spacing) -> np.ndarray:

@@ -926,3 +926,16 @@ int oracle_num_threads(void)
     return 1;
 #endif
 }
+
+/* sets the OpenMP thread count of later calls; returns the previous one */
+int oracle_set_num_threads(int n)
+{
+    int prev = oracle_num_threads();
+#ifdef _OPENMP
+    extern void omp_set_num_threads(int);
+    if (n > 0) omp_set_num_threads(n);
+#else
+    (void)n;
+#endif
+    return prev;
+}
