@@ -354,8 +354,8 @@ PYRO_API int pyro_bb_update(float *x, float *x_prev, const float *g, float *g_pr
  * channels-last BF16 [batch][nz][ny][nx][c]; weights are BF16
  * [27][cout][cin] (tap = (dz*3+dy)*3+dx of a 3x3x3 window, stride 1, zero
  * padding 1); bias, gradients of weights and biases are FP32.  Supported
- * (cin, cout): both in {16, 32, 64} (tensor cores, mma.sync bf16 -> fp32),
- * or (1, 16) / (16, 1) (CUDA cores).  The tensor-core shapes work on
+ * (cin, cout): both in {16, 32, 64} (5th-generation tensor cores, tcgen05,
+ * bf16 -> fp32 in tensor memory), or (1, 16) / (16, 1) (CUDA cores).  The tensor-core shapes work on
  * blocks of 128 voxels TX x TY x TZ with TX = min(nx, 64),
  * TY = min(ny, 128 / TX), TZ = 128 / (TX TY): nx must be 8, 16, 32 or a
  * multiple of 64, and ny, nz must be multiples of TY, TZ.

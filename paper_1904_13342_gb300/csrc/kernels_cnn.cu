@@ -10,10 +10,8 @@
 // (tcgen05.mma, bf16 in, FP32 accumulate in tensor memory); a block computes
 // 128 output voxels (a TX x TY x TZ box) x Cout.  The same kernel computes the
 // data gradient with the spatially flipped, channel-transposed weights.
-// conv3d_wgrad_mma_kernel: dW[tap][co][ci] = sum_v dY[v][co] X[v+tap][ci] as a
-// GEMM with M = Cout, N = taps x Cin, K = voxels on mma.sync.m16n8k16: a
-// block owns a group of taps, walks a strided set of voxel tiles accumulating
-// in registers, and adds its partial sums to dW with FP32 atomics at the end.
+// conv3d_wgrad_tc_kernel: dW[tap][co][ci] = sum_v dY[v][co] X[v+tap][ci] as a
+// GEMM on tcgen05 with M = (tap, ci) rows, N = Cout, K = voxels.
 #include <cuda_bf16.h>
 
 #include <algorithm>
@@ -27,22 +25,11 @@ namespace {
 
 using bf16 = __nv_bfloat16;
 
-__device__ __forceinline__ void mma_bf16(float (&d)[4], unsigned a0, unsigned a1, unsigned a2, unsigned a3,
-                                         unsigned b0, unsigned b1)
-{
-    asm volatile(
-        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
-        "{%0,%1,%2,%3};\n"
-        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
-        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
-}
-
 __device__ __forceinline__ unsigned pack_bf16(bf16 lo, bf16 hi)
 {
     return (unsigned)__bfloat16_as_ushort(lo) | ((unsigned)__bfloat16_as_ushort(hi) << 16);
 }
 
-constexpr int kConvThreads = 256;
 
 // 128 output voxels per block: TX x TY x TZ (x fastest)
 struct Tile {
@@ -205,106 +192,157 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
-// taps per wgrad block: enough to keep COUT x CIN x TP accumulators <= 64 per thread
-__host__ __device__ constexpr int wgrad_taps(int cin, int cout)
-{
-    return cin * cout * 27 <= 64 * kConvThreads ? 27 : (cin * cout * 9 <= 64 * kConvThreads ? 9 : 3);
-}
+// ---- conv3d_wgrad_tc_kernel: the weight gradient on tcgen05.  As a GEMM,
+// dW^T[(tap, ci)][co] = sum_v X[v + tap][ci] dY[v][co]: M = 128 rows of
+// (tap, ci) pairs (128 / Cin taps per block), N = Cout, K = voxels.  Both
+// operands come straight from the channels-last tensors, so they are staged
+// MN-major: for each voxel the 128 (tap, ci) values, resp. the Cout values,
+// are contiguous, in core matrices of 8 voxels x 8 channels (16 bytes per
+// voxel).  For this layout the descriptor's leading offset is the step
+// between core matrices along K (voxels) and its stride offset the 128-byte
+// step along M or N (checked on a single-tile probe against a CPU GEMM).  A
+// block takes 64-voxel chunks (four K = 16 MMAs) in a strided loop with two
+// shared-memory stages, so the gather of one chunk overlaps the MMAs of the
+// previous one; the [128 x Cout] FP32 accumulator lives in tensor memory and
+// every thread finally adds its row to dW with FP32 atomics.  Waits are
+// time-bounded; a block whose wait gives up adds nothing and sets the status
+// word.  The voxel count must be a multiple of 64.
+constexpr int kWgChunk = 64;
 
 template <int CIN, int COUT>
-__global__ void __launch_bounds__(kConvThreads) conv3d_wgrad_mma_kernel(const bf16 *__restrict__ X,
-                                                                        const bf16 *__restrict__ dY,
-                                                                        float *__restrict__ dW, int B, int D, int H,
-                                                                        int Wd)
+__global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ dY,
+                                                              float *__restrict__ dW, long nvox, int D, int H, int Wd,
+                                                              int lw, int lh, int ld, int *status)
 {
-    constexpr int TP = wgrad_taps(CIN, COUT);
-    constexpr int MT = COUT / 16;                 // m tiles (output channels)
-    constexpr int NT = TP * CIN / 8;              // n tiles (tap, 8 input channels)
-    constexpr int PER_WARP = (MT * NT + 7) / 8;   // mma tiles per warp
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    const Tile tl = conv_tile(Wd, H);
-    const int TX = tl.TX, TY = tl.TY, TZ = tl.TZ, HX = TX + 2, HY = TY + 2, HZ = TZ + 2;
-    constexpr int DYP = 128 + 8;                  // padded voxel stride of the transposed dY tile
-    bf16 *dyt = reinterpret_cast<bf16 *>(smem_raw);                 // [COUT][DYP]
-    bf16 *halo = dyt + COUT * DYP;                                  // [3*HY*HX][CIN + 8]
-    constexpr int CP = CIN + 8;
-    const int tap0 = blockIdx.y * TP;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, g = lane >> 2, tg = lane & 3;
-    float acc[PER_WARP][4];
+    constexpr int TPB = 128 / CIN;  // taps per block
+    constexpr int CA = CIN / 8, CB = COUT / 8;
+    constexpr int A_EL = kWgChunk * 128, B_EL = kWgChunk * COUT;
+    constexpr unsigned TCOLS = COUT < 32 ? 32 : COUT;
+    extern __shared__ __align__(128) unsigned char wg_smem[];
+    bf16 *sA = reinterpret_cast<bf16 *>(wg_smem);  // [2][64 voxels x 128 rows], MN-major
+    bf16 *sB = sA + 2 * A_EL;                       // [2][64 voxels x Cout], MN-major
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ unsigned tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5;
+    const int tap0 = blockIdx.y * TPB;
+    const long n_chunks = nvox / kWgChunk;
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_slot;
+    // f32 accumulate, bf16 A and B, A and B MN-major, N = Cout, M = 128
+    constexpr unsigned idesc =
+        (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) | ((unsigned)(COUT >> 3) << 17) | (8u << 24);
+    bool ok = true;
+    int it = 0;
+    for (long c = blockIdx.x; c < n_chunks; c += gridDim.x, ++it) {
+        const int buf = it & 1;
+        // the MMAs of chunk it - 2 read this stage
+        if (it >= 2 && !mbar_wait(&bar[buf], (unsigned)((it - 2) >> 1) & 1u)) ok = false;
+        bf16 *A = sA + buf * A_EL;
+        bf16 *Bs = sB + buf * B_EL;
+        const long v0 = c * kWgChunk;
+        // A: 16-byte items (voxel k, tap tp, channel chunk cc), k mod 8 fastest
+        // so that a warp's stores fill whole core matrices
 #pragma unroll
-    for (int i = 0; i < PER_WARP; ++i) acc[i][0] = acc[i][1] = acc[i][2] = acc[i][3] = 0.0f;
-    const int tiles_x = Wd / TX, tiles_y = H / TY, tiles_z = D / TZ;
-    const long n_tiles = (long)B * tiles_z * tiles_y * tiles_x;
-    for (long t0 = blockIdx.x; t0 < n_tiles; t0 += gridDim.x) {
-        long t = t0;
-        const int tx0 = (int)(t % tiles_x) * TX;
-        t /= tiles_x;
-        const int ty0 = (int)(t % tiles_y) * TY;
-        t /= tiles_y;
-        const int tz0 = (int)(t % tiles_z) * TZ;
-        const int b = (int)(t / tiles_z);
-        // dY tile transposed: dyt[co][m], m = (lz * TY + ly) * TX + lx
-        for (int e = threadIdx.x; e < 128 * COUT; e += kConvThreads) {
-            const int m = e / COUT, co = e - m * COUT;
-            const int lz = m / (TX * TY), ly = (m / TX) % TY, lx = m % TX;
-            dyt[co * DYP + m] = dY[((((size_t)b * D + tz0 + lz) * H + ty0 + ly) * Wd + tx0 + lx) * COUT + co];
-        }
-        constexpr int CH = CIN / 8;
-        const int nvox = HZ * HY * HX;
-        for (int e = threadIdx.x; e < nvox * CH; e += kConvThreads) {
-            const int vox = e / CH, ch = e - vox * CH;
-            const int hx = vox % HX, r = vox / HX;
-            const int hy = r % HY, hz = r / HY;
-            const int gx = tx0 + hx - 1, gy = ty0 + hy - 1, gz = tz0 + hz - 1;
+        for (int j = 0; j < A_EL / 8 / 128; ++j) {
+            const int i = t + 128 * j;
+            const int klo = i & 7, r = i >> 3;
+            const int cc = r % CA, r2 = r / CA;
+            const int tp = r2 % TPB, khi = r2 / TPB;
+            const int tap = tap0 + tp;
             uint4 val = make_uint4(0u, 0u, 0u, 0u);
-            if ((unsigned)gx < (unsigned)Wd && (unsigned)gy < (unsigned)H && (unsigned)gz < (unsigned)D)
-                val = __ldg(reinterpret_cast<const uint4 *>(X + ((((size_t)b * D + gz) * H + gy) * Wd + gx) * CIN) +
-                            ch);
-            *reinterpret_cast<uint4 *>(halo + (size_t)vox * CP + ch * 8) = val;
+            if (tap < 27) {
+                const long v = v0 + khi * 8 + klo;
+                // (x, y, z) by shifts when W, H and D are powers of two (lw, lh, ld >= 0)
+                int x, y, z;
+                if (lw >= 0 && lh >= 0 && ld >= 0) {
+                    x = (int)v & (Wd - 1);
+                    y = (int)(v >> lw) & (H - 1);
+                    z = (int)(v >> (lw + lh)) & (D - 1);
+                } else {
+                    x = (int)(v % Wd);
+                    const long q = v / Wd;
+                    y = (int)(q % H);
+                    z = (int)((q / H) % D);
+                }
+                const int gx = x + tap % 3 - 1, gy = y + (tap / 3) % 3 - 1, gz = z + tap / 9 - 1;
+                // the shifted voxel's offset from v, when it lies inside the volume
+                if ((unsigned)gx < (unsigned)Wd && (unsigned)gy < (unsigned)H && (unsigned)gz < (unsigned)D)
+                    val = __ldg(reinterpret_cast<const uint4 *>(
+                                    X + (v + ((long)(gz - z) * H + (gy - y)) * Wd + (gx - x)) * CIN) +
+                                cc);
+            }
+            *reinterpret_cast<uint4 *>(A + (khi * 16 + tp * CA + cc) * 64 + klo * 8) = val;
         }
+        // B: (voxel k, channel chunk cc) of dY
+        for (int i = t; i < B_EL / 8; i += 128) {
+            const int klo = i & 7, r = i >> 3;
+            const int cc = r % CB, khi = r / CB;
+            const long v = v0 + khi * 8 + klo;
+            *reinterpret_cast<uint4 *>(Bs + (khi * CB + cc) * 64 + klo * 8) =
+                __ldg(reinterpret_cast<const uint4 *>(dY + v * COUT) + cc);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
         __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
 #pragma unroll
-        for (int kc = 0; kc < 8; ++kc) {  // K = 128 voxels in steps of 16
-            const int v0 = kc * 16 + 2 * tg;  // voxels v0, v0+1 and v0+8, v0+9 of this thread's fragments
-            const int lzA = v0 / (TX * TY), lyA = (v0 / TX) % TY, lxA = v0 % TX;
-            const int lzB = (v0 + 8) / (TX * TY), lyB = ((v0 + 8) / TX) % TY, lxB = (v0 + 8) % TX;
+            for (int kk = 0; kk < kWgChunk / 16; ++kk) {
+                const uint64_t ad = umma_desc(A + kk * 2 * 16 * 64, 128 * 16, 128);
+                const uint64_t bd = umma_desc(Bs + kk * 2 * CB * 64, COUT * 16, 128);
+                const unsigned accumulate = (it > 0 || kk > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n"
+                    " .reg .pred p;\n"
+                    " setp.ne.b32 p, %4, 0;\n"
+                    " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                    "}\n" ::"r"(tmem),
+                    "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&bar[buf]))
+                         : "memory");
+        }
+    }
+    // the last commit tracks every MMA issued before it
+    if (it > 0 && !mbar_wait(&bar[(it - 1) & 1], (unsigned)((it - 1) >> 1) & 1u)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int all_ok = __syncthreads_and(ok ? 1 : 0);
+    const int tap = tap0 + t / CIN, ci = t % CIN;
+    if (all_ok && it > 0) {
 #pragma unroll
-            for (int i = 0; i < PER_WARP; ++i) {
-                const int tile = warp + 8 * i;
-                if (tile >= MT * NT) break;
-                const int mt = tile / NT, nt = tile - mt * NT;
-                const int co = mt * 16 + g;
-                const unsigned a0 = *reinterpret_cast<const unsigned *>(dyt + co * DYP + v0);
-                const unsigned a1 = *reinterpret_cast<const unsigned *>(dyt + (co + 8) * DYP + v0);
-                const unsigned a2 = *reinterpret_cast<const unsigned *>(dyt + co * DYP + v0 + 8);
-                const unsigned a3 = *reinterpret_cast<const unsigned *>(dyt + (co + 8) * DYP + v0 + 8);
-                const int tap = tap0 + nt / (CIN / 8);
-                const int ci = (nt % (CIN / 8)) * 8 + g;
-                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
-                // B[k = voxel][n = ci] = X[voxel + tap][ci]: voxels v0, v0+1 (same row) and v0+8, v0+9
-                const bf16 *hA = halo + (((lzA + dz) * HY + lyA + dy) * HX + lxA + dx) * CP + ci;
-                const bf16 *hB = halo + (((lzB + dz) * HY + lyB + dy) * HX + lxB + dx) * CP + ci;
-                const unsigned b0 = pack_bf16(hA[0], hA[CP]);
-                const unsigned b1 = pack_bf16(hB[0], hB[CP]);
-                mma_bf16(acc[i], a0, a1, a2, a3, b0, b1);
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            unsigned r[16];
+            const unsigned addr = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            if (tap < 27) {
+                float *w = dW + ((size_t)tap * COUT + c0) * CIN + ci;
+#pragma unroll
+                for (int c = 0; c < 16; ++c) atomicAdd(w + (size_t)c * CIN, __uint_as_float(r[c]));
             }
         }
-        __syncthreads();
+    } else if (!all_ok && t == 0) {
+        atomicExch(status, 1);
     }
-#pragma unroll
-    for (int i = 0; i < PER_WARP; ++i) {
-        const int tile = warp + 8 * i;
-        if (tile >= MT * NT) break;
-        const int mt = tile / NT, nt = tile - mt * NT;
-        const int tap = tap0 + nt / (CIN / 8);
-        const int ci = (nt % (CIN / 8)) * 8 + 2 * tg;
-        const int co = mt * 16 + g;
-        float *w = dW + (size_t)tap * COUT * CIN;
-        atomicAdd(w + (size_t)co * CIN + ci, acc[i][0]);
-        atomicAdd(w + (size_t)co * CIN + ci + 1, acc[i][1]);
-        atomicAdd(w + (size_t)(co + 8) * CIN + ci, acc[i][2]);
-        atomicAdd(w + (size_t)(co + 8) * CIN + ci + 1, acc[i][3]);
-    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
 }
 
 // Direct convolution on the CUDA cores for the narrow layers (Cin or Cout
@@ -588,19 +626,26 @@ cudaError_t conv_tc_launch(const bf16 *X, const bf16 *W, const float *bias, bf16
 }
 
 template <int CIN, int COUT>
-cudaError_t wgrad_mma_launch(const bf16 *X, const bf16 *dY, float *dW, int B, int D, int H, int Wd, cudaStream_t s)
+cudaError_t wgrad_tc_launch(const bf16 *X, const bf16 *dY, float *dW, int B, int D, int H, int Wd, cudaStream_t s)
 {
-    const Tile tl = conv_tile(Wd, H);
-    constexpr int TP = wgrad_taps(CIN, COUT);
-    const size_t smem =
-        ((size_t)COUT * (128 + 8) + (size_t)(tl.TZ + 2) * (tl.TY + 2) * (tl.TX + 2) * (CIN + 8)) * sizeof(bf16);
-    auto k = conv3d_wgrad_mma_kernel<CIN, COUT>;
+    const size_t smem = (size_t)2 * kWgChunk * (128 + COUT) * sizeof(bf16);
+    auto k = conv3d_wgrad_tc_kernel<CIN, COUT>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    const long n_tiles = (long)B * (D / tl.TZ) * (H / tl.TY) * (Wd / tl.TX);
-    const long per_group = std::max<long>(1, std::min<long>(n_tiles, (long)device_sm_count() * 4 / (27 / TP) + 1));
-    dim3 grid((unsigned)per_group, 27 / TP);
-    k<<<grid, kConvThreads, smem, s>>>(X, dY, dW, B, D, H, Wd);
+    int *status = nullptr;
+    e = status_word(&status);
+    if (e != cudaSuccess) return e;
+    const long nvox = (long)B * D * H * Wd;
+    constexpr int groups = (27 + 128 / CIN - 1) / (128 / CIN);
+    const long chunks = nvox / kWgChunk;
+    const long per_group = std::max<long>(1, std::min<long>(chunks, (long)device_sm_count() * 4 / groups));
+    auto log2_or_minus1 = [](int n) {
+        int l = 0;
+        while ((1 << l) < n) ++l;
+        return (1 << l) == n ? l : -1;
+    };
+    k<<<dim3((unsigned)per_group, groups), 128, smem, s>>>(X, dY, dW, nvox, D, H, Wd, log2_or_minus1(Wd),
+                                                           log2_or_minus1(H), log2_or_minus1(D), status);
     return cudaGetLastError();
 }
 
@@ -651,8 +696,11 @@ cudaError_t launch_conv3d_wgrad(const void *X, const void *dY, float *dW, int B,
     cudaError_t e = cudaMemsetAsync(dW, 0, sizeof(float) * 27 * cin * cout, s);
     if (e != cudaSuccess) return e;
     const bf16 *x = (const bf16 *)X, *dy = (const bf16 *)dY;
+    // the tensor-core kernel takes 64-voxel chunks (the shapes the convolutions
+    // accept are multiples of 128 voxels); anything else runs on the CUDA cores
+    const bool tc = ((long)B * D * H * Wd) % kWgChunk == 0;
 #define PYRO_WG_CASE(ci, co) \
-    if (cin == ci && cout == co) return wgrad_mma_launch<ci, co>(x, dy, dW, B, D, H, Wd, s);
+    if (tc && cin == ci && cout == co) return wgrad_tc_launch<ci, co>(x, dy, dW, B, D, H, Wd, s);
     PYRO_WG_CASE(16, 16)
     PYRO_WG_CASE(16, 32)
     PYRO_WG_CASE(16, 64)

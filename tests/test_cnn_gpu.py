@@ -63,10 +63,24 @@ def test_conv3d_data_gradient_by_flipped_weights(cin, cout):
     assert rel(dx, ref.permute(0, 2, 3, 4, 1)) < 4e-3
 
 
-@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 32), (32, 64), (64, 64), (64, 32), (1, 16), (16, 1)])
+@pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (16, 64), (32, 16), (32, 32), (32, 64), (64, 16), (64, 32),
+                                      (64, 64), (1, 16), (16, 1)])
 def test_conv3d_weight_gradient(cin, cout):
     x = rand_bf16((2, 4, 32, 32, cin), 8)
     dy = rand_bf16((2, 4, 32, 32, cout), 9)
+    dw = B.pyro_conv3d_wgrad(x, dy)
+    ref = R.conv3d_wgrad(x.double().cpu(), dy.double().cpu())
+    assert rel(dw, ref) < 1e-4
+
+
+@pytest.mark.parametrize("shape", [(1, 8, 8, 8), (1, 4, 4, 128), (3, 8, 16, 64), (2, 3, 6, 64)])
+@pytest.mark.parametrize("cin,cout", [(16, 32), (64, 16)])
+def test_conv3d_weight_gradient_shapes(shape, cin, cout):
+    """The tensor-core weight gradient over 64-voxel chunks: a volume of
+    eight chunks, rows wider than a chunk, a batch of three, and depth and
+    height that are not powers of two (the division path)."""
+    x = rand_bf16((*shape, cin), 20)
+    dy = rand_bf16((*shape, cout), 21)
     dw = B.pyro_conv3d_wgrad(x, dy)
     ref = R.conv3d_wgrad(x.double().cpu(), dy.double().cpu())
     assert rel(dw, ref) < 1e-4
