@@ -584,9 +584,9 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__
 {
     const int lane = threadIdx.x;
     const int k = blockIdx.y * kFPCWarps + threadIdx.y;
-    const int v = blockIdx.z;
+    const int v = blockIdx.x;
     if (k >= p.nu) return;  // whole warp
-    const int row0 = blockIdx.x * (32 * R);
+    const int row0 = blockIdx.z * (32 * R);
     Ray3 rc;
     ColumnWindow W[R];
     int mlo, mhi, clo, chi;
@@ -618,13 +618,13 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_adjoint_kernel(con
     __shared__ float runs[kFPCWarps][R * 32];
     const int lane = threadIdx.x;
     const int k = blockIdx.y * kFPCWarps + threadIdx.y;
-    const int v = blockIdx.z;
+    const int v = blockIdx.x;
     if (k >= p.nu) return;  // whole warp
     float *run = runs[threadIdx.y];
 #pragma unroll
     for (int r = 0; r < R; ++r) run[32 * r + lane] = 0.0f;
     __syncwarp();
-    const int row0 = blockIdx.x * (32 * R);
+    const int row0 = blockIdx.z * (32 * R);
     Ray3 rc;
     ColumnWindow W[R];
     int mlo, mhi, clo, chi;
@@ -907,11 +907,15 @@ cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, in
     return cudaGetLastError();
 }
 
+// Grid (views, column groups, row groups): blocks start in linear index
+// order, so the blocks in flight share a band of detector rows across the
+// views, and with it a band of the volume's z (measured 1 % faster than
+// the row groups varying fastest).
 template <typename T, int R>
 static void column_launch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
 {
     dim3 block(32, kFPCWarps);
-    dim3 grid((p.nv + 32 * R - 1) / (32 * R), (p.nu + kFPCWarps - 1) / kFPCWarps, (unsigned)p.n_views);
+    dim3 grid((unsigned)p.n_views, (p.nu + kFPCWarps - 1) / kFPCWarps, (p.nv + 32 * R - 1) / (32 * R));
     fp3d_column_kernel<T, R><<<grid, block, 0, s>>>((const T *)vp, (T *)sino, p, b);
 }
 
@@ -968,7 +972,7 @@ template <int R>
 static void column_adjoint_launch(const float *sino, float *vp, int b, const FP3DParams &p, cudaStream_t s)
 {
     dim3 block(32, kFPCWarps);
-    dim3 grid((p.nv + 32 * R - 1) / (32 * R), (p.nu + kFPCWarps - 1) / kFPCWarps, (unsigned)p.n_views);
+    dim3 grid((unsigned)p.n_views, (p.nu + kFPCWarps - 1) / kFPCWarps, (p.nv + 32 * R - 1) / (32 * R));
     fp3d_column_adjoint_kernel<R><<<grid, block, 0, s>>>(sino, vp, p, b);
 }
 
