@@ -326,9 +326,10 @@ class Texture:
         return self
 
     def close(self):
+        """Release the array (after the device has finished every queued use of it)."""
         if getattr(self, "_h", None) is not None and self._h.value:
+            torch.cuda.synchronize(self.device)
             with torch.cuda.device(self.device):
-                torch.cuda.current_stream().synchronize()
                 _check(lib().pyro_texture_destroy(self._h))
             self._h = None
 
