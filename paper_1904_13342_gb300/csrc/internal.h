@@ -58,6 +58,7 @@ struct FP3DParams {
     int nx, ny, nz, nu, nv, n_views, view0, views_total;
     int column_shared;         // every view: rows of a detector column share (x, y) (see fill_fp3d)
     int zs0, zs1;              // column adjoint: the z range [zs0, zs1) whose taps it writes
+    int pair_rows;             // > 0: rows per window of the two-rays-per-lane column kernels (33..64)
     int M;
     float cx, cy, cz;          // (n-1)/2 per axis
     float dt;

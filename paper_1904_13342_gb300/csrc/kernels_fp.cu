@@ -644,6 +644,231 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_adjoint_kernel(con
     }
 }
 
+// ---- two rays per lane: windows of up to 64 rows on one 32-voxel run -----
+// When a row step moves a ray by less than about 0.76 voxel in z, 32 rows
+// use only part of their window's 32-voxel run.  These kernels give each
+// lane two rays, rows row0 + lane and row0 + 32 + lane of a window of WR
+// rows (WR = pair_rows <= 64, chosen on the host so that WR - 1 row steps
+// stay below 29.5 voxels; the lanes past WR - 32 have no second ray), and
+// both rays take their taps from the same run: one set of loads and x/y
+// combinations for up to twice the rays.  The arithmetic of every ray is
+// that of fp3d_column_kernel.
+struct PairRowsWindow {
+    float pz[2], qz[2];  // the lane's two rays: z(m) = pz + m qz
+    float pzb, qzb;      // the window's lowest row
+    float acc[2];        // forward: the ray sums; adjoint: w times the rays' data
+    int ma, mb;          // samples of the window's rows that can touch the volume
+};
+
+template <int R>
+__device__ __forceinline__ void pair_rows_setup(const FP3DParams &p, int v, int k, int row0, int lane, Ray3 &rc,
+                                                PairRowsWindow (&W)[R], int &mlo, int &mhi, int &clo, int &chi,
+                                                float zlo, float zhi)
+{
+    const unsigned full = 0xffffffffu;
+    const int WR = p.pair_rows;
+    rc = ray3d(p, v, k, row0);
+    float lo = -(float)p.M, hi = (float)p.M;
+    clip_axis(rc.px, rc.qx, p.nx, lo, hi);
+    clip_axis(rc.py, rc.qy, p.ny, lo, hi);
+    int m0 = max(-p.M, (int)floorf(lo)), m1 = min(p.M, (int)ceilf(hi));
+    auto inside = [&](int m) {
+        const float fx = fmaf((float)m, rc.qx, rc.px), fy = fmaf((float)m, rc.qy, rc.py);
+        return fx >= -1.0f && fx < (float)p.nx && fy >= -1.0f && fy < (float)p.ny;
+    };
+    while (m0 <= m1 && !inside(m0)) ++m0;
+    while (m1 >= m0 && !inside(m1)) --m1;
+    mlo = INT_MAX;
+    mhi = INT_MIN;
+    clo = INT_MIN;
+    chi = INT_MAX;
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        int a = INT_MAX, e = INT_MIN;
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int l = row0 + r * WR + 32 * h + lane;
+            const Ray3 rr = ray3d(p, v, k, l);
+            W[r].pz[h] = rr.pz;
+            W[r].qz[h] = rr.qz;
+            W[r].acc[h] = 0.0f;
+            const bool real = l < p.nv && 32 * h + lane < WR;
+            float zl = (float)m0, zh = (float)m1;
+            clip_open(rr.pz, rr.qz, zlo, zhi, zl, zh);
+            const int aa = max(m0, (int)floorf(zl)), ee = min(m1, (int)ceilf(zh));
+            if (real && aa <= ee) {
+                a = min(a, aa);
+                e = max(e, ee);
+            }
+        }
+        // the window's lowest z is at its first row (lane 0's first ray) or its
+        // last (lane WR - 33's second ray): depth > 0
+        const float zf = __shfl_sync(full, W[r].pz[0], 0), zq = __shfl_sync(full, W[r].qz[0], 0);
+        const float zl = __shfl_sync(full, W[r].pz[1], WR - 33), zlq = __shfl_sync(full, W[r].qz[1], WR - 33);
+        W[r].pzb = zl >= zf ? zf : zl;
+        W[r].qzb = zl >= zf ? zq : zlq;
+        W[r].ma = __reduce_min_sync(full, a);
+        W[r].mb = __reduce_max_sync(full, e);
+        if (W[r].ma <= W[r].mb) {
+            mlo = min(mlo, W[r].ma);
+            mhi = max(mhi, W[r].mb);
+            clo = max(clo, W[r].ma);
+            chi = min(chi, W[r].mb);
+        }
+    }
+    if (mlo <= mhi && clo > chi) {
+        clo = mhi + 1;
+        chi = mhi;
+    }
+}
+
+
+// one depth plane of one window: the run as in column_step, then both rays'
+// z interpolations from it
+template <typename T>
+__device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, float fm, int lane, int nz, const T *const (&c)[4],
+                                               const PlaneXY &q)
+{
+    const float tzb = floor_magic(fmaf(fm, W.qzb, W.pzb));
+    const int zi = min(max(magic_to_int(tzb) + lane, -1), nz);
+    const float g = q.w00 * ld(c[0] + zi) + q.w10 * ld(c[1] + zi) + q.w01 * ld(c[2] + zi) + q.w11 * ld(c[3] + zi);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float fz = fmaf(fm, W.qz[h], W.pz[h]);
+        const float tz = floor_magic(fz);
+        const int j = __float_as_int(tz) - __float_as_int(tzb);
+        const float g0 = __shfl_sync(0xffffffffu, g, j), g1 = __shfl_sync(0xffffffffu, g, j + 1);
+        W.acc[h] += fmaf(fz - magic_to_float(tz), g1 - g0, g0);
+    }
+}
+
+// transpose of pair_rows_step: both rays' data go into the run's cells, then
+// each lane spreads its cell over the four (x, y) columns (as
+// column_step_adjoint)
+__device__ __forceinline__ void pair_rows_step_adjoint(const PairRowsWindow &W, float fm, int lane, int zs0, int zs1,
+                                                       float *const (&c)[4], const PlaneXY &q, float *run)
+{
+    const float tzb = floor_magic(fmaf(fm, W.qzb, W.pzb));
+    const int zi = magic_to_int(tzb) + lane;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+        const float fz = fmaf(fm, W.qz[h], W.pz[h]);
+        const float tz = floor_magic(fz);
+        const int j = min(max(__float_as_int(tz) - __float_as_int(tzb), 0), 30);
+        const float az = fz - magic_to_float(tz);
+        const float y = W.acc[h];
+        if (y != 0.0f) {
+            atomicAdd(run + j, fmaf(-az, y, y));
+            atomicAdd(run + j + 1, az * y);
+        }
+    }
+    __syncwarp();
+    const float d = run[lane];
+    run[lane] = 0.0f;
+    __syncwarp();
+    if (d != 0.0f && zi >= zs0 && zi < zs1) {
+        atomicAdd(c[0] + zi, q.w00 * d);
+        atomicAdd(c[1] + zi, q.w10 * d);
+        atomicAdd(c[2] + zi, q.w01 * d);
+        atomicAdd(c[3] + zi, q.w11 * d);
+    }
+}
+
+template <typename T, int R, bool CHECK, bool ADJ>
+__device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], int m0, int m1, const Ray3 &rc, int lane,
+                                                 T *vp, int nz, int sxp, int syp, float *runs, int zs0, int zs1)
+{
+    constexpr int kUnroll = ADJ ? 2 : 4;
+    float fm = (float)m0;
+#pragma unroll kUnroll
+    for (int m = m0; m <= m1; ++m, fm += 1.0f) {
+        const PlaneXY q = plane_xy(fm, rc, sxp, syp);
+        T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
+            if constexpr (ADJ) {
+                pair_rows_step_adjoint(W[r], fm, lane, zs0, zs1, c, q, runs + 32 * r);
+            } else {
+                const T *const cr[4] = {c[0], c[1], c[2], c[3]};
+                pair_rows_step(W[r], fm, lane, nz, cr, q);
+            }
+        }
+    }
+}
+
+template <typename T, int R>
+__global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_kernel(const T *__restrict__ vp,
+                                                                        T *__restrict__ sino,
+                                                                        const __grid_constant__ FP3DParams p, int b)
+{
+    const int lane = threadIdx.x;
+    const int k = blockIdx.y * kFPCWarps + threadIdx.y;
+    const int v = blockIdx.x;
+    if (k >= p.nu) return;  // whole warp
+    const int WR = p.pair_rows;
+    const int row0 = blockIdx.z * (R * WR);
+    Ray3 rc;
+    PairRowsWindow W[R];
+    int mlo, mhi, clo, chi;
+    pair_rows_setup<R>(p, v, k, row0, lane, rc, W, mlo, mhi, clo, chi, -1.0f, (float)p.nz);
+    const int sxp = p.nz + 2, syp = (p.nx + 2) * (p.nz + 2);
+    if (mlo <= mhi) {
+        T *vq = const_cast<T *>(vp);  // read only on the forward path
+        pair_rows_planes<T, R, true, false>(W, mlo, clo - 1, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
+        pair_rows_planes<T, R, false, false>(W, clo, chi, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
+        pair_rows_planes<T, R, true, false>(W, max(chi + 1, clo), mhi, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int l = row0 + r * WR + 32 * h + lane;
+            if (l < p.nv && 32 * h + lane < WR)
+                sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] =
+                    to_storage<T>(ray3d(p, v, k, l).w * W[r].acc[h]);
+        }
+}
+
+template <int R>
+__global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_adjoint_kernel(const float *__restrict__ sino,
+                                                                                float *__restrict__ vp,
+                                                                                const __grid_constant__ FP3DParams p,
+                                                                                int b)
+{
+    __shared__ float runs[kFPCWarps][R * 32];
+    const int lane = threadIdx.x;
+    const int k = blockIdx.y * kFPCWarps + threadIdx.y;
+    const int v = blockIdx.x;
+    if (k >= p.nu) return;  // whole warp
+    float *run = runs[threadIdx.y];
+#pragma unroll
+    for (int r = 0; r < R; ++r) run[32 * r + lane] = 0.0f;
+    __syncwarp();
+    const int WR = p.pair_rows;
+    const int row0 = blockIdx.z * (R * WR);
+    Ray3 rc;
+    PairRowsWindow W[R];
+    int mlo, mhi, clo, chi;
+    pair_rows_setup<R>(p, v, k, row0, lane, rc, W, mlo, mhi, clo, chi, (float)(p.zs0 - 1), (float)p.zs1);
+    if (mlo > mhi) return;  // whole warp: no sample of its rays touches the slab
+#pragma unroll
+    for (int r = 0; r < R; ++r)
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int l = row0 + r * WR + 32 * h + lane;
+            W[r].acc[h] = (l < p.nv && 32 * h + lane < WR)
+                              ? ray3d(p, v, k, l).w * sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k]
+                              : 0.0f;
+        }
+    const int sxp = p.nz + 2, syp = (p.nx + 2) * (p.nz + 2);
+    pair_rows_planes<float, R, true, true>(W, mlo, clo - 1, rc, lane, vp, p.nz, sxp, syp, run, p.zs0, p.zs1);
+    pair_rows_planes<float, R, false, true>(W, clo, chi, rc, lane, vp, p.nz, sxp, syp, run, p.zs0, p.zs1);
+    pair_rows_planes<float, R, true, true>(W, max(chi + 1, clo), mhi, rc, lane, vp, p.nz, sxp, syp, run, p.zs0,
+                                           p.zs1);
+}
+
+
 // interior of the padded z-major array -> [z][y][x]
 __global__ void __launch_bounds__(256) relayout_unpad_kernel(const float *__restrict__ vp, float *__restrict__ vol,
                                                              int nx, int ny, int nz)
@@ -952,8 +1177,51 @@ static void column_dispatch(const void *vp, void *sino, int b, const FP3DParams 
         column_launch<T, 1>(vp, sino, b, p, s);
 }
 
+// two-ray windows per warp: about 40 issue slots per window and depth plane
+// plus about 30 shared by the warp's windows
+static int pair_rows_windows_per_warp(int nv, int wr)
+{
+    const int windows = (nv + wr - 1) / wr;
+    int best = 1, cost = INT_MAX;
+    for (int r = 1; r <= 4 && r <= windows; ++r) {
+        const int c = (windows + r - 1) / r * (40 * r + 30);
+        if (c <= cost) {
+            best = r;
+            cost = c;
+        }
+    }
+    return best;
+}
+
+template <typename T, int R>
+static void pair_rows_launch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
+{
+    dim3 block(32, kFPCWarps);
+    dim3 grid((unsigned)p.n_views, (p.nu + kFPCWarps - 1) / kFPCWarps, (p.nv + R * p.pair_rows - 1) / (R * p.pair_rows));
+    fp3d_pair_rows_kernel<T, R><<<grid, block, 0, s>>>((const T *)vp, (T *)sino, p, b);
+}
+
+template <typename T>
+static void pair_rows_dispatch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
+{
+    switch (pair_rows_windows_per_warp(p.nv, p.pair_rows)) {
+    case 4: pair_rows_launch<T, 4>(vp, sino, b, p, s); break;
+    case 3: pair_rows_launch<T, 3>(vp, sino, b, p, s); break;
+    case 2: pair_rows_launch<T, 2>(vp, sino, b, p, s); break;
+    default: pair_rows_launch<T, 1>(vp, sino, b, p, s); break;
+    }
+}
+
 cudaError_t launch_fp3d_column(const void *vp, void *sino, int b, const FP3DParams &p, pyro_dtype dt, cudaStream_t s)
 {
+    if (p.pair_rows > 0) {
+        switch (dt) {
+        case PYRO_F32: pair_rows_dispatch<float>(vp, sino, b, p, s); break;
+        case PYRO_F16: pair_rows_dispatch<__half>(vp, sino, b, p, s); break;
+        case PYRO_BF16: pair_rows_dispatch<__nv_bfloat16>(vp, sino, b, p, s); break;
+        }
+        return cudaGetLastError();
+    }
     switch (dt) {
     case PYRO_F32:
         column_dispatch<float>(vp, sino, b, p, s);
@@ -976,8 +1244,27 @@ static void column_adjoint_launch(const float *sino, float *vp, int b, const FP3
     fp3d_column_adjoint_kernel<R><<<grid, block, 0, s>>>(sino, vp, p, b);
 }
 
+template <int R>
+static void pair_rows_adjoint_launch(const float *sino, float *vp, int b, const FP3DParams &p, cudaStream_t s)
+{
+    dim3 block(32, kFPCWarps);
+    dim3 grid((unsigned)p.n_views, (p.nu + kFPCWarps - 1) / kFPCWarps, (p.nv + R * p.pair_rows - 1) / (R * p.pair_rows));
+    fp3d_pair_rows_adjoint_kernel<R><<<grid, block, 0, s>>>(sino, vp, p, b);
+}
+
 cudaError_t launch_fp3d_column_adjoint(const void *sino, void *vp, int b, const FP3DParams &p, cudaStream_t s)
 {
+    if (p.pair_rows > 0) {
+        const float *si = (const float *)sino;
+        float *vo = (float *)vp;
+        switch (pair_rows_windows_per_warp(p.nv, p.pair_rows)) {
+        case 4: pair_rows_adjoint_launch<4>(si, vo, b, p, s); break;
+        case 3: pair_rows_adjoint_launch<3>(si, vo, b, p, s); break;
+        case 2: pair_rows_adjoint_launch<2>(si, vo, b, p, s); break;
+        default: pair_rows_adjoint_launch<1>(si, vo, b, p, s); break;
+        }
+        return cudaGetLastError();
+    }
     switch (column_windows_per_warp(p.nv)) {
     case 5:
         column_adjoint_launch<5>((const float *)sino, (float *)vp, b, p, s);

@@ -309,6 +309,7 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
     p.dt = (float)G.step;
     const double inv_s[3] = {1.0 / G.sx, 1.0 / G.sy, 1.0 / G.sz};
     p.column_shared = 1;
+    p.pair_rows = 64;
     p.zs0 = 0;
     p.zs1 = G.nz;
     for (int v = 0; v < nvw; ++v) {
@@ -360,7 +361,13 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
         const double w_far = -dot(r2, S) + G.M * G.step;
         const double dz_row = std::fabs(b0 * r1[2] * inv_s[2]) * w_far;
         if (!col || !(31.0 * dz_row <= 29.5)) p.column_shared = 0;
+        // rows whose z span stays within a 32-voxel run, for two rays per lane
+        const int rows = dz_row > 0.0 ? (int)std::min(64.0, std::floor(29.5 / dz_row) + 1.0) : 64;
+        p.pair_rows = std::min(p.pair_rows, rows);
     }
+    // two rays per lane pay off from 40 rows per window (a row step below
+    // about 0.76 voxel); below that the one-ray kernels run
+    if (p.pair_rows < 40) p.pair_rows = 0;
     return PYRO_OK;
 }
 

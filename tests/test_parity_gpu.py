@@ -221,13 +221,17 @@ def test_fp_cone_staged(traj, dtype):
 # (a row step just above one voxel) and every tilted trajectory take the
 # general z-major kernel.
 # "near_limit": a row step of 0.949 voxel, 31 steps = 29.43 voxels, just
-# inside the kernel's 29.5-voxel bound.
+# inside the kernel's 29.5-voxel bound.  Row steps below about 0.76 voxel
+# take the two-rays-per-lane kernels: "three_windows" and "four_windows"
+# (windows of 64 rows) and "pair_rows_50" (a row step of 0.598 voxel:
+# windows of 50 rows, so lanes 18..31 carry one ray).
 COLUMN_CASES = {
     "one_window": dict(CONE, det=(20, 41), dspacing=(1.2, 1.4)),
     "three_windows": dict(CONE, shape=(23, 37, 45), det=(70, 41), dspacing=(0.45, 1.4)),
     "four_windows": dict(CONE, shape=(23, 37, 45), det=(150, 43), dspacing=(0.2, 1.3)),
     "wide_rows": dict(CONE, det=(64, 41), dspacing=(1.4, 1.4)),
     "near_limit": dict(CONE, det=(64, 41), dspacing=(1.412, 1.4)),
+    "pair_rows_50": dict(CONE, det=(110, 41), dspacing=(0.89, 1.4)),
 }
 
 
