@@ -132,3 +132,28 @@ def test_missing_library_fails_loudly(monkeypatch):
         B.lib()
     with pytest.raises(RuntimeError):
         B.pyro_filter_pad_length(100)
+
+
+def test_validation_of_scan_weights_staged_2d_and_textures():
+    """Host-side checks of the scan-range weights, the staged 2D calls and the
+    texture calls fail before any GPU work."""
+    L = B.lib()
+    fan = FanGeometry2D((8, 8), (1.0, 1.0), 9, 1.0, 4, 7.0, 300.0, 500.0).to_c()  # range above 2 pi
+    assert L.pyro_weights2d(fake_ptr(), 1, ctypes.byref(fan), 1, B.REDUND_SCAN, B.PYRO_F32, None) == 1
+    assert "2 pi" in L.pyro_last_error().decode()
+    assert L.pyro_weights2d(fake_ptr(), 1, ctypes.byref(fan), 1, 9, B.PYRO_F32, None) == 1  # unknown mode
+    par = ParallelGeometry2D((8, 8), (1.0, 1.0), 9, 1.0, 4).to_c()
+    need = L.pyro_fp2d_workspace_bytes(ctypes.byref(par), 2, B.PYRO_F32)
+    assert need == 2 * 8 * 8 * 4
+    for fn in (L.pyro_fp_par2d_ws, L.pyro_fpT_par2d_ws):
+        assert fn(fake_ptr(), fake_ptr(), 2, ctypes.byref(par), fake_ptr(), need - 16, B.PYRO_F32, None) == 5
+        assert fn(fake_ptr(), fake_ptr(), 2, ctypes.byref(par), None, need, B.PYRO_F32, None) == 1
+    h = ctypes.c_void_p()
+    assert L.pyro_texture_volume_create(0, 4, 4, B.PYRO_F32, ctypes.byref(h)) == 1 and not h.value
+    assert L.pyro_texture_sinogram_create(4, 4, -1, B.PYRO_F32, ctypes.byref(h)) == 1 and not h.value
+    assert L.pyro_texture_volume_create(4, 4, 4, B.PYRO_BF16, ctypes.byref(h)) == 4 and not h.value
+    assert L.pyro_texture_destroy(None) == 0
+    assert L.pyro_texture_upload(None, fake_ptr(), None) == 1
+    cone = ConeGeometry3D((4, 4, 4), (1.0, 1.0, 1.0), (6, 6), (1.0, 1.0), 3, 6.0, 300.0, 500.0).to_c()
+    assert L.pyro_fp_cone3d_tex(None, fake_ptr(), ctypes.byref(cone), B.PYRO_F32, None) == 1
+    assert L.pyro_bp_cone3d_tex(None, fake_ptr(), ctypes.byref(cone), 2, 1.0, B.PYRO_F32, None) == 1
