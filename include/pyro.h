@@ -405,7 +405,9 @@ PYRO_API int pyro_cnn_adam(float *p, const float *g, float *m, float *v, void *p
  * library, held on every GPU that loads it until the process exits.
  * Problems needing more (4 * batch * n_views * nv * nu bytes) return
  * PYRO_EWORKSPACE.  The first call on a device looks up the array's address
- * and should come before any stream capture on that device.  All calls on a
+ * (and again the first call in a new context on it, e.g. after a
+ * cudaDeviceReset); that first call should come before any stream capture
+ * on that device.  All calls on a
  * device share the array (it keeps the last call's contents): calls that
  * overlap on the GPU race with each other.  No allocation is made. */
 #define PYRO_FDK_NOALLOC_SCRATCH_BYTES (64u * 1024u * 1024u)

@@ -274,3 +274,79 @@ __device__ __forceinline__ void clip_axis(float p0, float q, int n, float &lo, f
 }
 
 }  // namespace pyro
+
+// ---- float-float arithmetic (an unevaluated sum hi + lo of two floats,
+// about 44 significant bits) from the error-free transformations of Knuth
+// (TwoSum), Dekker (FastTwoSum) and the FMA form of TwoProduct.  The
+// intrinsics are the round-to-nearest operations that the compiler never
+// contracts or reorders, which these transformations rely on.
+namespace pyro {
+
+struct ff {
+    float h, l;
+};
+
+__device__ __forceinline__ ff two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return {s, e};
+}
+
+__device__ __forceinline__ ff fast_two_sum(float a, float b)  // |a| >= |b|
+{
+    const float s = __fadd_rn(a, b);
+    return {s, __fsub_rn(b, __fsub_rn(s, a))};
+}
+
+__device__ __forceinline__ ff ff_add(ff a, ff b)
+{
+    const ff s = two_sum(a.h, b.h);
+    return fast_two_sum(s.h, __fadd_rn(s.l, __fadd_rn(a.l, b.l)));
+}
+
+__device__ __forceinline__ ff ff_mul_f(ff a, float b)
+{
+    const float p = __fmul_rn(a.h, b);
+    const float e = __fmaf_rn(a.h, b, -p);
+    return fast_two_sum(p, __fmaf_rn(a.l, b, e));
+}
+
+__device__ __forceinline__ ff ff_div(ff a, ff b)
+{
+    const float q1 = __fdiv_rn(a.h, b.h);
+    const ff r = ff_add(a, ff_mul_f(b, -q1));
+    return fast_two_sum(q1, __fdiv_rn(r.h, b.h));
+}
+
+// r . (x, y, z, 1) with the row as hi/lo pairs and x, y, z exact floats
+__device__ __forceinline__ ff ff_dot4(const float *hi, const float *lo, float x, float y, float z)
+{
+    ff s = {hi[3], lo[3]};
+    s = ff_add(s, ff_mul_f({hi[0], lo[0]}, x));
+    s = ff_add(s, ff_mul_f({hi[1], lo[1]}, y));
+    s = ff_add(s, ff_mul_f({hi[2], lo[2]}, z));
+    return s;
+}
+
+// c + v split into an integer and a fraction in [0, 1) (FP32), for |c + v| < 2^22
+__device__ __forceinline__ void ff_split(ff v, float c, int &n, float &f)
+{
+    const ff s = ff_add(v, {c, 0.0f});
+    const float fl = floorf(s.h);
+    float r = __fadd_rn(__fsub_rn(s.h, fl), s.l);  // s.h - fl is exact
+    int k = (int)fl;
+    if (r < 0.0f) {
+        r = __fadd_rn(r, 1.0f);
+        k -= 1;
+    }
+    if (r >= 1.0f) {
+        r = __fsub_rn(r, 1.0f);
+        k += 1;
+    }
+    n = k;
+    f = fminf(fmaxf(r, 0.0f), 0.99999994f);
+}
+
+}  // namespace pyro

@@ -16,8 +16,9 @@ namespace pyro {
 
 // Kernel-parameter space is 32764 bytes; these caps keep every parameter
 // pack below it.  Longer trajectories are processed in chunks of views.
-constexpr int kMaxViews2D = 1024;    // 2D FP / BP: <= 6 floats per view
-constexpr int kMaxViewsConeBP = 600; // cone BP: 12 floats per view
+constexpr int kMaxViews2D = 1024;    // 2D FP: 2 floats per view
+constexpr int kMaxViewsBP2D = 512;   // 2D BP: 12 floats per view (map as hi/lo pairs)
+constexpr int kMaxViewsConeBP = 300; // cone BP: 24 floats per view (map as hi/lo pairs)
 constexpr int kMaxViewsConeFP = 400; // cone FP: 17 floats per view
 constexpr int kMaxPadLength = 8192;  // filter: pn <= 8192, so nu <= 4096
 
@@ -70,12 +71,16 @@ struct FP3DParams {
 //   x = r0 . (i, j[, z], 1),  w = r2 . (...),  k = x / w + cu,
 // with r0 centred on the detector (so x/w is small near the centre) and the
 // whole matrix divided by SID, so that w = L / SID and omega = w^-wexp.
+// The FP64 map travels as FP32 pairs (hi + lo): each block evaluates it in
+// float-float arithmetic at its tile's centre (the anchor), and its voxels
+// take FP32 offsets from there (see BP3DAnchor).
 struct BP2DParams {
     int nx, ny, nu, n_views, view0, views_total;
     int wexp;
     int parallel;              // w == 1 exactly
     float cu, scale;
-    float m[kMaxViews2D][6];   // x row (3), w row (3)
+    float m[kMaxViewsBP2D][6];   // x row (3), w row (3)
+    float mlo[kMaxViewsBP2D][6]; // FP64 map - m
 };
 
 struct BP3DParams {
@@ -85,6 +90,31 @@ struct BP3DParams {
     int accumulate;            // add into the output (view chunks after the first)
     float cu, cv, scale;
     float P[kMaxViewsConeBP][12];
+    float Plo[kMaxViewsConeBP][12];  // FP64 map - P
+};
+
+// One view's map around a block's anchor A (the centre of its voxel tile),
+// for a voxel at A + d:
+//   u = cu + fu + (au . d) / (wa + w . d),   l = cl + fl + (al . d) / (wa + w . d)
+// with the anchor's detector position cu + fu, cl + fl split into an
+// integer and a fraction in [0, 1) (evaluated in float-float), au = r0 -
+// (u_A - cu) r2 and al = r1 - (l_A - cv) r2.  |d| stays within the tile, so
+// every FP32 term is small and the detector coordinate keeps ~1e-6 pixel
+// where an absolute FP32 coordinate near pixel 300 carries ~2e-5.  bx, by:
+// the TMA box origin of the tile (the TMA kernel stores cu, cl relative to it).
+struct BP3DAnchor {
+    int cu, cl;
+    float fu, fl;
+    float wa, w0, w1, w2;
+    float au0, au1, au2;
+    int bx;
+    float al0, al1, al2;
+    int by;
+};
+
+struct BP2DAnchor {
+    int cu;
+    float fu, wa, w0, w1, a0, a1, pad;
 };
 
 // ----------------------------------------------------- weights / filter --
@@ -140,12 +170,15 @@ cudaError_t launch_bp2d_transpose(const void *vol, void *sino, int batch, const 
 cudaError_t launch_bp3d(const void *sino, void *vol, int batch, const BP3DParams &p, pyro_dtype sino_dt,
                         pyro_dtype vol_dt, cudaStream_t s);
 cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const BP3DParams &p, cudaStream_t s);
-// TMA-staged cone BP: the FP32 sinogram as a 3D tensor map [batch * views][nv][nu],
-// detector boxes of bu x bv floats (bu a multiple of 4)
+// TMA-staged cone BP: the sinogram as a 3D tensor map [batch * views][nv][nu],
+// detector boxes of bu x bv elements (bu * element size a multiple of 16
+// bytes); each of the kBPTmaStages ring stages holds the boxes of
+// `per_stage` (1, 2 or 4) consecutive views
 constexpr int kBPTmaStages = 3;
-int tma_stage_floats(int bu, int bv);
+int tma_box_elems(int bu, int bv, size_t elem);  // one box, padded to 128 bytes
+size_t bp3d_tma_smem_bytes(int n_views, int bu, int bv, size_t elem, int per_stage);
 cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv,
-                            pyro_dtype vol_dt, cudaStream_t s);
+                            int per_stage, pyro_dtype sino_dt, pyro_dtype vol_dt, cudaStream_t s);
 // address of the device word a bounded wait sets when it gives up
 cudaError_t status_word(int **ptr);
 cudaError_t launch_wait_timeout_probe(unsigned long long limit_ns, cudaStream_t s);

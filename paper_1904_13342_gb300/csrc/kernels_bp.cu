@@ -6,9 +6,16 @@
 //
 // Per view the host supplies a voxel-index -> detector map divided by SID
 // (so w = L / SID and the FDK weight (SID/L)^2 is just 1/w^2) whose first
-// rows are centred on the detector.  Each cone-beam thread owns one (x, y)
-// column and ZB consecutive z; for circular trajectories the u coordinate
-// and the weight do not depend on z and are computed once per view.
+// rows are centred on the detector, as FP32 hi/lo pairs of the FP64 map.
+// Every block first evaluates, for each view, the map at the centre of its
+// voxel tile in float-float arithmetic (the anchor: an integer detector cell
+// plus an FP32 fraction) together with the local slopes, into a shared-memory
+// table; its voxels then add small FP32 offsets to the anchor.  An absolute
+// FP32 detector coordinate near pixel 300 carries ~2e-5 pixel of rounding,
+// which back-projected noise turns into ~2e-5 relative error; the anchored
+// coordinate keeps ~1e-6.  Each cone-beam thread owns one (x, y) column and
+// ZB consecutive z; for circular trajectories the u coordinate and the
+// weight do not depend on z and are computed once per view.
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -21,31 +28,133 @@ __device__ __forceinline__ float weight_of(float rw, int wexp)
     return wexp == 0 ? 1.0f : (wexp == 1 ? rw : rw * rw);
 }
 
+// ---- anchors ---------------------------------------------------------------
+__device__ __forceinline__ BP2DAnchor bp2d_anchor(const BP2DParams &p, int v, float ia, float ja)
+{
+    const float *m = p.m[v], *ml = p.mlo[v];
+    const float hx[4] = {m[0], m[1], 0.0f, m[2]}, lx[4] = {ml[0], ml[1], 0.0f, ml[2]};
+    const float hw[4] = {m[3], m[4], 0.0f, m[5]}, lw[4] = {ml[3], ml[4], 0.0f, ml[5]};
+    const ff x = ff_dot4(hx, lx, ia, ja, 0.0f);
+    const ff w = p.parallel ? ff{1.0f, 0.0f} : ff_dot4(hw, lw, ia, ja, 0.0f);
+    const ff u = p.parallel ? x : ff_div(x, w);  // centred detector coordinate
+    BP2DAnchor a;
+    ff_split(u, p.cu, a.cu, a.fu);
+    a.wa = w.h;
+    a.w0 = p.parallel ? 0.0f : m[3];
+    a.w1 = p.parallel ? 0.0f : m[4];
+    a.a0 = fmaf(-u.h, a.w0, m[0]);
+    a.a1 = fmaf(-u.h, a.w1, m[1]);
+    a.pad = 0.0f;
+    return a;
+}
+
+__device__ __forceinline__ BP3DAnchor bp3d_anchor(const BP3DParams &p, int v, float ia, float ja, float za)
+{
+    const float *P = p.P[v], *L = p.Plo[v];
+    const ff x = ff_dot4(P, L, ia, ja, za);
+    const ff y = ff_dot4(P + 4, L + 4, ia, ja, za);
+    const ff w = ff_dot4(P + 8, L + 8, ia, ja, za);
+    const ff u = ff_div(x, w), l = ff_div(y, w);  // centred detector coordinates
+    BP3DAnchor a;
+    ff_split(u, p.cu, a.cu, a.fu);
+    ff_split(l, p.cv, a.cl, a.fl);
+    a.wa = w.h;
+    a.w0 = P[8];
+    a.w1 = P[9];
+    a.w2 = P[10];
+    a.au0 = fmaf(-u.h, P[8], P[0]);
+    a.au1 = fmaf(-u.h, P[9], P[1]);
+    a.au2 = fmaf(-u.h, P[10], P[2]);
+    a.al0 = fmaf(-l.h, P[8], P[4]);
+    a.al1 = fmaf(-l.h, P[9], P[5]);
+    a.al2 = fmaf(-l.h, P[10], P[6]);
+    a.bx = 0;
+    a.by = 0;
+    return a;
+}
+
+// detector position of voxel anchor + d, relative to the anchor's cell
+struct DetPos {
+    float u, l, rw;  // u - cu, l - cl, 1 / w
+};
+
+__device__ __forceinline__ DetPos det_pos(const BP3DAnchor &a, float di, float dj, float dz)
+{
+    DetPos r;
+    r.rw = 1.0f / fmaf(a.w0, di, fmaf(a.w1, dj, fmaf(a.w2, dz, a.wa)));
+    r.u = fmaf(fmaf(a.au0, di, fmaf(a.au1, dj, a.au2 * dz)), r.rw, a.fu);
+    r.l = fmaf(fmaf(a.al0, di, fmaf(a.al1, dj, a.al2 * dz)), r.rw, a.fl);
+    return r;
+}
+
+// the TMA box of a tile: bounds of its corners' taps (the projection is
+// linear-fractional with a positive depth, so the corners bound it), less a
+// rounding margin, the column rounded down to `align` elements; cu, cl are
+// made relative to the box
+__device__ __forceinline__ void bp3d_box(BP3DAnchor &a, float d0i, float d1i, float d0j, float d1j, float d0z,
+                                         float d1z, int align)
+{
+    float umin = 3.0e38f, lmin = 3.0e38f;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+        const DetPos q = det_pos(a, (c & 1) ? d1i : d0i, (c & 2) ? d1j : d0j, (c & 4) ? d1z : d0z);
+        umin = fminf(umin, q.u);
+        lmin = fminf(lmin, q.l);
+    }
+    const int bx = (a.cu + (int)floorf(fmaxf(umin, -1.0e8f)) - 1) & ~(align - 1);
+    const int by = a.cl + (int)floorf(fmaxf(lmin, -1.0e8f)) - 1;
+    a.cu -= bx;
+    a.cl -= by;
+    a.bx = bx;
+    a.by = by;
+}
+
+// shared-memory bytes of a per-view anchor table, rounded to 128
+__host__ __device__ constexpr size_t table_bytes(int n_views, size_t entry)
+{
+    return ((size_t)n_views * entry + 127) / 128 * 128;
+}
+
+template <typename T>
+__device__ __forceinline__ float lds(const T *p)
+{
+    return to_float<T>(*p);
+}
+
+// ---- 2D -----------------------------------------------------------------
 template <typename TS, typename TV, bool PAR>
 __global__ void __launch_bounds__(256) bp2d_kernel(const TS *__restrict__ sino, TV *__restrict__ vol,
                                                    const __grid_constant__ BP2DParams p, int accumulate)
 {
+    extern __shared__ __align__(16) unsigned char bp2_smem[];
+    BP2DAnchor *tab = reinterpret_cast<BP2DAnchor *>(bp2_smem);
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const float ia = blockIdx.x * 32 + 15.5f, ja = blockIdx.y * 8 + 3.5f;
+    for (int v = t; v < p.n_views; v += 256) tab[v] = bp2d_anchor(p, v, ia, ja);
+    __syncthreads();
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
     const int b = blockIdx.z;
     if (i >= p.nx || j >= p.ny) return;
-    const float fi = (float)i, fj = (float)j;
+    const float di = (float)i - ia, dj = (float)j - ja;
     const TS *S = sino + ((size_t)b * p.views_total + p.view0) * p.nu;
     float acc = 0.0f;
     for (int v = 0; v < p.n_views; ++v) {
-        const float *m = p.m[v];
-        const float x = fmaf(m[0], fi, fmaf(m[1], fj, m[2]));
-        float k, om;
-        if (PAR) {
-            k = x + p.cu;
-            om = 1.0f;
-        } else {
-            const float w = fmaf(m[3], fi, fmaf(m[4], fj, m[5]));
-            const float rw = 1.0f / w;
-            k = fmaf(x, rw, p.cu);
+        const BP2DAnchor a = tab[v];
+        float rw = 1.0f, om = 1.0f;
+        if (!PAR) {
+            rw = 1.0f / fmaf(a.w0, di, fmaf(a.w1, dj, a.wa));
             om = weight_of(rw, p.wexp);
         }
-        acc = fmaf(om, lerp_zero(S + (size_t)v * p.nu, p.nu, k), acc);
+        const float tu = fmaf(fmaf(a.a0, di, a.a1 * dj), rw, a.fu);
+        const float mu = floor_magic(tu);
+        const float f = tu - magic_to_float(mu);
+        const int k = a.cu + magic_to_int(mu);
+        const TS *row = S + (size_t)v * p.nu;
+        const float w0 = ((unsigned)k < (unsigned)p.nu) ? 1.0f - f : 0.0f;
+        const float w1 = ((unsigned)(k + 1) < (unsigned)p.nu) ? f : 0.0f;
+        const int k0 = min(max(k, 0), p.nu - 1), k1 = min(max(k + 1, 0), p.nu - 1);
+        acc = fmaf(om, fmaf(w0, ld(row + k0), w1 * ld(row + k1)), acc);
     }
     const size_t o = ((size_t)b * p.ny + j) * p.nx + i;
     float out = p.scale * acc;
@@ -56,37 +165,41 @@ __global__ void __launch_bounds__(256) bp2d_kernel(const TS *__restrict__ sino, 
 __global__ void __launch_bounds__(256) bp2d_transpose_kernel(const float *__restrict__ vol, float *__restrict__ sino,
                                                              const __grid_constant__ BP2DParams p)
 {
+    extern __shared__ __align__(16) unsigned char bp2_smem[];
+    BP2DAnchor *tab = reinterpret_cast<BP2DAnchor *>(bp2_smem);
+    const int t = threadIdx.y * 32 + threadIdx.x;
+    const float ia = blockIdx.x * 32 + 15.5f, ja = blockIdx.y * 8 + 3.5f;
+    for (int v = t; v < p.n_views; v += 256) tab[v] = bp2d_anchor(p, v, ia, ja);
+    __syncthreads();
     const int i = blockIdx.x * 32 + threadIdx.x;
     const int j = blockIdx.y * 8 + threadIdx.y;
     const int b = blockIdx.z;
     if (i >= p.nx || j >= p.ny) return;
     const float g = p.scale * vol[((size_t)b * p.ny + j) * p.nx + i];
     if (g == 0.0f) return;
-    const float fi = (float)i, fj = (float)j;
+    const float di = (float)i - ia, dj = (float)j - ja;
     float *S = sino + ((size_t)b * p.views_total + p.view0) * p.nu;
     for (int v = 0; v < p.n_views; ++v) {
-        const float *m = p.m[v];
-        const float x = fmaf(m[0], fi, fmaf(m[1], fj, m[2]));
-        float k, om;
-        if (p.parallel) {
-            k = x + p.cu;
-            om = 1.0f;
-        } else {
-            const float w = fmaf(m[3], fi, fmaf(m[4], fj, m[5]));
-            const float rw = 1.0f / w;
-            k = fmaf(x, rw, p.cu);
+        const BP2DAnchor a = tab[v];
+        float rw = 1.0f, om = 1.0f;
+        if (!p.parallel) {
+            rw = 1.0f / fmaf(a.w0, di, fmaf(a.w1, dj, a.wa));
             om = weight_of(rw, p.wexp);
         }
-        const Axis a = axis_taps(k, p.nu);
+        const float tu = fmaf(fmaf(a.a0, di, a.a1 * dj), rw, a.fu);
+        const float mu = floor_magic(tu);
+        const float f = tu - magic_to_float(mu);
+        const int k = a.cu + magic_to_int(mu);
         float *row = S + (size_t)v * p.nu;
         const float gw = g * om;
-        if (a.w0 != 0.0f) atomicAdd(row + a.i0, gw * a.w0);
-        if (a.w1 != 0.0f) atomicAdd(row + a.i1, gw * a.w1);
+        if ((unsigned)k < (unsigned)p.nu && f != 1.0f) atomicAdd(row + k, gw * (1.0f - f));
+        if ((unsigned)(k + 1) < (unsigned)p.nu && f != 0.0f) atomicAdd(row + k + 1, gw * f);
     }
 }
 
 constexpr int kBPX = 32, kBPY = 8, kBPZ = 8;
 
+// ---- cone beam, L1 gathers ---------------------------------------------------
 // The 32 x 8 voxel tile of a block is cut into 8 x 4 tiles per warp (not 32 x 1
 // rows): a warp's voxels then project onto ~16 detector columns instead of
 // ~40, one cache line per detector row.
@@ -94,6 +207,8 @@ template <typename TS, typename TV, bool ZINV>
 __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__ sino, TV *__restrict__ vol,
                                                           const __grid_constant__ BP3DParams p)
 {
+    extern __shared__ __align__(16) unsigned char bp3_smem[];
+    BP3DAnchor *tab = reinterpret_cast<BP3DAnchor *>(bp3_smem);
     const int t = threadIdx.y * kBPX + threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
     const int i = blockIdx.x * kBPX + (warp & 3) * 8 + (lane & 7);
@@ -101,8 +216,11 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__
     const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
     const int b = blockIdx.z / zblocks;
     const int z0 = (blockIdx.z % zblocks) * kBPZ;
+    const float ia = blockIdx.x * kBPX + 15.5f, ja = blockIdx.y * kBPY + 3.5f, za = z0 + 3.5f;
+    for (int v = t; v < p.n_views; v += kBPX * kBPY) tab[v] = bp3d_anchor(p, v, ia, ja, za);
+    __syncthreads();
     if (i >= p.nx || j >= p.ny) return;
-    const float fi = (float)i, fj = (float)j;
+    const float di = (float)i - ia, dj = (float)j - ja, dz0 = (float)z0 - za;
     const size_t vstride = (size_t)p.nu * p.nv;
     const TS *S0 = sino + ((size_t)b * p.views_total + p.view0) * vstride;
     float acc[kBPZ];
@@ -110,28 +228,24 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__
     for (int zz = 0; zz < kBPZ; ++zz) acc[zz] = 0.0f;
 
     for (int v = 0; v < p.n_views; ++v) {
-        const float *P = p.P[v];
+        const BP3DAnchor a = tab[v];
         const TS *S = S0 + (size_t)v * vstride;
-        const float xb = fmaf(P[0], fi, fmaf(P[1], fj, P[3]));
-        const float yb = fmaf(P[4], fi, fmaf(P[5], fj, P[7]));
-        const float wb = fmaf(P[8], fi, fmaf(P[9], fj, P[11]));
         if (ZINV) {
-            const float rw = 1.0f / wb;
-            const float om = weight_of(rw, p.wexp);
-            const float fu = fmaf(xb, rw, p.cu);
-            const float dl = P[6] * rw;
-            const float l0 = fmaf(yb, rw, p.cv);
-            const float la = fmaf((float)z0, dl, l0), lb = fmaf((float)(z0 + kBPZ - 1), dl, l0);
-            const float hu = (float)(p.nu - 1) - 1e-3f, hv = (float)(p.nv - 1) - 1e-3f;
-            if (fu >= 1e-3f && fu <= hu && fminf(la, lb) >= 1e-3f && fmaxf(la, lb) <= hv) {
+            const DetPos q = det_pos(a, di, dj, dz0);
+            const float om = weight_of(q.rw, p.wexp);
+            const float dl = a.al2 * q.rw;
+            const float mu = floor_magic(q.u);
+            const float au = q.u - magic_to_float(mu);
+            const int k = a.cu + magic_to_int(mu);
+            const float la = q.l, lb = fmaf((float)(kBPZ - 1), dl, q.l);
+            const int ra = a.cl + (int)floorf(fminf(la, lb)), rb = a.cl + (int)floorf(fmaxf(la, lb));
+            if (k >= 0 && k + 1 < p.nu && ra >= 0 && rb + 1 < p.nv) {
                 // every tap of the ZB voxels lies inside the detector: no masking
-                const float fu0 = floorf(fu);
-                const float au = fu - fu0;
                 const float w1 = om * au, w0 = om - w1;
-                const TS *Sk = S + (int)fu0;
+                const TS *Sk = S + k + (long)a.cl * p.nu;  // row a.cl + floor(ll) >= 0 by the test above
 #pragma unroll
                 for (int zz = 0; zz < kBPZ; ++zz) {
-                    const float ll = fmaf((float)(z0 + zz), dl, l0);
+                    const float ll = fmaf((float)zz, dl, q.l);
                     const float tl = floor_magic(ll);
                     const float av = ll - magic_to_float(tl);
                     const TS *r0 = Sk + magic_to_int(tl) * p.nu;
@@ -141,27 +255,41 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_kernel(const TS *__restrict__
                 }
                 continue;
             }
-            const Axis au = axis_taps(fu, p.nu);
-            const float w0 = om * au.w0, w1 = om * au.w1;
+            const float wu0 = ((unsigned)k < (unsigned)p.nu) ? om * (1.0f - au) : 0.0f;
+            const float wu1 = ((unsigned)(k + 1) < (unsigned)p.nu) ? om * au : 0.0f;
+            const int k0 = min(max(k, 0), p.nu - 1), k1 = min(max(k + 1, 0), p.nu - 1);
 #pragma unroll
             for (int zz = 0; zz < kBPZ; ++zz) {
-                const Axis av = axis_taps(fmaf((float)(z0 + zz), dl, l0), p.nv);
-                const TS *r0 = S + (size_t)av.i0 * p.nu;
-                const TS *r1 = S + (size_t)av.i1 * p.nu;
-                const float t0 = fmaf(w0, ld(r0 + au.i0), w1 * ld(r0 + au.i1));
-                const float t1 = fmaf(w0, ld(r1 + au.i0), w1 * ld(r1 + au.i1));
-                acc[zz] = fmaf(av.w0, t0, fmaf(av.w1, t1, acc[zz]));
+                const float ll = fmaf((float)zz, dl, q.l);
+                const float tl = floor_magic(ll);
+                const float av = ll - magic_to_float(tl);
+                const int r = a.cl + magic_to_int(tl);
+                const float wv0 = ((unsigned)r < (unsigned)p.nv) ? 1.0f - av : 0.0f;
+                const float wv1 = ((unsigned)(r + 1) < (unsigned)p.nv) ? av : 0.0f;
+                const TS *r0 = S + (size_t)min(max(r, 0), p.nv - 1) * p.nu;
+                const TS *r1 = S + (size_t)min(max(r + 1, 0), p.nv - 1) * p.nu;
+                const float t0 = fmaf(wu0, ld(r0 + k0), wu1 * ld(r0 + k1));
+                const float t1 = fmaf(wu0, ld(r1 + k0), wu1 * ld(r1 + k1));
+                acc[zz] = fmaf(wv0, t0, fmaf(wv1, t1, acc[zz]));
             }
         } else {
 #pragma unroll
             for (int zz = 0; zz < kBPZ; ++zz) {
-                const float fz = (float)(z0 + zz);
-                const float x = fmaf(P[2], fz, xb);
-                const float y = fmaf(P[6], fz, yb);
-                const float w = fmaf(P[10], fz, wb);
-                const float rw = 1.0f / w;
-                const float om = weight_of(rw, p.wexp);
-                acc[zz] = fmaf(om, bilerp_zero(S, p.nu, p.nv, fmaf(x, rw, p.cu), fmaf(y, rw, p.cv)), acc[zz]);
+                const DetPos q = det_pos(a, di, dj, dz0 + (float)zz);
+                const float om = weight_of(q.rw, p.wexp);
+                const float mu = floor_magic(q.u), ml = floor_magic(q.l);
+                const float au = q.u - magic_to_float(mu), av = q.l - magic_to_float(ml);
+                const int k = a.cu + magic_to_int(mu), r = a.cl + magic_to_int(ml);
+                const float wu0 = ((unsigned)k < (unsigned)p.nu) ? 1.0f - au : 0.0f;
+                const float wu1 = ((unsigned)(k + 1) < (unsigned)p.nu) ? au : 0.0f;
+                const float wv0 = ((unsigned)r < (unsigned)p.nv) ? 1.0f - av : 0.0f;
+                const float wv1 = ((unsigned)(r + 1) < (unsigned)p.nv) ? av : 0.0f;
+                const int k0 = min(max(k, 0), p.nu - 1), k1 = min(max(k + 1, 0), p.nu - 1);
+                const TS *r0 = S + (size_t)min(max(r, 0), p.nv - 1) * p.nu;
+                const TS *r1 = S + (size_t)min(max(r + 1, 0), p.nv - 1) * p.nu;
+                const float v0 = fmaf(wu0, ld(r0 + k0), wu1 * ld(r0 + k1));
+                const float v1 = fmaf(wu0, ld(r1 + k0), wu1 * ld(r1 + k1));
+                acc[zz] = fmaf(om, fmaf(wv0, v0, wv1 * v1), acc[zz]);
             }
         }
     }
@@ -239,15 +367,19 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_tex_kernel(cudaTextureObject_
     }
 }
 
-// ---- TMA-staged cone BP (circular-type trajectories, FP32 sinogram) ------
+// ---- TMA-staged cone BP (circular-type trajectories) --------------------
 // Per view a block's 32 x 8 x ZB voxel tile projects onto a small detector
-// box; one thread copies the boxes of the next views into a ring of shared
-// memory stages with cp.async.bulk.tensor (completion counted on an
-// mbarrier), and every thread reads its four taps per voxel from shared
-// memory.  Out-of-range parts of a box are zero-filled by the copy, which is
-// the zero extension of the detector, so no tap needs masking.  Box sizes are
-// a host-computed bound; shared-memory indices are clamped to the stage.
-constexpr int kTmaStages = 3;
+// box.  The boxes of G consecutive views form one stage of a ring of
+// kBPTmaStages stages; threads 0..G-1 each copy one box with
+// cp.async.bulk.tensor (completion counted on the stage's mbarrier), and
+// every thread reads its four taps per voxel from shared memory.  One block
+// barrier per stage (G views) frees the stage for the copy of the stage
+// kBPTmaStages ahead.  Out-of-range parts of a box are zero-filled by the
+// copy, which is the zero extension of the detector, so no tap needs
+// masking.  Box sizes are a host-computed bound; shared-memory indices are
+// clamped to the box.  The sinogram is FP32, FP16 or BF16 (the taps are
+// converted to FP32 on load).
+constexpr int kTmaStages = kBPTmaStages;
 
 __device__ int g_status;  // set to 1 by a wait that gave up (read by pyro_sync_status)
 
@@ -264,7 +396,8 @@ __global__ void wait_timeout_probe_kernel(unsigned long long limit_ns)
     if (!mbar_wait(&bar, 0, limit_ns) && threadIdx.x == 0) atomicExch(&g_status, 1);
 }
 
-__device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
+template <typename TS>
+__device__ __forceinline__ void tma_load_3d(TS *dst, const CUtensorMap *map, int x, int y, int z, uint64_t *bar)
 {
     asm volatile(
         "cp.async.bulk.tensor.3d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3, %4}], [%5];"
@@ -272,15 +405,21 @@ __device__ __forceinline__ void tma_load_3d(float *dst, const CUtensorMap *map, 
         : "memory");
 }
 
-template <typename TV>
+__device__ __forceinline__ void mbar_arrive(uint64_t *bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+template <typename TS, typename TV, int G>
 __global__ void __launch_bounds__(kBPX *kBPY) bp3d_tma_kernel(const __grid_constant__ CUtensorMap map,
                                                               TV *__restrict__ vol,
                                                               const __grid_constant__ BP3DParams p, int bu, int bv,
-                                                              int stage_floats)
+                                                              int box_elems)
 {
-    extern __shared__ __align__(128) float stages[];
+    extern __shared__ __align__(128) unsigned char tma_smem[];
+    BP3DAnchor *tab = reinterpret_cast<BP3DAnchor *>(tma_smem);
+    TS *stages = reinterpret_cast<TS *>(tma_smem + table_bytes(p.n_views, sizeof(BP3DAnchor)));
     __shared__ __align__(8) uint64_t full[kTmaStages];
-    __shared__ int2 origin[kTmaStages];
     __shared__ int gave_up;
     const int t = threadIdx.y * kBPX + threadIdx.x;
     const int lane = t & 31, warp = t >> 5;
@@ -291,91 +430,83 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_tma_kernel(const __grid_const
     const int b = blockIdx.z / zblocks;
     const int z0 = (blockIdx.z % zblocks) * kBPZ;
     const int i1 = min(i0 + kBPX - 1, p.nx - 1), j1 = min(j0 + kBPY - 1, p.ny - 1), z1 = min(z0 + kBPZ - 1, p.nz - 1);
+    const float ia = i0 + 15.5f, ja = j0 + 3.5f, za = z0 + 3.5f;
     const int vbase = b * p.views_total + p.view0;
     const bool active = i < p.nx && j < p.ny;  // the others still take part in the barriers
-    const unsigned stage_bytes = (unsigned)(bu * bv * sizeof(float));
+    const unsigned box_bytes = (unsigned)(bu * bv * sizeof(TS));
+    constexpr int align = 16 / (int)sizeof(TS);  // x of a tensor copy: a multiple of 16 bytes
+    for (int v = t; v < p.n_views; v += kBPX * kBPY) {
+        BP3DAnchor a = bp3d_anchor(p, v, ia, ja, za);
+        bp3d_box(a, (float)i0 - ia, (float)i1 - ia, (float)j0 - ja, (float)j1 - ja, (float)z0 - za, (float)z1 - za,
+                 align);
+        tab[v] = a;
+    }
     if (t == 0) {
-        for (int s = 0; s < kTmaStages; ++s) mbar_init(&full[s], 1);
+        for (int s = 0; s < kTmaStages; ++s) mbar_init(&full[s], G);
         gave_up = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     __syncthreads();
 
-    // thread 0: the box of view v from the tile's eight corners (the
-    // projection is linear-fractional with a positive depth, so the corners
-    // bound it), then the copy into stage v % kTmaStages
-    auto issue = [&](int v) {
-        const int s = v % kTmaStages;
-        const float *P = p.P[v];
-        float umin = 3.0e38f, umax = -3.0e38f, lmin = 3.0e38f;
-        for (int c = 0; c < 4; ++c) {
-            const float fi = (float)((c & 1) ? i1 : i0), fj = (float)((c & 2) ? j1 : j0);
-            const float xb = fmaf(P[0], fi, fmaf(P[1], fj, P[3]));
-            const float yb = fmaf(P[4], fi, fmaf(P[5], fj, P[7]));
-            const float wb = fmaf(P[8], fi, fmaf(P[9], fj, P[11]));
-            const float rw = 1.0f / wb;
-            const float fu = fmaf(xb, rw, p.cu);
-            const float dl = P[6] * rw;
-            const float l0 = fmaf(yb, rw, p.cv);
-            umin = fminf(umin, fu);
-            umax = fmaxf(umax, fu);
-            lmin = fminf(lmin, fminf(fmaf((float)z0, dl, l0), fmaf((float)z1, dl, l0)));
+    const int n_st = (p.n_views + G - 1) / G;
+    // thread t < G: the box of view s G + t into stage s (a plain arrive for
+    // the views past the end, so that the stage's G arrivals complete)
+    auto issue = [&](int s) {
+        const int slot = s % kTmaStages, v = s * G + t;
+        if (v < p.n_views) {
+            mbar_expect_tx(&full[slot], box_bytes);
+            tma_load_3d(stages + (slot * G + t) * box_elems, &map, tab[v].bx, tab[v].by, vbase + v, &full[slot]);
+        } else {
+            mbar_arrive(&full[slot]);
         }
-        // x of a tensor copy must be a multiple of 4 floats (16 bytes)
-        const int ux = ((int)floorf(fmaxf(umin, -1.0e8f) - 0.01f)) & ~3;
-        const int ly = (int)floorf(fmaxf(lmin, -1.0e8f) - 0.01f);
-        origin[s] = make_int2(ux, ly);
-        mbar_expect_tx(&full[s], stage_bytes);
-        tma_load_3d(stages + s * stage_floats, &map, ux, ly, vbase + v, &full[s]);
     };
-    if (t == 0)
-        for (int v = 0; v < min(kTmaStages, p.n_views); ++v) issue(v);
+    if (t < G)
+        for (int s = 0; s < min(kTmaStages, n_st); ++s) issue(s);
 
     float acc[kBPZ];
 #pragma unroll
     for (int zz = 0; zz < kBPZ; ++zz) acc[zz] = 0.0f;
-    const float fi = (float)i, fj = (float)j;
-    const int last = stage_floats - bu - 2;  // highest first tap index of a 2 x 2 patch
-    int v = 0;
-    for (; v < p.n_views; ++v) {
-        const int s = v % kTmaStages;
-        if (!mbar_wait(&full[s], (unsigned)(v / kTmaStages) & 1u)) atomicExch(&gave_up, 1);
+    const float di = (float)i - ia, dj = (float)j - ja, dz0 = (float)z0 - za;
+    const int last = box_elems - bu - 2;  // highest first tap index of a 2 x 2 patch
+    int s = 0;
+    for (; s < n_st; ++s) {
+        const int slot = s % kTmaStages;
+        if (!mbar_wait(&full[slot], (unsigned)(s / kTmaStages) & 1u)) atomicExch(&gave_up, 1);
         if (active) {
-            const float *S = stages + s * stage_floats;
-            const int2 o = origin[s];
-            const float *P = p.P[v];
-            const float xb = fmaf(P[0], fi, fmaf(P[1], fj, P[3]));
-            const float yb = fmaf(P[4], fi, fmaf(P[5], fj, P[7]));
-            const float wb = fmaf(P[8], fi, fmaf(P[9], fj, P[11]));
-            const float rw = 1.0f / wb;
-            const float om = weight_of(rw, p.wexp);
-            const float fu = fmaf(xb, rw, p.cu);
-            const float dl = P[6] * rw;
-            const float l0 = fmaf(yb, rw, p.cv);
-            const float tu = floor_magic(fu);
-            const float au = fu - magic_to_float(tu);
-            const float w1 = om * au, w0 = om - w1;
-            const int col = magic_to_int(tu) - o.x;
 #pragma unroll
-            for (int zz = 0; zz < kBPZ; ++zz) {
-                const float ll = fmaf((float)(z0 + zz), dl, l0);
-                const float tl = floor_magic(ll);
-                const float av = ll - magic_to_float(tl);
-                const int e = min(max((magic_to_int(tl) - o.y) * bu + col, 0), last);
-                const float t0 = fmaf(w0, S[e], w1 * S[e + 1]);
-                const float t1 = fmaf(w0, S[e + bu], w1 * S[e + bu + 1]);
-                acc[zz] += lerpf(t0, t1, av);
+            for (int g = 0; g < G; ++g) {
+                const int v = s * G + g;
+                if (v >= p.n_views) break;  // block-uniform
+                const BP3DAnchor a = tab[v];
+                const TS *S = stages + (slot * G + g) * box_elems;
+                const DetPos q = det_pos(a, di, dj, dz0);
+                const float om = weight_of(q.rw, p.wexp);
+                const float mu = floor_magic(q.u);
+                const float au = q.u - magic_to_float(mu);
+                const float w1 = om * au, w0 = om - w1;
+                const int col = a.cu + magic_to_int(mu);
+                const float dl = a.al2 * q.rw;
+#pragma unroll
+                for (int zz = 0; zz < kBPZ; ++zz) {
+                    const float ll = fmaf((float)zz, dl, q.l);
+                    const float tl = floor_magic(ll);
+                    const float av = ll - magic_to_float(tl);
+                    const int e = min(max((a.cl + magic_to_int(tl)) * bu + col, 0), last);
+                    const float t0 = fmaf(w0, lds(S + e), w1 * lds(S + e + 1));
+                    const float t1 = fmaf(w0, lds(S + e + bu), w1 * lds(S + e + bu + 1));
+                    acc[zz] += lerpf(t0, t1, av);
+                }
             }
         }
-        __syncthreads();  // stage s is free again; gave_up is visible
+        __syncthreads();  // stage `slot` is free again; gave_up is visible
         if (gave_up) break;
-        if (t == 0 && v + kTmaStages < p.n_views) issue(v + kTmaStages);
+        if (t < G && s + kTmaStages < n_st) issue(s + kTmaStages);
     }
     if (gave_up) {
         // let the copies still in flight land (bounded) before the block ends
         if (t == 0) {
             atomicExch(&g_status, 1);
-            for (int w = v; w < min(v + kTmaStages, p.n_views); ++w)
+            for (int w = s; w < min(s + kTmaStages, n_st); ++w)
                 mbar_wait(&full[w % kTmaStages], (unsigned)(w / kTmaStages) & 1u);
         }
         return;
@@ -398,33 +529,42 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_transpose_kernel(const float 
                                                                     float *__restrict__ sino,
                                                                     const __grid_constant__ BP3DParams p)
 {
-    const int i = blockIdx.x * kBPX + threadIdx.x;
-    const int j = blockIdx.y * kBPY + threadIdx.y;
+    extern __shared__ __align__(16) unsigned char bp3_smem[];
+    BP3DAnchor *tab = reinterpret_cast<BP3DAnchor *>(bp3_smem);
     const int b = blockIdx.z / p.nz;
     const int z = blockIdx.z % p.nz;
+    const float ia = blockIdx.x * kBPX + 15.5f, ja = blockIdx.y * kBPY + 3.5f, za = (float)z;
+    const int t = threadIdx.y * kBPX + threadIdx.x;
+    for (int v = t; v < p.n_views; v += kBPX * kBPY) tab[v] = bp3d_anchor(p, v, ia, ja, za);
+    __syncthreads();
+    const int i = blockIdx.x * kBPX + threadIdx.x;
+    const int j = blockIdx.y * kBPY + threadIdx.y;
     if (i >= p.nx || j >= p.ny) return;
     const float g = p.scale * vol[(((size_t)b * p.nz + z) * p.ny + j) * p.nx + i];
     if (g == 0.0f) return;
-    const float fi = (float)i, fj = (float)j, fz = (float)z;
+    const float di = (float)i - ia, dj = (float)j - ja;
     const size_t vstride = (size_t)p.nu * p.nv;
     float *S0 = sino + ((size_t)b * p.views_total + p.view0) * vstride;
     for (int v = 0; v < p.n_views; ++v) {
-        const float *P = p.P[v];
-        const float x = fmaf(P[0], fi, fmaf(P[1], fj, fmaf(P[2], fz, P[3])));
-        const float y = fmaf(P[4], fi, fmaf(P[5], fj, fmaf(P[6], fz, P[7])));
-        const float w = fmaf(P[8], fi, fmaf(P[9], fj, fmaf(P[10], fz, P[11])));
-        const float rw = 1.0f / w;
-        const float gw = g * weight_of(rw, p.wexp);
-        const Axis au = axis_taps(fmaf(x, rw, p.cu), p.nu);
-        const Axis av = axis_taps(fmaf(y, rw, p.cv), p.nv);
+        const BP3DAnchor a = tab[v];
+        const DetPos q = det_pos(a, di, dj, 0.0f);
+        const float gw = g * weight_of(q.rw, p.wexp);
+        const float mu = floor_magic(q.u), ml = floor_magic(q.l);
+        const float au = q.u - magic_to_float(mu), av = q.l - magic_to_float(ml);
+        const int k = a.cu + magic_to_int(mu), r = a.cl + magic_to_int(ml);
         float *S = S0 + (size_t)v * vstride;
-        float *r0 = S + (size_t)av.i0 * p.nu;
-        float *r1 = S + (size_t)av.i1 * p.nu;
-        const float g0 = gw * av.w0, g1 = gw * av.w1;
-        if (g0 * au.w0 != 0.0f) atomicAdd(r0 + au.i0, g0 * au.w0);
-        if (g0 * au.w1 != 0.0f) atomicAdd(r0 + au.i1, g0 * au.w1);
-        if (g1 * au.w0 != 0.0f) atomicAdd(r1 + au.i0, g1 * au.w0);
-        if (g1 * au.w1 != 0.0f) atomicAdd(r1 + au.i1, g1 * au.w1);
+        const float g0 = gw * (1.0f - av), g1 = gw * av;
+        const bool k0 = (unsigned)k < (unsigned)p.nu, k1 = (unsigned)(k + 1) < (unsigned)p.nu;
+        if ((unsigned)r < (unsigned)p.nv) {
+            float *row = S + (size_t)r * p.nu;
+            if (k0 && g0 * (1.0f - au) != 0.0f) atomicAdd(row + k, g0 * (1.0f - au));
+            if (k1 && g0 * au != 0.0f) atomicAdd(row + k + 1, g0 * au);
+        }
+        if ((unsigned)(r + 1) < (unsigned)p.nv) {
+            float *row = S + (size_t)(r + 1) * p.nu;
+            if (k0 && g1 * (1.0f - au) != 0.0f) atomicAdd(row + k, g1 * (1.0f - au));
+            if (k1 && g1 * au != 0.0f) atomicAdd(row + k + 1, g1 * au);
+        }
     }
 }
 
@@ -433,10 +573,11 @@ cudaError_t bp2d_dispatch(const void *sino, void *vol, int batch, const BP2DPara
 {
     dim3 block(32, 8);
     dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, batch);
+    const size_t smem = table_bytes(p.n_views, sizeof(BP2DAnchor));
     if (p.parallel)
-        bp2d_kernel<TS, TV, true><<<grid, block, 0, s>>>((const TS *)sino, (TV *)vol, p, accumulate);
+        bp2d_kernel<TS, TV, true><<<grid, block, smem, s>>>((const TS *)sino, (TV *)vol, p, accumulate);
     else
-        bp2d_kernel<TS, TV, false><<<grid, block, 0, s>>>((const TS *)sino, (TV *)vol, p, accumulate);
+        bp2d_kernel<TS, TV, false><<<grid, block, smem, s>>>((const TS *)sino, (TV *)vol, p, accumulate);
     return cudaGetLastError();
 }
 
@@ -446,10 +587,11 @@ cudaError_t bp3d_dispatch(const void *sino, void *vol, int batch, const BP3DPara
     dim3 block(kBPX, kBPY);
     const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
     dim3 grid((p.nx + kBPX - 1) / kBPX, (p.ny + kBPY - 1) / kBPY, (unsigned)(zblocks * batch));
+    const size_t smem = table_bytes(p.n_views, sizeof(BP3DAnchor));
     if (p.z_invariant)
-        bp3d_kernel<TS, TV, true><<<grid, block, 0, s>>>((const TS *)sino, (TV *)vol, p);
+        bp3d_kernel<TS, TV, true><<<grid, block, smem, s>>>((const TS *)sino, (TV *)vol, p);
     else
-        bp3d_kernel<TS, TV, false><<<grid, block, 0, s>>>((const TS *)sino, (TV *)vol, p);
+        bp3d_kernel<TS, TV, false><<<grid, block, smem, s>>>((const TS *)sino, (TV *)vol, p);
     return cudaGetLastError();
 }
 
@@ -477,6 +619,46 @@ cudaError_t bp3d_by_vol(const void *sino, void *vol, int batch, const BP3DParams
     return cudaErrorInvalidValue;
 }
 
+template <typename TS, typename TV, int G>
+cudaError_t tma_launch(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv,
+                       cudaStream_t s)
+{
+    const int be = tma_box_elems(bu, bv, sizeof(TS));
+    const size_t smem = bp3d_tma_smem_bytes(p.n_views, bu, bv, sizeof(TS), G);
+    auto kern = bp3d_tma_kernel<TS, TV, G>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    dim3 block(kBPX, kBPY);
+    const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
+    dim3 grid((p.nx + kBPX - 1) / kBPX, (p.ny + kBPY - 1) / kBPY, (unsigned)(zblocks * batch));
+    kern<<<grid, block, smem, s>>>(map, (TV *)vol, p, bu, bv, be);
+    return cudaGetLastError();
+}
+
+template <typename TS, typename TV>
+cudaError_t tma_by_stage(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv, int G,
+                         cudaStream_t s)
+{
+    switch (G) {
+    case 1: return tma_launch<TS, TV, 1>(map, vol, batch, p, bu, bv, s);
+    case 2: return tma_launch<TS, TV, 2>(map, vol, batch, p, bu, bv, s);
+    case 4: return tma_launch<TS, TV, 4>(map, vol, batch, p, bu, bv, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
+template <typename TS>
+cudaError_t tma_by_vol(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv, int G,
+                       pyro_dtype vol_dt, cudaStream_t s)
+{
+    switch (vol_dt) {
+    case PYRO_F32: return tma_by_stage<TS, float>(map, vol, batch, p, bu, bv, G, s);
+    case PYRO_F16: return tma_by_stage<TS, __half>(map, vol, batch, p, bu, bv, G, s);
+    case PYRO_BF16: return tma_by_stage<TS, __nv_bfloat16>(map, vol, batch, p, bu, bv, G, s);
+    }
+    return cudaErrorInvalidValue;
+}
+
 }  // namespace
 
 cudaError_t launch_bp2d(const void *sino, void *vol, int batch, const BP2DParams &p, pyro_dtype sino_dt,
@@ -494,7 +676,8 @@ cudaError_t launch_bp2d_transpose(const void *vol, void *sino, int batch, const 
 {
     dim3 block(32, 8);
     dim3 grid((p.nx + 31) / 32, (p.ny + 7) / 8, batch);
-    bp2d_transpose_kernel<<<grid, block, 0, s>>>((const float *)vol, (float *)sino, p);
+    bp2d_transpose_kernel<<<grid, block, table_bytes(p.n_views, sizeof(BP2DAnchor)), s>>>((const float *)vol,
+                                                                                        (float *)sino, p);
     return cudaGetLastError();
 }
 
@@ -527,31 +710,27 @@ cudaError_t launch_bp3d_tex(cudaTextureObject_t tex, void *vol, const BP3DParams
     return cudaGetLastError();
 }
 
-int tma_stage_floats(int bu, int bv)
+int tma_box_elems(int bu, int bv, size_t elem)
 {
-    return (bu * bv + 31) / 32 * 32;  // stages start on 128-byte boundaries
+    const size_t per = 128 / elem;  // boxes start on 128-byte boundaries
+    return (int)(((size_t)bu * bv + per - 1) / per * per);
+}
+
+size_t bp3d_tma_smem_bytes(int n_views, int bu, int bv, size_t elem, int per_stage)
+{
+    return table_bytes(n_views, sizeof(BP3DAnchor)) +
+           (size_t)kTmaStages * per_stage * tma_box_elems(bu, bv, elem) * elem;
 }
 
 cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv,
-                            pyro_dtype vol_dt, cudaStream_t s)
+                            int per_stage, pyro_dtype sino_dt, pyro_dtype vol_dt, cudaStream_t s)
 {
-    const int sf = tma_stage_floats(bu, bv);
-    const size_t smem = (size_t)kTmaStages * sf * sizeof(float);
-    dim3 block(kBPX, kBPY);
-    const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
-    dim3 grid((p.nx + kBPX - 1) / kBPX, (p.ny + kBPY - 1) / kBPY, (unsigned)(zblocks * batch));
-    switch (vol_dt) {
-    case PYRO_F32:
-        bp3d_tma_kernel<float><<<grid, block, smem, s>>>(map, (float *)vol, p, bu, bv, sf);
-        break;
-    case PYRO_F16:
-        bp3d_tma_kernel<__half><<<grid, block, smem, s>>>(map, (__half *)vol, p, bu, bv, sf);
-        break;
-    case PYRO_BF16:
-        bp3d_tma_kernel<__nv_bfloat16><<<grid, block, smem, s>>>(map, (__nv_bfloat16 *)vol, p, bu, bv, sf);
-        break;
+    switch (sino_dt) {
+    case PYRO_F32: return tma_by_vol<float>(map, vol, batch, p, bu, bv, per_stage, vol_dt, s);
+    case PYRO_F16: return tma_by_vol<__half>(map, vol, batch, p, bu, bv, per_stage, vol_dt, s);
+    case PYRO_BF16: return tma_by_vol<__nv_bfloat16>(map, vol, batch, p, bu, bv, per_stage, vol_dt, s);
     }
-    return cudaGetLastError();
+    return cudaErrorInvalidValue;
 }
 
 cudaError_t launch_wait_timeout_probe(unsigned long long limit_ns, cudaStream_t s)
@@ -569,7 +748,8 @@ cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const 
 {
     dim3 block(kBPX, kBPY);
     dim3 grid((p.nx + kBPX - 1) / kBPX, (p.ny + kBPY - 1) / kBPY, (unsigned)(p.nz * batch));
-    bp3d_transpose_kernel<<<grid, block, 0, s>>>((const float *)vol, (float *)sino, p);
+    bp3d_transpose_kernel<<<grid, block, table_bytes(p.n_views, sizeof(BP3DAnchor)), s>>>((const float *)vol,
+                                                                                        (float *)sino, p);
     return cudaGetLastError();
 }
 

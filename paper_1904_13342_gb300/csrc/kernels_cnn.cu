@@ -55,8 +55,11 @@ __host__ __device__ inline Tile conv_tile(int W, int H)
 // one thread issues Cin / 16 tcgen05.mma (M = 128, N = Cout, K = 16) and
 // commits them to the stage's mbarrier, so the gather of tap t + 1 overlaps
 // the MMAs of tap t.  The epilogue reads the accumulator with tcgen05.ld and
-// adds the bias and the ReLU.  Waits are time-bounded; a block whose wait
-// gives up writes nothing and sets the status word.
+// adds the bias and the ReLU.  Waits are time-bounded.  A block whose wait
+// gives up stops at once (every thread leaves the tap loop together: no
+// further stage writes or MMAs), drains the last commit with another bounded
+// wait, writes nothing, sets the status word and then frees its tensor
+// memory.
 __device__ __forceinline__ uint64_t umma_desc(const void *smem, unsigned lbo, unsigned sbo)
 {
     uint64_t d = (uint64_t)((smem_addr(smem) >> 4) & 0x3FFF);
@@ -108,10 +111,15 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__
     // f32 accumulate, bf16 A and B, both K-major, N = Cout, M = 128
     constexpr unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COUT >> 3) << 17) | (8u << 24);
     bool ok = true;
+    int last = -1;  // the last tap whose MMAs were committed
     for (int tap = 0; tap < 27; ++tap) {
         const int buf = tap & 1;
-        // the MMAs of tap - 2 read this stage
-        if (tap >= 2 && !mbar_wait(&bar[buf], (unsigned)((tap - 2) >> 1) & 1u)) ok = false;
+        // the MMAs of tap - 2 read this stage; after a wait gives up the
+        // block writes no stage and issues no MMA any more
+        if (tap >= 2) {
+            if (!mbar_wait(&bar[buf], (unsigned)((tap - 2) >> 1) & 1u)) ok = false;
+            if (!__syncthreads_and(ok ? 1 : 0)) break;
+        }
         const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
         const int gz = vz + dz - 1, gy = vy + dy - 1, gx = vx + dx - 1;
         const bool in = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < Wd;
@@ -149,11 +157,13 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__
                              smem_addr(&bar[buf]))
                          : "memory");
         }
+        last = tap;
     }
-    // the last commit tracks every MMA issued before it
-    if (!mbar_wait(&bar[26 & 1], (26 >> 1) & 1u)) ok = false;
+    // the last commit tracks every MMA issued before it: drain it (bounded)
+    // before the accumulator is read or the tensor memory released
+    if (last >= 0 && !mbar_wait(&bar[last & 1], (unsigned)(last >> 1) & 1u)) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
-    const int all_ok = __syncthreads_and(ok ? 1 : 0);
+    const int all_ok = __syncthreads_and(ok && last == 26 ? 1 : 0);
     if (all_ok) {
         bf16 *out = Y + ((((size_t)b * D + vz) * H + vy) * Wd + vx) * COUT;
 #pragma unroll
@@ -205,8 +215,9 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__
 // shared-memory stages, so the gather of one chunk overlaps the MMAs of the
 // previous one; the [128 x Cout] FP32 accumulator lives in tensor memory and
 // every thread finally adds its row to dW with FP32 atomics.  Waits are
-// time-bounded; a block whose wait gives up adds nothing and sets the status
-// word.  The voxel count must be a multiple of 64.
+// time-bounded; a block whose wait gives up stops issuing (as the forward
+// kernel), drains its last commit with a bounded wait, adds nothing and sets
+// the status word.  The voxel count must be a multiple of 64.
 constexpr int kWgChunk = 64;
 
 template <int CIN, int COUT>
@@ -247,8 +258,12 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const bf16 *__rest
     int it = 0;
     for (long c = blockIdx.x; c < n_chunks; c += gridDim.x, ++it) {
         const int buf = it & 1;
-        // the MMAs of chunk it - 2 read this stage
-        if (it >= 2 && !mbar_wait(&bar[buf], (unsigned)((it - 2) >> 1) & 1u)) ok = false;
+        // the MMAs of chunk it - 2 read this stage; after a wait gives up the
+        // block writes no stage and issues no MMA any more
+        if (it >= 2) {
+            if (!mbar_wait(&bar[buf], (unsigned)((it - 2) >> 1) & 1u)) ok = false;
+            if (!__syncthreads_and(ok ? 1 : 0)) break;
+        }
         bf16 *A = sA + buf * A_EL;
         bf16 *Bs = sB + buf * B_EL;
         const long v0 = c * kWgChunk;
@@ -315,7 +330,9 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const bf16 *__rest
                          : "memory");
         }
     }
-    // the last commit tracks every MMA issued before it
+    // the last commit tracks every MMA issued before it: drain it (bounded)
+    // before the accumulator is read or the tensor memory released (after a
+    // break, `it` is the chunk that issued nothing, so it - 1 is the last commit)
     if (it > 0 && !mbar_wait(&bar[(it - 1) & 1], (unsigned)((it - 1) >> 1) & 1u)) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int all_ok = __syncthreads_and(ok ? 1 : 0);

@@ -174,7 +174,10 @@ void fill_bp2d(const Geo2D &G, int v0, int nvw, int wexp, float scale, BP2DParam
             m[4] = dy / G.sid;
             m[5] = dz / G.sid + 1.0;
         }
-        for (int a = 0; a < 6; ++a) p.m[v][a] = (float)m[a];
+        for (int a = 0; a < 6; ++a) {
+            p.m[v][a] = (float)m[a];
+            p.mlo[v][a] = (float)(m[a] - (double)p.m[v][a]);
+        }
     }
 }
 
@@ -408,7 +411,11 @@ void fill_bp3d(const Geo3D &G, int v0, int nvw, int wexp, float scale, int accum
             A[a] -= cu * A[8 + a];
             A[4 + a] -= cv * A[8 + a];
         }
-        for (int a = 0; a < 12; ++a) p.P[v][a] = (float)(A[a] * wscale);
+        for (int a = 0; a < 12; ++a) {
+            const double x = A[a] * wscale;
+            p.P[v][a] = (float)x;
+            p.Plo[v][a] = (float)(x - (double)p.P[v][a]);
+        }
         if (p.P[v][2] != 0.0f || p.P[v][10] != 0.0f) zinv = 0;
     }
     p.z_invariant = zinv;
@@ -625,8 +632,8 @@ int bp2d(bool fan, const void *sino, void *vol, int batch, const pyro_geom2d *g,
     if (batch == 0) return PYRO_OK;
     const int V = (int)G.beta.size();
     static thread_local BP2DParams p;
-    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
-        const int nvw = std::min(kMaxViews2D, V - v0);
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsBP2D) {
+        const int nvw = std::min(kMaxViewsBP2D, V - v0);
         fill_bp2d(G, v0, nvw, wexp, scale, p);
         for (int b0 = 0; b0 < batch; b0 += 65535) {
             const int nb = std::min(65535, batch - b0);
@@ -652,8 +659,8 @@ int bp2d_transpose(bool fan, const void *vol, void *sino, int batch, const pyro_
     const int V = (int)G.beta.size();
     PYRO_CUDA(cudaMemsetAsync(sino, 0, sizeof(float) * (size_t)batch * V * G.nu, as_stream(stream)));
     static thread_local BP2DParams p;
-    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
-        const int nvw = std::min(kMaxViews2D, V - v0);
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsBP2D) {
+        const int nvw = std::min(kMaxViewsBP2D, V - v0);
         fill_bp2d(G, v0, nvw, wexp, scale, p);
         for (int b0 = 0; b0 < batch; b0 += 65535) {
             const int nb = std::min(65535, batch - b0);
@@ -787,9 +794,11 @@ int fp3d_adjoint_staged(const void *sino, void *vol, int batch, const pyro_geom3
 // along a segment inside the volume d(x/w) = (dx - (x/w) dw) / w, so the
 // extent is at most (|dx| + max|x/w| |dw|) / min w, and likewise for l.  The
 // extrema of x/w, y/w and w over the volume sit at its corners (linear-
-// fractional maps with a positive depth).  False when the TMA path does not
+// fractional maps with a positive depth).  Then the views per ring stage:
+// the most (4, 2, 1) whose shared memory stays within a quarter of an SM's,
+// so that four blocks can be resident.  False when the TMA path does not
 // apply (non-circular maps, a depth <= 0, boxes too large).
-bool tma_boxes(const BP3DParams &p, int &bu, int &bv)
+bool tma_boxes(const BP3DParams &p, size_t elem, int &bu, int &bv, int &per_stage)
 {
     if (!p.z_invariant) return false;
     const double di = std::min(31, p.nx - 1), dj = std::min(7, p.ny - 1), dk = std::min(7, p.nz - 1);
@@ -811,11 +820,17 @@ bool tma_boxes(const BP3DParams &p, int &bu, int &bv)
         ext_u = std::max(ext_u, (std::fabs(P[0]) * di + std::fabs(P[1]) * dj + xr * dw) / wmin);
         ext_l = std::max(ext_l, (std::fabs(P[4]) * di + std::fabs(P[5]) * dj + std::fabs(P[6]) * dk + yr * dw) / wmin);
     }
-    if (!(ext_u < 240.0 && ext_l < 240.0)) return false;
-    // two taps, the 16-byte alignment of x (3) and rounding margins
-    bu = ((int)std::ceil(ext_u) + 7 + 3) / 4 * 4;
+    if (!(ext_u < 200.0 && ext_l < 200.0)) return false;
+    // two taps, rounding margins and the 16-byte alignment of the box's x
+    const int align = (int)(16 / elem);
+    bu = ((int)std::ceil(ext_u) + 7 + align - 1) / align * align;
     bv = (int)std::ceil(ext_l) + 4;
-    return bu <= 256 && bv <= 256 && (size_t)kBPTmaStages * tma_stage_floats(bu, bv) * sizeof(float) <= 48 * 1024;
+    if (bu > 256 || bv > 256) return false;
+    for (int g : {4, 2, 1}) {
+        per_stage = g;
+        if (bp3d_tma_smem_bytes(p.n_views, bu, bv, elem, g) <= 56 * 1024) return true;
+    }
+    return bp3d_tma_smem_bytes(p.n_views, bu, bv, elem, 1) <= 200 * 1024;
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -836,18 +851,23 @@ EncodeTiledFn encode_tiled()
     return fn;
 }
 
-// FP32 sinogram [views][nv][nu] as a 3D tensor map with bu x bv x 1 boxes;
-// reads outside it return 0
-bool sino_tensor_map(const void *sino, int views, int nv, int nu, int bu, int bv, CUtensorMap &map)
+// sinogram [views][nv][nu] (FP32, FP16 or BF16) as a 3D tensor map with
+// bu x bv x 1 boxes; reads outside it return 0.  The row pitch must be a
+// multiple of 16 bytes.
+bool sino_tensor_map(const void *sino, pyro_dtype dt, int views, int nv, int nu, int bu, int bv, CUtensorMap &map)
 {
     EncodeTiledFn fn = encode_tiled();
-    if (!fn || ((uintptr_t)sino & 15) || (nu % 4)) return false;
+    const size_t es = elem_size(dt);
+    if (!fn || ((uintptr_t)sino & 15) || ((size_t)nu * es) % 16) return false;
+    const CUtensorMapDataType type = dt == PYRO_F32   ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                     : dt == PYRO_F16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                                      : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
     const cuuint64_t dims[3] = {(cuuint64_t)nu, (cuuint64_t)nv, (cuuint64_t)views};
-    const cuuint64_t strides[2] = {(cuuint64_t)nu * 4, (cuuint64_t)nu * nv * 4};
+    const cuuint64_t strides[2] = {(cuuint64_t)nu * es, (cuuint64_t)nu * nv * es};
     const cuuint32_t box[3] = {(cuuint32_t)bu, (cuuint32_t)bv, 1};
     const cuuint32_t estr[3] = {1, 1, 1};
-    return fn(&map, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 3, const_cast<void *>(sino), dims, strides, box, estr,
-              CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+    return fn(&map, type, 3, const_cast<void *>(sino), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+              CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) == CUDA_SUCCESS;
 }
 
@@ -862,15 +882,16 @@ int bp3d_impl(const void *sino, void *vol, int batch, const Geo3D &G, int wexp, 
     for (int v0 = 0; v0 < V; v0 += kMaxViewsConeBP) {
         const int nvw = std::min(kMaxViewsConeBP, V - v0);
         fill_bp3d(G, v0, nvw, wexp, scale, v0 > 0, p);
-        int bu = 0, bv = 0;
-        const bool tma = sino_dt == PYRO_F32 && tma_boxes(p, bu, bv);
+        int bu = 0, bv = 0, per_stage = 1;
+        const bool tma = tma_boxes(p, elem_size(sino_dt), bu, bv, per_stage);
         for (int b0 = 0; b0 < batch; b0 += bstep) {
             const int nb = std::min(bstep, batch - b0);
             const char *si = (const char *)sino + b0 * V * det * elem_size(sino_dt);
             char *vo = (char *)vol + b0 * vox * elem_size(vol_dt);
             CUtensorMap map;
-            if (tma && sino_tensor_map(si, nb * V, G.nv, G.nu, bu, bv, map))
-                PYRO_CUDA(launch_bp3d_tma(map, vo, nb, p, bu, bv, vol_dt, as_stream(stream)));
+            if (tma && sino_tensor_map(si, sino_dt, nb * V, G.nv, G.nu, bu, bv, map))
+                PYRO_CUDA(
+                    launch_bp3d_tma(map, vo, nb, p, bu, bv, per_stage, sino_dt, vol_dt, as_stream(stream)));
             else
                 PYRO_CUDA(launch_bp3d(si, vo, nb, p, sino_dt, vol_dt, as_stream(stream)));
         }
@@ -1400,8 +1421,8 @@ static int fbp2d(bool fan, const void *sino, void *vol, int batch, const pyro_ge
     const double pi = 3.14159265358979323846;
     const float scale = (float)(fan ? std::fabs(G.range) / V : pi / V);
     static thread_local BP2DParams bp;
-    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
-        const int nvw = std::min(kMaxViews2D, V - v0);
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsBP2D) {
+        const int nvw = std::min(kMaxViewsBP2D, V - v0);
         fill_bp2d(G, v0, nvw, fan ? 2 : 0, scale, bp);
         for (int b0 = 0; b0 < batch; b0 += 65535) {
             const int nb = std::min(65535, batch - b0);

@@ -288,9 +288,11 @@ def test_fp_adjoint_cone_staged_large_footprint():
     ref = oracle.fpT_cone3d(f32(y), shape, spacing, P)
     assert rel(got, ref) < 1e-5
     assert rel(got, host(B.pyro_fpT_cone3d(to_dev(y), g))) < 1e-6
+    # noise data: the sample positions are absolute FP32 voxel coordinates
+    # (up to ~720 here), whose rounding noise data lifts to ~2e-5
     noise = ph.random_sinogram((views, *det), 43)
     assert rel(host(B.pyro_fpT_cone3d_ws(to_dev(noise), g)),
-               oracle.fpT_cone3d(f32(noise), shape, spacing, P)) < NOISE_TOL
+               oracle.fpT_cone3d(f32(noise), shape, spacing, P)) < 1e-4
 
 
 def test_fp_cone_staged_workspace_checks():
@@ -409,7 +411,6 @@ def test_filter_grad_K():
 
 
 # ------------------------------------------------------------- FBP/FDK ----
-NOISE_TOL = 1e-4  # filtered noise: FP32 detector-coordinate rounding, amplified by cancellation over views
 
 
 @pytest.mark.parametrize("data", ["phantom", "noise"])
@@ -431,8 +432,7 @@ def test_fdk(redund, kind, dtype, data):
     got = B.pyro_fdk(to_dev(y, dtype), cone_geom(c), kind=kind, redund=redund)
     ref = np.stack([oracle.fdk(f32(s), c["shape"], c["spacing"], c["dspacing"], ang, P, c["sid"], c["sdd"],
                                c["range"] / c["views"], kind, redund, scan_range=c["range"]) for s in y])
-    tol = TOL[dtype] if (data == "phantom" or dtype != torch.float32) else NOISE_TOL
-    assert rel(host(got), ref) < tol
+    assert rel(host(got), ref) < TOL[dtype]
 
 
 @pytest.mark.parametrize("data", ["phantom", "noise"])
@@ -460,7 +460,7 @@ def test_fbp_2d(geom, data):
         got = B.pyro_fbp_fan2d(to_dev(y), fan_geom(c), kind=B.SHEPP_LOGAN, redund=red)
         ref = [oracle.fbp_fan2d(f32(s), c["shape"], c["spacing"], c["su"], ang, c["sid"], c["sdd"],
                                 c["range"] / c["views"], B.SHEPP_LOGAN, red, scan_range=c["range"]) for s in y]
-    assert rel(host(got), np.stack(ref)) < (1e-5 if data == "phantom" else NOISE_TOL)
+    assert rel(host(got), np.stack(ref)) < 1e-5
 
 
 # ------------------------------------------------------- edge cases -------

@@ -5,8 +5,9 @@ projection and volume buffers by an acquisition pipeline, or a plug-in whose
 host application owns all device memory and forbids allocating more) cannot
 supply the workspace pyro_fdk asks for; this entry point uses the library's
 static 64 MiB scratch array instead.  The test calls it through the C ABI and
-compares it with pyro_fdk (caller workspace) on two calls in a row with
-different inputs, so a stale scratch array from the first call would show.
+compares it with pyro_fdk (caller workspace) and with the FP64 oracle's FDK
+on two calls in a row with different inputs, so a stale scratch array from
+the first call would show.
 This file sorts last so that a run stopping at the first failure has already
 run every other test.
 """
@@ -17,6 +18,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1904_13342_gb300 import binding as B
 from paper_1904_13342_gb300 import phantoms as ph
 from paper_1904_13342_gb300.geometry import ConeGeometry3D, short_scan_range
@@ -48,6 +50,14 @@ def call_noalloc(sino, g, kind, redund):
     return out
 
 
+def oracle_fdk(y, g, kind, redund):
+    ang = g.view_angles()
+    P = oracle.circular_pmats(ang, g.sid, g.sdd, g.detector_shape, g.detector_spacing)
+    return np.stack([oracle.fdk(s, g.volume_shape, g.volume_spacing, g.detector_spacing, ang, P, g.sid, g.sdd,
+                                g.angular_range / g.number_of_projections, kind, redund)
+                     for s in y.double().cpu().numpy()])
+
+
 def test_noalloc_matches_fdk_on_two_calls_in_a_row():
     g = geometry()
     for seed, kind, redund in ((1, B.SHEPP_LOGAN, B.REDUND_PARKER), (2, B.RAMLAK, B.REDUND_PARKER)):
@@ -57,6 +67,9 @@ def test_noalloc_matches_fdk_on_two_calls_in_a_row():
         ref = B.pyro_fdk(y, g, kind=kind, redund=redund)
         torch.cuda.synchronize()
         assert rel(got, ref) < TOL
+        exact = oracle_fdk(y, g, kind, redund)
+        err = np.linalg.norm(got.double().cpu().numpy() - exact) / np.linalg.norm(exact)
+        assert err < TOL
 
 
 def test_noalloc_rejects_problems_beyond_the_static_scratch():
