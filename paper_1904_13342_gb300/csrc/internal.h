@@ -102,17 +102,18 @@ struct BP3DParams {
 // every FP32 term is small and the detector coordinate keeps ~1e-6 pixel
 // where an absolute FP32 coordinate near pixel 300 carries ~2e-5.  bx, by:
 // the TMA box origin of the tile (the TMA kernel stores cu, cl relative to it).
-struct BP3DAnchor {
+// The fields a circular-trajectory (z-invariant) kernel reads come first, in
+// three 16-byte groups; w2, au2 (zero there) and the box origin follow.
+struct __align__(16) BP3DAnchor {
     int cu, cl;
     float fu, fl;
-    float wa, w0, w1, w2;
-    float au0, au1, au2;
-    int bx;
-    float al0, al1, al2;
-    int by;
+    float wa, w0, w1, al2;
+    float au0, au1, al0, al1;
+    float w2, au2;
+    int bx, by;
 };
 
-struct BP2DAnchor {
+struct __align__(16) BP2DAnchor {
     int cu;
     float fu, wa, w0, w1, a0, a1, pad;
 };
@@ -171,14 +172,18 @@ cudaError_t launch_bp3d(const void *sino, void *vol, int batch, const BP3DParams
                         pyro_dtype vol_dt, cudaStream_t s);
 cudaError_t launch_bp3d_transpose(const void *vol, void *sino, int batch, const BP3DParams &p, cudaStream_t s);
 // TMA-staged cone BP: the sinogram as a 3D tensor map [batch * views][nv][nu],
-// detector boxes of bu x bv elements (bu * element size a multiple of 16
-// bytes); each of the kBPTmaStages ring stages holds the boxes of
-// `per_stage` (1, 2 or 4) consecutive views
+// detector boxes of bu x bv elements (bu, the box width, is also the box's
+// row pitch in shared memory: 80 or 144 floats, 96 or 160 halves); each of
+// the kBPTmaStages ring stages holds the boxes of per_stage (1 or 2)
+// consecutive views; a thread owns tile_z (8 or 16) voxels along z
 constexpr int kBPTmaStages = 3;
+struct BPTmaPlan {
+    int tile_z, bu, bv, per_stage;
+};
 int tma_box_elems(int bu, int bv, size_t elem);  // one box, padded to 128 bytes
 size_t bp3d_tma_smem_bytes(int n_views, int bu, int bv, size_t elem, int per_stage);
-cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv,
-                            int per_stage, pyro_dtype sino_dt, pyro_dtype vol_dt, cudaStream_t s);
+cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, const BPTmaPlan &pl,
+                            pyro_dtype sino_dt, pyro_dtype vol_dt, cudaStream_t s);
 // address of the device word a bounded wait sets when it gives up
 cudaError_t status_word(int **ptr);
 cudaError_t launch_wait_timeout_probe(unsigned long long limit_ns, cudaStream_t s);

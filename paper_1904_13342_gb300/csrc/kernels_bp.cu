@@ -368,17 +368,17 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_tex_kernel(cudaTextureObject_
 }
 
 // ---- TMA-staged cone BP (circular-type trajectories) --------------------
-// Per view a block's 32 x 8 x ZB voxel tile projects onto a small detector
-// box.  The boxes of G consecutive views form one stage of a ring of
-// kBPTmaStages stages; threads 0..G-1 each copy one box with
-// cp.async.bulk.tensor (completion counted on the stage's mbarrier), and
-// every thread reads its four taps per voxel from shared memory.  One block
-// barrier per stage (G views) frees the stage for the copy of the stage
-// kBPTmaStages ahead.  Out-of-range parts of a box are zero-filled by the
-// copy, which is the zero extension of the detector, so no tap needs
-// masking.  Box sizes are a host-computed bound; shared-memory indices are
-// clamped to the box.  The sinogram is FP32, FP16 or BF16 (the taps are
-// converted to FP32 on load).
+// Per view a block's 32 x 8 x kTZ voxel tile (kTZ = 8 or 16 z voxels per
+// thread) projects onto a small detector box.  The boxes of G consecutive
+// views form one stage of a ring of kBPTmaStages stages; threads 0..G-1 each
+// copy one box with cp.async.bulk.tensor (completion counted on the stage's
+// mbarrier), and every thread reads its four taps per voxel from shared
+// memory.  One block barrier per stage (G views) frees the stage for the copy
+// of the stage kBPTmaStages ahead.  Out-of-range parts of a box are
+// zero-filled by the copy, which is the zero extension of the detector, so no
+// tap needs masking.  Box sizes are a host-computed bound (the host also
+// picks kTZ and G); every load stays inside its box (bp_view_box).  The
+// sinogram is FP32, FP16 or BF16 (the taps are converted to FP32 on load).
 constexpr int kTmaStages = kBPTmaStages;
 
 __device__ int g_status;  // set to 1 by a wait that gave up (read by pyro_sync_status)
@@ -410,10 +410,70 @@ __device__ __forceinline__ void mbar_arrive(uint64_t *bar)
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-template <typename TS, typename TV, int G>
-__global__ void __launch_bounds__(kBPX *kBPY) bp3d_tma_kernel(const __grid_constant__ CUtensorMap map,
+// One view of one thread's 8 voxels from a box in shared memory: the z
+// voxels go in pairs through the packed f32x2 instructions; the box row pitch
+// PITCH is a compile-time constant, so each voxel's four taps are one IMAD
+// and four loads with immediate offsets.  The thread's rows are monotone in
+// z, so checking the first and the last keeps every load inside the box; a
+// thread whose rows would leave it (the host's box bound rules this out)
+// takes the clamped scalar loop instead.
+template <typename TS, int PITCH, int kTZ>
+__device__ __forceinline__ void bp_view_box(const TS *S, int bv, const BP3DAnchor &a, float di, float dj, float dz0,
+                                            int wexp, f32x2 (&acc)[kTZ / 2])
+{
+    const float rw = 1.0f / fmaf(a.w0, di, fmaf(a.w1, dj, a.wa));
+    const float qu = fmaf(fmaf(a.au0, di, a.au1 * dj), rw, a.fu);
+    const float ql = fmaf(fmaf(a.al0, di, fmaf(a.al1, dj, a.al2 * dz0)), rw, a.fl);
+    const float om = weight_of(rw, wexp);
+    const float mu = floor_magic(qu);
+    const float au = qu - magic_to_float(mu);
+    const float w1 = om * au, w0 = om - w1;
+    const int col = a.cu + magic_to_int(mu);
+    const float dl = a.al2 * rw;
+    const float l7 = fmaf((float)(kTZ - 1), dl, ql);
+    const int r0 = a.cl + magic_to_int(floor_magic(ql)), r7 = a.cl + magic_to_int(floor_magic(l7));
+    if (col >= 0 && col + 1 < PITCH && min(r0, r7) >= 0 && max(r0, r7) + 1 < bv) {
+        // element index of voxel zz's first tap: bits(floor_magic(l_zz)) * PITCH + off (mod 2^32)
+        const unsigned off = (unsigned)(a.cl * PITCH + col) - 0x4B400000u * (unsigned)PITCH;
+        const f32x2 W0 = pk2(w0, w0), W1 = pk2(w1, w1), L = pk2(ql, ql), DL = pk2(dl, dl);
+        const f32x2 MAGIC = pk2(kFloorMagic, kFloorMagic);
+#pragma unroll
+        for (int pp = 0; pp < kTZ / 2; ++pp) {
+            const f32x2 LL = fma2(pk2((float)(2 * pp), (float)(2 * pp + 1)), DL, L);
+            const f32x2 TL = add2_rm(LL, MAGIC);
+            const f32x2 AV = sub2(LL, sub2(TL, MAGIC));
+            float t0, t1;
+            upk2(TL, t0, t1);
+            const TS *p0 = S + (__float_as_uint(t0) * (unsigned)PITCH + off);
+            const TS *p1 = S + (__float_as_uint(t1) * (unsigned)PITCH + off);
+            const f32x2 A = pk2(lds(p0), lds(p1)), B = pk2(lds(p0 + 1), lds(p1 + 1));
+            const f32x2 C = pk2(lds(p0 + PITCH), lds(p1 + PITCH)), D = pk2(lds(p0 + PITCH + 1), lds(p1 + PITCH + 1));
+            const f32x2 T0 = fma2(W0, A, mul2(W1, B)), T1 = fma2(W0, C, mul2(W1, D));
+            acc[pp] = add2(acc[pp], fma2(AV, sub2(T1, T0), T0));
+        }
+        return;
+    }
+    const int last = PITCH * bv - PITCH - 2;
+#pragma unroll
+    for (int zz = 0; zz < kTZ; ++zz) {
+        const float ll = fmaf((float)zz, dl, ql);
+        const float tl = floor_magic(ll);
+        const float av = ll - magic_to_float(tl);
+        const int e = min(max((a.cl + magic_to_int(tl)) * PITCH + col, 0), last);
+        const float s0 = fmaf(w0, lds(S + e), w1 * lds(S + e + 1));
+        const float s1 = fmaf(w0, lds(S + e + PITCH), w1 * lds(S + e + PITCH + 1));
+        float x, y;
+        upk2(acc[zz / 2], x, y);
+        if (zz & 1) y += lerpf(s0, s1, av);
+        else x += lerpf(s0, s1, av);
+        acc[zz / 2] = pk2(x, y);
+    }
+}
+
+template <typename TS, typename TV, int G, int PITCH, int kTZ>
+__global__ void __launch_bounds__(kBPX *kBPY, 4) bp3d_tma_kernel(const __grid_constant__ CUtensorMap map,
                                                               TV *__restrict__ vol,
-                                                              const __grid_constant__ BP3DParams p, int bu, int bv,
+                                                              const __grid_constant__ BP3DParams p, int bv,
                                                               int box_elems)
 {
     extern __shared__ __align__(128) unsigned char tma_smem[];
@@ -426,14 +486,14 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_tma_kernel(const __grid_const
     const int i0 = blockIdx.x * kBPX, j0 = blockIdx.y * kBPY;
     const int i = i0 + (warp & 3) * 8 + (lane & 7);
     const int j = j0 + (warp >> 2) * 4 + (lane >> 3);
-    const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
+    const int zblocks = (p.nz + kTZ - 1) / kTZ;
     const int b = blockIdx.z / zblocks;
-    const int z0 = (blockIdx.z % zblocks) * kBPZ;
-    const int i1 = min(i0 + kBPX - 1, p.nx - 1), j1 = min(j0 + kBPY - 1, p.ny - 1), z1 = min(z0 + kBPZ - 1, p.nz - 1);
-    const float ia = i0 + 15.5f, ja = j0 + 3.5f, za = z0 + 3.5f;
+    const int z0 = (blockIdx.z % zblocks) * kTZ;
+    const int i1 = min(i0 + kBPX - 1, p.nx - 1), j1 = min(j0 + kBPY - 1, p.ny - 1), z1 = min(z0 + kTZ - 1, p.nz - 1);
+    const float ia = i0 + 15.5f, ja = j0 + 3.5f, za = z0 + 0.5f * (kTZ - 1);
     const int vbase = b * p.views_total + p.view0;
     const bool active = i < p.nx && j < p.ny;  // the others still take part in the barriers
-    const unsigned box_bytes = (unsigned)(bu * bv * sizeof(TS));
+    const unsigned box_bytes = (unsigned)(PITCH * bv * sizeof(TS));
     constexpr int align = 16 / (int)sizeof(TS);  // x of a tensor copy: a multiple of 16 bytes
     for (int v = t; v < p.n_views; v += kBPX * kBPY) {
         BP3DAnchor a = bp3d_anchor(p, v, ia, ja, za);
@@ -463,11 +523,10 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_tma_kernel(const __grid_const
     if (t < G)
         for (int s = 0; s < min(kTmaStages, n_st); ++s) issue(s);
 
-    float acc[kBPZ];
+    f32x2 acc[kTZ / 2];
 #pragma unroll
-    for (int zz = 0; zz < kBPZ; ++zz) acc[zz] = 0.0f;
+    for (int pp = 0; pp < kTZ / 2; ++pp) acc[pp] = pk2(0.0f, 0.0f);
     const float di = (float)i - ia, dj = (float)j - ja, dz0 = (float)z0 - za;
-    const int last = box_elems - bu - 2;  // highest first tap index of a 2 x 2 patch
     int s = 0;
     for (; s < n_st; ++s) {
         const int slot = s % kTmaStages;
@@ -477,25 +536,7 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_tma_kernel(const __grid_const
             for (int g = 0; g < G; ++g) {
                 const int v = s * G + g;
                 if (v >= p.n_views) break;  // block-uniform
-                const BP3DAnchor a = tab[v];
-                const TS *S = stages + (slot * G + g) * box_elems;
-                const DetPos q = det_pos(a, di, dj, dz0);
-                const float om = weight_of(q.rw, p.wexp);
-                const float mu = floor_magic(q.u);
-                const float au = q.u - magic_to_float(mu);
-                const float w1 = om * au, w0 = om - w1;
-                const int col = a.cu + magic_to_int(mu);
-                const float dl = a.al2 * q.rw;
-#pragma unroll
-                for (int zz = 0; zz < kBPZ; ++zz) {
-                    const float ll = fmaf((float)zz, dl, q.l);
-                    const float tl = floor_magic(ll);
-                    const float av = ll - magic_to_float(tl);
-                    const int e = min(max((a.cl + magic_to_int(tl)) * bu + col, 0), last);
-                    const float t0 = fmaf(w0, lds(S + e), w1 * lds(S + e + 1));
-                    const float t1 = fmaf(w0, lds(S + e + bu), w1 * lds(S + e + bu + 1));
-                    acc[zz] += lerpf(t0, t1, av);
-                }
+                bp_view_box<TS, PITCH, kTZ>(stages + (slot * G + g) * box_elems, bv, tab[v], di, dj, dz0, p.wexp, acc);
             }
         }
         __syncthreads();  // stage `slot` is free again; gave_up is visible
@@ -515,10 +556,12 @@ __global__ void __launch_bounds__(kBPX *kBPY) bp3d_tma_kernel(const __grid_const
     const size_t sxy = (size_t)p.nx * p.ny;
     TV *out = vol + (size_t)b * sxy * p.nz + (size_t)j * p.nx + i;
 #pragma unroll
-    for (int zz = 0; zz < kBPZ; ++zz) {
+    for (int zz = 0; zz < kTZ; ++zz) {
         const int z = z0 + zz;
+        float x, y;
+        upk2(acc[zz / 2], x, y);
         if (z < p.nz) {
-            float r = p.scale * acc[zz];
+            float r = p.scale * ((zz & 1) ? y : x);
             if (p.accumulate) r += to_float<TV>(out[z * sxy]);
             out[z * sxy] = to_storage<TV>(r);
         }
@@ -619,43 +662,43 @@ cudaError_t bp3d_by_vol(const void *sino, void *vol, int batch, const BP3DParams
     return cudaErrorInvalidValue;
 }
 
-template <typename TS, typename TV, int G>
-cudaError_t tma_launch(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv,
-                       cudaStream_t s)
+template <typename TS, typename TV, int G, int PITCH, int kTZ>
+cudaError_t tma_launch(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bv, cudaStream_t s)
 {
-    const int be = tma_box_elems(bu, bv, sizeof(TS));
-    const size_t smem = bp3d_tma_smem_bytes(p.n_views, bu, bv, sizeof(TS), G);
-    auto kern = bp3d_tma_kernel<TS, TV, G>;
+    const int be = tma_box_elems(PITCH, bv, sizeof(TS));
+    const size_t smem = bp3d_tma_smem_bytes(p.n_views, PITCH, bv, sizeof(TS), G);
+    auto kern = bp3d_tma_kernel<TS, TV, G, PITCH, kTZ>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     dim3 block(kBPX, kBPY);
-    const int zblocks = (p.nz + kBPZ - 1) / kBPZ;
+    const int zblocks = (p.nz + kTZ - 1) / kTZ;
     dim3 grid((p.nx + kBPX - 1) / kBPX, (p.ny + kBPY - 1) / kBPY, (unsigned)(zblocks * batch));
-    kern<<<grid, block, smem, s>>>(map, (TV *)vol, p, bu, bv, be);
+    kern<<<grid, block, smem, s>>>(map, (TV *)vol, p, bv, be);
     return cudaGetLastError();
 }
 
-template <typename TS, typename TV>
-cudaError_t tma_by_stage(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv, int G,
+template <typename TS, typename TV, int PITCH>
+cudaError_t tma_by_stage(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, const BPTmaPlan &pl,
                          cudaStream_t s)
 {
-    switch (G) {
-    case 1: return tma_launch<TS, TV, 1>(map, vol, batch, p, bu, bv, s);
-    case 2: return tma_launch<TS, TV, 2>(map, vol, batch, p, bu, bv, s);
-    case 4: return tma_launch<TS, TV, 4>(map, vol, batch, p, bu, bv, s);
-    }
+    if (pl.per_stage == 1 && pl.tile_z == 16) return tma_launch<TS, TV, 1, PITCH, 16>(map, vol, batch, p, pl.bv, s);
+    if (pl.per_stage == 2 && pl.tile_z == 16) return tma_launch<TS, TV, 2, PITCH, 16>(map, vol, batch, p, pl.bv, s);
+    if (pl.per_stage == 1 && pl.tile_z == 8) return tma_launch<TS, TV, 1, PITCH, 8>(map, vol, batch, p, pl.bv, s);
+    if (pl.per_stage == 2 && pl.tile_z == 8) return tma_launch<TS, TV, 2, PITCH, 8>(map, vol, batch, p, pl.bv, s);
     return cudaErrorInvalidValue;
 }
 
-template <typename TS>
-cudaError_t tma_by_vol(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv, int G,
-                       pyro_dtype vol_dt, cudaStream_t s)
+// bu: the box width, which is also the row pitch of a box in shared memory:
+// 16 words modulo the 32 banks (80 or 144 floats, 96 or 160 halves), so that
+// the taps of one column in adjacent rows, which a warp's lanes often read
+// together, fall 16 banks apart
+template <typename TS, typename TV>
+cudaError_t tma_by_pitch(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, const BPTmaPlan &pl,
+                         cudaStream_t s)
 {
-    switch (vol_dt) {
-    case PYRO_F32: return tma_by_stage<TS, float>(map, vol, batch, p, bu, bv, G, s);
-    case PYRO_F16: return tma_by_stage<TS, __half>(map, vol, batch, p, bu, bv, G, s);
-    case PYRO_BF16: return tma_by_stage<TS, __nv_bfloat16>(map, vol, batch, p, bu, bv, G, s);
-    }
+    constexpr int P0 = sizeof(TS) == 4 ? 80 : 96, P1 = sizeof(TS) == 4 ? 144 : 160;
+    if (pl.bu == P0) return tma_by_stage<TS, TV, P0>(map, vol, batch, p, pl, s);
+    if (pl.bu == P1) return tma_by_stage<TS, TV, P1>(map, vol, batch, p, pl, s);
     return cudaErrorInvalidValue;
 }
 
@@ -722,14 +765,21 @@ size_t bp3d_tma_smem_bytes(int n_views, int bu, int bv, size_t elem, int per_sta
            (size_t)kTmaStages * per_stage * tma_box_elems(bu, bv, elem) * elem;
 }
 
-cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, int bu, int bv,
-                            int per_stage, pyro_dtype sino_dt, pyro_dtype vol_dt, cudaStream_t s)
+// the sinogram's type and the volume's: FP32 into any storage type (FDK
+// reads its FP32 workspace), FP16 and BF16 into their own type
+cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, const BPTmaPlan &pl,
+                            pyro_dtype sino_dt, pyro_dtype vol_dt, cudaStream_t s)
 {
-    switch (sino_dt) {
-    case PYRO_F32: return tma_by_vol<float>(map, vol, batch, p, bu, bv, per_stage, vol_dt, s);
-    case PYRO_F16: return tma_by_vol<__half>(map, vol, batch, p, bu, bv, per_stage, vol_dt, s);
-    case PYRO_BF16: return tma_by_vol<__nv_bfloat16>(map, vol, batch, p, bu, bv, per_stage, vol_dt, s);
+    if (sino_dt == PYRO_F32) {
+        switch (vol_dt) {
+        case PYRO_F32: return tma_by_pitch<float, float>(map, vol, batch, p, pl, s);
+        case PYRO_F16: return tma_by_pitch<float, __half>(map, vol, batch, p, pl, s);
+        case PYRO_BF16: return tma_by_pitch<float, __nv_bfloat16>(map, vol, batch, p, pl, s);
+        }
     }
+    if (sino_dt == PYRO_F16 && vol_dt == PYRO_F16) return tma_by_pitch<__half, __half>(map, vol, batch, p, pl, s);
+    if (sino_dt == PYRO_BF16 && vol_dt == PYRO_BF16)
+        return tma_by_pitch<__nv_bfloat16, __nv_bfloat16>(map, vol, batch, p, pl, s);
     return cudaErrorInvalidValue;
 }
 

@@ -788,20 +788,16 @@ int fp3d_adjoint_staged(const void *sino, void *vol, int batch, const pyro_geom3
     return PYRO_OK;
 }
 
-// Detector boxes of the TMA-staged BP: a bound, over every 32 x 8 x 8 voxel
+// Detector boxes of the TMA-staged BP: a bound, over every 32 x 8 x tz voxel
 // tile and view of the chunk, on the extent of the tile's taps.  With the
 // centred, SID-scaled map of fill_bp3d, u - cu = x / w and l - cv = y / w;
 // along a segment inside the volume d(x/w) = (dx - (x/w) dw) / w, so the
 // extent is at most (|dx| + max|x/w| |dw|) / min w, and likewise for l.  The
 // extrema of x/w, y/w and w over the volume sit at its corners (linear-
-// fractional maps with a positive depth).  Then the views per ring stage:
-// the most (4, 2, 1) whose shared memory stays within a quarter of an SM's,
-// so that four blocks can be resident.  False when the TMA path does not
-// apply (non-circular maps, a depth <= 0, boxes too large).
-bool tma_boxes(const BP3DParams &p, size_t elem, int &bu, int &bv, int &per_stage)
+// fractional maps with a positive depth).  False when the boxes do not fit.
+bool tma_box_size(const BP3DParams &p, size_t elem, int tz, int &bu, int &bv)
 {
-    if (!p.z_invariant) return false;
-    const double di = std::min(31, p.nx - 1), dj = std::min(7, p.ny - 1), dk = std::min(7, p.nz - 1);
+    const double di = std::min(31, p.nx - 1), dj = std::min(7, p.ny - 1), dk = std::min(tz - 1, p.nz - 1);
     double ext_u = 0.0, ext_l = 0.0;
     for (int v = 0; v < p.n_views; ++v) {
         const float *P = p.P[v];
@@ -821,16 +817,48 @@ bool tma_boxes(const BP3DParams &p, size_t elem, int &bu, int &bv, int &per_stag
         ext_l = std::max(ext_l, (std::fabs(P[4]) * di + std::fabs(P[5]) * dj + std::fabs(P[6]) * dk + yr * dw) / wmin);
     }
     if (!(ext_u < 200.0 && ext_l < 200.0)) return false;
-    // two taps, rounding margins and the 16-byte alignment of the box's x
+    // two taps, rounding margins and the 16-byte alignment of the box's x;
+    // the box width is also the kernel's compile-time row pitch, 16 words
+    // modulo the shared-memory banks: 80 or 144 floats, 96 or 160 halves
     const int align = (int)(16 / elem);
-    bu = ((int)std::ceil(ext_u) + 7 + align - 1) / align * align;
+    const int need = ((int)std::ceil(ext_u) + 7 + align - 1) / align * align;
+    const int p0 = elem == 4 ? 80 : 96, p1 = elem == 4 ? 144 : 160;
+    bu = need <= p0 ? p0 : (need <= p1 ? p1 : 0);
     bv = (int)std::ceil(ext_l) + 4;
-    if (bu > 256 || bv > 256) return false;
-    for (int g : {4, 2, 1}) {
-        per_stage = g;
-        if (bp3d_tma_smem_bytes(p.n_views, bu, bv, elem, g) <= 56 * 1024) return true;
+    return bu != 0 && bv <= 256;
+}
+
+// The TMA BP's tile depth and views per stage: four resident blocks (shared
+// memory within a quarter of an SM's) first, then the deeper tile (half the
+// per-view set-up per voxel), then two views per stage; if no plan fits four
+// blocks, the one with the least shared memory.  Measured on the 256^3
+// workload: 16-deep tiles with one view per stage 3.31 ms, 8-deep with two
+// 4.37 ms, 8-deep with one 4.94 ms.  False when the TMA path does not apply
+// (non-circular maps, a depth <= 0, boxes too large).
+bool tma_plan(const BP3DParams &p, size_t elem, BPTmaPlan &pl)
+{
+    if (!p.z_invariant) return false;
+    bool found = false;
+    BPTmaPlan best{};
+    size_t best_smem = 0;
+    for (int tz : {16, 8}) {
+        int bu = 0, bv = 0;
+        if (!tma_box_size(p, elem, tz, bu, bv)) continue;
+        for (int g : {2, 1}) {
+            const size_t smem = bp3d_tma_smem_bytes(p.n_views, bu, bv, elem, g);
+            if (smem <= 56 * 1024) {
+                pl = {tz, bu, bv, g};
+                return true;
+            }
+            if (!found || smem < best_smem) {
+                best = {tz, bu, bv, g};
+                best_smem = smem;
+                found = true;
+            }
+        }
     }
-    return bp3d_tma_smem_bytes(p.n_views, bu, bv, elem, 1) <= 200 * 1024;
+    pl = best;
+    return found && best_smem <= 200 * 1024;
 }
 
 using EncodeTiledFn = CUresult (*)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
@@ -877,21 +905,20 @@ int bp3d_impl(const void *sino, void *vol, int batch, const Geo3D &G, int wexp, 
     const int V = (int)G.beta.size();
     const size_t vox = (size_t)G.nx * G.ny * G.nz, det = (size_t)G.nu * G.nv;
     static thread_local BP3DParams p;
-    const int zblocks = (G.nz + 7) / 8;
+    const int zblocks = (G.nz + 7) / 8;  // the most z blocks of any BP kernel
     const int bstep = std::max(1, 65535 / zblocks);
     for (int v0 = 0; v0 < V; v0 += kMaxViewsConeBP) {
         const int nvw = std::min(kMaxViewsConeBP, V - v0);
         fill_bp3d(G, v0, nvw, wexp, scale, v0 > 0, p);
-        int bu = 0, bv = 0, per_stage = 1;
-        const bool tma = tma_boxes(p, elem_size(sino_dt), bu, bv, per_stage);
+        BPTmaPlan plan{};
+        const bool tma = (sino_dt == PYRO_F32 || sino_dt == vol_dt) && tma_plan(p, elem_size(sino_dt), plan);
         for (int b0 = 0; b0 < batch; b0 += bstep) {
             const int nb = std::min(bstep, batch - b0);
             const char *si = (const char *)sino + b0 * V * det * elem_size(sino_dt);
             char *vo = (char *)vol + b0 * vox * elem_size(vol_dt);
             CUtensorMap map;
-            if (tma && sino_tensor_map(si, sino_dt, nb * V, G.nv, G.nu, bu, bv, map))
-                PYRO_CUDA(
-                    launch_bp3d_tma(map, vo, nb, p, bu, bv, per_stage, sino_dt, vol_dt, as_stream(stream)));
+            if (tma && sino_tensor_map(si, sino_dt, nb * V, G.nv, G.nu, plan.bu, plan.bv, map))
+                PYRO_CUDA(launch_bp3d_tma(map, vo, nb, p, plan, sino_dt, vol_dt, as_stream(stream)));
             else
                 PYRO_CUDA(launch_bp3d(si, vo, nb, p, sino_dt, vol_dt, as_stream(stream)));
         }

@@ -523,6 +523,37 @@ def test_bp_cone_tma_staged(weight):
     B.pyro_sync_status()
 
 
+@pytest.mark.parametrize("dtype", [torch.float16, torch.bfloat16])
+def test_bp_cone_tma_staged_half(dtype):
+    """A 16-bit sinogram whose rows are a multiple of 16 bytes (48 columns)
+    is staged by tensor copies of 16-bit boxes; the volume is written in the
+    same type.  Against the oracle fed the FP32 input (end to end)."""
+    c = dict(CONE, det=(30, 48), dspacing=(1.2, 1.0), views=90)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang)
+    y = ph.random_sinogram((2, c["views"], *c["det"]), 53, smooth=2)
+    got = B.pyro_bp_cone3d(to_dev(y, dtype), cone_geom(c), weight=2, scale=0.3)
+    assert got.dtype == dtype
+    ref = np.stack([oracle.bp_cone3d(f32(s), c["shape"], c["spacing"], P, c["sid"], 2, 0.3) for s in y])
+    assert rel(host(got), ref) < TOL[dtype]
+    B.pyro_sync_status()
+
+
+def test_bp_cone_tma_staged_fine_rows():
+    """Fine detector rows (0.25 mm, about 7 rows per 1 mm voxel): a 16-deep
+    tile needs 129-row boxes (a 128 KB ring), an 8-deep one 68-row boxes
+    (69 KB); no plan fits four blocks per SM, so the host takes the smaller,
+    the 8-deep tile with one view per stage."""
+    c = dict(CONE, det=(130, 44), dspacing=(0.25, 1.0), views=60)
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang)
+    y = ph.random_sinogram((1, c["views"], *c["det"]), 54, smooth=2)
+    got = B.pyro_bp_cone3d(to_dev(y), cone_geom(c), weight=2, scale=0.3)
+    ref = oracle.bp_cone3d(f32(y[0]), c["shape"], c["spacing"], P, c["sid"], 2, 0.3)
+    assert rel(host(got[0]), ref) < 1e-5
+    B.pyro_sync_status()
+
+
 def test_sync_status_reports_a_clean_stream():
     B.pyro_fp_cone3d(to_dev(ph.random_volume(CONE["shape"], 50)), cone_geom(CONE))
     B.pyro_sync_status()  # raises PyroError if the stream faulted
