@@ -193,7 +193,8 @@ PYRO_API int pyro_cone_projection_matrices(const pyro_geom3d *g, double *out);
 /* --- The same cone-beam forward projection, computed from a copy of the
  * volume re-laid out z-fastest in `workspace` (device, at least
  * pyro_fp_cone3d_workspace_bytes bytes, i.e. one volume of `dtype` padded
- * by one voxel on every face; PYRO_EWORKSPACE otherwise).  This is the memory-for-speed trade the paper
+ * by two voxels before and after the data in x and y and one in z;
+ * PYRO_EWORKSPACE otherwise).  This is the memory-for-speed trade the paper
  * describes for its texture mode (the volume is held twice, Section "The
  * Operator as a Layer"); pyro_fp_cone3d is the memory-lean mode.  Results
  * are identical up to FP32 summation order; the workspace is scratch. */

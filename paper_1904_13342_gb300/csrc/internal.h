@@ -16,29 +16,37 @@ namespace pyro {
 
 // Kernel-parameter space is 32764 bytes; these caps keep every parameter
 // pack below it.  Longer trajectories are processed in chunks of views.
-constexpr int kMaxViews2D = 1024;    // 2D FP: 2 floats per view
+constexpr int kMaxViews2D = 1024;    // 2D weights: views of one beta table
 constexpr int kMaxViewsBP2D = 512;   // 2D BP: 12 floats per view (map as hi/lo pairs)
 constexpr int kMaxViewsConeBP = 300; // cone BP: 24 floats per view (map as hi/lo pairs)
-constexpr int kMaxViewsConeFP = 400; // cone FP: 17 floats per view
+constexpr int kMaxViewsConeFP = 200; // cone FP: 34 floats per view (hi/lo pairs)
 constexpr int kMaxPadLength = 8192;  // filter: pn <= 8192, so nu <= 4096
 
 // ---------------------------------------------------------------- FP 2D --
-// Ray of bin k in view j, in millimetres: parallel beam a = u e_u, d = c;
-// fan beam written around the closest approach B to the iso-centre,
-// B = SID u / L^2 (SDD e_u - u c), d = (SDD c + u e_u) / L, L^2 = SDD^2+u^2,
-// which avoids the cancellation of S - (S.d) d in FP32.
+// Ray of bin k in view j: sample m at p(k) + m q(k) in pixel-index units,
+// with p and q affine in k; parallel beam a = u e_u, g = c; fan beam
+// a = (SID u / SDD) e_u (the sample on the iso-centre's depth plane),
+// g = c + (u / SDD) e_u.  The host evaluates the affine coefficients in FP64
+// and passes them as FP32 pairs (hi + lo); the kernels anchor the sample
+// positions every kFPSegment samples in float-float (see FP3DParams).
+constexpr int kMaxViewsFP2D = 384;   // 2D FP: 18 floats per view
+struct FP2DLine {
+    float p0x, pkx, p0y, pky;  // p(k) = p0 + k pk
+    float q0x, qkx, q0y, qky;  // q(k) = q0 + k qk
+};
+
 struct FP2DParams {
     int nx, ny, nu, n_views;   // n_views in this chunk
     int view0;                 // first view of this chunk (sinogram offset)
     int views_total;           // views in the full sinogram
     int fan;
     int M;                     // samples m = -M..M around the closest approach
-    float inv_sx, inv_sy;      // 1 / spacing
-    float cx, cy;              // (n-1)/2
     float su, cu;              // bin spacing, (nu-1)/2
-    float sid, sdd;
+    float sdd;
     float dt;
-    float2 dir[kMaxViews2D];   // central-ray vector c_j = (cos b_j, sin b_j)
+    float2 dir[kMaxViewsFP2D];    // central-ray vector c_j = (cos b_j, sin b_j)
+    FP2DLine ln[kMaxViewsFP2D];   // the rays' affine maps, FP32
+    FP2DLine lnlo[kMaxViewsFP2D]; // FP64 maps - ln
 };
 
 // ---------------------------------------------------------------- FP 3D --
@@ -55,6 +63,21 @@ struct ConeFPView {
     float s1, s2, s3;          // source in camera coordinates
 };
 
+// The FP64 set-up travels as FP32 pairs (v + vlo, dt + dt_lo): the kernels
+// evaluate each ray's sample positions in float-float arithmetic every
+// kFPSegment depth planes (an integer cell plus an FP32 fraction per axis) and
+// step in FP32 from there, so a sample position near voxel index 500 keeps
+// ~1e-6 voxel where an absolute FP32 index carries ~3e-5.
+constexpr int kFPSegment = 64;
+// The column kernels' padded z-major copy of the volume: [ny + 2 P][nx + 2 P]
+// [nz + 2], P = kFPPadXY zero voxels before and after the data in x and y
+// and one in z.  Two in x and y keep the taps inside the copy when an
+// anchored sample lands one cell beyond the FP32 range test that chose it.
+constexpr int kFPPadXY = 2;
+inline size_t fp_padded_elems(int nx, int ny, int nz)
+{
+    return (size_t)(nx + 2 * kFPPadXY) * (ny + 2 * kFPPadXY) * (nz + 2);
+}
 struct FP3DParams {
     int nx, ny, nz, nu, nv, n_views, view0, views_total;
     int column_shared;         // every view: rows of a detector column share (x, y) (see fill_fp3d)
@@ -62,8 +85,9 @@ struct FP3DParams {
     int pair_rows;             // > 0: rows per window of the two-rays-per-lane column kernels (33..64)
     int M;
     float cx, cy, cz;          // (n-1)/2 per axis
-    float dt;
+    float dt, dt_lo;
     ConeFPView v[kMaxViewsConeFP];
+    ConeFPView vlo[kMaxViewsConeFP];  // FP64 set-up - v
 };
 
 // ------------------------------------------------------------- BP 2D/3D --

@@ -12,6 +12,15 @@
 // their (x, y) point: the warps below put consecutive detector rows on
 // consecutive lanes.  Arithmetic and accumulation are FP32; storage is FP32,
 // FP16 or BF16.
+//
+// Sample positions.  A sample's voxel-index coordinate is p + m q per axis;
+// written as one FP32 number it carries half an ulp of its size (~3e-5 voxel
+// near index 500), which noise data turns into ~2e-5 relative error.  So p
+// and q are evaluated in float-float arithmetic from the host's FP64 set-up
+// (passed as hi/lo pairs), and every kFPSegment samples the position is
+// re-anchored: an integer cell plus an FP32 fraction per axis (a Seg); the
+// samples of the segment step in FP32 from the fraction, so their
+// coordinates stay within ~1e-6 voxel of the exact ones.
 #include "device_common.cuh"
 #include "internal.h"
 
@@ -19,49 +28,139 @@ namespace pyro {
 
 namespace {
 
-// ---- 2D ray set-up: sample position p0 + m q in pixel-index units --------
-struct Ray2 {
-    float px, py, qx, qy, w;  // sample m at (px + m qx, py + m qy); weight w = dt |g|
+__device__ __forceinline__ ff ff_mul(ff a, ff b)
+{
+    const float p = __fmul_rn(a.h, b.h);
+    float e = __fmaf_rn(a.h, b.h, -p);
+    e = __fmaf_rn(a.h, b.l, e);
+    e = __fmaf_rn(a.l, b.h, e);
+    return fast_two_sum(p, e);
+}
+
+__device__ __forceinline__ ff ff_neg(ff a)
+{
+    return {-a.h, -a.l};
+}
+
+// one axis of a ray's samples near segment start ms: the coordinate of
+// sample m is i + f + (m - ms) q, i an integer, f in [0, 1)
+struct Seg {
+    int i;
+    float f, q;
 };
 
-// parallel beam: a = u e_u, g = c, w0 = 0; fan beam: g = c + (u / SDD) e_u and
-// the sample on the iso-centre's depth plane is a + SID g = (SID u / SDD) e_u
-__device__ __forceinline__ Ray2 ray2d(const FP2DParams &p, int v, int k)
+__device__ __forceinline__ Seg seg_at(ff p, ff q, int ms)
 {
-    const float2 c = p.dir[v];
-    const float u = ((float)k - p.cu) * p.su;
-    float bx, by, gx, gy, w;
-    if (p.fan) {
-        const float t = u / p.sdd;
-        const float f = p.sid * t;
-        bx = -f * c.y;  // e_u = (-c.y, c.x)
-        by = f * c.x;
-        gx = fmaf(-t, c.y, c.x);
-        gy = fmaf(t, c.x, c.y);
-        w = p.dt * sqrtf(fmaf(t, t, 1.0f));
-    } else {
-        bx = -u * c.y;
-        by = u * c.x;
-        gx = c.x;
-        gy = c.y;
-        w = p.dt;
-    }
-    Ray2 r;
-    r.px = fmaf(bx, p.inv_sx, p.cx);
-    r.py = fmaf(by, p.inv_sy, p.cy);
-    r.qx = gx * p.dt * p.inv_sx;
-    r.qy = gy * p.dt * p.inv_sy;
-    r.w = w;
+    Seg s;
+    ff_split(ff_add(p, ff_mul_f(q, (float)ms)), 0.0f, s.i, s.f);
+    s.q = q.h;
+    return s;
+}
+
+// cell and fraction of sample ms + dm on one axis
+struct Tap {
+    int i;
+    float a;
+};
+
+__device__ __forceinline__ Tap seg_tap(const Seg &s, float dm)
+{
+    const float x = fmaf(dm, s.q, s.f);
+    const float t = floor_magic(x);
+    return {s.i + magic_to_int(t), x - magic_to_float(t)};
+}
+
+// zero-extended linear interpolation weights of a tap on an axis of n cells:
+// taps i (weight 1 - a) and i + 1 (weight a), a weight zeroed outside, the
+// indices clamped for addressing
+__device__ __forceinline__ Axis tap_axis(Tap t, int n)
+{
+    Axis r;
+    r.w0 = ((unsigned)t.i < (unsigned)n) ? 1.0f - t.a : 0.0f;
+    r.w1 = ((unsigned)(t.i + 1) < (unsigned)n) ? t.a : 0.0f;
+    r.i0 = min(max(t.i, 0), n - 1);
+    r.i1 = min(max(t.i + 1, 0), n - 1);
     return r;
 }
 
-__device__ __forceinline__ void range2d(const Ray2 &r, const FP2DParams &p, int &m0, int &m1)
+// ---- 2D rays: sample m at p + m q in pixel-index units (float-float) ----
+struct Ray2 {
+    ff px, py, qx, qy;
+    float w;  // dt |g|
+};
+
+__device__ __forceinline__ Ray2 ray2d(const FP2DParams &p, int v, int k)
+{
+    const FP2DLine &H = p.ln[v], &L = p.lnlo[v];
+    const float fk = (float)k;
+    Ray2 r;
+    r.px = ff_add({H.p0x, L.p0x}, ff_mul_f({H.pkx, L.pkx}, fk));
+    r.py = ff_add({H.p0y, L.p0y}, ff_mul_f({H.pky, L.pky}, fk));
+    r.qx = ff_add({H.q0x, L.q0x}, ff_mul_f({H.qkx, L.qkx}, fk));
+    r.qy = ff_add({H.q0y, L.q0y}, ff_mul_f({H.qky, L.qky}, fk));
+    if (p.fan) {
+        const float t = ((float)k - p.cu) * p.su / p.sdd;
+        r.w = p.dt * sqrtf(fmaf(t, t, 1.0f));
+    } else {
+        r.w = p.dt;
+    }
+    return r;
+}
+
+__device__ __forceinline__ void range2d(const Ray2 &r, const FP2DParams &p, int nx, int ny, int &m0, int &m1)
 {
     float lo = -(float)p.M, hi = (float)p.M;
-    clip_axis(r.px, r.qx, p.nx, lo, hi);
-    clip_axis(r.py, r.qy, p.ny, lo, hi);
+    clip_axis(r.px.h, r.qx.h, nx, lo, hi);
+    clip_axis(r.py.h, r.qy.h, ny, lo, hi);
     m0 = max(-p.M, (int)floorf(lo));
     m1 = min(p.M, (int)ceilf(hi));
+}
+
+// the views whose rays run closer to x than to y read (or scatter into) the
+// transposed image: swap the roles of x and y
+__device__ __forceinline__ void swap_xy(Ray2 &r)
+{
+    const ff t0 = r.px, t1 = r.qx;
+    r.px = r.py;
+    r.qx = r.qy;
+    r.py = t0;
+    r.qy = t1;
+}
+
+template <typename T>
+__device__ __forceinline__ float bilerp_taps_zero(const T *img, int nx, int ny, Tap tx, Tap ty)
+{
+    const Axis ax = tap_axis(tx, nx), ay = tap_axis(ty, ny);
+    const T *r0 = img + (size_t)ay.i0 * nx;
+    const T *r1 = img + (size_t)ay.i1 * nx;
+    const float v0 = ax.w0 * ld(r0 + ax.i0) + ax.w1 * ld(r0 + ax.i1);
+    const float v1 = ax.w0 * ld(r1 + ax.i0) + ax.w1 * ld(r1 + ax.i1);
+    return ay.w0 * v0 + ay.w1 * v1;
+}
+
+// all four taps inside the image (0 <= i < n - 1 on both axes)
+template <typename T>
+__device__ __forceinline__ float bilerp_taps_interior(const T *img, int nx, Tap tx, Tap ty)
+{
+    const T *b = img + (tx.i + ty.i * nx);
+    return lerpf(lerpf(ld(b), ld(b + 1), tx.a), lerpf(ld(b + nx), ld(b + nx + 1), tx.a), ty.a);
+}
+
+// samples m0..m1 of a 2D ray split into a first zero-extended part, an
+// interior part [i0, i1] (rounded inwards by clip_axis_interior's margin, so
+// that the anchored positions of its samples are interior too) and a last
+// zero-extended part
+__device__ __forceinline__ void interior2d(const Ray2 &r, int nx, int ny, int m0, int m1, int &i0, int &i1)
+{
+    float lo = (float)m0, hi = (float)m1;
+    clip_axis_interior(r.px.h, r.qx.h, nx, lo, hi);
+    clip_axis_interior(r.py.h, r.qy.h, ny, lo, hi);
+    i0 = max(m0, (int)ceilf(lo));
+    i1 = min(m1, (int)floorf(hi));
+    if (i0 > i1) {  // no interior sample
+        i0 = m1 + 1;
+        i1 = m1;
+    }
 }
 
 // volT (may be NULL): the batch transposed, [b][x][y].  The lanes of a warp
@@ -78,51 +177,45 @@ __global__ void __launch_bounds__(128) fp2d_kernel(const T *__restrict__ vol, co
     const int b = blockIdx.z;
     if (k >= p.nu) return;
     Ray2 r = ray2d(p, v, k);
-    int m0, m1;
-    range2d(r, p, m0, m1);
     const T *img = vol + (size_t)b * p.nx * p.ny;
     int nx = p.nx, ny = p.ny;
     if (volT && fabsf(p.dir[v].x) > fabsf(p.dir[v].y)) {  // the whole block: one view
         img = volT + (size_t)b * p.nx * p.ny;
         nx = p.ny;
         ny = p.nx;
-        const float t0 = r.px, t1 = r.qx;
-        r.px = r.py;
-        r.qx = r.qy;
-        r.py = t0;
-        r.qy = t1;
+        swap_xy(r);
     }
-    // samples whose four taps are all inside the image take the unmasked path
-    float lo = (float)m0, hi = (float)m1;
-    clip_axis_interior(r.px, r.qx, nx, lo, hi);
-    clip_axis_interior(r.py, r.qy, ny, lo, hi);
-    int i0 = max(m0, (int)ceilf(lo)), i1 = min(m1, (int)floorf(hi));
-    if (i0 > i1) {  // no interior sample
-        i0 = m1 + 1;
-        i1 = m1;
-    }
-    float acc = 0.0f;
-    for (int m = m0; m < i0; ++m) {
-        const float fm = (float)m;
-        acc += bilerp_zero(img, nx, ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
-    }
-    // two samples per iteration with separate partial sums (unrolled twice
-    // more by the compiler), so that several samples' loads are in flight
-    float acc2 = 0.0f;
-    int m = i0;
+    int m0, m1, i0, i1;
+    range2d(r, p, nx, ny, m0, m1);
+    interior2d(r, nx, ny, m0, m1, i0, i1);
+    float acc = 0.0f, acc2 = 0.0f;
+    for (int ms = m0; ms <= m1; ms += kFPSegment) {
+        const int me = min(ms + kFPSegment - 1, m1);
+        const Seg X = seg_at(r.px, r.qx, ms), Y = seg_at(r.py, r.qy, ms);
+        for (int m = ms; m <= min(me, i0 - 1); ++m) {
+            const float dm = (float)(m - ms);
+            acc += bilerp_taps_zero(img, nx, ny, seg_tap(X, dm), seg_tap(Y, dm));
+        }
+        // two samples per iteration with separate partial sums, so that
+        // several samples' loads are in flight
+        int m = max(ms, i0);
+        const int ie = min(me, i1);
 #pragma unroll 2
-    for (; m + 1 <= i1; m += 2) {
-        const float fa = (float)m, fb = (float)(m + 1);
-        acc += bilerp_interior(img, 1, nx, fmaf(fa, r.qx, r.px), fmaf(fa, r.qy, r.py));
-        acc2 += bilerp_interior(img, 1, nx, fmaf(fb, r.qx, r.px), fmaf(fb, r.qy, r.py));
+        for (; m + 1 <= ie; m += 2) {
+            const float da = (float)(m - ms), db = da + 1.0f;
+            acc += bilerp_taps_interior(img, nx, seg_tap(X, da), seg_tap(Y, da));
+            acc2 += bilerp_taps_interior(img, nx, seg_tap(X, db), seg_tap(Y, db));
+        }
+        if (m <= ie) {
+            const float dm = (float)(m - ms);
+            acc += bilerp_taps_interior(img, nx, seg_tap(X, dm), seg_tap(Y, dm));
+        }
+        for (m = max(ms, i1 + 1); m <= me; ++m) {
+            const float dm = (float)(m - ms);
+            acc += bilerp_taps_zero(img, nx, ny, seg_tap(X, dm), seg_tap(Y, dm));
+        }
     }
-    if (m <= i1) acc += bilerp_interior(img, 1, nx, fmaf((float)m, r.qx, r.px), fmaf((float)m, r.qy, r.py));
-    acc += acc2;
-    for (int m = max(i1 + 1, i0); m <= m1; ++m) {
-        const float fm = (float)m;
-        acc += bilerp_zero(img, nx, ny, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py));
-    }
-    sino[((size_t)b * p.views_total + p.view0 + v) * p.nu + k] = to_storage<T>(r.w * acc);
+    sino[((size_t)b * p.views_total + p.view0 + v) * p.nu + k] = to_storage<T>(r.w * (acc + acc2));
 }
 
 // volT (may be NULL): a zeroed transposed accumulator [b][x][y] that takes
@@ -141,42 +234,42 @@ __global__ void __launch_bounds__(128) fp2d_adjoint_kernel(const float *__restri
     if (y0s == 0.0f) return;
     Ray2 r = ray2d(p, v, k);
     const float y = r.w * y0s;
-    int m0, m1;
-    range2d(r, p, m0, m1);
     float *img = vol + (size_t)b * p.nx * p.ny;
     int nx = p.nx, ny = p.ny;
     if (volT && fabsf(p.dir[v].x) > fabsf(p.dir[v].y)) {  // the whole block: one view
         img = volT + (size_t)b * p.nx * p.ny;
         nx = p.ny;
         ny = p.nx;
-        const float t0 = r.px, t1 = r.qx;
-        r.px = r.py;
-        r.qx = r.qy;
-        r.py = t0;
-        r.qy = t1;
+        swap_xy(r);
     }
-    for (int m = m0; m <= m1; ++m) {
-        const float fm = (float)m;
-        const Axis ax = axis_taps(fmaf(fm, r.qx, r.px), nx);
-        const Axis ay = axis_taps(fmaf(fm, r.qy, r.py), ny);
-        float *r0 = img + (size_t)ay.i0 * nx;
-        float *r1 = img + (size_t)ay.i1 * nx;
-        const float y0 = y * ay.w0, y1 = y * ay.w1;
-        if (y0 * ax.w0 != 0.0f) atomicAdd(r0 + ax.i0, y0 * ax.w0);
-        if (y0 * ax.w1 != 0.0f) atomicAdd(r0 + ax.i1, y0 * ax.w1);
-        if (y1 * ax.w0 != 0.0f) atomicAdd(r1 + ax.i0, y1 * ax.w0);
-        if (y1 * ax.w1 != 0.0f) atomicAdd(r1 + ax.i1, y1 * ax.w1);
+    int m0, m1;
+    range2d(r, p, nx, ny, m0, m1);
+    for (int ms = m0; ms <= m1; ms += kFPSegment) {
+        const int me = min(ms + kFPSegment - 1, m1);
+        const Seg X = seg_at(r.px, r.qx, ms), Y = seg_at(r.py, r.qy, ms);
+        for (int m = ms; m <= me; ++m) {
+            const float dm = (float)(m - ms);
+            const Axis ax = tap_axis(seg_tap(X, dm), nx);
+            const Axis ay = tap_axis(seg_tap(Y, dm), ny);
+            float *r0 = img + (size_t)ay.i0 * nx;
+            float *r1 = img + (size_t)ay.i1 * nx;
+            const float y0 = y * ay.w0, y1 = y * ay.w1;
+            if (y0 * ax.w0 != 0.0f) atomicAdd(r0 + ax.i0, y0 * ax.w0);
+            if (y0 * ax.w1 != 0.0f) atomicAdd(r0 + ax.i1, y0 * ax.w1);
+            if (y1 * ax.w0 != 0.0f) atomicAdd(r1 + ax.i0, y1 * ax.w0);
+            if (y1 * ax.w1 != 0.0f) atomicAdd(r1 + ax.i1, y1 * ax.w1);
+        }
     }
 }
 
-// ---- 3D cone ray set-up --------------------------------------------------
-struct Ray3 {
-    float px, py, pz, qx, qy, qz, w;  // sample m at p + m q (voxel-index units); weight w = dt |g|
-};
-
+// ---- 3D cone rays --------------------------------------------------------
 // In camera coordinates the ray of pixel (k, l) is S + w q, q = K^-1 (k, l, 1)
 // = (q_x, q_y, 1) (unit depth).  Its sample on the iso-centre's depth plane
 // (w0 = -s3) is (s1 - s3 q_x, s2 - s3 q_y, 0): no FP32 cancellation.
+struct Ray3 {
+    float px, py, pz, qx, qy, qz, w;  // FP32: sample m near p + m q (voxel-index units); weight w = dt |g|
+};
+
 __device__ __forceinline__ Ray3 ray3d(const FP3DParams &p, int v, int k, int l)
 {
     const ConeFPView &V = p.v[v];
@@ -197,6 +290,34 @@ __device__ __forceinline__ Ray3 ray3d(const FP3DParams &p, int v, int k, int l)
     return r;
 }
 
+// the same ray in float-float: axis a (0, 1, 2) of the sample position p + m q
+struct RayFF {
+    ff p[3], q[3];
+};
+
+__device__ __forceinline__ RayFF ray3d_ff(const FP3DParams &p, int v, int k, int l, int axes = 7)
+{
+    const ConeFPView &H = p.v[v], &L = p.vlo[v];
+    const float fk = (float)k, fl = (float)l;
+    const ff qx = ff_add(ff_add({H.a2, L.a2}, ff_mul_f({H.a0, L.a0}, fk)), ff_mul_f({H.a1, L.a1}, fl));
+    const ff qy = ff_add({H.b2, L.b2}, ff_mul_f({H.b0, L.b0}, fl));
+    const ff s3 = {H.s3, L.s3};
+    const ff c0 = ff_add({H.s1, L.s1}, ff_neg(ff_mul(s3, qx)));
+    const ff c1 = ff_add({H.s2, L.s2}, ff_neg(ff_mul(s3, qy)));
+    const ff dt = {p.dt, p.dt_lo};
+    const float cen[3] = {p.cx, p.cy, p.cz};
+    RayFF r;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (!(axes & (1 << a))) continue;
+        const ff w0 = {H.W[3 * a], L.W[3 * a]}, w1 = {H.W[3 * a + 1], L.W[3 * a + 1]};
+        const ff w2 = {H.W[3 * a + 2], L.W[3 * a + 2]};
+        r.p[a] = ff_add(ff_add(ff_mul(w0, c0), ff_mul(w1, c1)), {cen[a], 0.0f});
+        r.q[a] = ff_mul(dt, ff_add(ff_add(ff_mul(w0, qx), ff_mul(w1, qy)), w2));
+    }
+    return r;
+}
+
 __device__ __forceinline__ void range3d(const Ray3 &r, const FP3DParams &p, int &m0, int &m1)
 {
     float lo = -(float)p.M, hi = (float)p.M;
@@ -207,37 +328,82 @@ __device__ __forceinline__ void range3d(const Ray3 &r, const FP3DParams &p, int 
     m1 = min(p.M, (int)ceilf(hi));
 }
 
-// Sum of the samples m0..m1 of one ray through a volume with element strides
-// (stx, sty, stz).  Samples strictly inside the array take the unmasked
-// interior path; the few near the faces take the zero-extended path.  The
-// sample positions are the same FMA p + m q on both paths.
-template <typename T>
-__device__ __forceinline__ float march3d(const T *vol, const FP3DParams &p, int stx, int sty, int stz, const Ray3 &r,
-                                         int m0, int m1)
+// the samples of m0..m1 strictly inside the array on every axis (rounded
+// inwards by clip_axis_interior's margin, far above the difference between
+// these FP32 positions and the anchored ones)
+__device__ __forceinline__ void interior3d(const Ray3 &r, const FP3DParams &p, int m0, int m1, int &i0, int &i1)
 {
     float lo = (float)m0, hi = (float)m1;
     clip_axis_interior(r.px, r.qx, p.nx, lo, hi);
     clip_axis_interior(r.py, r.qy, p.ny, lo, hi);
     clip_axis_interior(r.pz, r.qz, p.nz, lo, hi);
-    int i0 = max(m0, (int)ceilf(lo)), i1 = min(m1, (int)floorf(hi));
+    i0 = max(m0, (int)ceilf(lo));
+    i1 = min(m1, (int)floorf(hi));
     if (i0 > i1) {  // no interior sample
         i0 = m1 + 1;
         i1 = m1;
     }
+}
+
+// trilinear interpolation at anchored taps of a volume with element strides
+// (stx, sty, stz): zero-extended, and the unmasked interior form
+template <typename T>
+__device__ __forceinline__ float trilerp_taps_zero(const T *vol, const FP3DParams &p, size_t stx, size_t sty,
+                                                   size_t stz, Tap tx, Tap ty, Tap tz)
+{
+    const Axis ax = tap_axis(tx, p.nx), ay = tap_axis(ty, p.ny), az = tap_axis(tz, p.nz);
+    const T *p00 = vol + ax.i0 * stx + ay.i0 * sty;
+    const T *p01 = vol + ax.i0 * stx + ay.i1 * sty;
+    const T *p10 = vol + ax.i1 * stx + ay.i0 * sty;
+    const T *p11 = vol + ax.i1 * stx + ay.i1 * sty;
+    const size_t z0 = az.i0 * stz, z1 = az.i1 * stz;
+    const float v00 = az.w0 * ld(p00 + z0) + az.w1 * ld(p00 + z1);
+    const float v01 = az.w0 * ld(p01 + z0) + az.w1 * ld(p01 + z1);
+    const float v10 = az.w0 * ld(p10 + z0) + az.w1 * ld(p10 + z1);
+    const float v11 = az.w0 * ld(p11 + z0) + az.w1 * ld(p11 + z1);
+    return ax.w0 * (ay.w0 * v00 + ay.w1 * v01) + ax.w1 * (ay.w0 * v10 + ay.w1 * v11);
+}
+
+template <typename T>
+__device__ __forceinline__ float trilerp_taps_interior(const T *vol, int stx, int sty, int stz, Tap tx, Tap ty,
+                                                       Tap tz)
+{
+    const T *b = vol + (tx.i * stx + ty.i * sty + tz.i * stz);
+    const float v00 = lerpf(ld(b), ld(b + stz), tz.a);
+    const float v01 = lerpf(ld(b + sty), ld(b + sty + stz), tz.a);
+    const float v10 = lerpf(ld(b + stx), ld(b + stx + stz), tz.a);
+    const float v11 = lerpf(ld(b + stx + sty), ld(b + stx + sty + stz), tz.a);
+    return lerpf(lerpf(v00, v01, ty.a), lerpf(v10, v11, ty.a), tx.a);
+}
+
+// Sum of the samples m0..m1 of one ray through a volume with element strides
+// (stx, sty, stz): segment by segment, the interior samples unmasked, the
+// few near the faces zero-extended.
+template <typename T>
+__device__ __forceinline__ float march3d(const T *vol, const FP3DParams &p, int stx, int sty, int stz,
+                                         const RayFF &rf, const Ray3 &r, int m0, int m1)
+{
+    int i0, i1;
+    interior3d(r, p, m0, m1, i0, i1);
     float acc = 0.0f;
-    for (int m = m0; m < i0; ++m) {
-        const float fm = (float)m;
-        acc += trilerp_zero_strided(vol, p.nx, p.ny, p.nz, (size_t)stx, (size_t)sty, (size_t)stz, fmaf(fm, r.qx, r.px),
-                                    fmaf(fm, r.qy, r.py), fmaf(fm, r.qz, r.pz));
-    }
-    for (int m = i0; m <= i1; ++m) {
-        const float fm = (float)m;
-        acc += trilerp_interior(vol, stx, sty, stz, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py), fmaf(fm, r.qz, r.pz));
-    }
-    for (int m = max(i1 + 1, i0); m <= m1; ++m) {
-        const float fm = (float)m;
-        acc += trilerp_zero_strided(vol, p.nx, p.ny, p.nz, (size_t)stx, (size_t)sty, (size_t)stz, fmaf(fm, r.qx, r.px),
-                                    fmaf(fm, r.qy, r.py), fmaf(fm, r.qz, r.pz));
+    for (int ms = m0; ms <= m1; ms += kFPSegment) {
+        const int me = min(ms + kFPSegment - 1, m1);
+        const Seg X = seg_at(rf.p[0], rf.q[0], ms), Y = seg_at(rf.p[1], rf.q[1], ms), Z = seg_at(rf.p[2], rf.q[2], ms);
+        int m = ms;
+        for (; m <= min(me, i0 - 1); ++m) {
+            const float dm = (float)(m - ms);
+            acc += trilerp_taps_zero(vol, p, (size_t)stx, (size_t)sty, (size_t)stz, seg_tap(X, dm), seg_tap(Y, dm),
+                                     seg_tap(Z, dm));
+        }
+        for (m = max(ms, i0); m <= min(me, i1); ++m) {
+            const float dm = (float)(m - ms);
+            acc += trilerp_taps_interior(vol, stx, sty, stz, seg_tap(X, dm), seg_tap(Y, dm), seg_tap(Z, dm));
+        }
+        for (m = max(ms, i1 + 1); m <= me; ++m) {
+            const float dm = (float)(m - ms);
+            acc += trilerp_taps_zero(vol, p, (size_t)stx, (size_t)sty, (size_t)stz, seg_tap(X, dm), seg_tap(Y, dm),
+                                     seg_tap(Z, dm));
+        }
     }
     return acc;
 }
@@ -258,7 +424,8 @@ __global__ void __launch_bounds__(kFP3DBlockX *kFP3DBlockY) fp3d_kernel(const T 
     int m0, m1;
     range3d(r, p, m0, m1);
     const T *V = vol + (size_t)b * p.nx * p.ny * p.nz;
-    const float acc = march3d(V, p, 1, p.nx, p.nx * p.ny, r, m0, m1);
+    float acc = 0.0f;
+    if (m0 <= m1) acc = march3d(V, p, 1, p.nx, p.nx * p.ny, ray3d_ff(p, v, k, l), r, m0, m1);
     sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(r.w * acc);
 }
 
@@ -300,6 +467,7 @@ __global__ void __launch_bounds__(kFPTexX *kFPTexY) fp3d_tex_kernel(cudaTextureO
     sino[((size_t)(p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(r.w * (acc0 + acc1));
 }
 
+
 // Staged forward projection: the volume has been re-laid out z-fastest
 // ([y][x][z]) and each warp's 32 lanes take 32 consecutive detector rows l of
 // one column k.  Those rays differ only in elevation, so at every sample
@@ -320,55 +488,53 @@ __global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const
     const Ray3 r = ray3d(p, v, k, l);
     int m0, m1;
     range3d(r, p, m0, m1);
-    // samples strictly inside the volume take the unmasked path; the rest the zero-extended one
-    float lo = (float)m0, hi = (float)m1;
-    clip_axis_interior(r.px, r.qx, p.nx, lo, hi);
-    clip_axis_interior(r.py, r.qy, p.ny, lo, hi);
-    clip_axis_interior(r.pz, r.qz, p.nz, lo, hi);
-    int i0 = max(m0, (int)ceilf(lo)), i1 = min(m1, (int)floorf(hi));
-    if (i0 > i1) {
-        i0 = m1 + 1;
-        i1 = m1;
-    }
-    const size_t sx = (size_t)p.nz, sy = (size_t)p.nz * p.nx;
     float acc = 0.0f;
-    for (int m = m0; m < i0; ++m) {
-        const float fm = (float)m;
-        acc += trilerp_zero_strided(vz, p.nx, p.ny, p.nz, sx, sy, (size_t)1, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py),
-                                    fmaf(fm, r.qz, r.pz));
-    }
-    // interior: consecutive samples are half a voxel apart and the warp's rays
-    // (consecutive detector rows) sit at one (x, y) point on every depth plane,
-    // so the 8 taps of the current cell stay in registers until the cell changes
-    const int stx = p.nz, sty = p.nz * p.nx;
-    int cur = -1;
-    float c000 = 0.f, c001 = 0.f, c010 = 0.f, c011 = 0.f, c100 = 0.f, c101 = 0.f, c110 = 0.f, c111 = 0.f;
-    for (int m = i0; m <= i1; ++m) {
-        const float fm = (float)m;
-        const float fx = fmaf(fm, r.qx, r.px), fy = fmaf(fm, r.qy, r.py), fz = fmaf(fm, r.qz, r.pz);
-        const float x0 = floorf(fx), y0 = floorf(fy), z0 = floorf(fz);
-        const int cell = (int)x0 * stx + (int)y0 * sty + (int)z0;
-        if (cell != cur) {
-            const T *q = vz + cell;
-            c000 = ld(q);
-            c001 = ld(q + 1);
-            c010 = ld(q + sty);
-            c011 = ld(q + sty + 1);
-            c100 = ld(q + stx);
-            c101 = ld(q + stx + 1);
-            c110 = ld(q + stx + sty);
-            c111 = ld(q + stx + sty + 1);
-            cur = cell;
+    if (m0 <= m1) {
+        const RayFF rf = ray3d_ff(p, v, k, l);
+        int i0, i1;
+        interior3d(r, p, m0, m1, i0, i1);
+        const size_t sx = (size_t)p.nz, sy = (size_t)p.nz * p.nx;
+        // interior: consecutive samples are half a voxel apart and the warp's
+        // rays (consecutive detector rows) sit at one (x, y) point on every
+        // depth plane, so the 8 taps of the current cell stay in registers
+        // until the cell changes
+        const int stx = p.nz, sty = p.nz * p.nx;
+        int cur = -1;
+        float c000 = 0.f, c001 = 0.f, c010 = 0.f, c011 = 0.f, c100 = 0.f, c101 = 0.f, c110 = 0.f, c111 = 0.f;
+        for (int ms = m0; ms <= m1; ms += kFPSegment) {
+            const int me = min(ms + kFPSegment - 1, m1);
+            const Seg X = seg_at(rf.p[0], rf.q[0], ms), Y = seg_at(rf.p[1], rf.q[1], ms);
+            const Seg Z = seg_at(rf.p[2], rf.q[2], ms);
+            int m = ms;
+            for (; m <= min(me, i0 - 1); ++m) {
+                const float dm = (float)(m - ms);
+                acc += trilerp_taps_zero(vz, p, sx, sy, (size_t)1, seg_tap(X, dm), seg_tap(Y, dm), seg_tap(Z, dm));
+            }
+            for (m = max(ms, i0); m <= min(me, i1); ++m) {
+                const float dm = (float)(m - ms);
+                const Tap tx = seg_tap(X, dm), ty = seg_tap(Y, dm), tz = seg_tap(Z, dm);
+                const int cell = tx.i * stx + ty.i * sty + tz.i;
+                if (cell != cur) {
+                    const T *q = vz + cell;
+                    c000 = ld(q);
+                    c001 = ld(q + 1);
+                    c010 = ld(q + sty);
+                    c011 = ld(q + sty + 1);
+                    c100 = ld(q + stx);
+                    c101 = ld(q + stx + 1);
+                    c110 = ld(q + stx + sty);
+                    c111 = ld(q + stx + sty + 1);
+                    cur = cell;
+                }
+                const float v00 = lerpf(c000, c001, tz.a), v01 = lerpf(c010, c011, tz.a);
+                const float v10 = lerpf(c100, c101, tz.a), v11 = lerpf(c110, c111, tz.a);
+                acc += lerpf(lerpf(v00, v01, ty.a), lerpf(v10, v11, ty.a), tx.a);
+            }
+            for (m = max(ms, i1 + 1); m <= me; ++m) {
+                const float dm = (float)(m - ms);
+                acc += trilerp_taps_zero(vz, p, sx, sy, (size_t)1, seg_tap(X, dm), seg_tap(Y, dm), seg_tap(Z, dm));
+            }
         }
-        const float ax = fx - x0, ay = fy - y0, az = fz - z0;
-        const float v00 = lerpf(c000, c001, az), v01 = lerpf(c010, c011, az);
-        const float v10 = lerpf(c100, c101, az), v11 = lerpf(c110, c111, az);
-        acc += lerpf(lerpf(v00, v01, ay), lerpf(v10, v11, ay), ax);
-    }
-    for (int m = max(i1 + 1, i0); m <= m1; ++m) {
-        const float fm = (float)m;
-        acc += trilerp_zero_strided(vz, p.nx, p.ny, p.nz, sx, sy, (size_t)1, fmaf(fm, r.qx, r.px), fmaf(fm, r.qy, r.py),
-                                    fmaf(fm, r.qz, r.pz));
     }
     sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(r.w * acc);
 }
@@ -384,29 +550,78 @@ __global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const
 // combines them in x and y, and each lane then takes the two z taps of its
 // own ray from the lanes holding them (two shuffles).  The host checks that
 // 31 row steps stay below 29.5 voxels in z, so a window's taps always fall in
-// its 32-voxel run.  The volume copy is [ny+2][nx+2][nz+2] with a zero voxel
-// on every face: loads need no bounds test, and the zero-extended
-// interpolant comes out of the padding.
+// its 32-voxel run.  The volume copy is [ny+4][nx+4][nz+2] with zero voxels
+// around the data (two in x and y, one in z): loads need no bounds test, and
+// the zero-extended interpolant comes out of the padding.
+//
+// Positions: the column's (x, y) track is anchored (float-float) at the
+// start of every kFPSegment planes; each ray's z once, at the middle plane of
+// the warp's range, since the rays' z moves by at most a few tens of voxels
+// over a whole ray (|q_z| stays near 0.1 voxel per plane for these
+// trajectories), which keeps the FP32 steps from the anchor within ~2e-6
+// voxel.
 constexpr int kFPCWarps = 4;
 
 struct ColumnWindow {
-    float pz, qz;    // this lane's ray: z(m) = pz + m qz
-    float pzb, qzb;  // the window's lowest row
-    float w;         // ray weight dt |g|
-    float acc;       // forward: the ray sum; adjoint: w times the ray's datum
-    int ma, mb;      // samples of the window's rows that can touch the volume
+    float acc;  // forward: the ray sum; adjoint: w times the ray's datum
+    int ma, mb; // samples of the window's rows that can touch the volume
 };
 
-// (x, y) cell of depth plane m shared by the column's rays: bilinear weights
+// the window's lowest z and the lane's z, anchored on the lowest row's
+// integer cell ib at plane mz: zb = ib + fb + dz qb, z = ib + f + dz q, dz =
+// m - mz (f holds the lane's offset from the lowest row, below 32)
+struct ZSeg {
+    float f, q;
+    float fb, qb;
+    int zbase;  // ib - 0x4B400000 + lane: the lane's run index minus the magic bits
+};
+
+__device__ __forceinline__ ZSeg zseg(const float4 &zr, int src, int lane, int mz)
+{
+    const Seg Z = seg_at({zr.x, zr.y}, {zr.z, zr.w}, mz);
+    const unsigned full = 0xffffffffu;
+    ZSeg s;
+    const int ib = __shfl_sync(full, Z.i, src);
+    s.fb = __shfl_sync(full, Z.f, src);
+    s.qb = __shfl_sync(full, Z.q, src);
+    s.f = Z.f + (float)(Z.i - ib);
+    s.q = Z.q;
+    s.zbase = ib - 0x4B400000 + lane;
+    return s;
+}
+
+// the track anchored at plane ms: x = X.i + X.f + dx X.q, and the padded
+// element index of cell (X.i, Y.i, z = 0) minus the magic bits of the
+// in-segment floors (mod 2^32)
+struct TrackSeg {
+    float xf, xq, yf, yq;
+    int col0;
+};
+
+__device__ __forceinline__ TrackSeg track_seg(const float4 *t, int ms, int sxp, int syp)
+{
+    const float4 a = t[0], b = t[1];  // (px, py) and (qx, qy) as hi/lo pairs
+    const Seg X = seg_at({a.x, a.y}, {b.x, b.y}, ms), Y = seg_at({a.z, a.w}, {b.z, b.w}, ms);
+    TrackSeg s;
+    s.xf = X.f;
+    s.xq = X.q;
+    s.yf = Y.f;
+    s.yq = Y.q;
+    s.col0 = (int)((unsigned)(Y.i + kFPPadXY - 0x4B400000) * (unsigned)syp +
+                   (unsigned)(X.i + kFPPadXY - 0x4B400000) * (unsigned)sxp + 1u);
+    return s;
+}
+
+// (x, y) cell of a depth plane shared by the column's rays: bilinear weights
 // and the padded element index of (x0, y0, z = 0)
 struct PlaneXY {
     float w00, w10, w01, w11;
     int col;
 };
 
-__device__ __forceinline__ PlaneXY plane_xy(float fm, const Ray3 &rc, int sxp, int syp)
+__device__ __forceinline__ PlaneXY plane_xy(const TrackSeg &s, float dx, int sxp, int syp)
 {
-    const float fx = fmaf(fm, rc.qx, rc.px), fy = fmaf(fm, rc.qy, rc.py);
+    const float fx = fmaf(dx, s.xq, s.xf), fy = fmaf(dx, s.yq, s.yf);
     const float tx = floor_magic(fx), ty = floor_magic(fy);
     const float ax = fx - magic_to_float(tx), ay = fy - magic_to_float(ty);
     const float bx = 1.0f - ax, by = 1.0f - ay;
@@ -415,20 +630,21 @@ __device__ __forceinline__ PlaneXY plane_xy(float fm, const Ray3 &rc, int sxp, i
     q.w10 = ax * by;
     q.w01 = bx * ay;
     q.w11 = ax * ay;
-    q.col = (magic_to_int(ty) + 1) * syp + (magic_to_int(tx) + 1) * sxp + 1;
+    q.col = (int)((unsigned)s.col0 + (unsigned)__float_as_int(ty) * (unsigned)syp +
+                  (unsigned)__float_as_int(tx) * (unsigned)sxp);  // mod 2^32: the magic bits cancel
     return q;
 }
 
 // One depth plane of one window: the lane's x/y-interpolated value at
 // z = zb + lane, then its own ray's z interpolation from two lanes.
 template <typename T>
-__device__ __forceinline__ void column_step(ColumnWindow &W, float fm, int lane, int nz, const T *const (&c)[4],
+__device__ __forceinline__ void column_step(ColumnWindow &W, const ZSeg &z, float dz, int nz, const T *const (&c)[4],
                                             const PlaneXY &q)
 {
-    const float tzb = floor_magic(fmaf(fm, W.qzb, W.pzb));
-    const int zi = min(max(magic_to_int(tzb) + lane, -1), nz);
+    const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
+    const int zi = min(max(z.zbase + __float_as_int(tzb), -1), nz);
     const float g = q.w00 * ld(c[0] + zi) + q.w10 * ld(c[1] + zi) + q.w01 * ld(c[2] + zi) + q.w11 * ld(c[3] + zi);
-    const float fz = fmaf(fm, W.qz, W.pz);
+    const float fz = fmaf(dz, z.q, z.f);
     const float tz = floor_magic(fz);
     const int j = __float_as_int(tz) - __float_as_int(tzb);  // own cell relative to the window's run
     const float g0 = __shfl_sync(0xffffffffu, g, j), g1 = __shfl_sync(0xffffffffu, g, j + 1);
@@ -443,12 +659,12 @@ __device__ __forceinline__ void column_step(ColumnWindow &W, float fm, int lane,
 // accumulating a volume larger than L2 slab by slab, each slab a launch,
 // was measured slower, 2.7 s against 1.7 s at 512^3, because windows that
 // straddle a slab boundary repeat their work).
-__device__ __forceinline__ void column_step_adjoint(const ColumnWindow &W, float fm, int lane, int zs0, int zs1,
-                                                    float *const (&c)[4], const PlaneXY &q, float *run)
+__device__ __forceinline__ void column_step_adjoint(const ColumnWindow &W, const ZSeg &z, float dz, int lane, int zs0,
+                                                    int zs1, float *const (&c)[4], const PlaneXY &q, float *run)
 {
-    const float tzb = floor_magic(fmaf(fm, W.qzb, W.pzb));
-    const int zi = magic_to_int(tzb) + lane;
-    const float fz = fmaf(fm, W.qz, W.pz);
+    const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
+    const int zi = z.zbase + __float_as_int(tzb);
+    const float fz = fmaf(dz, z.q, z.f);
     const float tz = floor_magic(fz);
     // 0..30 for every real row (host-checked); clamped so that no shared
     // access leaves the run
@@ -472,38 +688,41 @@ __device__ __forceinline__ void column_step_adjoint(const ColumnWindow &W, float
     }
 }
 
-// Depth planes m0..m1 of all R windows.  CHECK skips the windows whose rows
-// cannot touch the volume on a plane (outside the planes every window
-// reaches; elsewhere the skipped terms would be exact zeros anyway: the
-// forward reads the zero padding, the adjoint writes into it).
+// Depth planes m0..m1 of all R windows, the track re-anchored every
+// kFPSegment planes.  CHECK skips the windows whose rows cannot touch the
+// volume on a plane (outside the planes every window reaches; elsewhere the
+// skipped terms would be exact zeros anyway: the forward reads the zero
+// padding, the adjoint writes into it).
 template <typename T, int R, bool CHECK, bool ADJ>
-__device__ __forceinline__ void column_planes(ColumnWindow (&W)[R], int m0, int m1, const Ray3 &rc, int lane, T *vp,
-                                              int nz, int sxp, int syp, float *runs, int zs0, int zs1)
+__device__ __forceinline__ void column_planes(ColumnWindow (&W)[R], const ZSeg (&zs)[R], const float4 *track, int mz,
+                                              int m0, int m1, int lane, T *vp, const FP3DParams &p, int sxp, int syp,
+                                              float *runs)
 {
     // unrolled by 4 on the forward path (measured 1 % faster than 2, while
     // 1, 6 and 8 were slower) and by 2 on the adjoint's
     constexpr int kUnroll = ADJ ? 2 : 4;
-    float fm = (float)m0;
+    for (int ms = m0; ms <= m1; ms += kFPSegment) {
+        const int me = min(ms + kFPSegment - 1, m1);
+        const TrackSeg ts = track_seg(track, ms, sxp, syp);
+        float dx = 0.0f, dz = (float)(ms - mz);
 #pragma unroll kUnroll
-    for (int m = m0; m <= m1; ++m, fm += 1.0f) {
-        const PlaneXY q = plane_xy(fm, rc, sxp, syp);
-        T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+        for (int m = ms; m <= me; ++m, dx += 1.0f, dz += 1.0f) {
+            const PlaneXY q = plane_xy(ts, dx, sxp, syp);
+            T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-            if constexpr (ADJ) {
-                column_step_adjoint(W[r], fm, lane, zs0, zs1, c, q, runs + 32 * r);
-            } else {
-                const T *const cr[4] = {c[0], c[1], c[2], c[3]};
-                column_step(W[r], fm, lane, nz, cr, q);
+            for (int r = 0; r < R; ++r) {
+                if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
+                if constexpr (ADJ) {
+                    column_step_adjoint(W[r], zs[r], dz, lane, p.zs0, p.zs1, c, q, runs + 32 * r);
+                } else {
+                    const T *const cr[4] = {c[0], c[1], c[2], c[3]};
+                    column_step(W[r], zs[r], dz, p.nz, cr, q);
+                }
             }
         }
     }
 }
 
-// Set-up shared by the forward and adjoint column kernels: the column's
-// (x, y) track rc, the windows' rays and ranges; returns the union [mlo, mhi]
-// of the windows' ranges and the planes [clo, chi] every window reaches.
 // Restrict m of p0 + m q to the open interval (a, b) (rounded outwards).
 __device__ __forceinline__ void clip_open(float p0, float q, float a, float b, float &lo, float &hi)
 {
@@ -517,27 +736,51 @@ __device__ __forceinline__ void clip_open(float p0, float q, float a, float b, f
     }
 }
 
-// zlo, zhi: the open z interval whose samples matter (the volume's (-1, nz),
-// or a slab's (zs0 - 1, zs1) for the slab-blocked adjoint)
-template <int R>
-__device__ __forceinline__ void column_setup(const FP3DParams &p, int v, int k, int row0, int lane, Ray3 &rc,
-                                             ColumnWindow (&W)[R], int &mlo, int &mhi, int &clo, int &chi,
-                                             float zlo, float zhi)
+// the planes whose (x, y) cell lies in [-1, n-1]^2 by the FP32 track (an
+// anchored cell may differ by one; the second padding voxel covers it)
+__device__ __forceinline__ void track_range(const FP3DParams &p, const Ray3 &rc, int &m0, int &m1)
 {
-    const unsigned full = 0xffffffffu;
-    rc = ray3d(p, v, k, row0);  // (x, y) track of the column, common to all its rows
     float lo = -(float)p.M, hi = (float)p.M;
     clip_axis(rc.px, rc.qx, p.nx, lo, hi);
     clip_axis(rc.py, rc.qy, p.ny, lo, hi);
-    int m0 = max(-p.M, (int)floorf(lo)), m1 = min(p.M, (int)ceilf(hi));
-    // keep the samples whose cell (x0, y0) lies in [-1, n-1]^2; the clip above
-    // is rounded outwards by at most one sample
+    m0 = max(-p.M, (int)floorf(lo));
+    m1 = min(p.M, (int)ceilf(hi));
+    // the clip above is rounded outwards by at most one sample
     auto inside = [&](int m) {
         const float fx = fmaf((float)m, rc.qx, rc.px), fy = fmaf((float)m, rc.qy, rc.py);
         return fx >= -1.0f && fx < (float)p.nx && fy >= -1.0f && fy < (float)p.ny;
     };
     while (m0 <= m1 && !inside(m0)) ++m0;
     while (m1 >= m0 && !inside(m1)) --m1;
+}
+
+// the column's track (float-float, uniform over the warp) into `track`
+__device__ __forceinline__ void store_track(const FP3DParams &p, int v, int k, int row0, int lane, float4 *track)
+{
+    if (lane == 0) {
+        const RayFF tf = ray3d_ff(p, v, k, row0, 3);
+        track[0] = make_float4(tf.p[0].h, tf.p[0].l, tf.p[1].h, tf.p[1].l);
+        track[1] = make_float4(tf.q[0].h, tf.q[0].l, tf.q[1].h, tf.q[1].l);
+    }
+}
+
+// Set-up shared by the forward and adjoint column kernels: the column's
+// (x, y) track (float-float, into `track`), the windows' rays and ranges
+// (each lane's z in float-float into `zray`); returns the union [mlo, mhi]
+// of the windows' ranges and the planes [clo, chi] every window reaches.
+// last_low: bit r set when window r's lowest row is its last (lane 31).
+// zlo, zhi: the open z interval whose samples matter (the volume's (-1, nz),
+// or a slab's (zs0 - 1, zs1) for the slab-blocked adjoint).
+template <int R>
+__device__ __forceinline__ void column_setup(const FP3DParams &p, int v, int k, int row0, int lane, float4 *track,
+                                             ColumnWindow (&W)[R], float4 *zray, int &last_low, int &mlo, int &mhi,
+                                             int &clo, int &chi, float zlo, float zhi)
+{
+    const unsigned full = 0xffffffffu;
+    last_low = 0;
+    store_track(p, v, k, row0, lane, track);
+    int m0, m1;
+    track_range(p, ray3d(p, v, k, row0), m0, m1);
     mlo = INT_MAX;
     mhi = INT_MIN;
     clo = INT_MIN;
@@ -546,15 +789,12 @@ __device__ __forceinline__ void column_setup(const FP3DParams &p, int v, int k, 
     for (int r = 0; r < R; ++r) {
         const int l = row0 + 32 * r + lane;
         const Ray3 rr = ray3d(p, v, k, l);
-        W[r].pz = rr.pz;
-        W[r].qz = rr.qz;
-        W[r].w = rr.w;
+        const RayFF zf = ray3d_ff(p, v, k, l, 4);
+        zray[32 * r + lane] = make_float4(zf.p[2].h, zf.p[2].l, zf.q[2].h, zf.q[2].l);
         W[r].acc = 0.0f;
         // the window's lowest z is at its first or its last row (depth > 0)
         const float z_first = __shfl_sync(full, rr.pz, 0), z_last = __shfl_sync(full, rr.pz, 31);
-        const int src = z_last >= z_first ? 0 : 31;
-        W[r].pzb = __shfl_sync(full, rr.pz, src);
-        W[r].qzb = __shfl_sync(full, rr.qz, src);
+        if (z_last < z_first) last_low |= 1 << r;
         float zl = (float)m0, zh = (float)m1;
         clip_open(rr.pz, rr.qz, zlo, zhi, zl, zh);
         int a = max(m0, (int)floorf(zl)), e = min(m1, (int)ceilf(zh));
@@ -575,6 +815,24 @@ __device__ __forceinline__ void column_setup(const FP3DParams &p, int v, int k, 
         clo = mhi + 1;
         chi = mhi;
     }
+    __syncwarp();
+}
+
+// all planes mlo..mhi: the rays' z anchored at the middle plane, then the
+// planes split by window coverage ([clo, chi] without window checks)
+template <typename T, int R, bool ADJ>
+__device__ __forceinline__ void column_march(ColumnWindow (&W)[R], const float4 *track, const float4 *zray,
+                                             int last_low, int mlo, int mhi, int clo, int chi, int lane, T *vp,
+                                             const FP3DParams &p, float *runs)
+{
+    const int sxp = p.nz + 2, syp = (p.nx + 2 * kFPPadXY) * (p.nz + 2);
+    const int mz = mlo + (mhi - mlo) / 2;
+    ZSeg zs[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) zs[r] = zseg(zray[32 * r + lane], (last_low >> r & 1) ? 31 : 0, lane, mz);
+    column_planes<T, R, true, ADJ>(W, zs, track, mz, mlo, clo - 1, lane, vp, p, sxp, syp, runs);
+    column_planes<T, R, false, ADJ>(W, zs, track, mz, clo, chi, lane, vp, p, sxp, syp, runs);
+    column_planes<T, R, true, ADJ>(W, zs, track, mz, max(chi + 1, clo), mhi, lane, vp, p, sxp, syp, runs);
 }
 
 template <typename T, int R>
@@ -582,27 +840,26 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__
                                                                      T *__restrict__ sino,
                                                                      const __grid_constant__ FP3DParams p, int b)
 {
+    __shared__ float4 zrays[kFPCWarps][R * 32];
+    __shared__ float4 tracks[kFPCWarps][2];
     const int lane = threadIdx.x;
     const int k = blockIdx.y * kFPCWarps + threadIdx.y;
     const int v = blockIdx.x;
     if (k >= p.nu) return;  // whole warp
     const int row0 = blockIdx.z * (32 * R);
-    Ray3 rc;
     ColumnWindow W[R];
-    int mlo, mhi, clo, chi;
-    column_setup<R>(p, v, k, row0, lane, rc, W, mlo, mhi, clo, chi, -1.0f, (float)p.nz);
-    const int sxp = p.nz + 2, syp = (p.nx + 2) * (p.nz + 2);
-    if (mlo <= mhi) {
-        T *vq = const_cast<T *>(vp);  // read only on the forward path
-        column_planes<T, R, true, false>(W, mlo, clo - 1, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
-        column_planes<T, R, false, false>(W, clo, chi, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
-        column_planes<T, R, true, false>(W, max(chi + 1, clo), mhi, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
-    }
+    int last_low, mlo, mhi, clo, chi;
+    column_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
+                    -1.0f, (float)p.nz);
+    if (mlo <= mhi)
+        column_march<T, R, false>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane,
+                                  const_cast<T *>(vp), p, nullptr);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int l = row0 + 32 * r + lane;
         if (l < p.nv)
-            sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] = to_storage<T>(W[r].w * W[r].acc);
+            sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] =
+                to_storage<T>(ray3d(p, v, k, l).w * W[r].acc);
     }
 }
 
@@ -616,6 +873,8 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_adjoint_kernel(con
                                                                              int b)
 {
     __shared__ float runs[kFPCWarps][R * 32];
+    __shared__ float4 zrays[kFPCWarps][R * 32];
+    __shared__ float4 tracks[kFPCWarps][2];
     const int lane = threadIdx.x;
     const int k = blockIdx.y * kFPCWarps + threadIdx.y;
     const int v = blockIdx.x;
@@ -625,23 +884,19 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_adjoint_kernel(con
     for (int r = 0; r < R; ++r) run[32 * r + lane] = 0.0f;
     __syncwarp();
     const int row0 = blockIdx.z * (32 * R);
-    Ray3 rc;
     ColumnWindow W[R];
-    int mlo, mhi, clo, chi;
-    column_setup<R>(p, v, k, row0, lane, rc, W, mlo, mhi, clo, chi, (float)(p.zs0 - 1), (float)p.zs1);
+    int last_low, mlo, mhi, clo, chi;
+    column_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
+                    (float)(p.zs0 - 1), (float)p.zs1);
     if (mlo > mhi) return;  // whole warp: no sample of its rays touches the slab
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int l = row0 + 32 * r + lane;
-        W[r].acc = l < p.nv ? W[r].w * sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] : 0.0f;
+        W[r].acc = l < p.nv ? ray3d(p, v, k, l).w * sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k]
+                            : 0.0f;
     }
-    const int sxp = p.nz + 2, syp = (p.nx + 2) * (p.nz + 2);
-    {
-        column_planes<float, R, true, true>(W, mlo, clo - 1, rc, lane, vp, p.nz, sxp, syp, run, p.zs0, p.zs1);
-        column_planes<float, R, false, true>(W, clo, chi, rc, lane, vp, p.nz, sxp, syp, run, p.zs0, p.zs1);
-        column_planes<float, R, true, true>(W, max(chi + 1, clo), mhi, rc, lane, vp, p.nz, sxp, syp, run, p.zs0,
-                                            p.zs1);
-    }
+    column_march<float, R, true>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp,
+                                 p, run);
 }
 
 // ---- two rays per lane: windows of up to 64 rows on one 32-voxel run -----
@@ -651,33 +906,49 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_adjoint_kernel(con
 // rows (WR = pair_rows <= 64, chosen on the host so that WR - 1 row steps
 // stay below 29.5 voxels; the lanes past WR - 32 have no second ray), and
 // both rays take their taps from the same run: one set of loads and x/y
-// combinations for up to twice the rays.  The arithmetic of every ray is
-// that of fp3d_column_kernel.
+// combinations for up to twice the rays.  The arithmetic and the anchoring
+// of every ray are those of fp3d_column_kernel.
 struct PairRowsWindow {
-    float pz[2], qz[2];  // the lane's two rays: z(m) = pz + m qz
-    float pzb, qzb;      // the window's lowest row
-    float acc[2];        // forward: the ray sums; adjoint: w times the rays' data
-    int ma, mb;          // samples of the window's rows that can touch the volume
+    float acc[2];  // forward: the ray sums; adjoint: w times the rays' data
+    int ma, mb;    // samples of the window's rows that can touch the volume
 };
 
+// as ZSeg, for the lane's two rays
+struct ZSeg2 {
+    float f[2], q[2];
+    float fb, qb;
+    int zbase;
+};
+
+// src, src_h: the lane and the ray (0: first, 1: second) of the window's lowest row
+__device__ __forceinline__ ZSeg2 zseg2(const float4 &z0, const float4 &z1, int src, int src_h, int lane, int mz)
+{
+    const Seg A = seg_at({z0.x, z0.y}, {z0.z, z0.w}, mz), B = seg_at({z1.x, z1.y}, {z1.z, z1.w}, mz);
+    const unsigned full = 0xffffffffu;
+    const int ib = __shfl_sync(full, src_h ? B.i : A.i, src);
+    ZSeg2 s;
+    s.fb = __shfl_sync(full, src_h ? B.f : A.f, src);
+    s.qb = __shfl_sync(full, src_h ? B.q : A.q, src);
+    s.f[0] = A.f + (float)(A.i - ib);
+    s.q[0] = A.q;
+    s.f[1] = B.f + (float)(B.i - ib);
+    s.q[1] = B.q;
+    s.zbase = ib - 0x4B400000 + lane;
+    return s;
+}
+
+// last_low: bit r set when window r's lowest row is its last (lane WR - 33's second ray)
 template <int R>
-__device__ __forceinline__ void pair_rows_setup(const FP3DParams &p, int v, int k, int row0, int lane, Ray3 &rc,
-                                                PairRowsWindow (&W)[R], int &mlo, int &mhi, int &clo, int &chi,
-                                                float zlo, float zhi)
+__device__ __forceinline__ void pair_rows_setup(const FP3DParams &p, int v, int k, int row0, int lane, float4 *track,
+                                                PairRowsWindow (&W)[R], float4 *zray, int &last_low, int &mlo,
+                                                int &mhi, int &clo, int &chi, float zlo, float zhi)
 {
     const unsigned full = 0xffffffffu;
     const int WR = p.pair_rows;
-    rc = ray3d(p, v, k, row0);
-    float lo = -(float)p.M, hi = (float)p.M;
-    clip_axis(rc.px, rc.qx, p.nx, lo, hi);
-    clip_axis(rc.py, rc.qy, p.ny, lo, hi);
-    int m0 = max(-p.M, (int)floorf(lo)), m1 = min(p.M, (int)ceilf(hi));
-    auto inside = [&](int m) {
-        const float fx = fmaf((float)m, rc.qx, rc.px), fy = fmaf((float)m, rc.qy, rc.py);
-        return fx >= -1.0f && fx < (float)p.nx && fy >= -1.0f && fy < (float)p.ny;
-    };
-    while (m0 <= m1 && !inside(m0)) ++m0;
-    while (m1 >= m0 && !inside(m1)) --m1;
+    last_low = 0;
+    store_track(p, v, k, row0, lane, track);
+    int m0, m1;
+    track_range(p, ray3d(p, v, k, row0), m0, m1);
     mlo = INT_MAX;
     mhi = INT_MIN;
     clo = INT_MIN;
@@ -685,12 +956,14 @@ __device__ __forceinline__ void pair_rows_setup(const FP3DParams &p, int v, int 
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         int a = INT_MAX, e = INT_MIN;
+        float pz[2];
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int l = row0 + r * WR + 32 * h + lane;
             const Ray3 rr = ray3d(p, v, k, l);
-            W[r].pz[h] = rr.pz;
-            W[r].qz[h] = rr.qz;
+            const RayFF zf = ray3d_ff(p, v, k, l, 4);
+            zray[(2 * r + h) * 32 + lane] = make_float4(zf.p[2].h, zf.p[2].l, zf.q[2].h, zf.q[2].l);
+            pz[h] = rr.pz;
             W[r].acc[h] = 0.0f;
             const bool real = l < p.nv && 32 * h + lane < WR;
             float zl = (float)m0, zh = (float)m1;
@@ -703,10 +976,8 @@ __device__ __forceinline__ void pair_rows_setup(const FP3DParams &p, int v, int 
         }
         // the window's lowest z is at its first row (lane 0's first ray) or its
         // last (lane WR - 33's second ray): depth > 0
-        const float zf = __shfl_sync(full, W[r].pz[0], 0), zq = __shfl_sync(full, W[r].qz[0], 0);
-        const float zl = __shfl_sync(full, W[r].pz[1], WR - 33), zlq = __shfl_sync(full, W[r].qz[1], WR - 33);
-        W[r].pzb = zl >= zf ? zf : zl;
-        W[r].qzb = zl >= zf ? zq : zlq;
+        const float zf0 = __shfl_sync(full, pz[0], 0), zl1 = __shfl_sync(full, pz[1], WR - 33);
+        if (zl1 < zf0) last_low |= 1 << r;
         W[r].ma = __reduce_min_sync(full, a);
         W[r].mb = __reduce_max_sync(full, e);
         if (W[r].ma <= W[r].mb) {
@@ -720,21 +991,21 @@ __device__ __forceinline__ void pair_rows_setup(const FP3DParams &p, int v, int 
         clo = mhi + 1;
         chi = mhi;
     }
+    __syncwarp();
 }
-
 
 // one depth plane of one window: the run as in column_step, then both rays'
 // z interpolations from it
 template <typename T>
-__device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, float fm, int lane, int nz, const T *const (&c)[4],
-                                               const PlaneXY &q)
+__device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, const ZSeg2 &z, float dz, int nz,
+                                               const T *const (&c)[4], const PlaneXY &q)
 {
-    const float tzb = floor_magic(fmaf(fm, W.qzb, W.pzb));
-    const int zi = min(max(magic_to_int(tzb) + lane, -1), nz);
+    const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
+    const int zi = min(max(z.zbase + __float_as_int(tzb), -1), nz);
     const float g = q.w00 * ld(c[0] + zi) + q.w10 * ld(c[1] + zi) + q.w01 * ld(c[2] + zi) + q.w11 * ld(c[3] + zi);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const float fz = fmaf(fm, W.qz[h], W.pz[h]);
+        const float fz = fmaf(dz, z.q[h], z.f[h]);
         const float tz = floor_magic(fz);
         const int j = __float_as_int(tz) - __float_as_int(tzb);
         const float g0 = __shfl_sync(0xffffffffu, g, j), g1 = __shfl_sync(0xffffffffu, g, j + 1);
@@ -745,14 +1016,15 @@ __device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, float fm, int 
 // transpose of pair_rows_step: both rays' data go into the run's cells, then
 // each lane spreads its cell over the four (x, y) columns (as
 // column_step_adjoint)
-__device__ __forceinline__ void pair_rows_step_adjoint(const PairRowsWindow &W, float fm, int lane, int zs0, int zs1,
-                                                       float *const (&c)[4], const PlaneXY &q, float *run)
+__device__ __forceinline__ void pair_rows_step_adjoint(const PairRowsWindow &W, const ZSeg2 &z, float dz, int lane,
+                                                       int zs0, int zs1, float *const (&c)[4], const PlaneXY &q,
+                                                       float *run)
 {
-    const float tzb = floor_magic(fmaf(fm, W.qzb, W.pzb));
-    const int zi = magic_to_int(tzb) + lane;
+    const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
+    const int zi = z.zbase + __float_as_int(tzb);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
-        const float fz = fmaf(fm, W.qz[h], W.pz[h]);
+        const float fz = fmaf(dz, z.q[h], z.f[h]);
         const float tz = floor_magic(fz);
         const int j = min(max(__float_as_int(tz) - __float_as_int(tzb), 0), 30);
         const float az = fz - magic_to_float(tz);
@@ -775,26 +1047,49 @@ __device__ __forceinline__ void pair_rows_step_adjoint(const PairRowsWindow &W, 
 }
 
 template <typename T, int R, bool CHECK, bool ADJ>
-__device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], int m0, int m1, const Ray3 &rc, int lane,
-                                                 T *vp, int nz, int sxp, int syp, float *runs, int zs0, int zs1)
+__device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], const ZSeg2 (&zs)[R], const float4 *track,
+                                                 int mz, int m0, int m1, int lane, T *vp, const FP3DParams &p, int sxp,
+                                                 int syp, float *runs)
 {
     constexpr int kUnroll = ADJ ? 2 : 4;
-    float fm = (float)m0;
+    for (int ms = m0; ms <= m1; ms += kFPSegment) {
+        const int me = min(ms + kFPSegment - 1, m1);
+        const TrackSeg ts = track_seg(track, ms, sxp, syp);
+        float dx = 0.0f, dz = (float)(ms - mz);
 #pragma unroll kUnroll
-    for (int m = m0; m <= m1; ++m, fm += 1.0f) {
-        const PlaneXY q = plane_xy(fm, rc, sxp, syp);
-        T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+        for (int m = ms; m <= me; ++m, dx += 1.0f, dz += 1.0f) {
+            const PlaneXY q = plane_xy(ts, dx, sxp, syp);
+            T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-            if constexpr (ADJ) {
-                pair_rows_step_adjoint(W[r], fm, lane, zs0, zs1, c, q, runs + 32 * r);
-            } else {
-                const T *const cr[4] = {c[0], c[1], c[2], c[3]};
-                pair_rows_step(W[r], fm, lane, nz, cr, q);
+            for (int r = 0; r < R; ++r) {
+                if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
+                if constexpr (ADJ) {
+                    pair_rows_step_adjoint(W[r], zs[r], dz, lane, p.zs0, p.zs1, c, q, runs + 32 * r);
+                } else {
+                    const T *const cr[4] = {c[0], c[1], c[2], c[3]};
+                    pair_rows_step(W[r], zs[r], dz, p.nz, cr, q);
+                }
             }
         }
     }
+}
+
+template <typename T, int R, bool ADJ>
+__device__ __forceinline__ void pair_rows_march(PairRowsWindow (&W)[R], const float4 *track, const float4 *zray,
+                                                int last_low, int mlo, int mhi, int clo, int chi, int lane, T *vp,
+                                                const FP3DParams &p, float *runs)
+{
+    const int sxp = p.nz + 2, syp = (p.nx + 2 * kFPPadXY) * (p.nz + 2);
+    const int mz = mlo + (mhi - mlo) / 2;
+    ZSeg2 zs[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        const bool hi = last_low >> r & 1;
+        zs[r] = zseg2(zray[(2 * r) * 32 + lane], zray[(2 * r + 1) * 32 + lane], hi ? p.pair_rows - 33 : 0, hi, lane, mz);
+    }
+    pair_rows_planes<T, R, true, ADJ>(W, zs, track, mz, mlo, clo - 1, lane, vp, p, sxp, syp, runs);
+    pair_rows_planes<T, R, false, ADJ>(W, zs, track, mz, clo, chi, lane, vp, p, sxp, syp, runs);
+    pair_rows_planes<T, R, true, ADJ>(W, zs, track, mz, max(chi + 1, clo), mhi, lane, vp, p, sxp, syp, runs);
 }
 
 template <typename T, int R>
@@ -802,23 +1097,21 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_kernel(const T 
                                                                         T *__restrict__ sino,
                                                                         const __grid_constant__ FP3DParams p, int b)
 {
+    __shared__ float4 zrays[kFPCWarps][2 * R * 32];
+    __shared__ float4 tracks[kFPCWarps][2];
     const int lane = threadIdx.x;
     const int k = blockIdx.y * kFPCWarps + threadIdx.y;
     const int v = blockIdx.x;
     if (k >= p.nu) return;  // whole warp
     const int WR = p.pair_rows;
     const int row0 = blockIdx.z * (R * WR);
-    Ray3 rc;
     PairRowsWindow W[R];
-    int mlo, mhi, clo, chi;
-    pair_rows_setup<R>(p, v, k, row0, lane, rc, W, mlo, mhi, clo, chi, -1.0f, (float)p.nz);
-    const int sxp = p.nz + 2, syp = (p.nx + 2) * (p.nz + 2);
-    if (mlo <= mhi) {
-        T *vq = const_cast<T *>(vp);  // read only on the forward path
-        pair_rows_planes<T, R, true, false>(W, mlo, clo - 1, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
-        pair_rows_planes<T, R, false, false>(W, clo, chi, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
-        pair_rows_planes<T, R, true, false>(W, max(chi + 1, clo), mhi, rc, lane, vq, p.nz, sxp, syp, nullptr, 0, 0);
-    }
+    int last_low, mlo, mhi, clo, chi;
+    pair_rows_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
+                       -1.0f, (float)p.nz);
+    if (mlo <= mhi)
+        pair_rows_march<T, R, false>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane,
+                                     const_cast<T *>(vp), p, nullptr);
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -837,6 +1130,8 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_adjoint_kernel(
                                                                                 int b)
 {
     __shared__ float runs[kFPCWarps][R * 32];
+    __shared__ float4 zrays[kFPCWarps][2 * R * 32];
+    __shared__ float4 tracks[kFPCWarps][2];
     const int lane = threadIdx.x;
     const int k = blockIdx.y * kFPCWarps + threadIdx.y;
     const int v = blockIdx.x;
@@ -847,10 +1142,10 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_adjoint_kernel(
     __syncwarp();
     const int WR = p.pair_rows;
     const int row0 = blockIdx.z * (R * WR);
-    Ray3 rc;
     PairRowsWindow W[R];
-    int mlo, mhi, clo, chi;
-    pair_rows_setup<R>(p, v, k, row0, lane, rc, W, mlo, mhi, clo, chi, (float)(p.zs0 - 1), (float)p.zs1);
+    int last_low, mlo, mhi, clo, chi;
+    pair_rows_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
+                       (float)(p.zs0 - 1), (float)p.zs1);
     if (mlo > mhi) return;  // whole warp: no sample of its rays touches the slab
 #pragma unroll
     for (int r = 0; r < R; ++r)
@@ -861,24 +1156,21 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_adjoint_kernel(
                               ? ray3d(p, v, k, l).w * sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k]
                               : 0.0f;
         }
-    const int sxp = p.nz + 2, syp = (p.nx + 2) * (p.nz + 2);
-    pair_rows_planes<float, R, true, true>(W, mlo, clo - 1, rc, lane, vp, p.nz, sxp, syp, run, p.zs0, p.zs1);
-    pair_rows_planes<float, R, false, true>(W, clo, chi, rc, lane, vp, p.nz, sxp, syp, run, p.zs0, p.zs1);
-    pair_rows_planes<float, R, true, true>(W, max(chi + 1, clo), mhi, rc, lane, vp, p.nz, sxp, syp, run, p.zs0,
-                                           p.zs1);
+    pair_rows_march<float, R, true>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp,
+                                    p, run);
 }
-
 
 // interior of the padded z-major array -> [z][y][x]
 __global__ void __launch_bounds__(256) relayout_unpad_kernel(const float *__restrict__ vp, float *__restrict__ vol,
                                                              int nx, int ny, int nz)
 {
     __shared__ float tile[32][33];
-    const int nxp = nx + 2, nzp = nz + 2;
+    const int nxp = nx + 2 * kFPPadXY, nzp = nz + 2;
     const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32, y = blockIdx.z;
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int x = x0 + i, z = z0 + threadIdx.x;
-        if (x < nx && z < nz) tile[i][threadIdx.x] = vp[((size_t)(y + 1) * nxp + x + 1) * nzp + z + 1];
+        if (x < nx && z < nz)
+            tile[i][threadIdx.x] = vp[((size_t)(y + kFPPadXY) * nxp + x + kFPPadXY) * nzp + z + 1];
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += 8) {
@@ -887,18 +1179,19 @@ __global__ void __launch_bounds__(256) relayout_unpad_kernel(const float *__rest
     }
 }
 
-// [z][y][x] -> [y+1][x+1][z+1] of a zero-padded (ny+2)(nx+2)(nz+2) array:
-// every padded element is written once (source voxel or 0)
+// [z][y][x] -> [y + P][x + P][z + 1] of the zero-padded (ny + 2P)(nx + 2P)
+// (nz + 2) array, P = kFPPadXY: every padded element is written once (source
+// voxel or 0)
 template <typename T>
 __global__ void __launch_bounds__(256) relayout_padded_kernel(const T *__restrict__ vol, T *__restrict__ vp, int nx,
                                                               int ny, int nz)
 {
     __shared__ T tile[32][33];
-    const int nxp = nx + 2, nzp = nz + 2;
+    const int nxp = nx + 2 * kFPPadXY, nzp = nz + 2;
     const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32, yp = blockIdx.z;
-    const int y = yp - 1;
+    const int y = yp - kFPPadXY;
     for (int i = threadIdx.y; i < 32; i += 8) {
-        const int z = z0 + i - 1, x = x0 + threadIdx.x - 1;
+        const int z = z0 + i - 1, x = x0 + threadIdx.x - kFPPadXY;
         const bool in = y >= 0 && y < ny && z >= 0 && z < nz && x >= 0 && x < nx;
         tile[i][threadIdx.x] = in ? vol[((size_t)z * ny + y) * nx + x] : to_storage<T>(0.0f);
     }
@@ -942,25 +1235,31 @@ __global__ void __launch_bounds__(kFP3DBlockX *kFP3DBlockY) fp3d_adjoint_kernel(
     const float y = r.w * y0s;
     int m0, m1;
     range3d(r, p, m0, m1);
+    if (m0 > m1) return;
+    const RayFF rf = ray3d_ff(p, v, k, l);
     float *V = vol + (size_t)b * p.nx * p.ny * p.nz;
     const size_t sxy = (size_t)p.nx * p.ny;
-    for (int m = m0; m <= m1; ++m) {
-        const float fm = (float)m;
-        const Axis ax = axis_taps(fmaf(fm, r.qx, r.px), p.nx);
-        const Axis ay = axis_taps(fmaf(fm, r.qy, r.py), p.ny);
-        const Axis az = axis_taps(fmaf(fm, r.qz, r.pz), p.nz);
+    for (int ms = m0; ms <= m1; ms += kFPSegment) {
+        const int me = min(ms + kFPSegment - 1, m1);
+        const Seg X = seg_at(rf.p[0], rf.q[0], ms), Y = seg_at(rf.p[1], rf.q[1], ms), Z = seg_at(rf.p[2], rf.q[2], ms);
+        for (int m = ms; m <= me; ++m) {
+            const float dm = (float)(m - ms);
+            const Axis ax = tap_axis(seg_tap(X, dm), p.nx);
+            const Axis ay = tap_axis(seg_tap(Y, dm), p.ny);
+            const Axis az = tap_axis(seg_tap(Z, dm), p.nz);
 #pragma unroll
-        for (int dz = 0; dz < 2; ++dz) {
-            const float wz = y * (dz ? az.w1 : az.w0);
-            if (wz == 0.0f) continue;
-            const size_t oz = (dz ? az.i1 : az.i0) * sxy;
+            for (int dz = 0; dz < 2; ++dz) {
+                const float wz = y * (dz ? az.w1 : az.w0);
+                if (wz == 0.0f) continue;
+                const size_t oz = (dz ? az.i1 : az.i0) * sxy;
 #pragma unroll
-            for (int dy = 0; dy < 2; ++dy) {
-                const float wzy = wz * (dy ? ay.w1 : ay.w0);
-                if (wzy == 0.0f) continue;
-                float *row = V + oz + (size_t)(dy ? ay.i1 : ay.i0) * p.nx;
-                if (ax.w0 != 0.0f) atomicAdd(row + ax.i0, wzy * ax.w0);
-                if (ax.w1 != 0.0f) atomicAdd(row + ax.i1, wzy * ax.w1);
+                for (int dy = 0; dy < 2; ++dy) {
+                    const float wzy = wz * (dy ? ay.w1 : ay.w0);
+                    if (wzy == 0.0f) continue;
+                    float *row = V + oz + (size_t)(dy ? ay.i1 : ay.i0) * p.nx;
+                    if (ax.w0 != 0.0f) atomicAdd(row + ax.i0, wzy * ax.w0);
+                    if (ax.w1 != 0.0f) atomicAdd(row + ax.i1, wzy * ax.w1);
+                }
             }
         }
     }
@@ -1116,7 +1415,7 @@ cudaError_t launch_fp3d_zmajor(const void *vz, void *sino, int b, const FP3DPara
 
 cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt, cudaStream_t s)
 {
-    dim3 block(32, 8), grid((nx + 2 + 31) / 32, (nz + 2 + 31) / 32, ny + 2);
+    dim3 block(32, 8), grid((nx + 2 * kFPPadXY + 31) / 32, (nz + 2 + 31) / 32, ny + 2 * kFPPadXY);
     switch (dt) {
     case PYRO_F32:
         relayout_padded_kernel<float><<<grid, block, 0, s>>>((const float *)vol, (float *)vp, nx, ny, nz);

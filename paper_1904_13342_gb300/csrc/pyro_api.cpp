@@ -125,16 +125,51 @@ void fill_fp2d(const Geo2D &G, int v0, int nvw, FP2DParams &p)
     p.views_total = (int)G.beta.size();
     p.fan = G.fan;
     p.M = G.M;
-    p.inv_sx = (float)(1.0 / G.sx);
-    p.inv_sy = (float)(1.0 / G.sy);
-    p.cx = (float)(0.5 * (G.nx - 1));
-    p.cy = (float)(0.5 * (G.ny - 1));
     p.su = (float)G.su;
-    p.cu = (float)(0.5 * (G.nu - 1));
-    p.sid = (float)G.sid;
+    const double cu = 0.5 * (G.nu - 1), cx = 0.5 * (G.nx - 1), cy = 0.5 * (G.ny - 1);
+    p.cu = (float)cu;
     p.sdd = (float)G.sdd;
     p.dt = (float)G.step;
-    for (int v = 0; v < nvw; ++v) p.dir[v] = make_float2((float)std::cos(G.beta[v0 + v]), (float)std::sin(G.beta[v0 + v]));
+    auto put = [](float &hi, float &lo, double x) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+    };
+    for (int v = 0; v < nvw; ++v) {
+        const double b = G.beta[v0 + v], c = std::cos(b), sn = std::sin(b);
+        p.dir[v] = make_float2((float)c, (float)sn);
+        // u = (k - cu) su; parallel: a = u e_u, g = c; fan: t = u / SDD,
+        // a = SID t e_u, g = c + t e_u; e_u = (-sin b, cos b)
+        double a0x, akx, a0y, aky, g0x, gkx, g0y, gky;
+        if (G.fan) {
+            const double t0 = -cu * G.su / G.sdd, tk = G.su / G.sdd;
+            a0x = -G.sid * t0 * sn;
+            akx = -G.sid * tk * sn;
+            a0y = G.sid * t0 * c;
+            aky = G.sid * tk * c;
+            g0x = c - t0 * sn;
+            gkx = -tk * sn;
+            g0y = sn + t0 * c;
+            gky = tk * c;
+        } else {
+            a0x = cu * G.su * sn;
+            akx = -G.su * sn;
+            a0y = -cu * G.su * c;
+            aky = G.su * c;
+            g0x = c;
+            gkx = 0.0;
+            g0y = sn;
+            gky = 0.0;
+        }
+        FP2DLine &h = p.ln[v], &l = p.lnlo[v];
+        put(h.p0x, l.p0x, cx + a0x / G.sx);
+        put(h.pkx, l.pkx, akx / G.sx);
+        put(h.p0y, l.p0y, cy + a0y / G.sy);
+        put(h.pky, l.pky, aky / G.sy);
+        put(h.q0x, l.q0x, g0x * G.step / G.sx);
+        put(h.qkx, l.qkx, gkx * G.step / G.sx);
+        put(h.q0y, l.q0y, g0y * G.step / G.sy);
+        put(h.qky, l.qky, gky * G.step / G.sy);
+    }
 }
 
 // k(X) - cu and depth for pixel (i, j), as affine maps divided by SID (fan)
@@ -310,6 +345,7 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
     p.cy = (float)(0.5 * (G.ny - 1));
     p.cz = (float)(0.5 * (G.nz - 1));
     p.dt = (float)G.step;
+    p.dt_lo = (float)(G.step - (double)p.dt);
     const double inv_s[3] = {1.0 / G.sx, 1.0 / G.sy, 1.0 / G.sz};
     p.column_shared = 1;
     p.pair_rows = 64;
@@ -345,20 +381,24 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
             K01s = 0.0;
         }
         // q = K^-1 (k, l, 1) / K22 scaled so that q_z = 1
-        ConeFPView &o = p.v[v];
+        ConeFPView &o = p.v[v], &ol = p.vlo[v];
+        auto put = [](float &hi, float &lo, double x) {
+            hi = (float)x;
+            lo = (float)(x - (double)hi);
+        };
         const double b0 = 1.0 / K11, b2 = -K12 / K11;
-        o.a0 = (float)(1.0 / K00);
-        o.a1 = (float)(-K01s * b0 / K00);
-        o.a2 = (float)((-K02 - K01 * b2) / K00);
-        o.b0 = (float)b0;
-        o.b2 = (float)b2;
+        put(o.a0, ol.a0, 1.0 / K00);
+        put(o.a1, ol.a1, -K01s * b0 / K00);
+        put(o.a2, ol.a2, (-K02 - K01 * b2) / K00);
+        put(o.b0, ol.b0, b0);
+        put(o.b2, ol.b2, b2);
         (void)K22;
-        o.s1 = (float)dot(r0, S);
-        o.s2 = (float)dot(r1, S);
-        o.s3 = (float)dot(r2, S);
+        put(o.s1, ol.s1, dot(r0, S));
+        put(o.s2, ol.s2, dot(r1, S));
+        put(o.s3, ol.s3, dot(r2, S));
         const double *R[3] = {r0, r1, r2};
         for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) o.W[3 * a + b] = (float)(R[b][a] * inv_s[a]);
+            for (int b = 0; b < 3; ++b) put(o.W[3 * a + b], ol.W[3 * a + b], R[b][a] * inv_s[a]);
         // one row step moves a sample by b0 W_zy w voxels in z at depth w; the
         // column kernel needs 31 steps below 29.5 voxels over the sampled depths
         const double w_far = -dot(r2, S) + G.M * G.step;
@@ -562,8 +602,8 @@ int fp2d(bool fan, const void *vol, void *sino, int batch, const pyro_geom2d *g,
                                      std::min(65535, batch - b0), G.nx, G.ny, dt, as_stream(stream)));
     const int V = (int)G.beta.size();
     static thread_local FP2DParams p;
-    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
-        const int nvw = std::min(kMaxViews2D, V - v0);
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsFP2D) {
+        const int nvw = std::min(kMaxViewsFP2D, V - v0);
         fill_fp2d(G, v0, nvw, p);
         for (int b0 = 0; b0 < batch; b0 += 65535) {
             const int nb = std::min(65535, batch - b0);
@@ -596,8 +636,8 @@ int fp2d_adjoint(bool fan, const void *sino, void *vol, int batch, const pyro_ge
     PYRO_CUDA(cudaMemsetAsync(vol, 0, vox_bytes * batch, as_stream(stream)));
     if (work) PYRO_CUDA(cudaMemsetAsync(work, 0, vox_bytes * batch, as_stream(stream)));
     static thread_local FP2DParams p;
-    for (int v0 = 0; v0 < V; v0 += kMaxViews2D) {
-        const int nvw = std::min(kMaxViews2D, V - v0);
+    for (int v0 = 0; v0 < V; v0 += kMaxViewsFP2D) {
+        const int nvw = std::min(kMaxViewsFP2D, V - v0);
         fill_fp2d(G, v0, nvw, p);
         for (int b0 = 0; b0 < batch; b0 += 65535) {
             const int nb = std::min(65535, batch - b0);
@@ -708,7 +748,7 @@ int fp3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtyp
 // view allows them and the padded copy is int-indexable.
 int column_path(const Geo3D &G, FP3DParams &p, bool &column)
 {
-    const size_t padded = (size_t)(G.nx + 2) * (G.ny + 2) * (G.nz + 2);
+    const size_t padded = fp_padded_elems(G.nx, G.ny, G.nz);
     const int V = (int)G.beta.size();
     column = padded < (size_t)INT32_MAX;
     for (int v0 = 0; v0 < V && column; v0 += kMaxViewsConeFP) {
@@ -726,7 +766,7 @@ int fp3d_staged(const void *vol, void *sino, int batch, const pyro_geom3d *g, vo
     Geo3D G;
     if (int e = prep3d(g, G)) return e;
     const size_t vox = (size_t)G.nx * G.ny * G.nz;
-    const size_t padded = (size_t)(G.nx + 2) * (G.ny + 2) * (G.nz + 2);
+    const size_t padded = fp_padded_elems(G.nx, G.ny, G.nz);
     const size_t need = padded * elem_size(dt);
     if (work_bytes < need || work == nullptr || !aligned16(work))
         return fail(PYRO_EWORKSPACE, "the staged forward projector needs a 16-byte aligned workspace of %zu bytes "
@@ -766,7 +806,7 @@ int fp3d_adjoint_staged(const void *sino, void *vol, int batch, const pyro_geom3
     Geo3D G;
     if (int e = prep3d(g, G)) return e;
     const size_t vox = (size_t)G.nx * G.ny * G.nz;
-    const size_t need = (size_t)(G.nx + 2) * (G.ny + 2) * (G.nz + 2) * sizeof(float);
+    const size_t need = fp_padded_elems(G.nx, G.ny, G.nz) * sizeof(float);
     if (work_bytes < need || work == nullptr || !aligned16(work))
         return fail(PYRO_EWORKSPACE, "the staged FP adjoint needs a 16-byte aligned workspace of %zu bytes (got %zu)",
                     need, work_bytes);
@@ -1033,7 +1073,7 @@ PYRO_API int pyro_cone_projection_matrices(const pyro_geom3d *g, double *out)
 PYRO_API size_t pyro_fp_cone3d_workspace_bytes(const pyro_geom3d *g, pyro_dtype dtype)
 {
     if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0 || !valid_dtype(dtype)) return 0;
-    return (size_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2) * elem_size(dtype);
+    return fp_padded_elems(g->nx, g->ny, g->nz) * elem_size(dtype);
 }
 
 // ---- texture mode (the paper's fast mode, with its second copy) ----------
@@ -1233,7 +1273,7 @@ PYRO_API int pyro_fpT_cone3d(const void *sino, void *vol, int batch, const pyro_
 PYRO_API size_t pyro_fpT_cone3d_workspace_bytes(const pyro_geom3d *g)
 {
     if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return 0;
-    return (size_t)(g->nx + 2) * (g->ny + 2) * (g->nz + 2) * sizeof(float);
+    return fp_padded_elems(g->nx, g->ny, g->nz) * sizeof(float);
 }
 
 PYRO_API int pyro_fpT_cone3d_ws(const void *sino, void *vol, int batch, const pyro_geom3d *g, void *workspace,

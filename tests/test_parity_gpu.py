@@ -288,11 +288,11 @@ def test_fp_adjoint_cone_staged_large_footprint():
     ref = oracle.fpT_cone3d(f32(y), shape, spacing, P)
     assert rel(got, ref) < 1e-5
     assert rel(got, host(B.pyro_fpT_cone3d(to_dev(y), g))) < 1e-6
-    # noise data: the sample positions are absolute FP32 voxel coordinates
-    # (up to ~720 here), whose rounding noise data lifts to ~2e-5
+    # noise data, the input that shows sample-position rounding (absolute FP32
+    # coordinates near index 500 gave 7e-6 here; anchored ones 3e-7)
     noise = ph.random_sinogram((views, *det), 43)
     assert rel(host(B.pyro_fpT_cone3d_ws(to_dev(noise), g)),
-               oracle.fpT_cone3d(f32(noise), shape, spacing, P)) < 1e-4
+               oracle.fpT_cone3d(f32(noise), shape, spacing, P)) < 1e-5
 
 
 def test_fp_cone_staged_workspace_checks():
