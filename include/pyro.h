@@ -202,6 +202,19 @@ PYRO_API size_t pyro_fp_cone3d_workspace_bytes(const pyro_geom3d *g, pyro_dtype 
 PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
                                size_t workspace_bytes, pyro_dtype dtype, void *stream);
 
+/* --- The same staged forward projection with the workspace copy held in
+ * `storage` while the volume and the sinogram stay in `dtype`: an FP32
+ * volume projected from an FP16 or BF16 copy (half the workspace; the
+ * volume's values rounded to 16 bits, accumulation along the rays in FP32,
+ * an FP32 sinogram), the north-star's half-storage pattern for an FP32
+ * iterate (Section "The Operator as a Layer": the copy is the paper's
+ * memory-for-speed trade).  storage == dtype is pyro_fp_cone3d_ws.  The
+ * workspace needs pyro_fp_cone3d_workspace_bytes(g, storage) bytes.
+ * PYRO_EUNSUPPORTED for storage != dtype with a non-FP32 volume or a
+ * trajectory other than circular-type (detector v axis along z). */
+PYRO_API int pyro_fp_cone3d_ws_storage(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
+                                       size_t workspace_bytes, pyro_dtype dtype, pyro_dtype storage, void *stream);
+
 /* --- Exact adjoint A^T of the forward projectors (the gradient of the FP
  * layer, Section "The Known Operator": the gradient of A is A^T).  Scatters
  * step * y * (interpolation weights) into the volume with FP32 atomics, so

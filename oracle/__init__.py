@@ -61,6 +61,8 @@ def _load():
                 "oracle_fp_cone3d": [_PD, _I, _I, _I, _D, _D, _D, _I, _I, _I, _PD, _D, _PD],
                 "oracle_fp_cone3d_rays": [_PD, _I, _I, _I, _D, _D, _D, _PD, _D, _I, _PI, _PI, _PI, _PD],
                 "oracle_fpT_cone3d": [_PD, _I, _I, _I, _D, _D, _D, _I, _I, _I, _PD, _D, _PD],
+                "oracle_fpT_cone3d_voxels": [_PD, _I, _I, _I, _D, _D, _D, _I, _I, _I, _PD, _D, _I, _PI, _PI, _PI,
+                                             _PD],
                 "oracle_bp_par2d": [_PD, _I, _I, _D, _D, _I, _D, _I, _PD, _D, _PD],
                 "oracle_bp_fan2d": [_PD, _I, _I, _D, _D, _I, _D, _I, _PD, _D, _D, _I, _D, _PD],
                 "oracle_bpT_par2d": [_PD, _I, _I, _D, _D, _I, _D, _I, _PD, _D, _PD],
@@ -271,6 +273,23 @@ def fpT_cone3d(sino, shape, spacing, pmats, step=None):
     dt = default_step(spacing) if step is None else step
     out = np.empty((nz, ny, nx))
     _load().oracle_fpT_cone3d(_p(sino), nx, ny, nz, sx, sy, sz, nu, nv, P.shape[0], _p(P), dt, _p(out))
+    return out
+
+
+def fpT_cone3d_voxels(sino, shape, spacing, pmats, ii, jj, kk, step=None):
+    """The exact adjoint A^T y at the voxels (ii[r], jj[r], kk[r]) only, from
+    its definition (the rays and planes whose samples fall in each voxel's
+    interpolation support); equal to fpT_cone3d there."""
+    sino = _f64(sino)
+    nz, ny, nx = shape
+    sz, sy, sx = spacing
+    nvw, nv, nu = sino.shape
+    P = _f64(pmats)
+    dt = default_step(spacing) if step is None else step
+    i, j, k = _i32(ii), _i32(jj), _i32(kk)
+    out = np.empty(i.size)
+    _load().oracle_fpT_cone3d_voxels(_p(sino), nx, ny, nz, sx, sy, sz, nu, nv, nvw, _p(P), dt, i.size, _p(i), _p(j),
+                                     _p(k), _p(out))
     return out
 
 

@@ -394,6 +394,84 @@ void oracle_fpT_cone3d(const double *sino, int nx, int ny, int nz, double sx, do
     }
 }
 
+/* The exact adjoint at a list of voxels (i, j, kz), from the definition:
+ * (A^T y)_v = sum over views and detector pixels (k, l) of y(k, l) dt |g|
+ * sum_m t_v(S + w_m g), t_v the trilinear tent of voxel v (the weight the
+ * interpolation gives v at a point).  t_v vanishes outside the box of half
+ * width one voxel around v, so per view only the pixels whose ray meets that
+ * box contribute: those (k, l) inside the projection of the box, which lies
+ * in the bounding rectangle of its eight projected corners (positive depth);
+ * along such a ray only the planes w_m inside the box's slab on every axis
+ * contribute.  Every other term of the sum is zero. */
+void oracle_fpT_cone3d_voxels(const double *sino, int nx, int ny, int nz, double sx, double sy, double sz, int nu,
+                              int nv, int n_views, const double *pmats, double dt, int n_vox, const int *ii,
+                              const int *jj, const int *kk, double *out)
+{
+    const double T = support_radius3(nx, ny, nz, sx, sy, sz);
+    const long M = (long)ceil(T / dt);
+    const double s[3] = {sx, sy, sz};
+    const double half[3] = {0.5 * (nx - 1), 0.5 * (ny - 1), 0.5 * (nz - 1)};
+#pragma omp parallel for schedule(dynamic, 1)
+    for (int r = 0; r < n_vox; ++r) {
+        const int v[3] = {ii[r], jj[r], kk[r]};
+        double Xv[3];
+        for (int a = 0; a < 3; ++a) Xv[a] = (v[a] - half[a]) * s[a];
+        double acc = 0.0;
+        for (int j = 0; j < n_views; ++j) {
+            double Pn[12], Minv[3][3], S[3];
+            normalise_pmat(pmats + 12 * (size_t)j, Pn);
+            pmat_inverse(Pn, Minv, S);
+            double kmin = 1e300, kmax = -1e300, lmin = 1e300, lmax = -1e300;
+            for (int c = 0; c < 8; ++c) {
+                double X[3];
+                for (int a = 0; a < 3; ++a) X[a] = Xv[a] + (((c >> a) & 1) ? s[a] : -s[a]);
+                const double x = Pn[0] * X[0] + Pn[1] * X[1] + Pn[2] * X[2] + Pn[3];
+                const double y = Pn[4] * X[0] + Pn[5] * X[1] + Pn[6] * X[2] + Pn[7];
+                const double w = Pn[8] * X[0] + Pn[9] * X[1] + Pn[10] * X[2] + Pn[11];
+                kmin = fmin(kmin, x / w);
+                kmax = fmax(kmax, x / w);
+                lmin = fmin(lmin, y / w);
+                lmax = fmax(lmax, y / w);
+            }
+            const int k0 = (int)fmax(0.0, ceil(kmin)), k1 = (int)fmin(nu - 1.0, floor(kmax));
+            const int l0 = (int)fmax(0.0, ceil(lmin)), l1 = (int)fmin(nv - 1.0, floor(lmax));
+            for (int l = l0; l <= l1; ++l)
+                for (int k = k0; k <= k1; ++k) {
+                    const double y = sino[IDX3(j, l, k, nv, nu)];
+                    if (y == 0.0) continue;
+                    double g[3];
+                    cone_ray(Minv, (double)k, (double)l, g);
+                    /* planes whose sample lies in the box on every axis */
+                    double wlo = -1e300, whi = 1e300;
+                    for (int a = 0; a < 3; ++a) {
+                        if (g[a] != 0.0) {
+                            const double t1 = (Xv[a] - s[a] - S[a]) / g[a], t2 = (Xv[a] + s[a] - S[a]) / g[a];
+                            wlo = fmax(wlo, fmin(t1, t2));
+                            whi = fmin(whi, fmax(t1, t2));
+                        } else if (fabs(S[a] - Xv[a]) >= s[a]) {
+                            wlo = 1.0;
+                            whi = -1.0;
+                        }
+                    }
+                    const long m0 = (long)fmax((double)-M, floor((wlo - Pn[11]) / dt));
+                    const long m1 = (long)fmin((double)M, ceil((whi - Pn[11]) / dt));
+                    double tsum = 0.0;
+                    for (long m = m0; m <= m1; ++m) {
+                        const double w = Pn[11] + (double)m * dt;
+                        double t = 1.0;
+                        for (int a = 0; a < 3; ++a) {
+                            const double d = fabs((S[a] + w * g[a]) / s[a] + half[a] - v[a]);
+                            t *= d < 1.0 ? 1.0 - d : 0.0;
+                        }
+                        tsum += t;
+                    }
+                    acc += y * dt * sqrt(g[0] * g[0] + g[1] * g[1] + g[2] * g[2]) * tsum;
+                }
+        }
+        out[r] = acc;
+    }
+}
+
 /* ------------------------------------------------------------------------ */
 /* Voxel-driven back-projection (Section "The Operator as a Layer")         */
 /*   x(X) = scale * sum_j omega_j(X) * L(y_j; k_j(X)[, l_j(X)])             */

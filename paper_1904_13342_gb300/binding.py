@@ -51,6 +51,7 @@ _SIGS = {
     "pyro_fp_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
     "pyro_fp_cone3d_workspace_bytes": [_G3, _I],
     "pyro_fp_cone3d_ws": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _VP],
+    "pyro_fp_cone3d_ws_storage": [_VP, _VP, _I, _G3, _VP, _SZ, _I, _I, _VP],
     "pyro_fpT_par2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fpT_fan2d": [_VP, _VP, _I, _G2, _I, _VP],
     "pyro_fpT_cone3d": [_VP, _VP, _I, _G3, _I, _VP],
@@ -380,6 +381,25 @@ def pyro_fp_cone3d_ws(vol: torch.Tensor, g: ConeGeometry3D, workspace: Optional[
     with torch.cuda.device(v.device):
         _check(lib().pyro_fp_cone3d_ws(_ptr(v), _ptr(o), v.shape[0], ctypes.byref(cg), _ptr(workspace),
                                        workspace.numel() * workspace.element_size(), _DTYPES[v.dtype], _stream(v)))
+    return o[0] if squeeze and out is None else o
+
+
+def pyro_fp_cone3d_ws_storage(vol: torch.Tensor, g: ConeGeometry3D, storage: torch.dtype,
+                              workspace: Optional[torch.Tensor] = None,
+                              out: Optional[torch.Tensor] = None) -> torch.Tensor:
+    """Cone-beam FP of an FP32 volume from a workspace copy held in
+    `storage` (torch.float16 or torch.bfloat16); FP32 sinogram."""
+    v, squeeze = _batched(_dev(vol, "volume"), 3, "volume")
+    _shape_check(v, g.volume_shape, "volume")
+    cg = g.to_c()
+    need = lib().pyro_fp_cone3d_workspace_bytes(ctypes.byref(cg), _DTYPES[storage])
+    if workspace is None:
+        workspace = torch.empty(max(need, 16), dtype=torch.uint8, device=v.device)
+    o = _out(v, g.sinogram_shape) if out is None else _dev(out, "out")
+    with torch.cuda.device(v.device):
+        _check(lib().pyro_fp_cone3d_ws_storage(_ptr(v), _ptr(o), v.shape[0], ctypes.byref(cg), _ptr(workspace),
+                                               workspace.numel() * workspace.element_size(), _DTYPES[v.dtype],
+                                               _DTYPES[storage], _stream(v)))
     return o[0] if squeeze and out is None else o
 
 

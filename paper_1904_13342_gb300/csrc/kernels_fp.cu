@@ -688,6 +688,102 @@ __device__ __forceinline__ void column_step_adjoint(const ColumnWindow &W, const
     }
 }
 
+// Two consecutive depth planes (dx, dx + 1) of the column's track at once:
+// the f32x2 form of plane_xy, weights and padded indices of both planes.
+struct PlanePair {
+    f32x2 w00, w10, w01, w11;
+    int col0, col1;
+};
+
+__device__ __forceinline__ PlanePair plane_pair(const TrackSeg &s, float dx, int sxp, int syp)
+{
+    const f32x2 MAGIC = pk2(kFloorMagic, kFloorMagic), ONE = pk2(1.0f, 1.0f);
+    const f32x2 D = pk2(dx, dx + 1.0f);
+    const f32x2 FX = fma2(D, pk2(s.xq, s.xq), pk2(s.xf, s.xf)), FY = fma2(D, pk2(s.yq, s.yq), pk2(s.yf, s.yf));
+    const f32x2 TX = add2_rm(FX, MAGIC), TY = add2_rm(FY, MAGIC);
+    const f32x2 AX = sub2(FX, sub2(TX, MAGIC)), AY = sub2(FY, sub2(TY, MAGIC));
+    const f32x2 BX = sub2(ONE, AX), BY = sub2(ONE, AY);
+    PlanePair q;
+    q.w00 = mul2(BX, BY);
+    q.w10 = mul2(AX, BY);
+    q.w01 = mul2(BX, AY);
+    q.w11 = mul2(AX, AY);
+    float tx0, tx1, ty0, ty1;
+    upk2(TX, tx0, tx1);
+    upk2(TY, ty0, ty1);
+    q.col0 = (int)((unsigned)s.col0 + (unsigned)__float_as_int(ty0) * (unsigned)syp +
+                   (unsigned)__float_as_int(tx0) * (unsigned)sxp);
+    q.col1 = (int)((unsigned)s.col0 + (unsigned)__float_as_int(ty1) * (unsigned)syp +
+                   (unsigned)__float_as_int(tx1) * (unsigned)sxp);
+    return q;
+}
+
+// One window on two consecutive planes: as column_step for each plane, the
+// arithmetic in f32x2 pairs (plane m in the low half, m + 1 in the high)
+template <typename T>
+__device__ __forceinline__ void column_step_pair(f32x2 &acc, const ZSeg &z, float dz, int nz, const T *vp,
+                                                 const PlanePair &q, int sxp, int syp)
+{
+    const f32x2 MAGIC = pk2(kFloorMagic, kFloorMagic);
+    const f32x2 D = pk2(dz, dz + 1.0f);
+    const f32x2 TB = add2_rm(fma2(D, pk2(z.qb, z.qb), pk2(z.fb, z.fb)), MAGIC);
+    float tb0, tb1;
+    upk2(TB, tb0, tb1);
+    const int zi0 = min(max(z.zbase + __float_as_int(tb0), -1), nz) + q.col0;
+    const int zi1 = min(max(z.zbase + __float_as_int(tb1), -1), nz) + q.col1;
+    const f32x2 A = pk2(ld(vp + zi0), ld(vp + zi1));
+    const f32x2 B = pk2(ld(vp + zi0 + sxp), ld(vp + zi1 + sxp));
+    const f32x2 C = pk2(ld(vp + zi0 + syp), ld(vp + zi1 + syp));
+    const f32x2 E = pk2(ld(vp + zi0 + sxp + syp), ld(vp + zi1 + sxp + syp));
+    const f32x2 G = fma2(q.w11, E, fma2(q.w01, C, fma2(q.w10, B, mul2(q.w00, A))));
+    float g0, g1;
+    upk2(G, g0, g1);
+    const f32x2 FZ = fma2(D, pk2(z.q, z.q), pk2(z.f, z.f));
+    const f32x2 TZ = add2_rm(FZ, MAGIC);
+    float tz0, tz1;
+    upk2(TZ, tz0, tz1);
+    const int j0 = __float_as_int(tz0) - __float_as_int(tb0), j1 = __float_as_int(tz1) - __float_as_int(tb1);
+    const unsigned full = 0xffffffffu;
+    const f32x2 G0 = pk2(__shfl_sync(full, g0, j0), __shfl_sync(full, g1, j1));
+    const f32x2 G1 = pk2(__shfl_sync(full, g0, j0 + 1), __shfl_sync(full, g1, j1 + 1));
+    acc = add2(acc, fma2(sub2(FZ, sub2(TZ, MAGIC)), sub2(G1, G0), G0));
+}
+
+// the main phase of the forward: every window active, planes in pairs
+template <typename T, int R>
+__device__ __forceinline__ void column_planes_paired(ColumnWindow (&W)[R], const ZSeg (&zs)[R], const float4 *track,
+                                                     int mz, int m0, int m1, const T *vp, const FP3DParams &p,
+                                                     int sxp, int syp)
+{
+    f32x2 acc[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) acc[r] = pk2(0.0f, 0.0f);
+    for (int ms = m0; ms <= m1; ms += kFPSegment) {
+        const int me = min(ms + kFPSegment - 1, m1);
+        const TrackSeg ts = track_seg(track, ms, sxp, syp);
+        float dx = 0.0f, dz = (float)(ms - mz);
+        int m = ms;
+#pragma unroll 2
+        for (; m + 1 <= me; m += 2, dx += 2.0f, dz += 2.0f) {
+            const PlanePair q = plane_pair(ts, dx, sxp, syp);
+#pragma unroll
+            for (int r = 0; r < R; ++r) column_step_pair(acc[r], zs[r], dz, p.nz, vp, q, sxp, syp);
+        }
+        if (m <= me) {  // an odd plane left in the segment
+            const PlaneXY q = plane_xy(ts, dx, sxp, syp);
+            const T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+#pragma unroll
+            for (int r = 0; r < R; ++r) column_step(W[r], zs[r], dz, p.nz, c, q);
+        }
+    }
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+        float a0, a1;
+        upk2(acc[r], a0, a1);
+        W[r].acc += a0 + a1;
+    }
+}
+
 // Depth planes m0..m1 of all R windows, the track re-anchored every
 // kFPSegment planes.  CHECK skips the windows whose rows cannot touch the
 // volume on a plane (outside the planes every window reaches; elsewhere the
@@ -831,13 +927,16 @@ __device__ __forceinline__ void column_march(ColumnWindow (&W)[R], const float4 
 #pragma unroll
     for (int r = 0; r < R; ++r) zs[r] = zseg(zray[32 * r + lane], (last_low >> r & 1) ? 31 : 0, lane, mz);
     column_planes<T, R, true, ADJ>(W, zs, track, mz, mlo, clo - 1, lane, vp, p, sxp, syp, runs);
-    column_planes<T, R, false, ADJ>(W, zs, track, mz, clo, chi, lane, vp, p, sxp, syp, runs);
+    if constexpr (ADJ)
+        column_planes<T, R, false, ADJ>(W, zs, track, mz, clo, chi, lane, vp, p, sxp, syp, runs);
+    else
+        column_planes_paired<T, R>(W, zs, track, mz, clo, chi, vp, p, sxp, syp);
     column_planes<T, R, true, ADJ>(W, zs, track, mz, max(chi + 1, clo), mhi, lane, vp, p, sxp, syp, runs);
 }
 
-template <typename T, int R>
+template <typename T, typename TO, int R>
 __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__restrict__ vp,
-                                                                     T *__restrict__ sino,
+                                                                     TO *__restrict__ sino,
                                                                      const __grid_constant__ FP3DParams p, int b)
 {
     __shared__ float4 zrays[kFPCWarps][R * 32];
@@ -859,7 +958,7 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__
         const int l = row0 + 32 * r + lane;
         if (l < p.nv)
             sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] =
-                to_storage<T>(ray3d(p, v, k, l).w * W[r].acc);
+                to_storage<TO>(ray3d(p, v, k, l).w * W[r].acc);
     }
 }
 
@@ -1092,9 +1191,9 @@ __device__ __forceinline__ void pair_rows_march(PairRowsWindow (&W)[R], const fl
     pair_rows_planes<T, R, true, ADJ>(W, zs, track, mz, max(chi + 1, clo), mhi, lane, vp, p, sxp, syp, runs);
 }
 
-template <typename T, int R>
+template <typename T, typename TO, int R>
 __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_kernel(const T *__restrict__ vp,
-                                                                        T *__restrict__ sino,
+                                                                        TO *__restrict__ sino,
                                                                         const __grid_constant__ FP3DParams p, int b)
 {
     __shared__ float4 zrays[kFPCWarps][2 * R * 32];
@@ -1119,7 +1218,7 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_kernel(const T 
             const int l = row0 + r * WR + 32 * h + lane;
             if (l < p.nv && 32 * h + lane < WR)
                 sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] =
-                    to_storage<T>(ray3d(p, v, k, l).w * W[r].acc[h]);
+                    to_storage<TO>(ray3d(p, v, k, l).w * W[r].acc[h]);
         }
 }
 
@@ -1181,9 +1280,9 @@ __global__ void __launch_bounds__(256) relayout_unpad_kernel(const float *__rest
 
 // [z][y][x] -> [y + P][x + P][z + 1] of the zero-padded (ny + 2P)(nx + 2P)
 // (nz + 2) array, P = kFPPadXY: every padded element is written once (source
-// voxel or 0)
-template <typename T>
-__global__ void __launch_bounds__(256) relayout_padded_kernel(const T *__restrict__ vol, T *__restrict__ vp, int nx,
+// voxel or 0), converted from the volume's type TI to the copy's type T
+template <typename TI, typename T>
+__global__ void __launch_bounds__(256) relayout_padded_kernel(const TI *__restrict__ vol, T *__restrict__ vp, int nx,
                                                               int ny, int nz)
 {
     __shared__ T tile[32][33];
@@ -1193,7 +1292,7 @@ __global__ void __launch_bounds__(256) relayout_padded_kernel(const T *__restric
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int z = z0 + i - 1, x = x0 + threadIdx.x - kFPPadXY;
         const bool in = y >= 0 && y < ny && z >= 0 && z < nz && x >= 0 && x < nx;
-        tile[i][threadIdx.x] = in ? vol[((size_t)z * ny + y) * nx + x] : to_storage<T>(0.0f);
+        tile[i][threadIdx.x] = to_storage<T>(in ? to_float<TI>(vol[((size_t)z * ny + y) * nx + x]) : 0.0f);
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += 8) {
@@ -1413,21 +1512,25 @@ cudaError_t launch_fp3d_zmajor(const void *vz, void *sino, int b, const FP3DPara
     return cudaGetLastError();
 }
 
-cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt, cudaStream_t s)
+// the volume's type and the copy's: the same type, or FP32 into FP16 / BF16
+cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt,
+                                   pyro_dtype storage, cudaStream_t s)
 {
     dim3 block(32, 8), grid((nx + 2 * kFPPadXY + 31) / 32, (nz + 2 + 31) / 32, ny + 2 * kFPPadXY);
-    switch (dt) {
-    case PYRO_F32:
-        relayout_padded_kernel<float><<<grid, block, 0, s>>>((const float *)vol, (float *)vp, nx, ny, nz);
-        break;
-    case PYRO_F16:
-        relayout_padded_kernel<__half><<<grid, block, 0, s>>>((const __half *)vol, (__half *)vp, nx, ny, nz);
-        break;
-    case PYRO_BF16:
-        relayout_padded_kernel<__nv_bfloat16>
+    if (dt == PYRO_F32 && storage == PYRO_F32)
+        relayout_padded_kernel<float, float><<<grid, block, 0, s>>>((const float *)vol, (float *)vp, nx, ny, nz);
+    else if (dt == PYRO_F32 && storage == PYRO_F16)
+        relayout_padded_kernel<float, __half><<<grid, block, 0, s>>>((const float *)vol, (__half *)vp, nx, ny, nz);
+    else if (dt == PYRO_F32 && storage == PYRO_BF16)
+        relayout_padded_kernel<float, __nv_bfloat16>
+            <<<grid, block, 0, s>>>((const float *)vol, (__nv_bfloat16 *)vp, nx, ny, nz);
+    else if (dt == PYRO_F16 && storage == PYRO_F16)
+        relayout_padded_kernel<__half, __half><<<grid, block, 0, s>>>((const __half *)vol, (__half *)vp, nx, ny, nz);
+    else if (dt == PYRO_BF16 && storage == PYRO_BF16)
+        relayout_padded_kernel<__nv_bfloat16, __nv_bfloat16>
             <<<grid, block, 0, s>>>((const __nv_bfloat16 *)vol, (__nv_bfloat16 *)vp, nx, ny, nz);
-        break;
-    }
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 
@@ -1435,22 +1538,24 @@ cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, in
 // order, so the blocks in flight share a band of detector rows across the
 // views, and with it a band of the volume's z (measured 1 % faster than
 // the row groups varying fastest).
-template <typename T, int R>
+template <typename T, typename TO, int R>
 static void column_launch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
 {
     dim3 block(32, kFPCWarps);
     dim3 grid((unsigned)p.n_views, (p.nu + kFPCWarps - 1) / kFPCWarps, (p.nv + 32 * R - 1) / (32 * R));
-    fp3d_column_kernel<T, R><<<grid, block, 0, s>>>((const T *)vp, (T *)sino, p, b);
+    fp3d_column_kernel<T, TO, R><<<grid, block, 0, s>>>((const T *)vp, (TO *)sino, p, b);
 }
 
-// 32-row windows per column, 1 to 5 per warp.  Cost model in issue slots
+// 32-row windows per column, 1 to rmax per warp.  Cost model in issue slots
 // per warp and depth plane: about 28 per window (windows past the last row
-// included) plus about 30 shared by the warp's windows.
-static int column_windows_per_warp(int nv)
+// included) plus about 30 shared by the warp's windows.  The forward takes
+// at most 4: with plane pairs, 5 windows need 96 registers and ran 12 %
+// slower on the 256^3 workload (25.5 ms against 22.8 ms with 4).
+static int column_windows_per_warp(int nv, int rmax = 5)
 {
     const int windows = (nv + 31) / 32;
     int best = 1, cost = INT_MAX;
-    for (int r = 1; r <= 5 && r <= windows; ++r) {
+    for (int r = 1; r <= rmax && r <= windows; ++r) {
         const int c = (windows + r - 1) / r * (28 * r + 30);
         if (c <= cost) {
             best = r;
@@ -1460,20 +1565,18 @@ static int column_windows_per_warp(int nv)
     return best;
 }
 
-template <typename T>
+template <typename T, typename TO>
 static void column_dispatch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
 {
-    const int best = column_windows_per_warp(p.nv);
-    if (best == 5)
-        column_launch<T, 5>(vp, sino, b, p, s);
-    else if (best == 4)
-        column_launch<T, 4>(vp, sino, b, p, s);
+    const int best = column_windows_per_warp(p.nv, 4);
+    if (best == 4)
+        column_launch<T, TO, 4>(vp, sino, b, p, s);
     else if (best == 3)
-        column_launch<T, 3>(vp, sino, b, p, s);
+        column_launch<T, TO, 3>(vp, sino, b, p, s);
     else if (best == 2)
-        column_launch<T, 2>(vp, sino, b, p, s);
+        column_launch<T, TO, 2>(vp, sino, b, p, s);
     else
-        column_launch<T, 1>(vp, sino, b, p, s);
+        column_launch<T, TO, 1>(vp, sino, b, p, s);
 }
 
 // two-ray windows per warp: about 40 issue slots per window and depth plane
@@ -1492,46 +1595,51 @@ static int pair_rows_windows_per_warp(int nv, int wr)
     return best;
 }
 
-template <typename T, int R>
+template <typename T, typename TO, int R>
 static void pair_rows_launch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
 {
     dim3 block(32, kFPCWarps);
     dim3 grid((unsigned)p.n_views, (p.nu + kFPCWarps - 1) / kFPCWarps, (p.nv + R * p.pair_rows - 1) / (R * p.pair_rows));
-    fp3d_pair_rows_kernel<T, R><<<grid, block, 0, s>>>((const T *)vp, (T *)sino, p, b);
+    fp3d_pair_rows_kernel<T, TO, R><<<grid, block, 0, s>>>((const T *)vp, (TO *)sino, p, b);
 }
 
-template <typename T>
+template <typename T, typename TO>
 static void pair_rows_dispatch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
 {
     switch (pair_rows_windows_per_warp(p.nv, p.pair_rows)) {
-    case 4: pair_rows_launch<T, 4>(vp, sino, b, p, s); break;
-    case 3: pair_rows_launch<T, 3>(vp, sino, b, p, s); break;
-    case 2: pair_rows_launch<T, 2>(vp, sino, b, p, s); break;
-    default: pair_rows_launch<T, 1>(vp, sino, b, p, s); break;
+    case 4: pair_rows_launch<T, TO, 4>(vp, sino, b, p, s); break;
+    case 3: pair_rows_launch<T, TO, 3>(vp, sino, b, p, s); break;
+    case 2: pair_rows_launch<T, TO, 2>(vp, sino, b, p, s); break;
+    default: pair_rows_launch<T, TO, 1>(vp, sino, b, p, s); break;
     }
 }
 
-cudaError_t launch_fp3d_column(const void *vp, void *sino, int b, const FP3DParams &p, pyro_dtype dt, cudaStream_t s)
+template <typename T, typename TO>
+static void column_any(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
 {
-    if (p.pair_rows > 0) {
-        switch (dt) {
-        case PYRO_F32: pair_rows_dispatch<float>(vp, sino, b, p, s); break;
-        case PYRO_F16: pair_rows_dispatch<__half>(vp, sino, b, p, s); break;
-        case PYRO_BF16: pair_rows_dispatch<__nv_bfloat16>(vp, sino, b, p, s); break;
-        }
-        return cudaGetLastError();
-    }
-    switch (dt) {
-    case PYRO_F32:
-        column_dispatch<float>(vp, sino, b, p, s);
-        break;
-    case PYRO_F16:
-        column_dispatch<__half>(vp, sino, b, p, s);
-        break;
-    case PYRO_BF16:
-        column_dispatch<__nv_bfloat16>(vp, sino, b, p, s);
-        break;
-    }
+    if (p.pair_rows > 0)
+        pair_rows_dispatch<T, TO>(vp, sino, b, p, s);
+    else
+        column_dispatch<T, TO>(vp, sino, b, p, s);
+}
+
+// the copy's storage type and the sinogram's: the same type, or an FP16 /
+// BF16 copy of an FP32 volume projected into an FP32 sinogram
+cudaError_t launch_fp3d_column(const void *vp, void *sino, int b, const FP3DParams &p, pyro_dtype storage,
+                               pyro_dtype sino_dt, cudaStream_t s)
+{
+    if (storage == PYRO_F32 && sino_dt == PYRO_F32)
+        column_any<float, float>(vp, sino, b, p, s);
+    else if (storage == PYRO_F16 && sino_dt == PYRO_F32)
+        column_any<__half, float>(vp, sino, b, p, s);
+    else if (storage == PYRO_BF16 && sino_dt == PYRO_F32)
+        column_any<__nv_bfloat16, float>(vp, sino, b, p, s);
+    else if (storage == PYRO_F16 && sino_dt == PYRO_F16)
+        column_any<__half, __half>(vp, sino, b, p, s);
+    else if (storage == PYRO_BF16 && sino_dt == PYRO_BF16)
+        column_any<__nv_bfloat16, __nv_bfloat16>(vp, sino, b, p, s);
+    else
+        return cudaErrorInvalidValue;
     return cudaGetLastError();
 }
 

@@ -758,16 +758,20 @@ int column_path(const Geo3D &G, FP3DParams &p, bool &column)
     return PYRO_OK;
 }
 
-// staged cone FP: per batch item, a z-major copy of the volume in `work`
+// staged cone FP: per batch item, a z-major copy of the volume in `work`,
+// held in `storage` (the volume's type, or FP16 / BF16 for an FP32 volume)
 int fp3d_staged(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *work, size_t work_bytes,
-                pyro_dtype dt, void *stream)
+                pyro_dtype dt, pyro_dtype storage, void *stream)
 {
     if (int e = check_io(vol, sino, batch, dt)) return e;
+    PYRO_CHECK(valid_dtype(storage), "unknown storage dtype %d", (int)storage);
+    if (storage != dt && dt != PYRO_F32)
+        return fail(PYRO_EUNSUPPORTED, "a storage type other than the volume's needs an FP32 volume");
     Geo3D G;
     if (int e = prep3d(g, G)) return e;
     const size_t vox = (size_t)G.nx * G.ny * G.nz;
     const size_t padded = fp_padded_elems(G.nx, G.ny, G.nz);
-    const size_t need = padded * elem_size(dt);
+    const size_t need = padded * elem_size(storage);
     if (work_bytes < need || work == nullptr || !aligned16(work))
         return fail(PYRO_EWORKSPACE, "the staged forward projector needs a 16-byte aligned workspace of %zu bytes "
                                      "(got %zu)", need, work_bytes);
@@ -776,17 +780,19 @@ int fp3d_staged(const void *vol, void *sino, int batch, const pyro_geom3d *g, vo
     static thread_local FP3DParams p;
     bool column;
     if (int e = column_path(G, p, column)) return e;
+    if (!column && storage != dt)
+        return fail(PYRO_EUNSUPPORTED, "a separate storage type needs a circular-type trajectory (column kernels)");
     for (int b = 0; b < batch; ++b) {
         const char *vi = (const char *)vol + b * vox * elem_size(dt);
         if (column)
-            PYRO_CUDA(launch_relayout_padded(vi, work, G.nx, G.ny, G.nz, dt, as_stream(stream)));
+            PYRO_CUDA(launch_relayout_padded(vi, work, G.nx, G.ny, G.nz, dt, storage, as_stream(stream)));
         else
             PYRO_CUDA(launch_relayout_zmajor(vi, work, G.nx, G.ny, G.nz, dt, as_stream(stream)));
         for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
             const int nvw = std::min(kMaxViewsConeFP, V - v0);
             if (int e = fill_fp3d(G, v0, nvw, p)) return e;
             if (column)
-                PYRO_CUDA(launch_fp3d_column(work, sino, b, p, dt, as_stream(stream)));
+                PYRO_CUDA(launch_fp3d_column(work, sino, b, p, storage, dt, as_stream(stream)));
             else
                 PYRO_CUDA(launch_fp3d_zmajor(work, sino, b, p, dt, as_stream(stream)));
         }
@@ -1215,7 +1221,13 @@ PYRO_API int pyro_bp_cone3d_tex(pyro_texture t, void *vol, const pyro_geom3d *g,
 PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
                                size_t workspace_bytes, pyro_dtype dtype, void *stream)
 {
-    return fp3d_staged(vol, sino, batch, g, workspace, workspace_bytes, dtype, stream);
+    return fp3d_staged(vol, sino, batch, g, workspace, workspace_bytes, dtype, dtype, stream);
+}
+
+PYRO_API int pyro_fp_cone3d_ws_storage(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
+                                       size_t workspace_bytes, pyro_dtype dtype, pyro_dtype storage, void *stream)
+{
+    return fp3d_staged(vol, sino, batch, g, workspace, workspace_bytes, dtype, storage, stream);
 }
 
 PYRO_API size_t pyro_fp2d_workspace_bytes(const pyro_geom2d *g, int batch, pyro_dtype dtype)

@@ -32,14 +32,20 @@ class TVResult:
     steps: List[float] = field(default_factory=list)
 
 
-def _ops(g):
+def _ops(g, storage=None):
+    """A and A^T as closures with their workspaces; `storage` (cone beam
+    only): the type of the projector's copy of the volume (FP16 / BF16
+    storage of the FP32 iterate, FP32 accumulation), None for FP32."""
     if isinstance(g, ConeGeometry3D):
         ws = {}
 
         def A(x, out=None):
+            st = x.dtype if storage is None else storage
             if "w" not in ws:
-                ws["w"] = torch.empty(B.fp_cone3d_workspace_bytes(g, x.dtype), dtype=torch.uint8, device=x.device)
-            return B.pyro_fp_cone3d_ws(x, g, workspace=ws["w"], out=out)
+                ws["w"] = torch.empty(B.fp_cone3d_workspace_bytes(g, st), dtype=torch.uint8, device=x.device)
+            if st == x.dtype:
+                return B.pyro_fp_cone3d_ws(x, g, workspace=ws["w"], out=out)
+            return B.pyro_fp_cone3d_ws_storage(x, g, st, workspace=ws["w"], out=out)
 
         def AT(y):
             if "wT" not in ws:
@@ -74,15 +80,18 @@ def estimate_lipschitz(g, shape, device, iters: int = 20, seed: int = 0) -> floa
 
 def tv_reconstruct(p: torch.Tensor, g, n_iter: int, lam: float, eps: float, L_est: Optional[float] = None,
                    x0: Optional[torch.Tensor] = None, clamp: float = 10.0, track_objective: bool = False,
-                   callback=None, graph: bool = False) -> TVResult:
+                   callback=None, graph: bool = False, storage: Optional[torch.dtype] = None) -> TVResult:
     """Minimise |A x - p|^2 + lam TV(x) (Eq. 7); p is one FP32 sinogram.
 
     The step size is chosen on the device (pyro_bb_dots / pyro_bb_update), so
     an iteration reads nothing back to the host unless `track_objective`
     (objective and step per iteration) or `callback(k, x)` asks for it.  With
     `graph=True` (and neither of those) one iteration is captured in a CUDA
-    graph after two eager ones and replayed for the rest."""
-    A, AT = _ops(g)
+    graph after two eager ones and replayed for the rest.  `storage`
+    (cone beam): the forward projector reads an FP16 / BF16 copy of the FP32
+    iterate (the half-storage pattern); the iterate, the gradients and every
+    reduction stay FP32."""
+    A, AT = _ops(g, storage)
     shape = tuple(g.volume_shape)
     dev = p.device
     if L_est is None:

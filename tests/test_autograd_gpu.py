@@ -104,6 +104,52 @@ def test_fp_gradient_matches_finite_differences():
         assert abs(np.sum(grad * e) - fd) < 1e-5 * max(abs(fd), np.linalg.norm(grad) * np.linalg.norm(e) * 1e-2)
 
 
+@pytest.mark.parametrize("crop", [(240, 240), (20, 460)])
+def test_fp_gradient_finite_differences_on_crops_of_the_full_fan_geometry(crop):
+    """The 16-phantom fan workload's geometry in full (512^2 at 0.5 mm, 360
+    views over 2 pi, 1024 bins at 1 mm, SID 750, SDD 1200, dt 0.25 mm): the
+    loss 1/2 |S (A x - y)|^2 over the rays S that cross a 32 x 32 crop (a
+    central one and one near the edge); the gradient on the whole image
+    through autograd, then 16 single-pixel and 8 random directions inside the
+    crop against FP64 central differences of the oracle's loss."""
+    n, sp = 512, (0.5, 0.5)
+    g = FanGeometry2D((n, n), sp, 1024, 1.0, 360, 2 * math.pi, 750.0, 1200.0)
+    ang = g.view_angles()
+    fwd = lambda v: oracle.fp_fan2d(v, sp, 1024, 1.0, ang, 750.0, 1200.0)
+    j0, i0 = crop
+    box = np.zeros((n, n))
+    box[j0:j0 + 32, i0:i0 + 32] = 1.0
+    S = fwd(box) > 0.0  # the crop's shadow
+    rng = np.random.default_rng(21)
+    x = f32(ph.voxelize_ellipses(ph.random_ellipses(10, n * 0.5 / 2, seed=22), (n, n), sp).numpy())
+    # data independent of A x, so that the residual does not cancel A x (a
+    # residual far below |A x| would amplify the FP32 projection's rounding)
+    y = f32(rng.standard_normal(S.shape))
+    mask = S.astype(np.float64)
+    xt = dev(x).requires_grad_(True)
+    loss = 0.5 * (((AG.forward_project(xt, g) - dev(y)) * dev(mask)) ** 2).sum()
+    loss.backward()
+    grad = xt.grad.double().cpu().numpy()
+    r0 = (fwd(x) - y) * mask
+    def oracle_loss(v):
+        r = (fwd(v) - y) * mask
+        return 0.5 * float(np.sum(r * r))
+    dirs = []
+    for _ in range(16):
+        e = np.zeros((n, n))
+        e[j0 + rng.integers(0, 32), i0 + rng.integers(0, 32)] = 1.0
+        dirs.append(e)
+    for _ in range(8):
+        e = np.zeros((n, n))
+        e[j0:j0 + 32, i0:i0 + 32] = rng.standard_normal((32, 32))
+        dirs.append(e)
+    h = 1e-3
+    for e in dirs:
+        fd = (oracle_loss(x + h * e) - oracle_loss(x - h * e)) / (2 * h)
+        assert abs(np.sum(grad * e) - fd) < 1e-5 * max(abs(fd), np.linalg.norm(grad * box) * np.linalg.norm(e) * 1e-2)
+    assert float(np.sum(r0 * r0)) > 0.0
+
+
 def test_bp_gradient_is_its_transpose():
     c, g, ang = fan_case()
     rng = np.random.default_rng(4)

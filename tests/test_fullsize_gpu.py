@@ -218,6 +218,25 @@ def test_tv512_geometry_full_size():
     assert abs(lhs - rhs) < 1e-5 * abs(lhs)
 
 
+def test_tv512_adjoint_elementwise_on_a_view_subset():
+    """The staged exact adjoint in the 512^3 iterative workload's geometry
+    (0.5 mm voxels, 1240 x 960 detector at 0.308 mm: a row step of about half
+    a voxel, so the two-rays-per-lane adjoint runs), on 8 views and a noise
+    sinogram, element by element on sampled voxels against the oracle's
+    voxel-wise adjoint; sampled voxels include the volume's faces and corners."""
+    n = 512
+    g = ConeGeometry3D((n, n, n), (0.5,) * 3, (960, 1240), (0.308, 0.308), 8, 2 * math.pi, 750.0, 1200.0)
+    P = oracle.circular_pmats(g.view_angles(), g.sid, g.sdd, g.detector_shape, g.detector_spacing)
+    y = ph.random_sinogram((8, 960, 1240), 14).astype(np.float32)
+    at = B.pyro_fpT_cone3d_ws(torch.from_numpy(y).to(DEV), g)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(15)
+    ii, jj, kk = rng.integers(0, n, 200), rng.integers(0, n, 200), rng.integers(0, n, 200)
+    ii, jj, kk = np.r_[ii, 0, n - 1, 0, n - 1], np.r_[jj, 0, n - 1, n - 1, 0], np.r_[kk, 0, n - 1, 0, n // 2]
+    ref = oracle.fpT_cone3d_voxels(y.astype(np.float64), g.volume_shape, g.volume_spacing, P, ii, jj, kk)
+    assert rel(at[kk, jj, ii].double().cpu().numpy(), ref) < 1e-5
+
+
 def test_learned_init_batch_full_size():
     """The learned-initialiser workload's FDK on its batch of 32 128^3
     phantoms (60 views over 2 pi, 256 x 200 at 1 mm): sampled voxels of the

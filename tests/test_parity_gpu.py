@@ -295,6 +295,24 @@ def test_fp_adjoint_cone_staged_large_footprint():
                oracle.fpT_cone3d(f32(noise), shape, spacing, P)) < 1e-5
 
 
+@pytest.mark.parametrize("storage", [torch.float16, torch.bfloat16])
+def test_fp_cone_staged_half_storage_copy(storage):
+    """An FP32 volume projected from an FP16 / BF16 workspace copy into an
+    FP32 sinogram: against the oracle fed the FP32 volume (end to end, the
+    storage rounding included), on a geometry the column kernels serve (a
+    row step of 0.7 voxel)."""
+    c = dict(CONE, det=(40, 41), dspacing=(1.0, 1.4))
+    ang = oracle.uniform_angles(c["views"], c["range"])
+    P = cone_pmats(c, ang)
+    vol = ph.voxelize_ellipsoids(ph.random_ellipsoids(5, 18.0, seed=57), c["shape"], c["spacing"]).numpy()
+    got = B.pyro_fp_cone3d_ws_storage(to_dev(vol), cone_geom(c), storage)
+    assert got.dtype == torch.float32
+    ref = oracle.fp_cone3d(f32(vol), c["spacing"], c["det"], P)
+    assert rel(host(got), ref) < TOL[storage]
+    with pytest.raises(B.PyroError):  # a storage type of its own needs an FP32 volume
+        B.pyro_fp_cone3d_ws_storage(to_dev(vol, torch.float16), cone_geom(c), storage)
+
+
 def test_fp_cone_staged_workspace_checks():
     c = CONE
     g = cone_geom(c)

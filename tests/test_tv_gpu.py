@@ -75,14 +75,33 @@ def parallel_problem(n=32, views=30, noise=0.02, seed=0):
 
 
 def test_tv_iteration_follows_the_oracle():
+    """12 steps of Eq. 7 (lambda 4, eps 1e-2) against the oracle's FP64
+    iteration, iterate and objective at the FP32 gate."""
     g, truth, p, fwd, adj, ang = parallel_problem()
     L = oracle.lipschitz(fwd, adj, g.volume_shape)
-    lam, eps, it = 4.0, 1e-3, 12
+    lam, eps, it = 4.0, 1e-2, 12
     x_ref, obj_ref = oracle.tv_solve(p, fwd, adj, lam, eps, it, L)
     res = TV.tv_reconstruct(dev(p), g, it, lam, eps, L_est=L, track_objective=True)
-    assert rel(res.x.double().cpu().numpy(), x_ref) < 1e-4
-    assert rel(res.objective, obj_ref) < 1e-4
+    assert rel(res.x.double().cpu().numpy(), x_ref) < 1e-5
+    assert rel(res.objective, obj_ref) < 1e-5
     assert res.objective[-1] < 0.15 * res.objective[0]
+
+
+def test_tv_iteration_stiff_smoothing():
+    """eps = 1e-3 makes the smoothed TV's curvature reach lambda / eps = 4000,
+    far above the data term's: each step still follows the oracle at FP32
+    rounding (two steps within 1e-6), but the Barzilai-Borwein step size, a
+    ratio of differences of successive iterates and gradients, amplifies
+    that rounding from step to step, so that 12 steps agree to about 4e-5
+    (7e-5 after 8): a property of the iteration on this problem, not of the
+    kernels (with eps = 1e-2 the same 12 steps agree to 5e-7)."""
+    g, truth, p, fwd, adj, ang = parallel_problem()
+    L = oracle.lipschitz(fwd, adj, g.volume_shape)
+    for it, tol in ((2, 1e-6), (12, 2e-4)):
+        x_ref, obj_ref = oracle.tv_solve(p, fwd, adj, 4.0, 1e-3, it, L)
+        res = TV.tv_reconstruct(dev(p), g, it, 4.0, 1e-3, L_est=L, track_objective=True)
+        assert rel(res.x.double().cpu().numpy(), x_ref) < tol
+        assert rel(res.objective, obj_ref) < 1e-5
 
 
 def test_cone_tv_iteration_follows_the_oracle():
@@ -99,8 +118,8 @@ def test_cone_tv_iteration_follows_the_oracle():
     lam, eps, it = 2.0, 1e-3, 10
     x_ref, obj_ref = oracle.tv_solve(p, fwd, adj, lam, eps, it, L)
     res = TV.tv_reconstruct(dev(p), g, it, lam, eps, L_est=L, track_objective=True)
-    assert rel(res.x.double().cpu().numpy(), x_ref) < 1e-4
-    assert rel(res.objective, obj_ref) < 1e-4
+    assert rel(res.x.double().cpu().numpy(), x_ref) < 1e-5
+    assert rel(res.objective, obj_ref) < 1e-5
     assert res.objective[-1] < 0.2 * res.objective[0]
 
 
@@ -132,11 +151,12 @@ def test_graph_replay_equals_the_eager_iteration(kind):
 
     a, b = eager.x.double().cpu().numpy(), graphed.x.double().cpu().numpy()
     # after 15 steps the adjoints' FP32 atomics (summation order changes from
-    # run to run) and the step sizes that follow the iterates leave differences
-    # of the size two eager runs show among themselves
-    spread = abs(objective(eager2.x) - objective(eager.x))
+    # run to run) and the step sizes that follow the iterates leave
+    # differences of the kind two eager runs show among themselves (their
+    # size varies from run to run: measured 1e-6 .. 1.3e-5 of the objective)
+    assert rel(eager2.x.double().cpu().numpy(), a) < 1e-3
     assert rel(b, a) < 1e-3
-    assert abs(objective(graphed.x) - objective(eager.x)) <= 10 * spread + 1e-6 * objective(eager.x)
+    assert abs(objective(graphed.x) - objective(eager.x)) <= 1e-4 * objective(eager.x)
 
 
 def test_sparse_view_tv_beats_fbp():
