@@ -227,14 +227,17 @@ PYRO_API int pyro_fpT_fan2d(const void *sino, void *vol, int batch, const pyro_g
 PYRO_API int pyro_fpT_cone3d(const void *sino, void *vol, int batch, const pyro_geom3d *g, pyro_dtype dtype,
                              void *stream);
 
-/* --- The same exact adjoint of the cone-beam projector, accumulated in a
- * zero-padded z-major FP32 copy of the volume in `workspace` (device, at
- * least pyro_fpT_cone3d_workspace_bytes bytes; PYRO_EWORKSPACE otherwise):
- * for circular-type trajectories (the detector's v axis along the volume's
- * z axis) each warp spreads 32 rays over a 32-voxel run of z in shared
- * memory and issues four global atomics per 32 samples instead of eight per
- * sample.  Other trajectories fall back to pyro_fpT_cone3d.  Results agree
- * with it to FP32 rounding; the workspace is scratch.  PYRO_F32 only. */
+/* --- The same exact adjoint of the cone-beam projector, gathered voxel by
+ * voxel for circular-type trajectories (the detector's v axis along the
+ * volume's z axis): the ray-weighted sinogram is transposed into
+ * `workspace` (device, at least pyro_fpT_cone3d_workspace_bytes bytes, one
+ * view x nu x nv FP32 sinogram; PYRO_EWORKSPACE otherwise), then every
+ * voxel sums the samples whose interpolation reaches it in a fixed order:
+ * no atomics, and the result is the same bit for bit from run to run.
+ * Other trajectories fall back to pyro_fpT_cone3d (the workspace is then
+ * unused).  Results agree with it to FP32 rounding; the workspace is
+ * scratch.  PYRO_F32 only.  pyro_sync_status reports PYRO_ECUDA if a
+ * shared-memory table outgrew its host-computed bound (never expected). */
 PYRO_API size_t pyro_fpT_cone3d_workspace_bytes(const pyro_geom3d *g);
 PYRO_API int pyro_fpT_cone3d_ws(const void *sino, void *vol, int batch, const pyro_geom3d *g, void *workspace,
                                 size_t workspace_bytes, pyro_dtype dtype, void *stream);

@@ -416,15 +416,17 @@ def pyro_fpT_cone3d(sino: torch.Tensor, g: ConeGeometry3D) -> torch.Tensor:
 
 
 def fpT_cone3d_workspace_bytes(g: ConeGeometry3D) -> int:
-    """Workspace pyro_fpT_cone3d_ws needs (one padded FP32 volume)."""
+    """Workspace pyro_fpT_cone3d_ws needs (the ray-weighted sinogram of one
+    batch item, transposed to [view][column][row], FP32)."""
     cg = g.to_c()
     return int(lib().pyro_fpT_cone3d_workspace_bytes(ctypes.byref(cg)))
 
 
 def pyro_fpT_cone3d_ws(sino: torch.Tensor, g: ConeGeometry3D, workspace: Optional[torch.Tensor] = None,
                        out: Optional[torch.Tensor] = None) -> torch.Tensor:
-    """Exact adjoint of the cone-beam FP accumulated in a padded z-major copy
-    kept in `workspace` (allocated here when not given)."""
+    """Exact adjoint of the cone-beam FP, gathered voxel by voxel from the
+    transposed, ray-weighted sinogram kept in `workspace` (allocated here
+    when not given): the same result bit for bit from run to run."""
     s, squeeze = _batched(_dev(sino, "sinogram"), 3, "sinogram")
     _shape_check(s, g.sinogram_shape, "sinogram")
     cg = g.to_c()

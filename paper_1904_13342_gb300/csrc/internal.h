@@ -90,6 +90,34 @@ struct FP3DParams {
     ConeFPView vlo[kMaxViewsConeFP];  // FP64 set-up - v
 };
 
+// --------------------------------------------------- gathered cone adjoint --
+// Per view, for circular-type trajectories (the detector's v axis along z),
+// in voxel-index units: the (x, y) point of column k on depth plane m,
+// X = px0 + k pxk + m (qx0 + k qxk) (and Y alike), the z of row l there,
+// z = A + m C + (B + m D) l, the detector column coordinate of the voxel
+// column (x, y), (u0 + ui x + uj y) / (w0 + wi x + wj y), and its depth-plane
+// coordinate mc + mi x + mj y.  Pairs are FP64 values as FP32 hi/lo.
+constexpr int kGatherTile = 4;    // voxel columns per tile side
+constexpr int kGatherWarps = 4;   // warps per block (32 z voxels each)
+constexpr int kGatherGroup = 4;   // depth planes that share one row window
+constexpr int kMaxViewsGather = 200;
+struct GatherView {
+    float px0[2], pxk[2], py0[2], pyk[2];
+    float qx0[2], qxk[2], qy0[2], qyk[2];
+    float A[2], B[2], C[2], D[2];
+    float u0, ui, uj, w0, wi, wj;
+    float mc, mi, mj, pad;
+};
+
+struct GatherParams {
+    int nx, ny, nz, nu, nv, n_views, view0, views_total, M;
+    int accumulate;                  // add into the output (view chunks after the first)
+    int kmax, plmax;                 // columns and depth planes that can reach a tile (host bounds)
+    int wrows;                       // rows of a lane's window (4, 8, 12 or 16)
+    int sc;                          // staged floats per warp (a column's rows at least)
+    GatherView v[kMaxViewsGather];
+};
+
 // ------------------------------------------------------------- BP 2D/3D --
 // Voxel-index to detector map, pre-scaled on the host: for voxel (i, j[, z])
 //   x = r0 . (i, j[, z], 1),  w = r2 . (...),  k = x / w + cu,
@@ -212,6 +240,12 @@ int tma_box_elems(int bu, int bv, size_t elem);  // one box, padded to 128 bytes
 size_t bp3d_tma_smem_bytes(int n_views, int bu, int bv, size_t elem, int per_stage);
 cudaError_t launch_bp3d_tma(const CUtensorMap &map, void *vol, int batch, const BP3DParams &p, const BPTmaPlan &pl,
                             pyro_dtype sino_dt, pyro_dtype vol_dt, cudaStream_t s);
+// gathered cone adjoint: the weighted transposed sinogram yT[v][k][l] =
+// dt |g| y[v][l][k] of batch item b for the chunk's views, then the gather
+size_t gather_smem_bytes(const GatherParams &g);
+cudaError_t launch_weighted_transpose(const void *sino, void *yT, int b, const FP3DParams &p, cudaStream_t s);
+cudaError_t launch_gather_adjoint(const void *yT, void *vol, const GatherParams &g, int *status,
+                                  cudaStream_t s);
 // address of the device word a bounded wait sets when it gives up
 cudaError_t status_word(int **ptr);
 cudaError_t launch_wait_timeout_probe(unsigned long long limit_ns, cudaStream_t s);

@@ -330,6 +330,71 @@ int prep3d(const pyro_geom3d *g, Geo3D &G)
     return PYRO_OK;
 }
 
+// One view's camera in FP64 for the ray-driven projector: the RQ split
+// P = K R [I | -S] of the normalised matrix, q = K^-1 (k, l, 1) scaled to
+// unit depth, q_x = a0 k + a1 l + a2, q_y = b0 l + b2, the source in camera
+// coordinates s = R S, W = diag(1/spacing) R^T (camera -> voxel index).
+// col: the rows of a detector column share their (x, y) point (the camera's
+// y axis along z and no skew; the FP64 residue of the split in those
+// entries, below 1e-12, is set to exact zeros so that FP32 rows agree bit
+// for bit).  dz_row: voxels in z one row step moves a sample at the far
+// sampled depth.
+struct CamView {
+    double W[9], a0, a1, a2, b0, b2, s1, s2, s3, K00, K11;
+    bool col;
+    double dz_row;
+};
+
+int cam_view(const Geo3D &G, int view, CamView &c)
+{
+    const double inv_s[3] = {1.0 / G.sx, 1.0 / G.sy, 1.0 / G.sz};
+    const double *Q = &G.P[12 * (size_t)view];
+    const double *S = &G.S[3 * (size_t)view];
+    const double m0[3] = {Q[0], Q[1], Q[2]}, m1[3] = {Q[4], Q[5], Q[6]}, m2[3] = {Q[8], Q[9], Q[10]};
+    auto dot = [](const double *x, const double *y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+    // RQ split M = K R by Gram-Schmidt from the last row (|m2| = 1 here)
+    double r2[3], r1[3], r0[3], t[3];
+    const double K22 = std::sqrt(dot(m2, m2));
+    for (int e = 0; e < 3; ++e) r2[e] = m2[e] / K22;
+    const double K12 = dot(m1, r2);
+    for (int e = 0; e < 3; ++e) t[e] = m1[e] - K12 * r2[e];
+    const double K11 = std::sqrt(dot(t, t));
+    for (int e = 0; e < 3; ++e) r1[e] = t[e] / K11;
+    const double K02 = dot(m0, r2), K01 = dot(m0, r1);
+    for (int e = 0; e < 3; ++e) t[e] = m0[e] - K02 * r2[e] - K01 * r1[e];
+    const double K00 = std::sqrt(dot(t, t));
+    if (!(K00 > 0 && K11 > 0)) return fail(PYRO_EINVAL, "projection matrix %d has a degenerate camera", view);
+    for (int e = 0; e < 3; ++e) r0[e] = t[e] / K00;
+    double K01s = K01;
+    c.col = std::fabs(r1[0]) < 1e-12 && std::fabs(r1[1]) < 1e-12 && std::fabs(K01) < 1e-12 * K00;
+    if (c.col) {
+        r1[0] = r1[1] = 0.0;
+        r1[2] = r1[2] > 0 ? 1.0 : -1.0;
+        K01s = 0.0;
+        // then r0 and r2 lie in the xy plane up to the split's rounding
+        r0[2] = 0.0;
+        r2[2] = 0.0;
+    }
+    const double b0 = 1.0 / K11, b2 = -K12 / K11;
+    c.a0 = 1.0 / K00;
+    c.a1 = -K01s * b0 / K00;
+    c.a2 = (-K02 - K01 * b2) / K00;
+    c.b0 = b0;
+    c.b2 = b2;
+    (void)K22;
+    c.s1 = dot(r0, S);
+    c.s2 = dot(r1, S);
+    c.s3 = dot(r2, S);
+    c.K00 = K00;
+    c.K11 = K11;
+    const double *R[3] = {r0, r1, r2};
+    for (int a = 0; a < 3; ++a)
+        for (int b = 0; b < 3; ++b) c.W[3 * a + b] = R[b][a] * inv_s[a];
+    const double w_far = -dot(r2, S) + G.M * G.step;
+    c.dz_row = std::fabs(b0 * r1[2] * inv_s[2]) * w_far;
+    return PYRO_OK;
+}
+
 int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
 {
     p.nx = G.nx;
@@ -346,71 +411,158 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
     p.cz = (float)(0.5 * (G.nz - 1));
     p.dt = (float)G.step;
     p.dt_lo = (float)(G.step - (double)p.dt);
-    const double inv_s[3] = {1.0 / G.sx, 1.0 / G.sy, 1.0 / G.sz};
     p.column_shared = 1;
     p.pair_rows = 64;
     p.zs0 = 0;
     p.zs1 = G.nz;
+    auto put = [](float &hi, float &lo, double x) {
+        hi = (float)x;
+        lo = (float)(x - (double)hi);
+    };
     for (int v = 0; v < nvw; ++v) {
-        const double *Q = &G.P[12 * (size_t)(v0 + v)];
-        const double *S = &G.S[3 * (size_t)(v0 + v)];
-        const double m0[3] = {Q[0], Q[1], Q[2]}, m1[3] = {Q[4], Q[5], Q[6]}, m2[3] = {Q[8], Q[9], Q[10]};
-        auto dot = [](const double *x, const double *y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
-        // RQ split M = K R by Gram-Schmidt from the last row (|m2| = 1 here)
-        double r2[3], r1[3], r0[3], t[3];
-        const double K22 = std::sqrt(dot(m2, m2));
-        for (int e = 0; e < 3; ++e) r2[e] = m2[e] / K22;
-        const double K12 = dot(m1, r2);
-        for (int e = 0; e < 3; ++e) t[e] = m1[e] - K12 * r2[e];
-        const double K11 = std::sqrt(dot(t, t));
-        for (int e = 0; e < 3; ++e) r1[e] = t[e] / K11;
-        const double K02 = dot(m0, r2), K01 = dot(m0, r1);
-        for (int e = 0; e < 3; ++e) t[e] = m0[e] - K02 * r2[e] - K01 * r1[e];
-        const double K00 = std::sqrt(dot(t, t));
-        if (!(K00 > 0 && K11 > 0)) return fail(PYRO_EINVAL, "projection matrix %d has a degenerate camera", v0 + v);
-        for (int e = 0; e < 3; ++e) r0[e] = t[e] / K00;
-        // Rows of a detector column share their (x, y) point when the camera's
-        // y axis is the volume's z axis and K has no skew.  FP64 rounding of
-        // the split leaves ~1e-16 in those entries; below 1e-12 they are set
-        // to exact zeros so that the FP32 (x, y) of every row agree bit for bit.
-        double K01s = K01;
-        const bool col = std::fabs(r1[0]) < 1e-12 && std::fabs(r1[1]) < 1e-12 && std::fabs(K01) < 1e-12 * K00;
-        if (col) {
-            r1[0] = r1[1] = 0.0;
-            r1[2] = r1[2] > 0 ? 1.0 : -1.0;
-            K01s = 0.0;
-        }
-        // q = K^-1 (k, l, 1) / K22 scaled so that q_z = 1
+        CamView c;
+        if (int e = cam_view(G, v0 + v, c)) return e;
         ConeFPView &o = p.v[v], &ol = p.vlo[v];
-        auto put = [](float &hi, float &lo, double x) {
-            hi = (float)x;
-            lo = (float)(x - (double)hi);
-        };
-        const double b0 = 1.0 / K11, b2 = -K12 / K11;
-        put(o.a0, ol.a0, 1.0 / K00);
-        put(o.a1, ol.a1, -K01s * b0 / K00);
-        put(o.a2, ol.a2, (-K02 - K01 * b2) / K00);
-        put(o.b0, ol.b0, b0);
-        put(o.b2, ol.b2, b2);
-        (void)K22;
-        put(o.s1, ol.s1, dot(r0, S));
-        put(o.s2, ol.s2, dot(r1, S));
-        put(o.s3, ol.s3, dot(r2, S));
-        const double *R[3] = {r0, r1, r2};
-        for (int a = 0; a < 3; ++a)
-            for (int b = 0; b < 3; ++b) put(o.W[3 * a + b], ol.W[3 * a + b], R[b][a] * inv_s[a]);
-        // one row step moves a sample by b0 W_zy w voxels in z at depth w; the
-        // column kernel needs 31 steps below 29.5 voxels over the sampled depths
-        const double w_far = -dot(r2, S) + G.M * G.step;
-        const double dz_row = std::fabs(b0 * r1[2] * inv_s[2]) * w_far;
-        if (!col || !(31.0 * dz_row <= 29.5)) p.column_shared = 0;
+        put(o.a0, ol.a0, c.a0);
+        put(o.a1, ol.a1, c.a1);
+        put(o.a2, ol.a2, c.a2);
+        put(o.b0, ol.b0, c.b0);
+        put(o.b2, ol.b2, c.b2);
+        put(o.s1, ol.s1, c.s1);
+        put(o.s2, ol.s2, c.s2);
+        put(o.s3, ol.s3, c.s3);
+        for (int a = 0; a < 9; ++a) put(o.W[a], ol.W[a], c.W[a]);
+        // the column kernel needs 31 row steps below 29.5 voxels over the sampled depths
+        if (!c.col || !(31.0 * c.dz_row <= 29.5)) p.column_shared = 0;
         // rows whose z span stays within a 32-voxel run, for two rays per lane
-        const int rows = dz_row > 0.0 ? (int)std::min(64.0, std::floor(29.5 / dz_row) + 1.0) : 64;
+        const int rows = c.dz_row > 0.0 ? (int)std::min(64.0, std::floor(29.5 / c.dz_row) + 1.0) : 64;
         p.pair_rows = std::min(p.pair_rows, rows);
     }
     // two rays per lane pay off from 40 rows per window (a row step below
     // about 0.76 voxel); below that the one-ray kernels run
     if (p.pair_rows < 40) p.pair_rows = 0;
+    return PYRO_OK;
+}
+
+// The gathered adjoint's per-view maps (circular-type trajectories), from
+// the same camera as the projector: the sample of ray (k, l) on plane m is
+// p + m q with p = W (s1 - s3 q_x, s2 - s3 q_y, 0) + c and q = dt W (q_x, q_y,
+// 1); with the camera's y axis along z, x and y depend on k only and z on l
+// only.  The detector column coordinate of a voxel column is the
+// projection's u = (P0 . X) / (P2 . X) in voxel-index units, its depth-plane
+// coordinate ((P2 . X) - depth of the iso-centre) / dt.
+//
+// Row step: plane m's rows step beta(m) = B + m D voxels in z, smallest in
+// magnitude at an end of the plane range; a z voxel's tent reaches at most
+// floor(2 / |beta|) + 1 rows, and a lane's window, starting at a multiple of
+// 4 rows, holds that many plus 3 (gather_rows: 0 when more than 16 rows).
+struct GatherRows {
+    double beta_min;  // smallest |beta| over the planes
+    double drift;     // largest |C + D l| over the rows: z shift per plane
+    int nmax, wrows;
+};
+
+int gather_rows(const Geo3D &G, const CamView &c, GatherRows &r)
+{
+    const double B = -c.W[7] * c.s3 * c.b0, D = G.step * c.W[7] * c.b0;
+    const double C0 = G.step * (c.W[7] * c.b2 + c.W[8]);
+    const double b1 = B - G.M * D, b2 = B + G.M * D;
+    if (b1 * b2 <= 0.0) return PYRO_EUNSUPPORTED;  // a depth plane of the support holds the source
+    r.beta_min = std::min(std::fabs(b1), std::fabs(b2));
+    r.drift = std::max(std::fabs(C0), std::fabs(C0 + D * (G.nv - 1)));
+    const double n = std::floor(2.0 / r.beta_min + 1e-3) + 1.0;
+    r.nmax = n > 64.0 ? 64 : (int)n;
+    const int w = (r.nmax + 3 + 3) / 4 * 4;
+    r.wrows = w <= 16 ? w : 0;
+    return PYRO_OK;
+}
+
+// Capacities of the kernel's shared tables are bounds over every tile and
+// view: the support of a tile's tents is (kGatherTile + 1) voxels square;
+// its diagonal, seen from the nearest depth, spans at most kmax detector
+// columns, and its depth at most plmax planes; a warp's 32 z voxels (and a
+// tent on either side) span at most 34 / |beta| rows, widened by the z
+// drift over the planes and a window.
+int fill_gather(const Geo3D &G, int v0, int nvw, int accumulate, GatherParams &g)
+{
+    g.nx = G.nx;
+    g.ny = G.ny;
+    g.nz = G.nz;
+    g.nu = G.nu;
+    g.nv = G.nv;
+    g.n_views = nvw;
+    g.view0 = v0;
+    g.views_total = (int)G.beta.size();
+    g.M = G.M;
+    g.accumulate = accumulate;
+    auto put = [](float (&hl)[2], double x) {
+        hl[0] = (float)x;
+        hl[1] = (float)(x - (double)hl[0]);
+    };
+    const double cen[3] = {0.5 * (G.nx - 1), 0.5 * (G.ny - 1), 0.5 * (G.nz - 1)};
+    const double side = kGatherTile + 1;
+    const double diag = std::sqrt(2.0) * side * std::max(G.sx, G.sy);
+    double kcols = 0.0, planes = 0.0, rows = 0.0;
+    int wrows = 0;
+    for (int v = 0; v < nvw; ++v) {
+        CamView c;
+        if (int e = cam_view(G, v0 + v, c)) return e;
+        if (!c.col) return fail(PYRO_EUNSUPPORTED, "the gathered adjoint needs a circular-type trajectory");
+        GatherRows gr;
+        if (gather_rows(G, c, gr) != PYRO_OK || gr.wrows == 0)
+            return fail(PYRO_EUNSUPPORTED, "detector rows too fine (or the source inside) for the gathered adjoint");
+        const double *W = c.W, dt = G.step;
+        GatherView &o = g.v[v];
+        // x and y: q_x = a0 k + a2 (a1 = 0 here), p_a = W[3a] (s1 - s3 q_x) + c_a, q_a = dt (W[3a] q_x + W[3a+2])
+        for (int a = 0; a < 2; ++a) {
+            const double w0 = W[3 * a], w2 = W[3 * a + 2];
+            float(&P0)[2] = a == 0 ? o.px0 : o.py0;
+            float(&Pk)[2] = a == 0 ? o.pxk : o.pyk;
+            float(&Q0)[2] = a == 0 ? o.qx0 : o.qy0;
+            float(&Qk)[2] = a == 0 ? o.qxk : o.qyk;
+            put(P0, w0 * (c.s1 - c.s3 * c.a2) + cen[a]);
+            put(Pk, -w0 * c.s3 * c.a0);
+            put(Q0, dt * (w0 * c.a2 + w2));
+            put(Qk, dt * w0 * c.a0);
+        }
+        // z: q_y = b0 l + b2, p_z = W[7] (s2 - s3 q_y) + c_z, q_z = dt (W[7] q_y + W[8])
+        put(o.A, c.W[7] * (c.s2 - c.s3 * c.b2) + cen[2]);
+        put(o.B, -c.W[7] * c.s3 * c.b0);
+        put(o.C, dt * (c.W[7] * c.b2 + c.W[8]));
+        put(o.D, dt * c.W[7] * c.b0);
+        // detector column and depth plane of voxel index (x, y): the
+        // normalised matrix on X = (idx - c) s
+        const double *Q = &G.P[12 * (size_t)(v0 + v)];
+        const double s[2] = {G.sx, G.sy};
+        double U[3], Wd[3];
+        for (int a = 0; a < 2; ++a) {
+            U[a] = Q[a] * s[a];
+            Wd[a] = Q[8 + a] * s[a];
+        }
+        U[2] = Q[3] - Q[0] * s[0] * cen[0] - Q[1] * s[1] * cen[1];
+        Wd[2] = Q[11] - Q[8] * s[0] * cen[0] - Q[9] * s[1] * cen[1];
+        o.ui = (float)U[0];
+        o.uj = (float)U[1];
+        o.u0 = (float)U[2];
+        o.wi = (float)Wd[0];
+        o.wj = (float)Wd[1];
+        o.w0 = (float)Wd[2];
+        o.mi = (float)(Wd[0] / dt);
+        o.mj = (float)(Wd[1] / dt);
+        o.mc = (float)(-(Q[8] * s[0] * cen[0] + Q[9] * s[1] * cen[1]) / dt);
+        o.pad = 0.0f;
+        const double w_near = std::max(Q[11] - G.T, 1e-9);  // the iso-centre's depth less the support radius
+        kcols = std::max(kcols, diag * c.K00 / w_near);
+        const double np = side * (std::fabs(Wd[0]) + std::fabs(Wd[1])) / dt;
+        planes = std::max(planes, np);
+        rows = std::max(rows, (34.0 + (np + 3.0) * gr.drift) / gr.beta_min);
+        wrows = std::max(wrows, gr.wrows);
+    }
+    g.kmax = (int)std::ceil(kcols) + 4;
+    g.plmax = (int)std::ceil(planes) + 3;
+    g.wrows = wrows;
+    const int rmax = ((int)std::ceil(rows) + wrows + 8 + 3) / 4 * 4;
+    g.sc = std::max(2048, rmax);
     return PYRO_OK;
 }
 
@@ -800,10 +952,23 @@ int fp3d_staged(const void *vol, void *sino, int batch, const pyro_geom3d *g, vo
     return PYRO_OK;
 }
 
-// staged exact adjoint: per batch item the column adjoint accumulates into
-// a zeroed padded z-major FP32 volume in `work`, whose interior is then
-// copied to the output; geometries the column kernels do not serve take the
-// per-sample scatter of fp3d (the workspace is then unused)
+// the gathered adjoint serves a geometry whose every view has its camera's y
+// axis along z (the rows of a detector column share their (x, y) point)
+bool gather_path(const Geo3D &G)
+{
+    for (int v = 0; v < (int)G.beta.size(); ++v) {
+        CamView c;
+        GatherRows r;
+        if (cam_view(G, v, c) != PYRO_OK || !c.col || gather_rows(G, c, r) != PYRO_OK || r.wrows == 0) return false;
+    }
+    return true;
+}
+
+// staged exact adjoint: per batch item the weighted sinogram is transposed
+// into `work` ([view][k][l], so that a column's rows are contiguous), then
+// the gather kernel writes the adjoint voxel by voxel (view chunks after the
+// first add); geometries it does not serve take the per-sample scatter of
+// fp3d (the workspace is then unused)
 int fp3d_adjoint_staged(const void *sino, void *vol, int batch, const pyro_geom3d *g, void *work, size_t work_bytes,
                         pyro_dtype dt, void *stream)
 {
@@ -811,25 +976,28 @@ int fp3d_adjoint_staged(const void *sino, void *vol, int batch, const pyro_geom3
     if (dt != PYRO_F32) return fail(PYRO_EUNSUPPORTED, "the FP adjoint supports PYRO_F32 only");
     Geo3D G;
     if (int e = prep3d(g, G)) return e;
-    const size_t vox = (size_t)G.nx * G.ny * G.nz;
-    const size_t need = fp_padded_elems(G.nx, G.ny, G.nz) * sizeof(float);
+    const int V = (int)G.beta.size();
+    const size_t vox = (size_t)G.nx * G.ny * G.nz, det = (size_t)G.nu * G.nv;
+    const size_t need = (size_t)V * det * sizeof(float);
     if (work_bytes < need || work == nullptr || !aligned16(work))
         return fail(PYRO_EWORKSPACE, "the staged FP adjoint needs a 16-byte aligned workspace of %zu bytes (got %zu)",
                     need, work_bytes);
     if (batch == 0) return PYRO_OK;
+    if (!gather_path(G)) return fp3d(sino, vol, batch, g, dt, true, stream);
     static thread_local FP3DParams p;
-    bool column;
-    if (int e = column_path(G, p, column)) return e;
-    if (!column) return fp3d(sino, vol, batch, g, dt, true, stream);
-    const int V = (int)G.beta.size();
+    static thread_local GatherParams gp;
+    int *status = nullptr;
+    PYRO_CUDA(status_word(&status));
     for (int b = 0; b < batch; ++b) {
-        PYRO_CUDA(cudaMemsetAsync(work, 0, need, as_stream(stream)));
         for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
-            const int nvw = std::min(kMaxViewsConeFP, V - v0);
-            if (int e = fill_fp3d(G, v0, nvw, p)) return e;  // the whole volume: zs0 = 0, zs1 = nz
-            PYRO_CUDA(launch_fp3d_column_adjoint(sino, work, b, p, as_stream(stream)));
+            if (int e = fill_fp3d(G, v0, std::min(kMaxViewsConeFP, V - v0), p)) return e;
+            PYRO_CUDA(launch_weighted_transpose(sino, work, b, p, as_stream(stream)));
         }
-        PYRO_CUDA(launch_relayout_unpad(work, (float *)vol + b * vox, G.nx, G.ny, G.nz, as_stream(stream)));
+        for (int v0 = 0; v0 < V; v0 += kMaxViewsGather) {
+            if (int e = fill_gather(G, v0, std::min(kMaxViewsGather, V - v0), v0 > 0, gp)) return e;
+            PYRO_CHECK(gather_smem_bytes(gp) <= 200 * 1024, "the gathered adjoint's tables exceed shared memory");
+            PYRO_CUDA(launch_gather_adjoint(work, (float *)vol + b * vox, gp, status, as_stream(stream)));
+        }
     }
     return PYRO_OK;
 }
@@ -1284,8 +1452,8 @@ PYRO_API int pyro_fpT_cone3d(const void *sino, void *vol, int batch, const pyro_
 
 PYRO_API size_t pyro_fpT_cone3d_workspace_bytes(const pyro_geom3d *g)
 {
-    if (!g || g->nx <= 0 || g->ny <= 0 || g->nz <= 0) return 0;
-    return fp_padded_elems(g->nx, g->ny, g->nz) * sizeof(float);
+    if (!g || g->nu <= 0 || g->nv <= 0 || g->n_views <= 0) return 0;
+    return (size_t)g->n_views * g->nu * g->nv * sizeof(float);
 }
 
 PYRO_API int pyro_fpT_cone3d_ws(const void *sino, void *vol, int batch, const pyro_geom3d *g, void *workspace,
@@ -1693,7 +1861,9 @@ PYRO_API int pyro_sync_status(void *stream)
     PYRO_CUDA(cudaMemcpy(&flag, word, sizeof(int), cudaMemcpyDeviceToHost));
     if (flag) {
         PYRO_CUDA(cudaMemset(word, 0, sizeof(int)));
-        return fail(PYRO_ETIMEOUT, "a device-side wait gave up; the results of that call are not valid");
+        if (flag & 1) return fail(PYRO_ETIMEOUT, "a device-side wait gave up; the results of that call are not valid");
+        return fail(PYRO_ECUDA, "a kernel's shared table outgrew its host-computed bound; the results of that call "
+                                "are not valid");
     }
     return PYRO_OK;
 }

@@ -254,8 +254,9 @@ def test_fp_cone_staged_column_kernel(case):
 
 @pytest.mark.parametrize("case", sorted(COLUMN_CASES) + ["general", "tilted"])
 def test_fp_adjoint_cone_staged(case):
-    """Exact adjoint through the padded z-major copy: the oracle's A^T, the
-    per-sample scatter, and <A x, y> = <x, A^T y> against the staged FP."""
+    """Exact adjoint through the gathered (circular) or per-sample scatter
+    (tilted) path: the oracle's A^T, the scatter, and <A x, y> = <x, A^T y>
+    against the staged FP."""
     c = COLUMN_CASES.get(case, CONE)
     ang = oracle.uniform_angles(c["views"], c["range"])
     P = tilted_pmats(c, ang) if case == "tilted" else cone_pmats(c, ang)
@@ -270,6 +271,23 @@ def test_fp_adjoint_cone_staged(case):
     lhs = float(np.sum(ax * f32(y[0])))
     rhs = float(np.sum(f32(x) * host(got[0])))
     assert abs(lhs - rhs) <= 1e-5 * abs(lhs)
+
+
+@pytest.mark.parametrize("case", ["one_window", "four_windows", "near_limit"])
+def test_fp_adjoint_cone_gathered_is_deterministic(case):
+    """The gathered adjoint sums every voxel in a fixed order: two calls
+    (and a call into a reused workspace) give the same bits, over several
+    view chunks (250 views: two launches, the second adding)."""
+    c = dict(COLUMN_CASES[case], views=250)
+    g = cone_geom(c)
+    y = to_dev(ph.random_sinogram((1, c["views"], *c["det"]), 43))
+    ws = torch.empty(B.fpT_cone3d_workspace_bytes(g), dtype=torch.uint8, device=DEV)
+    a = B.pyro_fpT_cone3d_ws(y, g, workspace=ws).clone()
+    b = B.pyro_fpT_cone3d_ws(y, g, workspace=ws)
+    c2 = B.pyro_fpT_cone3d_ws(y, g)
+    assert torch.equal(a, b) and torch.equal(a, c2)
+    # and the scatter (atomics, any order) agrees to rounding
+    assert rel(host(a), host(B.pyro_fpT_cone3d(y, g))) < 1e-5
 
 
 def test_fp_adjoint_cone_staged_large_footprint():
@@ -309,8 +327,9 @@ def test_fp_cone_staged_half_storage_copy(storage):
     assert got.dtype == torch.float32
     ref = oracle.fp_cone3d(f32(vol), c["spacing"], c["det"], P)
     assert rel(host(got), ref) < TOL[storage]
+    other = torch.bfloat16 if storage == torch.float16 else torch.float16
     with pytest.raises(B.PyroError):  # a storage type of its own needs an FP32 volume
-        B.pyro_fp_cone3d_ws_storage(to_dev(vol, torch.float16), cone_geom(c), storage)
+        B.pyro_fp_cone3d_ws_storage(to_dev(vol, other), cone_geom(c), storage)
 
 
 def test_fp_cone_staged_workspace_checks():
@@ -322,8 +341,9 @@ def test_fp_cone_staged_workspace_checks():
         B.pyro_fp_cone3d_ws(vol, g, workspace=small)
     assert e.value.status == 5
     sino = B.pyro_fp_cone3d(vol, g)
+    small_t = torch.empty(B.fpT_cone3d_workspace_bytes(g) - 4, dtype=torch.uint8, device=DEV)
     with pytest.raises(B.PyroError) as e:
-        B.pyro_fpT_cone3d_ws(sino, g, workspace=small)
+        B.pyro_fpT_cone3d_ws(sino, g, workspace=small_t)
     assert e.value.status == 5
     with pytest.raises(B.PyroError) as e:  # the adjoint is FP32 only
         B.pyro_fpT_cone3d_ws(sino.half(), g)
