@@ -234,7 +234,9 @@ PYRO_API int pyro_fpT_cone3d(const void *sino, void *vol, int batch, const pyro_
  * view x nu x nv FP32 sinogram; PYRO_EWORKSPACE otherwise), then every
  * voxel sums the samples whose interpolation reaches it in a fixed order:
  * no atomics, and the result is the same bit for bit from run to run.
- * Other trajectories fall back to pyro_fpT_cone3d (the workspace is then
+ * Other trajectories, and detectors whose rows are so fine that one voxel's
+ * tent reaches more than 29 of them (a row step under 1/14.5 voxel on the
+ * nearest plane), fall back to pyro_fpT_cone3d (the workspace is then
  * unused).  Results agree with it to FP32 rounding; the workspace is
  * scratch.  PYRO_F32 only.  pyro_sync_status reports PYRO_ECUDA if a
  * shared-memory table outgrew its host-computed bound (never expected). */

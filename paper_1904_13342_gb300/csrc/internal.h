@@ -99,7 +99,6 @@ struct FP3DParams {
 // coordinate mc + mi x + mj y.  Pairs are FP64 values as FP32 hi/lo.
 constexpr int kGatherTile = 4;    // voxel columns per tile side
 constexpr int kGatherWarps = 4;   // warps per block (32 z voxels each)
-constexpr int kGatherGroup = 4;   // depth planes that share one row window
 constexpr int kMaxViewsGather = 200;
 struct GatherView {
     float px0[2], pxk[2], py0[2], pyk[2];
@@ -113,7 +112,7 @@ struct GatherParams {
     int nx, ny, nz, nu, nv, n_views, view0, views_total, M;
     int accumulate;                  // add into the output (view chunks after the first)
     int kmax, plmax;                 // columns and depth planes that can reach a tile (host bounds)
-    int wrows;                       // rows of a lane's window (4, 8, 12 or 16)
+    int wrows;                       // rows of a lane's window (a multiple of 4, at most 32)
     int sc;                          // staged floats per warp (a column's rows at least)
     GatherView v[kMaxViewsGather];
 };

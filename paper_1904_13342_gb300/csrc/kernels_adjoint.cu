@@ -14,7 +14,7 @@
 // voxels (one per lane).  Per view it tabulates the points (k, m) whose
 // tents reach the tile (cell and bilinear weights), and every warp stages
 // the rows its 32 z voxels can reach, for every column of the view that
-// crosses the tile.  Planes are taken in groups of up to kGG: a lane's tent
+// crosses the tile.  Planes are taken in groups of up to G: a lane's tent
 // weights for a plane depend on the plane only, so they are computed once
 // per group, and the rows of one column that the group's planes reach fit
 // one window of W rows, read once per column with 128-bit loads.  The
@@ -37,7 +37,6 @@ namespace {
 
 constexpr int kGT = kGatherTile;   // voxel columns per tile side
 constexpr int kGW = kGatherWarps;  // warps per block, 32 z voxels each
-constexpr int kGG = kGatherGroup;  // planes per window group
 constexpr int kGZ = 32 * kGW;
 
 __device__ __forceinline__ ff ffv(const float (&a)[2])
@@ -129,13 +128,26 @@ __host__ __device__ inline GatherSmem gather_smem(const GatherParams &g)
     return s;
 }
 
-template <int W>
+// add a point's four corner terms w Z to the warp's accumulators: c packs
+// the offset of corner (0, 0) plus 4096 and, times 65536, the mask of the
+// corners inside the tile
+__device__ __forceinline__ void corner_update(float *acc, int c, float4 w, float Z)
+{
+    const int mk = c >> 16;
+    float *a = acc + ((c & 0xffff) - 4096);
+    if (mk & 1) a[0] = fmaf(w.x, Z, a[0]);
+    if (mk & 2) a[32] = fmaf(w.y, Z, a[32]);
+    if (mk & 4) a[32 * kGT] = fmaf(w.z, Z, a[32 * kGT]);
+    if (mk & 8) a[32 * kGT + 32] = fmaf(w.w, Z, a[32 * kGT + 32]);
+}
+
+template <int W, int G>
 __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const float *__restrict__ yT,
                                                                           float *__restrict__ vol,
                                                                           const __grid_constant__ GatherParams g,
                                                                           int *status)
 {
-    static_assert(W % 4 == 0 && W >= 4 && W <= 16, "the window is whole float4s");
+    static_assert(W % 4 == 0 && W >= 4 && W <= 32 && G >= 1 && G <= 4, "the window is whole float4s");
     extern __shared__ __align__(16) unsigned char gsm[];
     const GatherSmem L = gather_smem(g);
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
@@ -290,7 +302,7 @@ __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const 
                 // one W-row window starting at a multiple of 4, for every lane
                 int lo = INT_MAX, hi = INT_MIN, gs = 0;
 #pragma unroll
-                for (int q = 0; q < kGG; ++q) {
+                for (int q = 0; q < G; ++q) {
                     if (gs == q && p0 + q < NP && ((p0 + q) >> 5) == (p0 >> 5)) {
                         const GPlane pl = zpl[p0 + q];
                         const int js = pl.lc + first_row(pl.f + (float)lane, pl.ib);
@@ -311,10 +323,10 @@ __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const 
                 const int ws = lo & ~3;
                 const int soff = min(max(ws - rlo4, 0), RP - W);  // in range by construction
                 // tent weights of rows ws + r, as pairs of rows (r even, r + 1)
-                f32x2 wt[kGG][W / 2];
+                f32x2 wt[G][W / 2];
                 int kf = INT_MAX, kl = -1;
 #pragma unroll
-                for (int q = 0; q < kGG; ++q) {
+                for (int q = 0; q < G; ++q) {
                     if (q < gs) {  // uniform
                         const GPlane pl = zpl[p0 + q];
                         const int2 pr = prange[p0 + q];
@@ -339,9 +351,9 @@ __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const 
                     const unsigned bits = (pm[k] >> sh) & gmask;
                     if (!bits) continue;  // warp-uniform
                     const int e0 = p0 * K + k;
-                    int cq[kGG];  // accumulator offsets and corner masks, fetched ahead of the sums
+                    int cq[G];  // accumulator offsets and corner masks, fetched ahead of the sums
 #pragma unroll
-                    for (int q = 0; q < kGG; ++q) cq[q] = (bits >> q) & 1u ? cell[e0 + min(q, gs - 1) * K] : 0;
+                    for (int q = 0; q < G; ++q) cq[q] = cell[e0 + min(q, gs - 1) * K];
                     const ulonglong2 *sp = reinterpret_cast<const ulonglong2 *>(stage + (k - c0) * RP + soff);
                     f32x2 sv[W / 2];
 #pragma unroll
@@ -352,27 +364,20 @@ __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const 
                     }
                     // the group's sums as independent chains of row pairs (a
                     // plane without a point here has zero weights or is skipped)
-                    f32x2 Zp[kGG];
+                    f32x2 Zp[G];
 #pragma unroll
-                    for (int q = 0; q < kGG; ++q) Zp[q] = 0ull;
+                    for (int q = 0; q < G; ++q) Zp[q] = 0ull;
 #pragma unroll
                     for (int r = 0; r < W / 2; ++r) {
 #pragma unroll
-                        for (int q = 0; q < kGG; ++q) Zp[q] = fma2(wt[q][r], sv[r], Zp[q]);
+                        for (int q = 0; q < G; ++q) Zp[q] = fma2(wt[q][r], sv[r], Zp[q]);
                     }
 #pragma unroll
-                    for (int q = 0; q < kGG; ++q) {
-                        const int mk = cq[q] >> 16;
-                        if (mk) {
+                    for (int q = 0; q < G; ++q) {
+                        if ((bits >> q) & 1u) {  // uniform
                             float za, zb;
                             upk2(Zp[q], za, zb);
-                            const float Z = za + zb;
-                            const float4 w = rec[e0 + q * K];
-                            float *a = acc + ((cq[q] & 0xffff) - 4096);
-                            if (mk & 1) a[0] = fmaf(w.x, Z, a[0]);
-                            if (mk & 2) a[32] = fmaf(w.y, Z, a[32]);
-                            if (mk & 4) a[32 * kGT] = fmaf(w.z, Z, a[32 * kGT]);
-                            if (mk & 8) a[32 * kGT + 32] = fmaf(w.w, Z, a[32 * kGT + 32]);
+                            corner_update(acc, cq[q], rec[e0 + q * K], za + zb);
                         }
                     }
                 }
@@ -411,31 +416,40 @@ cudaError_t launch_weighted_transpose(const void *sino, void *yT, int b, const F
     return cudaGetLastError();
 }
 
-template <int W>
+template <int W, int G>
 static cudaError_t gather_launch(const void *yT, void *vol, const GatherParams &g, int *status, cudaStream_t s)
 {
     if (g.sc % 4 != 0 || g.sc < W || g.kmax < 1 || g.plmax < 1) return cudaErrorInvalidValue;
     const size_t smem = gather_smem_bytes(g);
-    cudaError_t e = cudaFuncSetAttribute(fp3d_gather_adjoint_kernel<W>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+    cudaError_t e = cudaFuncSetAttribute(fp3d_gather_adjoint_kernel<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          (int)smem);
     if (e != cudaSuccess) return e;
     dim3 grid((g.nx + kGT - 1) / kGT, (g.ny + kGT - 1) / kGT, (g.nz + kGZ - 1) / kGZ);
-    fp3d_gather_adjoint_kernel<W><<<grid, 32 * kGW, smem, s>>>((const float *)yT, (float *)vol, g, status);
+    fp3d_gather_adjoint_kernel<W, G><<<grid, 32 * kGW, smem, s>>>((const float *)yT, (float *)vol, g, status);
     return cudaGetLastError();
 }
 
 // one batch item: yT holds its transposed, weighted views
 cudaError_t launch_gather_adjoint(const void *yT, void *vol, const GatherParams &g, int *status, cudaStream_t s)
 {
+    // planes per group: their tent weights stay in registers (G W / 2 pairs)
     switch (g.wrows) {
     case 4:
-        return gather_launch<4>(yT, vol, g, status, s);
+        return gather_launch<4, 4>(yT, vol, g, status, s);
     case 8:
-        return gather_launch<8>(yT, vol, g, status, s);
+        return gather_launch<8, 4>(yT, vol, g, status, s);
     case 12:
-        return gather_launch<12>(yT, vol, g, status, s);
+        return gather_launch<12, 4>(yT, vol, g, status, s);
     case 16:
-        return gather_launch<16>(yT, vol, g, status, s);
+        return gather_launch<16, 3>(yT, vol, g, status, s);
+    case 20:
+        return gather_launch<20, 2>(yT, vol, g, status, s);
+    case 24:
+        return gather_launch<24, 2>(yT, vol, g, status, s);
+    case 28:
+        return gather_launch<28, 1>(yT, vol, g, status, s);
+    case 32:
+        return gather_launch<32, 1>(yT, vol, g, status, s);
     default:
         return cudaErrorInvalidValue;
     }

@@ -455,7 +455,7 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
 // Row step: plane m's rows step beta(m) = B + m D voxels in z, smallest in
 // magnitude at an end of the plane range; a z voxel's tent reaches at most
 // floor(2 / |beta|) + 1 rows, and a lane's window, starting at a multiple of
-// 4 rows, holds that many plus 3 (gather_rows: 0 when more than 16 rows).
+// 4 rows, holds that many plus 3 (gather_rows: 0 when more than 32 rows).
 struct GatherRows {
     double beta_min;  // smallest |beta| over the planes
     double drift;     // largest |C + D l| over the rows: z shift per plane
@@ -473,7 +473,7 @@ int gather_rows(const Geo3D &G, const CamView &c, GatherRows &r)
     const double n = std::floor(2.0 / r.beta_min + 1e-3) + 1.0;
     r.nmax = n > 64.0 ? 64 : (int)n;
     const int w = (r.nmax + 3 + 3) / 4 * 4;
-    r.wrows = w <= 16 ? w : 0;
+    r.wrows = w <= 32 ? w : 0;
     return PYRO_OK;
 }
 
