@@ -81,7 +81,6 @@ inline size_t fp_padded_elems(int nx, int ny, int nz)
 struct FP3DParams {
     int nx, ny, nz, nu, nv, n_views, view0, views_total;
     int column_shared;         // every view: rows of a detector column share (x, y) (see fill_fp3d)
-    int zs0, zs1;              // column adjoint: the z range [zs0, zs1) whose taps it writes
     int pair_rows;             // > 0: rows per window of the two-rays-per-lane column kernels (33..64)
     int M;
     float cx, cy, cz;          // (n-1)/2 per axis
@@ -212,8 +211,6 @@ cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, in
                                    pyro_dtype storage, cudaStream_t s);
 cudaError_t launch_fp3d_column(const void *vp, void *sino, int b, const FP3DParams &p, pyro_dtype storage,
                                pyro_dtype sino_dt, cudaStream_t s);
-cudaError_t launch_fp3d_column_adjoint(const void *sino, void *vp, int b, const FP3DParams &p, cudaStream_t s);
-cudaError_t launch_relayout_unpad(const void *vp, void *vol, int nx, int ny, int nz, cudaStream_t s);
 // forward projection of batch item b from its z-major copy; `sino` is the whole
 // [batch][views_total][nv][nu] sinogram
 cudaError_t launch_fp3d_zmajor(const void *vz, void *sino, int b, const FP3DParams &p, pyro_dtype dt,

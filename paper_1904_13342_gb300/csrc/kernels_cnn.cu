@@ -69,11 +69,15 @@ __device__ __forceinline__ uint64_t umma_desc(const void *smem, unsigned lbo, un
     return d;
 }
 
-template <int CIN, int COUT>
+// COUTR <= COUT output channels are real: the weights are [27][COUTR][Cin],
+// the MMA's other rows of B are zero, and only COUTR channels are stored
+// (a layer with one output channel runs as N = 16).
+template <int CIN, int COUT, int COUTR = COUT>
 __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
                                                         const float *__restrict__ bias, bf16 *__restrict__ Y, int D,
                                                         int H, int Wd, int relu, int *status)
 {
+    static_assert(COUTR >= 1 && COUTR <= COUT && (COUTR == COUT || COUTR < 16), "real output channels");
     constexpr int KCH = CIN / 8;  // 16-byte chunks of a row
     constexpr int A_EL = 128 * CIN, B_EL = COUT * CIN;
     constexpr unsigned TCOLS = COUT < 32 ? 32 : COUT;  // tensor-memory columns (a power of two >= 32)
@@ -105,6 +109,9 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         asm volatile("tcgen05.fence::before_thread_sync;");
     }
+    if constexpr (COUTR < COUT) {  // rows of B past the real channels: zero in both stages
+        for (int q = t; q < 2 * B_EL / 8; q += 128) reinterpret_cast<uint4 *>(sB)[q] = make_uint4(0u, 0u, 0u, 0u);
+    }
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const unsigned tmem = tmem_slot;
@@ -131,8 +138,8 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__
             *reinterpret_cast<uint4 *>(A + ((t >> 3) * KCH + c) * 64 + (t & 7) * 8) = v;
         }
         bf16 *Bs = sB + buf * B_EL;
-        const uint4 *wsrc = reinterpret_cast<const uint4 *>(Wt + (size_t)tap * COUT * CIN);
-        for (int q = t; q < COUT * KCH; q += 128) {
+        const uint4 *wsrc = reinterpret_cast<const uint4 *>(Wt + (size_t)tap * COUTR * CIN);
+        for (int q = t; q < COUTR * KCH; q += 128) {
             const int n = q / KCH, c = q - n * KCH;
             *reinterpret_cast<uint4 *>(Bs + ((n >> 3) * KCH + c) * 64 + (n & 7) * 8) = __ldg(wsrc + q);
         }
@@ -164,6 +171,150 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__
     if (last >= 0 && !mbar_wait(&bar[last & 1], (unsigned)(last >> 1) & 1u)) ok = false;
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int all_ok = __syncthreads_and(ok && last == 26 ? 1 : 0);
+    if (all_ok && COUTR < 16) {  // the first COUTR columns only
+        unsigned r[16];
+        const unsigned addr = tmem + ((unsigned)(32 * warp) << 16);
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        bf16 *out = Y + ((((size_t)b * D + vz) * H + vy) * Wd + vx) * COUTR;
+#pragma unroll
+        for (int c = 0; c < COUTR; ++c) {
+            float a = __uint_as_float(r[c]);
+            if (bias) a += bias[c];
+            if (relu) a = fmaxf(a, 0.0f);
+            out[c] = __float2bfloat16(a);
+        }
+    } else if (all_ok) {
+        bf16 *out = Y + ((((size_t)b * D + vz) * H + vy) * Wd + vx) * COUT;
+#pragma unroll
+        for (int c0 = 0; c0 < COUT; c0 += 16) {
+            unsigned r[16];
+            const unsigned addr = tmem + ((unsigned)(32 * warp) << 16) + (unsigned)c0;
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+                : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                  "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+                : "r"(addr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            unsigned pk[8];
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                float a = __uint_as_float(r[c]), d = __uint_as_float(r[c + 1]);
+                if (bias) {
+                    a += bias[c0 + c];
+                    d += bias[c0 + c + 1];
+                }
+                if (relu) {
+                    a = fmaxf(a, 0.0f);
+                    d = fmaxf(d, 0.0f);
+                }
+                pk[c / 2] = pack_bf16(__float2bfloat16(a), __float2bfloat16(d));
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(out + c0);
+            o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+    } else if (t == 0) {
+        atomicExch(status, 1);
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+}
+
+// ---- conv3d_tc_k27_kernel: one input channel (the first layer).  The 27
+// taps are the GEMM's K (padded to 32 with zeros): every thread gathers its
+// voxel's 27 neighbours into one row of A, the block stages B = the [Cout x
+// 32] tap weights once, and two tcgen05.mma (K = 16 each) make the whole
+// convolution; epilogue as conv3d_tc_kernel.
+template <int COUT>
+__global__ void __launch_bounds__(128) conv3d_tc_k27_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
+                                                            const float *__restrict__ bias, bf16 *__restrict__ Y,
+                                                            int D, int H, int Wd, int relu, int *status)
+{
+    constexpr int KCH = 4;  // 32 bf16 of K in 16-byte chunks
+    constexpr unsigned TCOLS = COUT < 32 ? 32 : COUT;
+    __shared__ __align__(128) bf16 sA[128 * 32];
+    __shared__ __align__(128) bf16 sB[COUT * 32];
+    __shared__ __align__(8) uint64_t bar;
+    __shared__ unsigned tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5;
+    const Tile tl = conv_tile(Wd, H);
+    const int TX = tl.TX, TY = tl.TY;
+    const int tiles_x = Wd / TX, tiles_y = H / TY, tiles_z = D / tl.TZ;
+    int blk = blockIdx.x;
+    const int tx0 = (blk % tiles_x) * TX;
+    blk /= tiles_x;
+    const int ty0 = (blk % tiles_y) * TY;
+    blk /= tiles_y;
+    const int tz0 = (blk % tiles_z) * tl.TZ;
+    const int b = blk / tiles_z;
+    const int vz = tz0 + t / (TX * TY), vy = ty0 + (t / TX) % TY, vx = tx0 + t % TX;
+    if (t == 0) {
+        mbar_init(&bar, 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    // A: row t = the 27 neighbours of voxel t (zero outside the volume), then 5 zeros
+    const bf16 zero = __float2bfloat16(0.0f);
+    bf16 v[32];
+#pragma unroll
+    for (int tap = 0; tap < 27; ++tap) {
+        const int gz = vz + tap / 9 - 1, gy = vy + (tap / 3) % 3 - 1, gx = vx + tap % 3 - 1;
+        const bool in = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < Wd;
+        v[tap] = in ? X[(((size_t)b * D + gz) * H + gy) * Wd + gx] : zero;
+    }
+#pragma unroll
+    for (int k = 27; k < 32; ++k) v[k] = zero;
+#pragma unroll
+    for (int c = 0; c < KCH; ++c) {
+        uint4 u;
+        u.x = pack_bf16(v[8 * c], v[8 * c + 1]);
+        u.y = pack_bf16(v[8 * c + 2], v[8 * c + 3]);
+        u.z = pack_bf16(v[8 * c + 4], v[8 * c + 5]);
+        u.w = pack_bf16(v[8 * c + 6], v[8 * c + 7]);
+        *reinterpret_cast<uint4 *>(sA + ((t >> 3) * KCH + c) * 64 + (t & 7) * 8) = u;
+    }
+    // B[n][k] = W[tap = k][n] (weights [27][Cout][1]), zero for k >= 27
+    for (int q = t; q < COUT * 32; q += 128) {
+        const int n = q >> 5, k = q & 31;
+        sB[((n >> 3) * KCH + (k >> 3)) * 64 + (n & 7) * 8 + (k & 7)] = k < 27 ? Wt[k * COUT + n] : zero;
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_slot;
+    constexpr unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COUT >> 3) << 17) | (8u << 24);
+    if (t == 0) {
+#pragma unroll
+        for (int kk = 0; kk < 2; ++kk) {
+            const uint64_t ad = umma_desc(sA + kk * 128, 128, 32 * 16);
+            const uint64_t bd = umma_desc(sB + kk * 128, 128, 32 * 16);
+            const unsigned accumulate = kk > 0 ? 1u : 0u;
+            asm volatile(
+                "{\n"
+                " .reg .pred p;\n"
+                " setp.ne.b32 p, %4, 0;\n"
+                " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                "}\n" ::"r"(tmem),
+                "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_addr(&bar))
+                     : "memory");
+    }
+    const bool ok = mbar_wait(&bar, 0u);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int all_ok = __syncthreads_and(ok ? 1 : 0);
     if (all_ok) {
         bf16 *out = Y + ((((size_t)b * D + vz) * H + vy) * Wd + vx) * COUT;
 #pragma unroll
@@ -197,6 +348,211 @@ __global__ void __launch_bounds__(128) conv3d_tc_kernel(const bf16 *__restrict__
     } else if (t == 0) {
         atomicExch(status, 1);
     }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+}
+
+// ---- conv3d_tc_rows_kernel: rows of 128 output voxels along x (W a
+// multiple of 128: the full-resolution 16-channel layers), walked along z.
+// A block owns output rows (b, z, y, x0 .. x0 + 127) for kRowsZ consecutive
+// z.  It keeps the input lines it needs in a ring of four z slots of three
+// lines (dy = -1, 0, 1), each line x0 - 1 .. x0 + 128 stored as Cin / 8
+// planes of 130 contiguous 16-byte rows, so that tap (dz, dy, dx) of row z
+// is the line (z + dz - 1, dy) read from row dx on: a K-major operand whose
+// 8-row groups sit 128 bytes apart and whose K chunks one plane apart.  Per
+// row only the three lines of z + 2 are new: they are fetched with cp.async
+// (zero-filled outside the volume) while the MMAs of the current row run,
+// and the accumulator is double-buffered in tensor memory, so the epilogue
+// of row z - 1 overlaps them too.  The 27 taps' weights are staged once per
+// block.  Waits are time-bounded; after a give-up the block stops issuing,
+// drains its last commit (bounded), writes nothing more, sets the status
+// word and frees its tensor memory.
+constexpr int kRowsZ = 16;
+
+__device__ __forceinline__ void cp_async16(void *dst, const void *src, bool in)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(in ? 16 : 0)
+                 : "memory");
+}
+
+template <int CIN, int COUT, int COUTR>
+__device__ __forceinline__ void rows_epilogue(unsigned tmem_acc, int warp, bf16 *out, const float *bias, int relu)
+{
+    unsigned r[16];
+#pragma unroll
+    for (int c0 = 0; c0 < COUT; c0 += 16) {
+        if (c0 >= COUTR) break;
+        const unsigned addr = tmem_acc + ((unsigned)(32 * warp) << 16) + (unsigned)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(addr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+        if constexpr (COUTR < 16) {
+#pragma unroll
+            for (int c = 0; c < COUTR; ++c) {
+                float a = __uint_as_float(r[c]);
+                if (bias) a += bias[c];
+                if (relu) a = fmaxf(a, 0.0f);
+                out[c] = __float2bfloat16(a);
+            }
+        } else {
+            unsigned pk[8];
+#pragma unroll
+            for (int c = 0; c < 16; c += 2) {
+                float a = __uint_as_float(r[c]), d = __uint_as_float(r[c + 1]);
+                if (bias) {
+                    a += bias[c0 + c];
+                    d += bias[c0 + c + 1];
+                }
+                if (relu) {
+                    a = fmaxf(a, 0.0f);
+                    d = fmaxf(d, 0.0f);
+                }
+                pk[c / 2] = pack_bf16(__float2bfloat16(a), __float2bfloat16(d));
+            }
+            uint4 *o = reinterpret_cast<uint4 *>(out + c0);
+            o[0] = make_uint4(pk[0], pk[1], pk[2], pk[3]);
+            o[1] = make_uint4(pk[4], pk[5], pk[6], pk[7]);
+        }
+    }
+}
+
+template <int CIN, int COUT, int COUTR = COUT>
+__global__ void __launch_bounds__(128) conv3d_tc_rows_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
+                                                             const float *__restrict__ bias, bf16 *__restrict__ Y,
+                                                             int D, int H, int Wd, int relu, int *status)
+{
+    static_assert(COUTR >= 1 && COUTR <= COUT && (COUTR == COUT || COUTR < 16), "real output channels");
+    constexpr int KCH = CIN / 8;
+    constexpr int ROWS = 130;          // input x0 - 1 .. x0 + 128
+    constexpr int P = ROWS * 16;       // bytes of one K-chunk plane of a line
+    constexpr int LINE = KCH * P;      // bytes of one staged line
+    constexpr int SET = 3 * LINE;      // the three lines (dy) of one input z
+    constexpr int B_TAP = COUT * CIN;  // bf16 of one tap's B
+    constexpr unsigned TCOLS = 2 * COUT < 32 ? 32 : 2 * COUT;  // two accumulators
+    extern __shared__ __align__(128) unsigned char rows_smem[];
+    unsigned char *ring = rows_smem;                              // [4 slots][3 lines][KCH][130][16 B]
+    bf16 *sB = reinterpret_cast<bf16 *>(rows_smem + 4 * SET);    // [27][COUT x CIN] canonical
+    __shared__ __align__(8) uint64_t bar[2];
+    __shared__ unsigned tmem_slot;
+    const int t = threadIdx.x, warp = t >> 5;
+    const int lines_x = Wd / 128, zchunks = (D + kRowsZ - 1) / kRowsZ;
+    int blk = blockIdx.x;
+    const int x0 = (blk % lines_x) * 128;
+    blk /= lines_x;
+    const int y = blk % H;
+    blk /= H;
+    const int z0 = (blk % zchunks) * kRowsZ;
+    const int b = blk / zchunks;
+    const int nrows = min(z0 + kRowsZ, D) - z0;
+    if (t == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(TCOLS));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    // every tap's weights (rows past the real channels zero)
+    if constexpr (COUTR < COUT) {
+        for (int q = t; q < 27 * B_TAP / 8; q += 128) reinterpret_cast<uint4 *>(sB)[q] = make_uint4(0u, 0u, 0u, 0u);
+        __syncthreads();
+    }
+    for (int q = t; q < 27 * COUTR * KCH; q += 128) {
+        const int tap = q / (COUTR * KCH), rem = q - tap * (COUTR * KCH);
+        const int n = rem / KCH, c = rem - n * KCH;
+        *reinterpret_cast<uint4 *>(sB + tap * B_TAP + ((n >> 3) * KCH + c) * 64 + (n & 7) * 8) =
+            __ldg(reinterpret_cast<const uint4 *>(Wt) + q);
+    }
+    // the three lines of input z zi into ring slot zi mod 4 (zero outside the volume)
+    auto fetch = [&](int zi) {
+        unsigned char *dst = ring + (zi & 3) * SET;
+        for (int q = t; q < 3 * ROWS * KCH; q += 128) {
+            const int L = q / (ROWS * KCH), rem = q - L * (ROWS * KCH);
+            const int r = rem / KCH, c = rem - r * KCH;
+            const int gy = y + L - 1, gx = x0 - 1 + r;
+            const bool in = zi >= 0 && zi < D && gy >= 0 && gy < H && gx >= 0 && gx < Wd;
+            const bf16 *src = in ? X + ((((size_t)b * D + zi) * H + gy) * Wd + gx) * CIN + 8 * c : X;
+            cp_async16(dst + L * LINE + c * P + r * 16, src, in);
+        }
+        asm volatile("cp.async.commit_group;" ::: "memory");
+    };
+    fetch(z0 - 1);
+    fetch(z0);
+    fetch(z0 + 1);
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const unsigned tmem = tmem_slot;
+    constexpr unsigned idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((unsigned)(COUT >> 3) << 17) | (8u << 24);
+    bool ok = true;
+    int issued = -1;  // the last row whose MMAs were committed
+    for (int i = 0; i < nrows; ++i) {
+        const int z = z0 + i;
+        if (i >= 1) {  // row z - 1 done: its lines' slot is refilled below, its accumulator read
+            if (!mbar_wait(&bar[(i - 1) & 1], (unsigned)((i - 1) >> 1) & 1u)) ok = false;
+            if (!__syncthreads_and(ok ? 1 : 0)) break;
+            asm volatile("tcgen05.fence::after_thread_sync;");
+        }
+        const bool more = i + 1 < nrows;
+        if (more) fetch(z + 2);  // slot (z + 2) mod 4 held the lines of z - 2, last read by row z - 1
+        // the lines of z - 1 .. z + 1 in place; the group just issued may stay in flight
+        if (more)
+            asm volatile("cp.async.wait_group 1;" ::: "memory");
+        else
+            asm volatile("cp.async.wait_group 0;" ::: "memory");
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");  // generic writes -> tensor-core reads
+        __syncthreads();
+        if (t == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;");
+            const unsigned d = tmem + (unsigned)((i & 1) * COUT);
+            for (int tap = 0; tap < 27; ++tap) {
+                const int dz = tap / 9, dy = (tap / 3) % 3, dx = tap % 3;
+                const unsigned char *Ab = ring + ((z + dz - 1) & 3) * SET + dy * LINE + dx * 16;
+#pragma unroll
+                for (int kk = 0; kk < CIN / 16; ++kk) {
+                    const uint64_t ad = umma_desc(Ab + kk * 2 * P, P, 128);
+                    const uint64_t bd = umma_desc(sB + tap * B_TAP + kk * 128, 128, CIN * 16);
+                    const unsigned accumulate = (tap > 0 || kk > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n"
+                        " .reg .pred p;\n"
+                        " setp.ne.b32 p, %4, 0;\n"
+                        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n"
+                        "}\n" ::"r"(d),
+                        "l"(ad), "l"(bd), "r"(idesc), "r"(accumulate));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&bar[i & 1]))
+                         : "memory");
+        }
+        issued = i;
+        // row z - 1 out of the other accumulator while the MMAs of row z run;
+        // its reads precede the next row's MMAs into it (barrier at the loop top)
+        if (i >= 1)
+            rows_epilogue<CIN, COUT, COUTR>(tmem + (unsigned)(((i - 1) & 1) * COUT), warp,
+                                            Y + ((((size_t)b * D + z - 1) * H + y) * Wd + x0 + t) * COUTR, bias,
+                                            relu);
+        asm volatile("tcgen05.fence::before_thread_sync;");
+    }
+    // the last commit tracks every MMA issued before it: drain it (bounded)
+    // before the accumulator is read or the tensor memory released
+    if (issued >= 0 && !mbar_wait(&bar[issued & 1], (unsigned)(issued >> 1) & 1u)) ok = false;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const int all_ok = __syncthreads_and(ok && issued == nrows - 1 ? 1 : 0);
+    if (all_ok)
+        rows_epilogue<CIN, COUT, COUTR>(tmem + (unsigned)((issued & 1) * COUT), warp,
+                                        Y + ((((size_t)b * D + z0 + issued) * H + y) * Wd + x0 + t) * COUTR, bias,
+                                        relu);
+    else if (t == 0)
+        atomicExch(status, 1);
+    asm volatile("cp.async.wait_group 0;" ::: "memory");  // no copy into shared memory outlives the block
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
@@ -360,54 +716,6 @@ __global__ void __launch_bounds__(128) conv3d_wgrad_tc_kernel(const bf16 *__rest
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
-}
-
-// Direct convolution on the CUDA cores for the narrow layers (Cin or Cout
-// below 16): one thread per output voxel, all output channels.
-template <int CIN, int COUT>
-__global__ void conv3d_direct_kernel(const bf16 *__restrict__ X, const bf16 *__restrict__ Wt,
-                                     const float *__restrict__ bias, bf16 *__restrict__ Y, long nvox, int D, int H,
-                                     int Wd, int relu)
-{
-    __shared__ float w[27 * COUT * CIN];
-    for (int i = threadIdx.x; i < 27 * COUT * CIN; i += blockDim.x) w[i] = __bfloat162float(Wt[i]);
-    __syncthreads();
-    for (long v = blockIdx.x * (long)blockDim.x + threadIdx.x; v < nvox; v += (long)gridDim.x * blockDim.x) {
-        const int x = (int)(v % Wd);
-        long r = v / Wd;
-        const int y = (int)(r % H);
-        r /= H;
-        const int z = (int)(r % D);
-        const long b = r / D;
-        float acc[COUT];
-#pragma unroll
-        for (int co = 0; co < COUT; ++co) acc[co] = bias ? bias[co] : 0.0f;
-        for (int dz = 0; dz < 3; ++dz) {
-            const int gz = z + dz - 1;
-            if ((unsigned)gz >= (unsigned)D) continue;
-            for (int dy = 0; dy < 3; ++dy) {
-                const int gy = y + dy - 1;
-                if ((unsigned)gy >= (unsigned)H) continue;
-                for (int dx = 0; dx < 3; ++dx) {
-                    const int gx = x + dx - 1;
-                    if ((unsigned)gx >= (unsigned)Wd) continue;
-                    const int tap = (dz * 3 + dy) * 3 + dx;
-                    const bf16 *xp = X + ((((size_t)b * D + gz) * H + gy) * Wd + gx) * CIN;
-#pragma unroll
-                    for (int ci = 0; ci < CIN; ++ci) {
-                        const float xv = __bfloat162float(xp[ci]);
-#pragma unroll
-                        for (int co = 0; co < COUT; ++co) acc[co] = fmaf(w[(tap * COUT + co) * CIN + ci], xv, acc[co]);
-                    }
-                }
-            }
-        }
-#pragma unroll
-        for (int co = 0; co < COUT; ++co) {
-            const float o = relu ? fmaxf(acc[co], 0.0f) : acc[co];
-            Y[v * COUT + co] = __float2bfloat16_rn(o);
-        }
-    }
 }
 
 // dW for the narrow layers: one block per (tap, co, ci) triple range, FP32 sums
@@ -625,13 +933,13 @@ long grid_for(long n)
     return std::max<long>(1, std::min<long>((n + 255) / 256, (long)device_sm_count() * 16));
 }
 
-template <int CIN, int COUT>
+template <int CIN, int COUT, int COUTR = COUT>
 cudaError_t conv_tc_launch(const bf16 *X, const bf16 *W, const float *bias, bf16 *Y, int B, int D, int H, int Wd,
                            int relu, cudaStream_t s)
 {
     const Tile tl = conv_tile(Wd, H);
     const size_t smem = (size_t)2 * (128 * CIN + COUT * CIN) * sizeof(bf16);
-    auto k = conv3d_tc_kernel<CIN, COUT>;
+    auto k = conv3d_tc_kernel<CIN, COUT, COUTR>;
     cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int *status = nullptr;
@@ -639,6 +947,35 @@ cudaError_t conv_tc_launch(const bf16 *X, const bf16 *W, const float *bias, bf16
     if (e != cudaSuccess) return e;
     const long blocks = (long)B * (D / tl.TZ) * (H / tl.TY) * (Wd / tl.TX);
     k<<<(unsigned)blocks, 128, smem, s>>>(X, W, bias, Y, D, H, Wd, relu, status);
+    return cudaGetLastError();
+}
+
+template <int CIN, int COUT, int COUTR = COUT>
+cudaError_t conv_rows_launch(const bf16 *X, const bf16 *W, const float *bias, bf16 *Y, int B, int D, int H, int Wd,
+                             int relu, cudaStream_t s)
+{
+    const size_t smem = (size_t)4 * 3 * (CIN / 8) * 130 * 16 + (size_t)27 * COUT * CIN * sizeof(bf16);
+    auto k = conv3d_tc_rows_kernel<CIN, COUT, COUTR>;
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+    int *status = nullptr;
+    e = status_word(&status);
+    if (e != cudaSuccess) return e;
+    const long blocks = (long)B * ((D + kRowsZ - 1) / kRowsZ) * H * (Wd / 128);
+    k<<<(unsigned)blocks, 128, smem, s>>>(X, W, bias, Y, D, H, Wd, relu, status);
+    return cudaGetLastError();
+}
+
+template <int COUT>
+cudaError_t conv_k27_launch(const bf16 *X, const bf16 *W, const float *bias, bf16 *Y, int B, int D, int H, int Wd,
+                            int relu, cudaStream_t s)
+{
+    const Tile tl = conv_tile(Wd, H);
+    int *status = nullptr;
+    cudaError_t e = status_word(&status);
+    if (e != cudaSuccess) return e;
+    const long blocks = (long)B * (D / tl.TZ) * (H / tl.TY) * (Wd / tl.TX);
+    conv3d_tc_k27_kernel<COUT><<<(unsigned)blocks, 128, 0, s>>>(X, W, bias, Y, D, H, Wd, relu, status);
     return cudaGetLastError();
 }
 
@@ -666,16 +1003,6 @@ cudaError_t wgrad_tc_launch(const bf16 *X, const bf16 *dY, float *dW, int B, int
     return cudaGetLastError();
 }
 
-template <int CIN, int COUT>
-cudaError_t direct_launch(const bf16 *X, const bf16 *W, const float *bias, bf16 *Y, int B, int D, int H, int Wd,
-                          int relu, cudaStream_t s)
-{
-    const long nvox = (long)B * D * H * Wd;
-    const long blocks = std::min<long>((nvox + 255) / 256, (long)device_sm_count() * 16);
-    conv3d_direct_kernel<CIN, COUT><<<(unsigned)blocks, 256, 0, s>>>(X, W, bias, Y, nvox, D, H, Wd, relu);
-    return cudaGetLastError();
-}
-
 }  // namespace
 
 bool conv_supported(int cin, int cout)
@@ -690,6 +1017,12 @@ cudaError_t launch_conv3d(const void *X, const void *W, const float *bias, void 
 {
     const bf16 *x = (const bf16 *)X, *w = (const bf16 *)W;
     bf16 *y = (bf16 *)Y;
+    // 16 input channels on rows of 128 voxels: the row-pipelined kernel
+    if (cin == 16 && Wd % 128 == 0) {
+        if (cout == 16) return conv_rows_launch<16, 16>(x, w, bias, y, B, D, H, Wd, relu, s);
+        if (cout == 32) return conv_rows_launch<16, 32>(x, w, bias, y, B, D, H, Wd, relu, s);
+        if (cout == 1) return conv_rows_launch<16, 16, 1>(x, w, bias, y, B, D, H, Wd, relu, s);
+    }
 #define PYRO_CONV_CASE(ci, co)                                                      \
     if (cin == ci && cout == co) return conv_tc_launch<ci, co>(x, w, bias, y, B, D, H, Wd, relu, s);
     PYRO_CONV_CASE(16, 16)
@@ -702,8 +1035,10 @@ cudaError_t launch_conv3d(const void *X, const void *W, const float *bias, void 
     PYRO_CONV_CASE(64, 32)
     PYRO_CONV_CASE(64, 64)
 #undef PYRO_CONV_CASE
-    if (cin == 1 && cout == 16) return direct_launch<1, 16>(x, w, bias, y, B, D, H, Wd, relu, s);
-    if (cin == 16 && cout == 1) return direct_launch<16, 1>(x, w, bias, y, B, D, H, Wd, relu, s);
+    // the narrow layers on the tensor cores too: one input channel as a
+    // K = 27 tap GEMM, one output channel as N = 16 with 15 zero rows
+    if (cin == 1 && cout == 16) return conv_k27_launch<16>(x, w, bias, y, B, D, H, Wd, relu, s);
+    if (cin == 16 && cout == 1) return conv_tc_launch<16, 16, 1>(x, w, bias, y, B, D, H, Wd, relu, s);
     return cudaErrorInvalidValue;
 }
 

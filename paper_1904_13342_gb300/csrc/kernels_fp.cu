@@ -563,7 +563,7 @@ __global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const
 constexpr int kFPCWarps = 4;
 
 struct ColumnWindow {
-    float acc;  // forward: the ray sum; adjoint: w times the ray's datum
+    float acc;  // the ray sum
     int ma, mb; // samples of the window's rows that can touch the volume
 };
 
@@ -649,43 +649,6 @@ __device__ __forceinline__ void column_step(ColumnWindow &W, const ZSeg &z, floa
     const int j = __float_as_int(tz) - __float_as_int(tzb);  // own cell relative to the window's run
     const float g0 = __shfl_sync(0xffffffffu, g, j), g1 = __shfl_sync(0xffffffffu, g, j + 1);
     W.acc += fmaf(fz - magic_to_float(tz), g1 - g0, g0);
-}
-
-// Transpose of column_step: the lane's ray datum y is split between the two
-// z cells of its sample in the window's run (a shared-memory array of 32
-// sums), then each lane spreads the sum of its cell over the four (x, y)
-// columns with global atomics: four atomics per 32 samples.  Only the taps
-// with z in [zs0, zs1) are written (the host passes the whole volume:
-// accumulating a volume larger than L2 slab by slab, each slab a launch,
-// was measured slower, 2.7 s against 1.7 s at 512^3, because windows that
-// straddle a slab boundary repeat their work).
-__device__ __forceinline__ void column_step_adjoint(const ColumnWindow &W, const ZSeg &z, float dz, int lane, int zs0,
-                                                    int zs1, float *const (&c)[4], const PlaneXY &q, float *run)
-{
-    const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
-    const int zi = z.zbase + __float_as_int(tzb);
-    const float fz = fmaf(dz, z.q, z.f);
-    const float tz = floor_magic(fz);
-    // 0..30 for every real row (host-checked); clamped so that no shared
-    // access leaves the run
-    const int j = min(max(__float_as_int(tz) - __float_as_int(tzb), 0), 30);
-    const float az = fz - magic_to_float(tz);
-    const float y = W.acc;
-    if (y != 0.0f) {
-        atomicAdd(run + j, fmaf(-az, y, y));
-        atomicAdd(run + j + 1, az * y);
-    }
-    __syncwarp();
-    const float d = run[lane];
-    run[lane] = 0.0f;
-    __syncwarp();
-    // only this launch's slab: the taps of the other z belong to other launches
-    if (d != 0.0f && zi >= zs0 && zi < zs1) {
-        atomicAdd(c[0] + zi, q.w00 * d);
-        atomicAdd(c[1] + zi, q.w10 * d);
-        atomicAdd(c[2] + zi, q.w01 * d);
-        atomicAdd(c[3] + zi, q.w11 * d);
-    }
 }
 
 // Two consecutive depth planes (dx, dx + 1) of the column's track at once:
@@ -787,33 +750,24 @@ __device__ __forceinline__ void column_planes_paired(ColumnWindow (&W)[R], const
 // Depth planes m0..m1 of all R windows, the track re-anchored every
 // kFPSegment planes.  CHECK skips the windows whose rows cannot touch the
 // volume on a plane (outside the planes every window reaches; elsewhere the
-// skipped terms would be exact zeros anyway: the forward reads the zero
-// padding, the adjoint writes into it).
-template <typename T, int R, bool CHECK, bool ADJ>
+// skipped terms would be exact zeros anyway: the taps read the zero padding).
+template <typename T, int R, bool CHECK>
 __device__ __forceinline__ void column_planes(ColumnWindow (&W)[R], const ZSeg (&zs)[R], const float4 *track, int mz,
-                                              int m0, int m1, int lane, T *vp, const FP3DParams &p, int sxp, int syp,
-                                              float *runs)
+                                              int m0, int m1, const T *vp, const FP3DParams &p, int sxp, int syp)
 {
-    // unrolled by 4 on the forward path (measured 1 % faster than 2, while
-    // 1, 6 and 8 were slower) and by 2 on the adjoint's
-    constexpr int kUnroll = ADJ ? 2 : 4;
+    // unrolled by 4 (measured 1 % faster than 2, while 1, 6 and 8 were slower)
     for (int ms = m0; ms <= m1; ms += kFPSegment) {
         const int me = min(ms + kFPSegment - 1, m1);
         const TrackSeg ts = track_seg(track, ms, sxp, syp);
         float dx = 0.0f, dz = (float)(ms - mz);
-#pragma unroll kUnroll
+#pragma unroll 4
         for (int m = ms; m <= me; ++m, dx += 1.0f, dz += 1.0f) {
             const PlaneXY q = plane_xy(ts, dx, sxp, syp);
-            T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+            const T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-                if constexpr (ADJ) {
-                    column_step_adjoint(W[r], zs[r], dz, lane, p.zs0, p.zs1, c, q, runs + 32 * r);
-                } else {
-                    const T *const cr[4] = {c[0], c[1], c[2], c[3]};
-                    column_step(W[r], zs[r], dz, p.nz, cr, q);
-                }
+                column_step(W[r], zs[r], dz, p.nz, c, q);
             }
         }
     }
@@ -860,13 +814,12 @@ __device__ __forceinline__ void store_track(const FP3DParams &p, int v, int k, i
     }
 }
 
-// Set-up shared by the forward and adjoint column kernels: the column's
-// (x, y) track (float-float, into `track`), the windows' rays and ranges
-// (each lane's z in float-float into `zray`); returns the union [mlo, mhi]
-// of the windows' ranges and the planes [clo, chi] every window reaches.
-// last_low: bit r set when window r's lowest row is its last (lane 31).
-// zlo, zhi: the open z interval whose samples matter (the volume's (-1, nz),
-// or a slab's (zs0 - 1, zs1) for the slab-blocked adjoint).
+// Set-up of the column kernel: the column's (x, y) track (float-float, into
+// `track`), the windows' rays and ranges (each lane's z in float-float into
+// `zray`); returns the union [mlo, mhi] of the windows' ranges and the
+// planes [clo, chi] every window reaches.  last_low: bit r set when window
+// r's lowest row is its last (lane 31).  zlo, zhi: the open z interval whose
+// samples matter (the volume's (-1, nz)).
 template <int R>
 __device__ __forceinline__ void column_setup(const FP3DParams &p, int v, int k, int row0, int lane, float4 *track,
                                              ColumnWindow (&W)[R], float4 *zray, int &last_low, int &mlo, int &mhi,
@@ -915,23 +868,21 @@ __device__ __forceinline__ void column_setup(const FP3DParams &p, int v, int k, 
 }
 
 // all planes mlo..mhi: the rays' z anchored at the middle plane, then the
-// planes split by window coverage ([clo, chi] without window checks)
-template <typename T, int R, bool ADJ>
+// planes split by window coverage ([clo, chi] without window checks, in
+// plane pairs)
+template <typename T, int R>
 __device__ __forceinline__ void column_march(ColumnWindow (&W)[R], const float4 *track, const float4 *zray,
-                                             int last_low, int mlo, int mhi, int clo, int chi, int lane, T *vp,
-                                             const FP3DParams &p, float *runs)
+                                             int last_low, int mlo, int mhi, int clo, int chi, int lane, const T *vp,
+                                             const FP3DParams &p)
 {
     const int sxp = p.nz + 2, syp = (p.nx + 2 * kFPPadXY) * (p.nz + 2);
     const int mz = mlo + (mhi - mlo) / 2;
     ZSeg zs[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) zs[r] = zseg(zray[32 * r + lane], (last_low >> r & 1) ? 31 : 0, lane, mz);
-    column_planes<T, R, true, ADJ>(W, zs, track, mz, mlo, clo - 1, lane, vp, p, sxp, syp, runs);
-    if constexpr (ADJ)
-        column_planes<T, R, false, ADJ>(W, zs, track, mz, clo, chi, lane, vp, p, sxp, syp, runs);
-    else
-        column_planes_paired<T, R>(W, zs, track, mz, clo, chi, vp, p, sxp, syp);
-    column_planes<T, R, true, ADJ>(W, zs, track, mz, max(chi + 1, clo), mhi, lane, vp, p, sxp, syp, runs);
+    column_planes<T, R, true>(W, zs, track, mz, mlo, clo - 1, vp, p, sxp, syp);
+    column_planes_paired<T, R>(W, zs, track, mz, clo, chi, vp, p, sxp, syp);
+    column_planes<T, R, true>(W, zs, track, mz, max(chi + 1, clo), mhi, vp, p, sxp, syp);
 }
 
 template <typename T, typename TO, int R>
@@ -951,8 +902,7 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__
     column_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
                     -1.0f, (float)p.nz);
     if (mlo <= mhi)
-        column_march<T, R, false>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane,
-                                  const_cast<T *>(vp), p, nullptr);
+        column_march<T, R>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp, p);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int l = row0 + 32 * r + lane;
@@ -960,42 +910,6 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__
             sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] =
                 to_storage<TO>(ray3d(p, v, k, l).w * W[r].acc);
     }
-}
-
-// Exact adjoint of fp3d_column_kernel, accumulated into a zeroed padded
-// z-major FP32 volume (the padding collects the terms of samples outside the
-// volume and is discarded afterwards).
-template <int R>
-__global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_adjoint_kernel(const float *__restrict__ sino,
-                                                                             float *__restrict__ vp,
-                                                                             const __grid_constant__ FP3DParams p,
-                                                                             int b)
-{
-    __shared__ float runs[kFPCWarps][R * 32];
-    __shared__ float4 zrays[kFPCWarps][R * 32];
-    __shared__ float4 tracks[kFPCWarps][2];
-    const int lane = threadIdx.x;
-    const int k = blockIdx.y * kFPCWarps + threadIdx.y;
-    const int v = blockIdx.x;
-    if (k >= p.nu) return;  // whole warp
-    float *run = runs[threadIdx.y];
-#pragma unroll
-    for (int r = 0; r < R; ++r) run[32 * r + lane] = 0.0f;
-    __syncwarp();
-    const int row0 = blockIdx.z * (32 * R);
-    ColumnWindow W[R];
-    int last_low, mlo, mhi, clo, chi;
-    column_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
-                    (float)(p.zs0 - 1), (float)p.zs1);
-    if (mlo > mhi) return;  // whole warp: no sample of its rays touches the slab
-#pragma unroll
-    for (int r = 0; r < R; ++r) {
-        const int l = row0 + 32 * r + lane;
-        W[r].acc = l < p.nv ? ray3d(p, v, k, l).w * sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k]
-                            : 0.0f;
-    }
-    column_march<float, R, true>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp,
-                                 p, run);
 }
 
 // ---- two rays per lane: windows of up to 64 rows on one 32-voxel run -----
@@ -1008,7 +922,7 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_adjoint_kernel(con
 // combinations for up to twice the rays.  The arithmetic and the anchoring
 // of every ray are those of fp3d_column_kernel.
 struct PairRowsWindow {
-    float acc[2];  // forward: the ray sums; adjoint: w times the rays' data
+    float acc[2];  // the rays' sums
     int ma, mb;    // samples of the window's rows that can touch the volume
 };
 
@@ -1112,71 +1026,32 @@ __device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, const ZSeg2 &z
     }
 }
 
-// transpose of pair_rows_step: both rays' data go into the run's cells, then
-// each lane spreads its cell over the four (x, y) columns (as
-// column_step_adjoint)
-__device__ __forceinline__ void pair_rows_step_adjoint(const PairRowsWindow &W, const ZSeg2 &z, float dz, int lane,
-                                                       int zs0, int zs1, float *const (&c)[4], const PlaneXY &q,
-                                                       float *run)
-{
-    const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
-    const int zi = z.zbase + __float_as_int(tzb);
-#pragma unroll
-    for (int h = 0; h < 2; ++h) {
-        const float fz = fmaf(dz, z.q[h], z.f[h]);
-        const float tz = floor_magic(fz);
-        const int j = min(max(__float_as_int(tz) - __float_as_int(tzb), 0), 30);
-        const float az = fz - magic_to_float(tz);
-        const float y = W.acc[h];
-        if (y != 0.0f) {
-            atomicAdd(run + j, fmaf(-az, y, y));
-            atomicAdd(run + j + 1, az * y);
-        }
-    }
-    __syncwarp();
-    const float d = run[lane];
-    run[lane] = 0.0f;
-    __syncwarp();
-    if (d != 0.0f && zi >= zs0 && zi < zs1) {
-        atomicAdd(c[0] + zi, q.w00 * d);
-        atomicAdd(c[1] + zi, q.w10 * d);
-        atomicAdd(c[2] + zi, q.w01 * d);
-        atomicAdd(c[3] + zi, q.w11 * d);
-    }
-}
-
-template <typename T, int R, bool CHECK, bool ADJ>
+template <typename T, int R, bool CHECK>
 __device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], const ZSeg2 (&zs)[R], const float4 *track,
-                                                 int mz, int m0, int m1, int lane, T *vp, const FP3DParams &p, int sxp,
-                                                 int syp, float *runs)
+                                                 int mz, int m0, int m1, const T *vp, const FP3DParams &p, int sxp,
+                                                 int syp)
 {
-    constexpr int kUnroll = ADJ ? 2 : 4;
     for (int ms = m0; ms <= m1; ms += kFPSegment) {
         const int me = min(ms + kFPSegment - 1, m1);
         const TrackSeg ts = track_seg(track, ms, sxp, syp);
         float dx = 0.0f, dz = (float)(ms - mz);
-#pragma unroll kUnroll
+#pragma unroll 4
         for (int m = ms; m <= me; ++m, dx += 1.0f, dz += 1.0f) {
             const PlaneXY q = plane_xy(ts, dx, sxp, syp);
-            T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+            const T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-                if constexpr (ADJ) {
-                    pair_rows_step_adjoint(W[r], zs[r], dz, lane, p.zs0, p.zs1, c, q, runs + 32 * r);
-                } else {
-                    const T *const cr[4] = {c[0], c[1], c[2], c[3]};
-                    pair_rows_step(W[r], zs[r], dz, p.nz, cr, q);
-                }
+                pair_rows_step(W[r], zs[r], dz, p.nz, c, q);
             }
         }
     }
 }
 
-template <typename T, int R, bool ADJ>
+template <typename T, int R>
 __device__ __forceinline__ void pair_rows_march(PairRowsWindow (&W)[R], const float4 *track, const float4 *zray,
-                                                int last_low, int mlo, int mhi, int clo, int chi, int lane, T *vp,
-                                                const FP3DParams &p, float *runs)
+                                                int last_low, int mlo, int mhi, int clo, int chi, int lane, const T *vp,
+                                                const FP3DParams &p)
 {
     const int sxp = p.nz + 2, syp = (p.nx + 2 * kFPPadXY) * (p.nz + 2);
     const int mz = mlo + (mhi - mlo) / 2;
@@ -1186,9 +1061,9 @@ __device__ __forceinline__ void pair_rows_march(PairRowsWindow (&W)[R], const fl
         const bool hi = last_low >> r & 1;
         zs[r] = zseg2(zray[(2 * r) * 32 + lane], zray[(2 * r + 1) * 32 + lane], hi ? p.pair_rows - 33 : 0, hi, lane, mz);
     }
-    pair_rows_planes<T, R, true, ADJ>(W, zs, track, mz, mlo, clo - 1, lane, vp, p, sxp, syp, runs);
-    pair_rows_planes<T, R, false, ADJ>(W, zs, track, mz, clo, chi, lane, vp, p, sxp, syp, runs);
-    pair_rows_planes<T, R, true, ADJ>(W, zs, track, mz, max(chi + 1, clo), mhi, lane, vp, p, sxp, syp, runs);
+    pair_rows_planes<T, R, true>(W, zs, track, mz, mlo, clo - 1, vp, p, sxp, syp);
+    pair_rows_planes<T, R, false>(W, zs, track, mz, clo, chi, vp, p, sxp, syp);
+    pair_rows_planes<T, R, true>(W, zs, track, mz, max(chi + 1, clo), mhi, vp, p, sxp, syp);
 }
 
 template <typename T, typename TO, int R>
@@ -1209,8 +1084,7 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_kernel(const T 
     pair_rows_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
                        -1.0f, (float)p.nz);
     if (mlo <= mhi)
-        pair_rows_march<T, R, false>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane,
-                                     const_cast<T *>(vp), p, nullptr);
+        pair_rows_march<T, R>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp, p);
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
@@ -1220,62 +1094,6 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_kernel(const T 
                 sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k] =
                     to_storage<TO>(ray3d(p, v, k, l).w * W[r].acc[h]);
         }
-}
-
-template <int R>
-__global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_adjoint_kernel(const float *__restrict__ sino,
-                                                                                float *__restrict__ vp,
-                                                                                const __grid_constant__ FP3DParams p,
-                                                                                int b)
-{
-    __shared__ float runs[kFPCWarps][R * 32];
-    __shared__ float4 zrays[kFPCWarps][2 * R * 32];
-    __shared__ float4 tracks[kFPCWarps][2];
-    const int lane = threadIdx.x;
-    const int k = blockIdx.y * kFPCWarps + threadIdx.y;
-    const int v = blockIdx.x;
-    if (k >= p.nu) return;  // whole warp
-    float *run = runs[threadIdx.y];
-#pragma unroll
-    for (int r = 0; r < R; ++r) run[32 * r + lane] = 0.0f;
-    __syncwarp();
-    const int WR = p.pair_rows;
-    const int row0 = blockIdx.z * (R * WR);
-    PairRowsWindow W[R];
-    int last_low, mlo, mhi, clo, chi;
-    pair_rows_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
-                       (float)(p.zs0 - 1), (float)p.zs1);
-    if (mlo > mhi) return;  // whole warp: no sample of its rays touches the slab
-#pragma unroll
-    for (int r = 0; r < R; ++r)
-#pragma unroll
-        for (int h = 0; h < 2; ++h) {
-            const int l = row0 + r * WR + 32 * h + lane;
-            W[r].acc[h] = (l < p.nv && 32 * h + lane < WR)
-                              ? ray3d(p, v, k, l).w * sino[(((size_t)b * p.views_total + p.view0 + v) * p.nv + l) * p.nu + k]
-                              : 0.0f;
-        }
-    pair_rows_march<float, R, true>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp,
-                                    p, run);
-}
-
-// interior of the padded z-major array -> [z][y][x]
-__global__ void __launch_bounds__(256) relayout_unpad_kernel(const float *__restrict__ vp, float *__restrict__ vol,
-                                                             int nx, int ny, int nz)
-{
-    __shared__ float tile[32][33];
-    const int nxp = nx + 2 * kFPPadXY, nzp = nz + 2;
-    const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32, y = blockIdx.z;
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int x = x0 + i, z = z0 + threadIdx.x;
-        if (x < nx && z < nz)
-            tile[i][threadIdx.x] = vp[((size_t)(y + kFPPadXY) * nxp + x + kFPPadXY) * nzp + z + 1];
-    }
-    __syncthreads();
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int z = z0 + i, x = x0 + threadIdx.x;
-        if (x < nx && z < nz) vol[((size_t)z * ny + y) * nx + x] = tile[threadIdx.x][i];
-    }
 }
 
 // [z][y][x] -> [y + P][x + P][z + 1] of the zero-padded (ny + 2P)(nx + 2P)
@@ -1640,62 +1458,6 @@ cudaError_t launch_fp3d_column(const void *vp, void *sino, int b, const FP3DPara
         column_any<__nv_bfloat16, __nv_bfloat16>(vp, sino, b, p, s);
     else
         return cudaErrorInvalidValue;
-    return cudaGetLastError();
-}
-
-template <int R>
-static void column_adjoint_launch(const float *sino, float *vp, int b, const FP3DParams &p, cudaStream_t s)
-{
-    dim3 block(32, kFPCWarps);
-    dim3 grid((unsigned)p.n_views, (p.nu + kFPCWarps - 1) / kFPCWarps, (p.nv + 32 * R - 1) / (32 * R));
-    fp3d_column_adjoint_kernel<R><<<grid, block, 0, s>>>(sino, vp, p, b);
-}
-
-template <int R>
-static void pair_rows_adjoint_launch(const float *sino, float *vp, int b, const FP3DParams &p, cudaStream_t s)
-{
-    dim3 block(32, kFPCWarps);
-    dim3 grid((unsigned)p.n_views, (p.nu + kFPCWarps - 1) / kFPCWarps, (p.nv + R * p.pair_rows - 1) / (R * p.pair_rows));
-    fp3d_pair_rows_adjoint_kernel<R><<<grid, block, 0, s>>>(sino, vp, p, b);
-}
-
-cudaError_t launch_fp3d_column_adjoint(const void *sino, void *vp, int b, const FP3DParams &p, cudaStream_t s)
-{
-    if (p.pair_rows > 0) {
-        const float *si = (const float *)sino;
-        float *vo = (float *)vp;
-        switch (pair_rows_windows_per_warp(p.nv, p.pair_rows)) {
-        case 4: pair_rows_adjoint_launch<4>(si, vo, b, p, s); break;
-        case 3: pair_rows_adjoint_launch<3>(si, vo, b, p, s); break;
-        case 2: pair_rows_adjoint_launch<2>(si, vo, b, p, s); break;
-        default: pair_rows_adjoint_launch<1>(si, vo, b, p, s); break;
-        }
-        return cudaGetLastError();
-    }
-    switch (column_windows_per_warp(p.nv)) {
-    case 5:
-        column_adjoint_launch<5>((const float *)sino, (float *)vp, b, p, s);
-        break;
-    case 4:
-        column_adjoint_launch<4>((const float *)sino, (float *)vp, b, p, s);
-        break;
-    case 3:
-        column_adjoint_launch<3>((const float *)sino, (float *)vp, b, p, s);
-        break;
-    case 2:
-        column_adjoint_launch<2>((const float *)sino, (float *)vp, b, p, s);
-        break;
-    default:
-        column_adjoint_launch<1>((const float *)sino, (float *)vp, b, p, s);
-        break;
-    }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_relayout_unpad(const void *vp, void *vol, int nx, int ny, int nz, cudaStream_t s)
-{
-    dim3 block(32, 8), grid((nx + 31) / 32, (nz + 31) / 32, ny);
-    relayout_unpad_kernel<<<grid, block, 0, s>>>((const float *)vp, (float *)vol, nx, ny, nz);
     return cudaGetLastError();
 }
 

@@ -413,8 +413,6 @@ int fill_fp3d(const Geo3D &G, int v0, int nvw, FP3DParams &p)
     p.dt_lo = (float)(G.step - (double)p.dt);
     p.column_shared = 1;
     p.pair_rows = 64;
-    p.zs0 = 0;
-    p.zs1 = G.nz;
     auto put = [](float &hi, float &lo, double x) {
         hi = (float)x;
         lo = (float)(x - (double)hi);
@@ -1762,7 +1760,10 @@ static int conv_dims_ok(int batch, int nz, int ny, int nx, int cin, int cout)
 {
     PYRO_CHECK(batch >= 0 && nz > 0 && ny > 0 && nx > 0, "bad activation shape");
     PYRO_CHECK(conv_supported(cin, cout), "unsupported channel pair (%d, %d)", cin, cout);
-    if (cin != 1 && cout != 1) {
+    if (cin == 16 && nx % 128 == 0) {
+        // rows of 128 output voxels along x: any nz, ny
+        PYRO_CHECK((long)batch * nz * ny * (nx / 128) < (1L << 31), "too many voxel rows");
+    } else {
         // blocks of 128 output voxels: TX = min(nx, 64), TY = min(ny, 128 / TX), TZ = 128 / (TX TY)
         PYRO_CHECK(nx == 8 || nx == 16 || nx == 32 || (nx >= 64 && nx % 64 == 0),
                    "nx=%d must be 8, 16, 32 or a multiple of 64", nx);

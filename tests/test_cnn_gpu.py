@@ -43,12 +43,31 @@ def test_conv3d_forward(cin, cout, n):
         assert rel(y, ref) < 4e-3
 
 
-def test_conv3d_forward_wide_row():
-    """nx = 128: two 64-voxel tiles per row."""
-    x = rand_bf16((1, 3, 4, 128, 16), 3)
-    w = rand_bf16((27, 32, 16), 4, scale=0.05)
-    y = B.pyro_conv3d(x, w, None, False)
-    assert rel(y, R.conv3d(x.double().cpu(), w.double().cpu())) < 4e-3
+@pytest.mark.parametrize("cout", [16, 32, 1])
+@pytest.mark.parametrize("shape", [(1, 3, 4, 128), (2, 2, 3, 256)])
+def test_conv3d_forward_wide_row(shape, cout):
+    """Rows of 128 voxels or more and 16 input channels take the kernel that
+    stages nine input lines per 128-voxel output row (every z, y and x edge
+    of the zero padding is in these shapes), one output channel included."""
+    x = rand_bf16((*shape, 16), 3)
+    w = rand_bf16((27, cout, 16), 4, scale=0.05)
+    bias = torch.linspace(-0.1, 0.1, cout, device=DEV)
+    for relu in (False, True):
+        y = B.pyro_conv3d(x, w, bias, relu)
+        assert rel(y, R.conv3d(x.double().cpu(), w.double().cpu(), bias.double().cpu(), relu)) < 4e-3
+
+
+@pytest.mark.parametrize("cin,cout", [(16, 16), (1, 16), (16, 1)])
+def test_conv3d_data_gradient_wide_row(cin, cout):
+    """The data gradient through the flipped weights on 128-voxel rows."""
+    x = rand_bf16((1, 3, 4, 128, cin), 8)
+    w = rand_bf16((27, cout, cin), 9, scale=0.05)
+    dy = rand_bf16((1, 3, 4, 128, cout), 10)
+    dx = B.pyro_conv3d(dy, B.pyro_conv3d_flip_weights(w), None, False)
+    xr = x.double().cpu().permute(0, 4, 1, 2, 3)
+    ref = torch.nn.grad.conv3d_input(xr.shape, R.to_kernel(w.double().cpu()),
+                                     dy.double().cpu().permute(0, 4, 1, 2, 3), padding=1)
+    assert rel(dx, ref.permute(0, 2, 3, 4, 1)) < 4e-3
 
 
 @pytest.mark.parametrize("cin,cout", [(16, 16), (16, 32), (32, 64), (64, 64), (16, 1)])
