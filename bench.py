@@ -48,6 +48,9 @@ the error on the central 64^3 crop.
 
 `--workload configs` times the 2D workloads (128^2 parallel beam; a batch of
 16 512^2 fan-beam phantoms) on the GPU and through the oracle.
+
+`--workload cnn-128` times the residual CNN initialiser's forward pass on two
+128^3 volumes (ms per pass) with a per-layer convolution breakdown.
 """
 from __future__ import annotations
 
@@ -320,7 +323,7 @@ def run_gpu(args):
         "e2e": {"value": round(e2e, 3), "unit": UNIT, "h2d_bytes_per_step": int(host_vol.numel() * 4),
                 "d2h_bytes_per_step": int(host_out[0].numel() * 4), "steps": E,
                 "copies": "pinned host buffers; H2D and D2H on their own streams, double-buffered"},
-        "gpu_launches": 4 * K,
+        "gpu_launches": 5 * K,  # per step: relayout, FP (two launches: 200 + 48 views), filter, BP
         "roofline": {"kernel": "fp3d_column_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                      "traffic": traffic,
@@ -949,6 +952,49 @@ def run_configs(args):
     print(json.dumps(line), flush=True)
 
 
+def run_cnn128(args):
+    """Forward pass of the residual CNN initialiser on two 128^3 volumes
+    (BF16 activations and weights, FP32 accumulation; random-init weights of
+    the network's architecture, synthetic inputs): W warm-up passes, then K
+    timed passes with CUDA events, and the per-layer convolution times."""
+    from paper_1904_13342_gb300 import binding as B
+    from paper_1904_13342_gb300.cnn import LAYERS, ResidualCNN
+
+    dev = torch.device("cuda:0")
+    net = ResidualCNN(device="cuda", seed=0)
+    g = torch.Generator().manual_seed(0)
+    x = torch.rand((2, 128, 128, 128), generator=g).to(dev)
+    out, acts = net.forward(x, keep=True)
+    inputs = {"c0": "x16", "c1": "a0", "c2": "p1", "c3": "a2", "c4": "p2", "c5": "a4", "c6": "p3", "c7": "a6",
+              "c8": "u3", "c9": "u2", "c10": "u1", "c11": "a10"}
+    layers = {}
+    for name, cin, cout in LAYERS:
+        xin, p = acts[inputs[name]], net.params[name]
+        ms = _timed_ms(dev, lambda: B.pyro_conv3d(xin, p.w16, p.b, name != "c11"), reps=5)
+        vox = xin.numel() // cin
+        layers[name] = {"cin": cin, "cout": cout, "size": list(xin.shape[1:4]), "ms": round(ms, 4),
+                        "tflops": round(2 * 27 * cin * cout * vox / (ms * 1e-3) / 1e12, 1)}
+    for _ in range(max(args.warmup, 3)):
+        net.forward(x)
+    torch.cuda.synchronize(dev)
+    with ClockSampler(dev.index or 0) as clk:
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(args.steps):
+            net.forward(x)
+        b.record()
+        torch.cuda.synchronize(dev)
+    ms = a.elapsed_time(b) / args.steps
+    line = {"metric": "residual CNN forward, ms per pass", "value": round(ms, 4), "unit": "ms",
+            "higher_is_better": False, "n_gpus": 1, "steps": args.steps, "warmup": max(args.warmup, 3),
+            "dtype": "bf16 (FP32 accumulate)", "data": "synthetic (uniform random volumes, random-init weights)",
+            "vs_baseline": None,
+            "config": {"workload": "residual CNN initialiser forward, 2 x 128^3 volumes, 12 3x3x3 convolutions",
+                       "l2": "inputs (2 x 128^3 x 16 channels, 134 MB per activation) larger than L2"},
+            "layers": layers, "clocks": clk.summary()}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -957,7 +1003,7 @@ def main():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
-    ap.add_argument("--workload", default="fdk-256", choices=["fdk-256", "learned-init", "tv-512", "configs"])
+    ap.add_argument("--workload", default="fdk-256", choices=["fdk-256", "learned-init", "tv-512", "configs", "cnn-128"])
     ap.add_argument("--train-steps", type=int, default=1000)
     ap.add_argument("--tv-lambda", type=float, default=10.0)
     ap.add_argument("--tv-steps", type=int, default=3, help="TV steps of the 512^3 slice and the 64^3 oracle check")
@@ -970,6 +1016,8 @@ def main():
         run_tv512(args)
     elif args.workload == "configs":
         run_configs(args)
+    elif args.workload == "cnn-128":
+        run_cnn128(args)
     elif args.impl == "reference":
         run_reference(args)
     else:

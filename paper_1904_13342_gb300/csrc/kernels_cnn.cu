@@ -264,15 +264,24 @@ __global__ void __launch_bounds__(128) conv3d_tc_k27_kernel(const bf16 *__restri
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
         asm volatile("tcgen05.fence::before_thread_sync;");
     }
-    // A: row t = the 27 neighbours of voxel t (zero outside the volume), then 5 zeros
+    // the block's voxels with a one-voxel halo (zero outside the volume):
+    // at most 3 x 4 x 66 values (TX TY TZ = 128, TX <= 64)
+    __shared__ bf16 sX[1024];
     const bf16 zero = __float2bfloat16(0.0f);
+    const int HX = TX + 2, HY = TY + 2, HZ = tl.TZ + 2;
+    for (int q = t; q < HX * HY * HZ; q += 128) {
+        const int hx = q % HX, hy = (q / HX) % HY, hz = q / (HX * HY);
+        const int gz = tz0 + hz - 1, gy = ty0 + hy - 1, gx = tx0 + hx - 1;
+        const bool in = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < Wd;
+        sX[q] = in ? X[(((size_t)b * D + gz) * H + gy) * Wd + gx] : zero;
+    }
+    __syncthreads();
+    // A: row t = the 27 neighbours of voxel t, then 5 zeros
+    const int lz = vz - tz0, ly = vy - ty0, lx = vx - tx0;
     bf16 v[32];
 #pragma unroll
-    for (int tap = 0; tap < 27; ++tap) {
-        const int gz = vz + tap / 9 - 1, gy = vy + (tap / 3) % 3 - 1, gx = vx + tap % 3 - 1;
-        const bool in = gz >= 0 && gz < D && gy >= 0 && gy < H && gx >= 0 && gx < Wd;
-        v[tap] = in ? X[(((size_t)b * D + gz) * H + gy) * Wd + gx] : zero;
-    }
+    for (int tap = 0; tap < 27; ++tap)
+        v[tap] = sX[((lz + tap / 9) * HY + ly + (tap / 3) % 3) * HX + lx + tap % 3];
 #pragma unroll
     for (int k = 27; k < 32; ++k) v[k] = zero;
 #pragma unroll
@@ -850,6 +859,120 @@ __global__ void upsample2_bwd_kernel(const bf16 *__restrict__ dy, bf16 *__restri
     }
 }
 
+// ---- the same four maps on 8 channels (16 bytes) per thread, for C a
+// multiple of 8 and fewer than 2^31 chunks (32-bit index arithmetic);
+// sums in FP32, one rounding to bf16, as the scalar kernels above
+__device__ __forceinline__ void bf8_to_f(const uint4 &u, float (&f)[8])
+{
+    const unsigned w[4] = {u.x, u.y, u.z, u.w};
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const float2 p = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&w[k]));
+        f[2 * k] = p.x;
+        f[2 * k + 1] = p.y;
+    }
+}
+
+__device__ __forceinline__ uint4 f_to_bf8(const float (&f)[8])
+{
+    unsigned w[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const __nv_bfloat162 p = __floats2bfloat162_rn(f[2 * k], f[2 * k + 1]);
+        w[k] = *reinterpret_cast<const unsigned *>(&p);
+    }
+    return make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+// chunk i of an output of [B][Do][Ho][Wo][C8 chunks] -> (b, z, y, x, c)
+struct Chunk {
+    int b, z, y, x, c;
+};
+
+__device__ __forceinline__ Chunk chunk_of(unsigned i, int C8, int Wo, int Ho, int Do)
+{
+    Chunk k;
+    k.c = (int)(i % (unsigned)C8);
+    unsigned r = i / (unsigned)C8;
+    k.x = (int)(r % (unsigned)Wo);
+    r /= (unsigned)Wo;
+    k.y = (int)(r % (unsigned)Ho);
+    r /= (unsigned)Ho;
+    k.z = (int)(r % (unsigned)Do);
+    k.b = (int)(r / (unsigned)Do);
+    return k;
+}
+
+__global__ void avgpool2_v8_kernel(const uint4 *__restrict__ x, uint4 *__restrict__ y, unsigned n, int D, int H, int W,
+                                   int C8)
+{
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Chunk k = chunk_of(i, C8, W / 2, H / 2, D / 2);
+        float s[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int zz = 2 * k.z + (d >> 2), yy = 2 * k.y + ((d >> 1) & 1), xx = 2 * k.x + (d & 1);
+            float f[8];
+            bf8_to_f(x[((((size_t)k.b * D + zz) * H + yy) * W + xx) * C8 + k.c], f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] += f[e];
+        }
+#pragma unroll
+        for (int e = 0; e < 8; ++e) s[e] *= 0.125f;
+        y[i] = f_to_bf8(s);
+    }
+}
+
+__global__ void avgpool2_bwd_v8_kernel(const uint4 *__restrict__ dy, uint4 *__restrict__ dx, unsigned n, int D, int H,
+                                       int W, int C8)
+{
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Chunk k = chunk_of(i, C8, W, H, D);
+        float f[8];
+        bf8_to_f(dy[((((size_t)k.b * (D / 2) + k.z / 2) * (H / 2) + k.y / 2) * (W / 2) + k.x / 2) * C8 + k.c], f);
+#pragma unroll
+        for (int e = 0; e < 8; ++e) f[e] *= 0.125f;
+        dx[i] = f_to_bf8(f);
+    }
+}
+
+__global__ void upsample2_v8_kernel(const uint4 *__restrict__ x, const uint4 *__restrict__ skip, uint4 *__restrict__ y,
+                                    unsigned n, int D, int H, int W, int C8)
+{
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Chunk k = chunk_of(i, C8, 2 * W, 2 * H, 2 * D);
+        const uint4 v = x[((((size_t)k.b * D + k.z / 2) * H + k.y / 2) * W + k.x / 2) * C8 + k.c];
+        if (skip) {
+            float f[8], g[8];
+            bf8_to_f(v, f);
+            bf8_to_f(skip[i], g);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) f[e] += g[e];
+            y[i] = f_to_bf8(f);
+        } else {
+            y[i] = v;
+        }
+    }
+}
+
+__global__ void upsample2_bwd_v8_kernel(const uint4 *__restrict__ dy, uint4 *__restrict__ dx, unsigned n, int D,
+                                        int H, int W, int C8)
+{
+    for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        const Chunk k = chunk_of(i, C8, W, H, D);
+        float s[8] = {0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f, 0.0f};
+#pragma unroll
+        for (int d = 0; d < 8; ++d) {
+            const int zz = 2 * k.z + (d >> 2), yy = 2 * k.y + ((d >> 1) & 1), xx = 2 * k.x + (d & 1);
+            float f[8];
+            bf8_to_f(dy[((((size_t)k.b * 2 * D + zz) * 2 * H + yy) * 2 * W + xx) * C8 + k.c], f);
+#pragma unroll
+            for (int e = 0; e < 8; ++e) s[e] += f[e];
+        }
+        dx[i] = f_to_bf8(s);
+    }
+}
+
 __global__ void add_bf16_kernel(const bf16 *__restrict__ a, const bf16 *__restrict__ b, bf16 *__restrict__ y, long n)
 {
     for (long i = blockIdx.x * (long)blockDim.x + threadIdx.x; i < n; i += (long)gridDim.x * blockDim.x)
@@ -1080,6 +1203,20 @@ cudaError_t launch_cnn_elementwise(int op, const void *a, const void *b, void *y
                                    int H, int W, int C, cudaStream_t s)
 {
     const unsigned g = (unsigned)grid_for(n);
+    const bool a16 = (((uintptr_t)a | (uintptr_t)b | (uintptr_t)y) & 15) == 0;
+    if (op >= 1 && op <= 4 && C % 8 == 0 && n / 8 < (1L << 31) && a16) {  // 8 channels per thread
+        const unsigned n8 = (unsigned)(n / 8), g8 = (unsigned)grid_for(n / 8);
+        const int C8 = C / 8;
+        switch (op) {
+        case 1: avgpool2_v8_kernel<<<g8, 256, 0, s>>>((const uint4 *)a, (uint4 *)y, n8, D, H, W, C8); break;
+        case 2: avgpool2_bwd_v8_kernel<<<g8, 256, 0, s>>>((const uint4 *)a, (uint4 *)y, n8, D, H, W, C8); break;
+        case 3:
+            upsample2_v8_kernel<<<g8, 256, 0, s>>>((const uint4 *)a, (const uint4 *)b, (uint4 *)y, n8, D, H, W, C8);
+            break;
+        default: upsample2_bwd_v8_kernel<<<g8, 256, 0, s>>>((const uint4 *)a, (uint4 *)y, n8, D, H, W, C8); break;
+        }
+        return cudaGetLastError();
+    }
     switch (op) {
     case 0: relu_bwd_kernel<<<g, 256, 0, s>>>((bf16 *)y, (const bf16 *)a, n); break;
     case 1: avgpool2_kernel<<<g, 256, 0, s>>>((const bf16 *)a, (bf16 *)y, n, D, H, W, C); break;

@@ -135,6 +135,33 @@ def test_elementwise_ops():
     assert rel(db, gu.double().cpu().sum(dim=(0, 1, 2, 3))) < 1e-5
 
 
+def test_elementwise_vector_and_scalar_kernels_agree():
+    """Pooling and upsampling run 8 channels per thread on 16-byte aligned
+    tensors and one element per thread otherwise: the same bits either way
+    (an output 4 elements into a buffer is 8-byte aligned only)."""
+    x = rand_bf16((2, 8, 8, 16, 16), 20)
+    skip = rand_bf16((2, 8, 8, 16, 16), 21)
+    def pair(shape):
+        buf = torch.empty(int(np.prod(shape)) + 4, device=DEV, dtype=torch.bfloat16)
+        return torch.empty(shape, device=DEV, dtype=torch.bfloat16), buf[4:].view(shape)
+    pa, pu = pair((2, 4, 4, 8, 16))
+    B.pyro_cnn_op(B.CNN_AVGPOOL2, x, pa, dims=(8, 8, 16, 16))
+    B.pyro_cnn_op(B.CNN_AVGPOOL2, x, pu, dims=(8, 8, 16, 16))
+    assert torch.equal(pa, pu)
+    ua, uu = pair((2, 8, 8, 16, 16))
+    B.pyro_cnn_op(B.CNN_UPSAMPLE2, pa, ua, b=skip, dims=(4, 4, 8, 16))
+    B.pyro_cnn_op(B.CNN_UPSAMPLE2, pa, uu, b=skip, dims=(4, 4, 8, 16))
+    assert torch.equal(ua, uu)
+    ga, gu = pair((2, 4, 4, 8, 16))
+    B.pyro_cnn_op(B.CNN_UPSAMPLE2_BWD, skip, ga, dims=(4, 4, 8, 16))
+    B.pyro_cnn_op(B.CNN_UPSAMPLE2_BWD, skip, gu, dims=(4, 4, 8, 16))
+    assert torch.equal(ga, gu)
+    da, du = pair((2, 8, 8, 16, 16))
+    B.pyro_cnn_op(B.CNN_AVGPOOL2_BWD, pa, da, dims=(8, 8, 16, 16))
+    B.pyro_cnn_op(B.CNN_AVGPOOL2_BWD, pa, du, dims=(8, 8, 16, 16))
+    assert torch.equal(da, du)
+
+
 def reference_params(net):
     return {n: (p.w16.double().cpu(), p.b.double().cpu()) for n, p in net.params.items()}
 
