@@ -315,7 +315,7 @@ def run_gpu(args):
     peak_tflops = props.multi_processor_count * 128 * 2 * sm_mhz * 1e6 / 1e12
     achieved = samples * FLOPS_PER_SAMPLE / (fp_avg_ms * 1e-3) / 1e12
     clocks = clk.summary()
-    traffic = fp_traffic_per_launch()
+    traffic = fp_traffic_per_call()
     out = {
         "metric": METRIC, "value": round(value, 3), "unit": UNIT, "n_gpus": world, "steps": K, "warmup": args.warmup,
         "ms_per_step": round(total_ms / K, 4), "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -327,7 +327,8 @@ def run_gpu(args):
         "roofline": {"kernel": "fp3d_column_kernel", "bound": "alu", "achieved": round(achieved, 3),
                      "peak": round(peak_tflops, 2), "unit": "TFLOP/s", "frac": round(achieved / peak_tflops, 4),
                      "traffic": traffic,
-                     "note": f"{samples:.4g} samples x {FLOPS_PER_SAMPLE} flop; peak = {props.multi_processor_count}"
+                     "note": f"per FP call (two launches: 200 + 48 views; traffic: DRAM bytes of both, ncu); "
+                             f"{samples:.4g} samples x {FLOPS_PER_SAMPLE} flop; peak = {props.multi_processor_count}"
                              f" SMs x 128 FP32 lanes x 2 x {sm_mhz:.0f} MHz"},
         "gather_view": gather_view(gather_gbs, samples, fp_avg_ms, tk["bp"]),
         "breakdown_ms": {"fp": round(fp_avg_ms, 4), "fdk": round(statistics.mean(fdk_ms), 4),
@@ -397,9 +398,10 @@ def _profile_record(key):
         return None
 
 
-def fp_traffic_per_launch():
-    """DRAM bytes (read + write) of one forward-projection launch"""
-    return _profile_record("dram_bytes_per_launch")
+def fp_traffic_per_call():
+    """DRAM bytes (read + write) of one forward projection (its two launches,
+    200 + 48 views), the unit the roofline's achieved rate is taken over"""
+    return _profile_record("dram_bytes_per_fp_call")
 
 
 def gather_view(probe_gbs, samples, fp_ms, bp_ms):
@@ -410,7 +412,7 @@ def gather_view(probe_gbs, samples, fp_ms, bp_ms):
     the FP moves through L2 come from the committed ncu counters (per launch,
     keyed to the kernel source) and are set against the library's random
     16-byte gather probe of an L2-resident buffer."""
-    l2 = _profile_record("lts_bytes_per_launch")
+    l2 = _profile_record("lts_bytes_per_fp_call")
     out = {"probe_l2_gather_GBps": round(probe_gbs, 1),
            "probe": "random 16-byte gathers from a 64 MB L2-resident buffer",
            "fp_effective_tap_rate_GBps": round(samples * 32 / (fp_ms * 1e-3) / 1e9, 1),
@@ -419,7 +421,7 @@ def gather_view(probe_gbs, samples, fp_ms, bp_ms):
                    "roofline fraction"}
     if l2 is not None:
         gbs = l2 / (fp_ms * 1e-3) / 1e9
-        out.update({"fp_l2_bytes_per_launch": l2, "fp_l2_GBps": round(gbs, 1),
+        out.update({"fp_l2_bytes_per_call": l2, "fp_l2_GBps": round(gbs, 1),
                     "fp_l2_frac_of_probe": round(gbs / probe_gbs, 3)})
     return out
 

@@ -219,11 +219,11 @@ def test_tv512_geometry_full_size():
 
 
 def test_tv512_adjoint_elementwise_on_a_view_subset():
-    """The staged exact adjoint in the 512^3 iterative workload's geometry
-    (0.5 mm voxels, 1240 x 960 detector at 0.308 mm: a row step of about half
-    a voxel, so the two-rays-per-lane adjoint runs), on 8 views and a noise
-    sinogram, element by element on sampled voxels against the oracle's
-    voxel-wise adjoint; sampled voxels include the volume's faces and corners."""
+    """The gathered exact adjoint in the 512^3 iterative workload's geometry
+    (0.5 mm voxels, 1240 x 960 detector at 0.308 mm: a row step of 0.27 to
+    0.5 voxel, so 12-row windows), on 8 views and a noise sinogram, element
+    by element on sampled voxels against the oracle's voxel-wise adjoint;
+    sampled voxels include the volume's faces and corners."""
     n = 512
     g = ConeGeometry3D((n, n, n), (0.5,) * 3, (960, 1240), (0.308, 0.308), 8, 2 * math.pi, 750.0, 1200.0)
     P = oracle.circular_pmats(g.view_angles(), g.sid, g.sdd, g.detector_shape, g.detector_spacing)
