@@ -192,12 +192,16 @@ PYRO_API int pyro_cone_projection_matrices(const pyro_geom3d *g, double *out);
 
 /* --- The same cone-beam forward projection, computed from a copy of the
  * volume re-laid out z-fastest in `workspace` (device, at least
- * pyro_fp_cone3d_workspace_bytes bytes, i.e. one volume of `dtype` padded
- * by two voxels before and after the data in x and y and one in z;
- * PYRO_EWORKSPACE otherwise).  This is the memory-for-speed trade the paper
- * describes for its texture mode (the volume is held twice, Section "The
- * Operator as a Layer"); pyro_fp_cone3d is the memory-lean mode.  Results
- * are identical up to FP32 summation order; the workspace is scratch. */
+ * pyro_fp_cone3d_workspace_bytes bytes; PYRO_EWORKSPACE otherwise).  For
+ * circular-type trajectories the copy is a quad copy: the volume padded by
+ * two voxels before and after the data in x and y and one in z, each cell
+ * (x, y, z) holding the four voxels (x, y), (x + 1, y), (x, y + 1),
+ * (x + 1, y + 1) at z, i.e. 4 (nx + 4)(ny + 4)(nz + 2) elements of `dtype`;
+ * other trajectories use the first nx ny nz of them.  This is the
+ * memory-for-speed trade the paper describes for its texture mode (the
+ * volume is held again, Section "The Operator as a Layer"); pyro_fp_cone3d
+ * is the memory-lean mode.  Results are identical up to FP32 summation
+ * order; the workspace is scratch. */
 PYRO_API size_t pyro_fp_cone3d_workspace_bytes(const pyro_geom3d *g, pyro_dtype dtype);
 PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyro_geom3d *g, void *workspace,
                                size_t workspace_bytes, pyro_dtype dtype, void *stream);
@@ -206,9 +210,8 @@ PYRO_API int pyro_fp_cone3d_ws(const void *vol, void *sino, int batch, const pyr
  * `storage` while the volume and the sinogram stay in `dtype`: an FP32
  * volume projected from an FP16 or BF16 copy (half the workspace; the
  * volume's values rounded to 16 bits, accumulation along the rays in FP32,
- * an FP32 sinogram), the north-star's half-storage pattern for an FP32
- * iterate (Section "The Operator as a Layer": the copy is the paper's
- * memory-for-speed trade).  storage == dtype is pyro_fp_cone3d_ws.  The
+ * an FP32 sinogram), a half-storage copy of an FP32 iterate (Section "The
+ * Operator as a Layer": the copy is the paper's memory-for-speed trade).  storage == dtype is pyro_fp_cone3d_ws.  The
  * workspace needs pyro_fp_cone3d_workspace_bytes(g, storage) bytes.
  * PYRO_EUNSUPPORTED for storage != dtype with a non-FP32 volume or a
  * trajectory other than circular-type (detector v axis along z). */

@@ -69,14 +69,20 @@ struct ConeFPView {
 // step in FP32 from there, so a sample position near voxel index 500 keeps
 // ~1e-6 voxel where an absolute FP32 index carries ~3e-5.
 constexpr int kFPSegment = 64;
-// The column kernels' padded z-major copy of the volume: [ny + 2 P][nx + 2 P]
-// [nz + 2], P = kFPPadXY zero voxels before and after the data in x and y
-// and one in z.  Two in x and y keep the taps inside the copy when an
-// anchored sample lands one cell beyond the FP32 range test that chose it.
+// The column kernels' padded z-major quad copy of the volume: cells
+// [ny + 2 P][nx + 2 P][nz + 2], P = kFPPadXY zero voxels before and after the
+// data in x and y and one in z; cell (x, y, z) holds the four voxels (x, y),
+// (x + 1, y), (x, y + 1), (x + 1, y + 1) at z (one load per plane).  Two in x
+// and y keep the taps inside the copy when an anchored sample lands one cell
+// beyond the FP32 range test that chose it.
 constexpr int kFPPadXY = 2;
-inline size_t fp_padded_elems(int nx, int ny, int nz)
+inline size_t fp_padded_cells(int nx, int ny, int nz)
 {
     return (size_t)(nx + 2 * kFPPadXY) * (ny + 2 * kFPPadXY) * (nz + 2);
+}
+inline size_t fp_padded_elems(int nx, int ny, int nz)  // elements of the quad copy
+{
+    return 4 * fp_padded_cells(nx, ny, nz);
 }
 struct FP3DParams {
     int nx, ny, nz, nu, nv, n_views, view0, views_total;

@@ -321,7 +321,10 @@ __global__ void __launch_bounds__(128) conv3d_tc_k27_kernel(const bf16 *__restri
                          smem_addr(&bar))
                      : "memory");
     }
-    const bool ok = mbar_wait(&bar, 0u);
+    bool ok = mbar_wait(&bar, 0u);
+    // after a give-up, drain the commit (bounded) before the accumulator is
+    // dropped and the tensor memory freed
+    if (!ok) mbar_wait(&bar, 0u);
     asm volatile("tcgen05.fence::after_thread_sync;");
     const int all_ok = __syncthreads_and(ok ? 1 : 0);
     if (all_ok) {

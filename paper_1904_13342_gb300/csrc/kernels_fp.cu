@@ -546,13 +546,15 @@ __global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const
 // l.  A warp takes column k and R windows of 32 consecutive rows.  On each
 // depth plane it computes the (x, y) cell and its bilinear weights once; in
 // each window every lane loads the four (x, y) columns at one z of the
-// window's 32-voxel run (one coalesced 128-byte load per column) and
-// combines them in x and y, and each lane then takes the two z taps of its
-// own ray from the lanes holding them (two shuffles).  The host checks that
-// 31 row steps stay below 29.5 voxels in z, so a window's taps always fall in
-// its 32-voxel run.  The volume copy is [ny+4][nx+4][nz+2] with zero voxels
-// around the data (two in x and y, one in z): loads need no bounds test, and
-// the zero-extended interpolant comes out of the padding.
+// window's 32-voxel run and combines them in x and y, and each lane then
+// takes the two z taps of its own ray from the lanes holding them (two
+// shuffles).  The host checks that 31 row steps stay below 29.5 voxels in z,
+// so a window's taps always fall in its 32-voxel run.  The volume copy is a
+// quad copy: cell (x, y, z) of [ny+4][nx+4][nz+2] holds the four columns
+// (x, y), (x + 1, y), (x, y + 1), (x + 1, y + 1) at z, so one 16-byte load
+// per lane (coalesced along z) brings the four taps of a plane; zero voxels
+// around the data (two in x and y, one in z) mean no load needs a bounds
+// test, and the zero-extended interpolant comes out of the padding.
 //
 // Positions: the column's (x, y) track is anchored (float-float) at the
 // start of every kFPSegment planes; each ray's z once, at the middle plane of
@@ -635,15 +637,42 @@ __device__ __forceinline__ PlaneXY plane_xy(const TrackSeg &s, float dx, int sxp
     return q;
 }
 
+// the four (x, y) columns of a cell at one z from the quad copy: (x, y),
+// (x + 1, y), (x, y + 1), (x + 1, y + 1), one 16-byte (FP32) or 8-byte load
+template <typename T>
+__device__ __forceinline__ float4 ldq(const T *p);
+template <>
+__device__ __forceinline__ float4 ldq<float>(const float *p)
+{
+    return __ldg(reinterpret_cast<const float4 *>(p));
+}
+template <>
+__device__ __forceinline__ float4 ldq<__half>(const __half *p)
+{
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 a = __half22float2(*reinterpret_cast<const __half2 *>(&u.x));
+    const float2 b = __half22float2(*reinterpret_cast<const __half2 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+template <>
+__device__ __forceinline__ float4 ldq<__nv_bfloat16>(const __nv_bfloat16 *p)
+{
+    const uint2 u = __ldg(reinterpret_cast<const uint2 *>(p));
+    const float2 a = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.x));
+    const float2 b = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(&u.y));
+    return make_float4(a.x, a.y, b.x, b.y);
+}
+
 // One depth plane of one window: the lane's x/y-interpolated value at
 // z = zb + lane, then its own ray's z interpolation from two lanes.
 template <typename T>
-__device__ __forceinline__ void column_step(ColumnWindow &W, const ZSeg &z, float dz, int nz, const T *const (&c)[4],
+__device__ __forceinline__ void column_step(ColumnWindow &W, const ZSeg &z, float dz, int nz, const T *cq,
                                             const PlaneXY &q)
 {
     const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
     const int zi = min(max(z.zbase + __float_as_int(tzb), -1), nz);
-    const float g = q.w00 * ld(c[0] + zi) + q.w10 * ld(c[1] + zi) + q.w01 * ld(c[2] + zi) + q.w11 * ld(c[3] + zi);
+    const float4 v = ldq(cq + 4 * zi);
+    const float g = q.w00 * v.x + q.w10 * v.y + q.w01 * v.z + q.w11 * v.w;
     const float fz = fmaf(dz, z.q, z.f);
     const float tz = floor_magic(fz);
     const int j = __float_as_int(tz) - __float_as_int(tzb);  // own cell relative to the window's run
@@ -694,10 +723,8 @@ __device__ __forceinline__ void column_step_pair(f32x2 &acc, const ZSeg &z, floa
     upk2(TB, tb0, tb1);
     const int zi0 = min(max(z.zbase + __float_as_int(tb0), -1), nz) + q.col0;
     const int zi1 = min(max(z.zbase + __float_as_int(tb1), -1), nz) + q.col1;
-    const f32x2 A = pk2(ld(vp + zi0), ld(vp + zi1));
-    const f32x2 B = pk2(ld(vp + zi0 + sxp), ld(vp + zi1 + sxp));
-    const f32x2 C = pk2(ld(vp + zi0 + syp), ld(vp + zi1 + syp));
-    const f32x2 E = pk2(ld(vp + zi0 + sxp + syp), ld(vp + zi1 + sxp + syp));
+    const float4 v0 = ldq(vp + 4 * (size_t)zi0), v1 = ldq(vp + 4 * (size_t)zi1);
+    const f32x2 A = pk2(v0.x, v1.x), B = pk2(v0.y, v1.y), C = pk2(v0.z, v1.z), E = pk2(v0.w, v1.w);
     const f32x2 G = fma2(q.w11, E, fma2(q.w01, C, fma2(q.w10, B, mul2(q.w00, A))));
     float g0, g1;
     upk2(G, g0, g1);
@@ -734,9 +761,9 @@ __device__ __forceinline__ void column_planes_paired(ColumnWindow (&W)[R], const
         }
         if (m <= me) {  // an odd plane left in the segment
             const PlaneXY q = plane_xy(ts, dx, sxp, syp);
-            const T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+            const T *cq = vp + 4 * (size_t)q.col;
 #pragma unroll
-            for (int r = 0; r < R; ++r) column_step(W[r], zs[r], dz, p.nz, c, q);
+            for (int r = 0; r < R; ++r) column_step(W[r], zs[r], dz, p.nz, cq, q);
         }
     }
 #pragma unroll
@@ -763,11 +790,11 @@ __device__ __forceinline__ void column_planes(ColumnWindow (&W)[R], const ZSeg (
 #pragma unroll 4
         for (int m = ms; m <= me; ++m, dx += 1.0f, dz += 1.0f) {
             const PlaneXY q = plane_xy(ts, dx, sxp, syp);
-            const T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+            const T *cq = vp + 4 * (size_t)q.col;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-                column_step(W[r], zs[r], dz, p.nz, c, q);
+                column_step(W[r], zs[r], dz, p.nz, cq, q);
             }
         }
     }
@@ -1010,12 +1037,13 @@ __device__ __forceinline__ void pair_rows_setup(const FP3DParams &p, int v, int 
 // one depth plane of one window: the run as in column_step, then both rays'
 // z interpolations from it
 template <typename T>
-__device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, const ZSeg2 &z, float dz, int nz,
-                                               const T *const (&c)[4], const PlaneXY &q)
+__device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, const ZSeg2 &z, float dz, int nz, const T *cq,
+                                               const PlaneXY &q)
 {
     const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
     const int zi = min(max(z.zbase + __float_as_int(tzb), -1), nz);
-    const float g = q.w00 * ld(c[0] + zi) + q.w10 * ld(c[1] + zi) + q.w01 * ld(c[2] + zi) + q.w11 * ld(c[3] + zi);
+    const float4 v = ldq(cq + 4 * zi);
+    const float g = q.w00 * v.x + q.w10 * v.y + q.w01 * v.z + q.w11 * v.w;
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const float fz = fmaf(dz, z.q[h], z.f[h]);
@@ -1038,11 +1066,11 @@ __device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], const Z
 #pragma unroll 4
         for (int m = ms; m <= me; ++m, dx += 1.0f, dz += 1.0f) {
             const PlaneXY q = plane_xy(ts, dx, sxp, syp);
-            const T *const c[4] = {vp + q.col, vp + q.col + sxp, vp + q.col + syp, vp + q.col + sxp + syp};
+            const T *cq = vp + 4 * (size_t)q.col;
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-                pair_rows_step(W[r], zs[r], dz, p.nz, c, q);
+                pair_rows_step(W[r], zs[r], dz, p.nz, cq, q);
             }
         }
     }
@@ -1096,26 +1124,61 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_pair_rows_kernel(const T 
         }
 }
 
-// [z][y][x] -> [y + P][x + P][z + 1] of the zero-padded (ny + 2P)(nx + 2P)
-// (nz + 2) array, P = kFPPadXY: every padded element is written once (source
-// voxel or 0), converted from the volume's type TI to the copy's type T
-template <typename TI, typename T>
-__global__ void __launch_bounds__(256) relayout_padded_kernel(const TI *__restrict__ vol, T *__restrict__ vp, int nx,
-                                                              int ny, int nz)
+// [z][y][x] -> the quad copy: cell (x + P, y + P, z + 1) of the zero-padded
+// (ny + 2P)(nx + 2P)(nz + 2) array (P = kFPPadXY) holds the voxels (x, y),
+// (x + 1, y), (x, y + 1), (x + 1, y + 1) at z, zero outside the volume; every
+// cell is written once, converted from the volume's type TI to the copy's T.
+// A block stages two y rows of a 32 (z) x 33 (x) tile in shared memory
+// (loads coalesced along x) and writes 32 x 32 cells (coalesced along z).
+template <typename T>
+__device__ __forceinline__ void store_quad(T *p, float a, float b, float c, float d);
+template <>
+__device__ __forceinline__ void store_quad<float>(float *p, float a, float b, float c, float d)
 {
-    __shared__ T tile[32][33];
+    *reinterpret_cast<float4 *>(p) = make_float4(a, b, c, d);
+}
+template <>
+__device__ __forceinline__ void store_quad<__half>(__half *p, float a, float b, float c, float d)
+{
+    const __half2 lo = __floats2half2_rn(a, b), hi = __floats2half2_rn(c, d);
+    *reinterpret_cast<uint2 *>(p) =
+        make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+}
+template <>
+__device__ __forceinline__ void store_quad<__nv_bfloat16>(__nv_bfloat16 *p, float a, float b, float c, float d)
+{
+    const __nv_bfloat162 lo = __floats2bfloat162_rn(a, b), hi = __floats2bfloat162_rn(c, d);
+    *reinterpret_cast<uint2 *>(p) =
+        make_uint2(*reinterpret_cast<const unsigned *>(&lo), *reinterpret_cast<const unsigned *>(&hi));
+}
+
+template <typename TI, typename T>
+__global__ void __launch_bounds__(256) relayout_quad_kernel(const TI *__restrict__ vol, T *__restrict__ vq, int nx,
+                                                            int ny, int nz)
+{
+    __shared__ float tile[2][32][33];  // [y, y + 1][z][x .. x + 32]
     const int nxp = nx + 2 * kFPPadXY, nzp = nz + 2;
     const int x0 = blockIdx.x * 32, z0 = blockIdx.y * 32, yp = blockIdx.z;
-    const int y = yp - kFPPadXY;
-    for (int i = threadIdx.y; i < 32; i += 8) {
-        const int z = z0 + i - 1, x = x0 + threadIdx.x - kFPPadXY;
-        const bool in = y >= 0 && y < ny && z >= 0 && z < nz && x >= 0 && x < nx;
-        tile[i][threadIdx.x] = to_storage<T>(in ? to_float<TI>(vol[((size_t)z * ny + y) * nx + x]) : 0.0f);
+#pragma unroll
+    for (int r = 0; r < 2; ++r) {
+        const int y = yp - kFPPadXY + r;
+        for (int i = threadIdx.y; i < 32; i += 8) {
+            const int z = z0 + i - 1;
+            for (int j = threadIdx.x; j < 33; j += 32) {
+                const int x = x0 + j - kFPPadXY;
+                const bool in = y >= 0 && y < ny && z >= 0 && z < nz && x >= 0 && x < nx;
+                // the copy's rounding happens once, on the stored values
+                tile[r][i][j] = in ? to_float<T>(to_storage<T>(to_float<TI>(vol[((size_t)z * ny + y) * nx + x])))
+                                   : 0.0f;
+            }
+        }
     }
     __syncthreads();
     for (int i = threadIdx.y; i < 32; i += 8) {
         const int xp = x0 + i, zp = z0 + threadIdx.x;
-        if (zp < nzp && xp < nxp) vp[((size_t)yp * nxp + xp) * nzp + zp] = tile[threadIdx.x][i];
+        if (zp < nzp && xp < nxp)
+            store_quad<T>(vq + 4 * (((size_t)yp * nxp + xp) * nzp + zp), tile[0][threadIdx.x][i],
+                          tile[0][threadIdx.x][i + 1], tile[1][threadIdx.x][i], tile[1][threadIdx.x][i + 1]);
     }
 }
 
@@ -1336,16 +1399,16 @@ cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, in
 {
     dim3 block(32, 8), grid((nx + 2 * kFPPadXY + 31) / 32, (nz + 2 + 31) / 32, ny + 2 * kFPPadXY);
     if (dt == PYRO_F32 && storage == PYRO_F32)
-        relayout_padded_kernel<float, float><<<grid, block, 0, s>>>((const float *)vol, (float *)vp, nx, ny, nz);
+        relayout_quad_kernel<float, float><<<grid, block, 0, s>>>((const float *)vol, (float *)vp, nx, ny, nz);
     else if (dt == PYRO_F32 && storage == PYRO_F16)
-        relayout_padded_kernel<float, __half><<<grid, block, 0, s>>>((const float *)vol, (__half *)vp, nx, ny, nz);
+        relayout_quad_kernel<float, __half><<<grid, block, 0, s>>>((const float *)vol, (__half *)vp, nx, ny, nz);
     else if (dt == PYRO_F32 && storage == PYRO_BF16)
-        relayout_padded_kernel<float, __nv_bfloat16>
+        relayout_quad_kernel<float, __nv_bfloat16>
             <<<grid, block, 0, s>>>((const float *)vol, (__nv_bfloat16 *)vp, nx, ny, nz);
     else if (dt == PYRO_F16 && storage == PYRO_F16)
-        relayout_padded_kernel<__half, __half><<<grid, block, 0, s>>>((const __half *)vol, (__half *)vp, nx, ny, nz);
+        relayout_quad_kernel<__half, __half><<<grid, block, 0, s>>>((const __half *)vol, (__half *)vp, nx, ny, nz);
     else if (dt == PYRO_BF16 && storage == PYRO_BF16)
-        relayout_padded_kernel<__nv_bfloat16, __nv_bfloat16>
+        relayout_quad_kernel<__nv_bfloat16, __nv_bfloat16>
             <<<grid, block, 0, s>>>((const __nv_bfloat16 *)vol, (__nv_bfloat16 *)vp, nx, ny, nz);
     else
         return cudaErrorInvalidValue;
@@ -1366,10 +1429,11 @@ static void column_launch(const void *vp, void *sino, int b, const FP3DParams &p
 
 // 32-row windows per column, 1 to rmax per warp.  Cost model in issue slots
 // per warp and depth plane: about 28 per window (windows past the last row
-// included) plus about 30 shared by the warp's windows.  The forward takes
-// at most 4: with plane pairs, 5 windows need 96 registers and ran 12 %
-// slower on the 256^3 workload (25.5 ms against 22.8 ms with 4).
-static int column_windows_per_warp(int nv, int rmax = 5)
+// included) plus about 30 shared by the warp's windows.  With the quad copy
+// (16-byte loads) the forward takes at most 2: more windows hold more
+// registers, and the fewer resident warps then hide the loads' latency
+// worse (256^3 workload: 18.2 ms with at most 2, 19.6 with 3, 21.6 with 4).
+static int column_windows_per_warp(int nv, int rmax = 2)
 {
     const int windows = (nv + 31) / 32;
     int best = 1, cost = INT_MAX;
@@ -1386,24 +1450,20 @@ static int column_windows_per_warp(int nv, int rmax = 5)
 template <typename T, typename TO>
 static void column_dispatch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
 {
-    const int best = column_windows_per_warp(p.nv, 4);
-    if (best == 4)
-        column_launch<T, TO, 4>(vp, sino, b, p, s);
-    else if (best == 3)
-        column_launch<T, TO, 3>(vp, sino, b, p, s);
-    else if (best == 2)
+    if (column_windows_per_warp(p.nv) == 2)
         column_launch<T, TO, 2>(vp, sino, b, p, s);
     else
         column_launch<T, TO, 1>(vp, sino, b, p, s);
 }
 
 // two-ray windows per warp: about 40 issue slots per window and depth plane
-// plus about 30 shared by the warp's windows
+// plus about 30 shared by the warp's windows; at most 2, as for the one-ray
+// kernel (512^3 TV workload: 490 ms with at most 2 or 3, 575 with 4)
 static int pair_rows_windows_per_warp(int nv, int wr)
 {
     const int windows = (nv + wr - 1) / wr;
     int best = 1, cost = INT_MAX;
-    for (int r = 1; r <= 4 && r <= windows; ++r) {
+    for (int r = 1; r <= 2 && r <= windows; ++r) {
         const int c = (windows + r - 1) / r * (40 * r + 30);
         if (c <= cost) {
             best = r;
@@ -1424,12 +1484,10 @@ static void pair_rows_launch(const void *vp, void *sino, int b, const FP3DParams
 template <typename T, typename TO>
 static void pair_rows_dispatch(const void *vp, void *sino, int b, const FP3DParams &p, cudaStream_t s)
 {
-    switch (pair_rows_windows_per_warp(p.nv, p.pair_rows)) {
-    case 4: pair_rows_launch<T, TO, 4>(vp, sino, b, p, s); break;
-    case 3: pair_rows_launch<T, TO, 3>(vp, sino, b, p, s); break;
-    case 2: pair_rows_launch<T, TO, 2>(vp, sino, b, p, s); break;
-    default: pair_rows_launch<T, TO, 1>(vp, sino, b, p, s); break;
-    }
+    if (pair_rows_windows_per_warp(p.nv, p.pair_rows) == 2)
+        pair_rows_launch<T, TO, 2>(vp, sino, b, p, s);
+    else
+        pair_rows_launch<T, TO, 1>(vp, sino, b, p, s);
 }
 
 template <typename T, typename TO>

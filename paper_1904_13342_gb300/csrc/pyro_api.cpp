@@ -898,9 +898,9 @@ int fp3d(const void *vol, void *sino, int batch, const pyro_geom3d *g, pyro_dtyp
 // view allows them and the padded copy is int-indexable.
 int column_path(const Geo3D &G, FP3DParams &p, bool &column)
 {
-    const size_t padded = fp_padded_elems(G.nx, G.ny, G.nz);
+    const size_t cells = fp_padded_cells(G.nx, G.ny, G.nz);
     const int V = (int)G.beta.size();
-    column = padded < (size_t)INT32_MAX;
+    column = cells < (size_t)INT32_MAX;  // cell indices are ints
     for (int v0 = 0; v0 < V && column; v0 += kMaxViewsConeFP) {
         if (int e = fill_fp3d(G, v0, std::min(kMaxViewsConeFP, V - v0), p)) return e;
         column = p.column_shared != 0;
