@@ -575,7 +575,7 @@ struct ColumnWindow {
 struct ZSeg {
     float f, q;
     float fb, qb;
-    int zbase;  // ib - 0x4B400000 + lane: the lane's run index minus the magic bits
+    int zbase;  // ib + 1 + lane - 0x4B400000: the lane's cell in the padded column minus the magic bits
 };
 
 __device__ __forceinline__ ZSeg zseg(const float4 &zr, int src, int lane, int mz)
@@ -588,13 +588,13 @@ __device__ __forceinline__ ZSeg zseg(const float4 &zr, int src, int lane, int mz
     s.qb = __shfl_sync(full, Z.q, src);
     s.f = Z.f + (float)(Z.i - ib);
     s.q = Z.q;
-    s.zbase = ib - 0x4B400000 + lane;
+    s.zbase = ib + 1 + lane - 0x4B400000;
     return s;
 }
 
-// the track anchored at plane ms: x = X.i + X.f + dx X.q, and the padded
-// element index of cell (X.i, Y.i, z = 0) minus the magic bits of the
-// in-segment floors (mod 2^32)
+// the track anchored at plane ms: x = X.i + X.f + dx X.q, and the index of
+// the padded column (X.i, Y.i) (its cell 0 is the zero below z = 0) minus
+// the magic bits of the in-segment floors (mod 2^32)
 struct TrackSeg {
     float xf, xq, yf, yq;
     int col0;
@@ -610,14 +610,15 @@ __device__ __forceinline__ TrackSeg track_seg(const float4 *t, int ms, int sxp, 
     s.yf = Y.f;
     s.yq = Y.q;
     s.col0 = (int)((unsigned)(Y.i + kFPPadXY - 0x4B400000) * (unsigned)syp +
-                   (unsigned)(X.i + kFPPadXY - 0x4B400000) * (unsigned)sxp + 1u);
+                   (unsigned)(X.i + kFPPadXY - 0x4B400000) * (unsigned)sxp);
     return s;
 }
 
-// (x, y) cell of a depth plane shared by the column's rays: bilinear weights
-// and the padded element index of (x0, y0, z = 0)
+// (x, y) cell of a depth plane shared by the column's rays: its bilinear
+// weights as the pairs (w00, w10) and (w01, w11), matching the two halves of
+// a quad-copy cell, and the index of the padded column (x0, y0)
 struct PlaneXY {
-    float w00, w10, w01, w11;
+    f32x2 wa, wb;
     int col;
 };
 
@@ -628,13 +629,27 @@ __device__ __forceinline__ PlaneXY plane_xy(const TrackSeg &s, float dx, int sxp
     const float ax = fx - magic_to_float(tx), ay = fy - magic_to_float(ty);
     const float bx = 1.0f - ax, by = 1.0f - ay;
     PlaneXY q;
-    q.w00 = bx * by;
-    q.w10 = ax * by;
-    q.w01 = bx * ay;
-    q.w11 = ax * ay;
+    q.wa = pk2(bx * by, ax * by);
+    q.wb = pk2(bx * ay, ax * ay);
     q.col = (int)((unsigned)s.col0 + (unsigned)__float_as_int(ty) * (unsigned)syp +
                   (unsigned)__float_as_int(tx) * (unsigned)sxp);  // mod 2^32: the magic bits cancel
     return q;
+}
+
+// a quad-copy cell's bilinear value: (w00 v00 + w01 v01) + (w10 v10 + w11 v11)
+__device__ __forceinline__ float bilerp_quad(f32x2 wa, f32x2 wb, float4 v)
+{
+    float a, b;
+    upk2(fma2(wb, pk2(v.z, v.w), mul2(wa, pk2(v.x, v.y))), a, b);
+    return a + b;
+}
+
+// the lane's cell in the padded column: run start zbase + tb (tb the magic
+// floor of the lowest row's z) clamped to the column's cells 0 .. nz + 1,
+// whose ends are zeros; one add-min-relu
+__device__ __forceinline__ unsigned run_cell(int zbase, float tb, int nz1)
+{
+    return (unsigned)__viaddmin_s32_relu(zbase, __float_as_int(tb), nz1);
 }
 
 // the four (x, y) columns of a cell at one z from the quad copy: (x, y),
@@ -666,13 +681,11 @@ __device__ __forceinline__ float4 ldq<__nv_bfloat16>(const __nv_bfloat16 *p)
 // One depth plane of one window: the lane's x/y-interpolated value at
 // z = zb + lane, then its own ray's z interpolation from two lanes.
 template <typename T>
-__device__ __forceinline__ void column_step(ColumnWindow &W, const ZSeg &z, float dz, int nz, const T *cq,
+__device__ __forceinline__ void column_step(ColumnWindow &W, const ZSeg &z, float dz, int nz1, const T *cq,
                                             const PlaneXY &q)
 {
     const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
-    const int zi = min(max(z.zbase + __float_as_int(tzb), -1), nz);
-    const float4 v = ldq(cq + 4 * zi);
-    const float g = q.w00 * v.x + q.w10 * v.y + q.w01 * v.z + q.w11 * v.w;
+    const float g = bilerp_quad(q.wa, q.wb, ldq(cq + 4 * run_cell(z.zbase, tzb, nz1)));
     const float fz = fmaf(dz, z.q, z.f);
     const float tz = floor_magic(fz);
     const int j = __float_as_int(tz) - __float_as_int(tzb);  // own cell relative to the window's run
@@ -681,13 +694,16 @@ __device__ __forceinline__ void column_step(ColumnWindow &W, const ZSeg &z, floa
 }
 
 // Two consecutive depth planes (dx, dx + 1) of the column's track at once:
-// the f32x2 form of plane_xy, weights and padded indices of both planes.
+// the cells' positions in f32x2 pairs, then each plane's weights as in
+// plane_xy, and the columns' pointers.
+template <typename T>
 struct PlanePair {
-    f32x2 w00, w10, w01, w11;
-    int col0, col1;
+    f32x2 wa0, wb0, wa1, wb1;
+    const T *c0, *c1;
 };
 
-__device__ __forceinline__ PlanePair plane_pair(const TrackSeg &s, float dx, int sxp, int syp)
+template <typename T>
+__device__ __forceinline__ PlanePair<T> plane_pair(const TrackSeg &s, float dx, const T *vp, int sxp, int syp)
 {
     const f32x2 MAGIC = pk2(kFloorMagic, kFloorMagic), ONE = pk2(1.0f, 1.0f);
     const f32x2 D = pk2(dx, dx + 1.0f);
@@ -695,39 +711,40 @@ __device__ __forceinline__ PlanePair plane_pair(const TrackSeg &s, float dx, int
     const f32x2 TX = add2_rm(FX, MAGIC), TY = add2_rm(FY, MAGIC);
     const f32x2 AX = sub2(FX, sub2(TX, MAGIC)), AY = sub2(FY, sub2(TY, MAGIC));
     const f32x2 BX = sub2(ONE, AX), BY = sub2(ONE, AY);
-    PlanePair q;
-    q.w00 = mul2(BX, BY);
-    q.w10 = mul2(AX, BY);
-    q.w01 = mul2(BX, AY);
-    q.w11 = mul2(AX, AY);
+    float ax0, ax1, ay0, ay1, bx0, bx1, by0, by1;
+    upk2(AX, ax0, ax1);
+    upk2(AY, ay0, ay1);
+    upk2(BX, bx0, bx1);
+    upk2(BY, by0, by1);
+    PlanePair<T> q;
+    q.wa0 = pk2(bx0 * by0, ax0 * by0);
+    q.wb0 = pk2(bx0 * ay0, ax0 * ay0);
+    q.wa1 = pk2(bx1 * by1, ax1 * by1);
+    q.wb1 = pk2(bx1 * ay1, ax1 * ay1);
     float tx0, tx1, ty0, ty1;
     upk2(TX, tx0, tx1);
     upk2(TY, ty0, ty1);
-    q.col0 = (int)((unsigned)s.col0 + (unsigned)__float_as_int(ty0) * (unsigned)syp +
-                   (unsigned)__float_as_int(tx0) * (unsigned)sxp);
-    q.col1 = (int)((unsigned)s.col0 + (unsigned)__float_as_int(ty1) * (unsigned)syp +
-                   (unsigned)__float_as_int(tx1) * (unsigned)sxp);
+    const unsigned col0 = (unsigned)s.col0 + (unsigned)__float_as_int(ty0) * (unsigned)syp +
+                          (unsigned)__float_as_int(tx0) * (unsigned)sxp;
+    const unsigned col1 = (unsigned)s.col0 + (unsigned)__float_as_int(ty1) * (unsigned)syp +
+                          (unsigned)__float_as_int(tx1) * (unsigned)sxp;
+    q.c0 = vp + 4 * (size_t)(int)col0;
+    q.c1 = vp + 4 * (size_t)(int)col1;
     return q;
 }
 
 // One window on two consecutive planes: as column_step for each plane, the
-// arithmetic in f32x2 pairs (plane m in the low half, m + 1 in the high)
+// z arithmetic in f32x2 pairs (plane m in the low half, m + 1 in the high)
 template <typename T>
-__device__ __forceinline__ void column_step_pair(f32x2 &acc, const ZSeg &z, float dz, int nz, const T *vp,
-                                                 const PlanePair &q, int sxp, int syp)
+__device__ __forceinline__ void column_step_pair(f32x2 &acc, const ZSeg &z, float dz, int nz1, const PlanePair<T> &q)
 {
     const f32x2 MAGIC = pk2(kFloorMagic, kFloorMagic);
     const f32x2 D = pk2(dz, dz + 1.0f);
     const f32x2 TB = add2_rm(fma2(D, pk2(z.qb, z.qb), pk2(z.fb, z.fb)), MAGIC);
     float tb0, tb1;
     upk2(TB, tb0, tb1);
-    const int zi0 = min(max(z.zbase + __float_as_int(tb0), -1), nz) + q.col0;
-    const int zi1 = min(max(z.zbase + __float_as_int(tb1), -1), nz) + q.col1;
-    const float4 v0 = ldq(vp + 4 * (size_t)zi0), v1 = ldq(vp + 4 * (size_t)zi1);
-    const f32x2 A = pk2(v0.x, v1.x), B = pk2(v0.y, v1.y), C = pk2(v0.z, v1.z), E = pk2(v0.w, v1.w);
-    const f32x2 G = fma2(q.w11, E, fma2(q.w01, C, fma2(q.w10, B, mul2(q.w00, A))));
-    float g0, g1;
-    upk2(G, g0, g1);
+    const float4 v0 = ldq(q.c0 + 4 * run_cell(z.zbase, tb0, nz1)), v1 = ldq(q.c1 + 4 * run_cell(z.zbase, tb1, nz1));
+    const float g0 = bilerp_quad(q.wa0, q.wb0, v0), g1 = bilerp_quad(q.wa1, q.wb1, v1);
     const f32x2 FZ = fma2(D, pk2(z.q, z.q), pk2(z.f, z.f));
     const f32x2 TZ = add2_rm(FZ, MAGIC);
     float tz0, tz1;
@@ -755,15 +772,15 @@ __device__ __forceinline__ void column_planes_paired(ColumnWindow (&W)[R], const
         int m = ms;
 #pragma unroll 2
         for (; m + 1 <= me; m += 2, dx += 2.0f, dz += 2.0f) {
-            const PlanePair q = plane_pair(ts, dx, sxp, syp);
+            const PlanePair<T> q = plane_pair(ts, dx, vp, sxp, syp);
 #pragma unroll
-            for (int r = 0; r < R; ++r) column_step_pair(acc[r], zs[r], dz, p.nz, vp, q, sxp, syp);
+            for (int r = 0; r < R; ++r) column_step_pair(acc[r], zs[r], dz, p.nz + 1, q);
         }
         if (m <= me) {  // an odd plane left in the segment
             const PlaneXY q = plane_xy(ts, dx, sxp, syp);
             const T *cq = vp + 4 * (size_t)q.col;
 #pragma unroll
-            for (int r = 0; r < R; ++r) column_step(W[r], zs[r], dz, p.nz, cq, q);
+            for (int r = 0; r < R; ++r) column_step(W[r], zs[r], dz, p.nz + 1, cq, q);
         }
     }
 #pragma unroll
@@ -794,7 +811,7 @@ __device__ __forceinline__ void column_planes(ColumnWindow (&W)[R], const ZSeg (
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-                column_step(W[r], zs[r], dz, p.nz, cq, q);
+                column_step(W[r], zs[r], dz, p.nz + 1, cq, q);
             }
         }
     }
@@ -973,7 +990,7 @@ __device__ __forceinline__ ZSeg2 zseg2(const float4 &z0, const float4 &z1, int s
     s.q[0] = A.q;
     s.f[1] = B.f + (float)(B.i - ib);
     s.q[1] = B.q;
-    s.zbase = ib - 0x4B400000 + lane;
+    s.zbase = ib + 1 + lane - 0x4B400000;
     return s;
 }
 
@@ -1037,13 +1054,11 @@ __device__ __forceinline__ void pair_rows_setup(const FP3DParams &p, int v, int 
 // one depth plane of one window: the run as in column_step, then both rays'
 // z interpolations from it
 template <typename T>
-__device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, const ZSeg2 &z, float dz, int nz, const T *cq,
+__device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, const ZSeg2 &z, float dz, int nz1, const T *cq,
                                                const PlaneXY &q)
 {
     const float tzb = floor_magic(fmaf(dz, z.qb, z.fb));
-    const int zi = min(max(z.zbase + __float_as_int(tzb), -1), nz);
-    const float4 v = ldq(cq + 4 * zi);
-    const float g = q.w00 * v.x + q.w10 * v.y + q.w01 * v.z + q.w11 * v.w;
+    const float g = bilerp_quad(q.wa, q.wb, ldq(cq + 4 * run_cell(z.zbase, tzb, nz1)));
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
         const float fz = fmaf(dz, z.q[h], z.f[h]);
@@ -1070,7 +1085,7 @@ __device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], const Z
 #pragma unroll
             for (int r = 0; r < R; ++r) {
                 if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-                pair_rows_step(W[r], zs[r], dz, p.nz, cq, q);
+                pair_rows_step(W[r], zs[r], dz, p.nz + 1, cq, q);
             }
         }
     }
