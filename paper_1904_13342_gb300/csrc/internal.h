@@ -102,7 +102,7 @@ struct FP3DParams {
 // z = A + m C + (B + m D) l, the detector column coordinate of the voxel
 // column (x, y), (u0 + ui x + uj y) / (w0 + wi x + wj y), and its depth-plane
 // coordinate mc + mi x + mj y.  Pairs are FP64 values as FP32 hi/lo.
-constexpr int kGatherTile = 4;    // voxel columns per tile side
+constexpr int kGatherTile = 6;    // voxel columns per tile side
 constexpr int kGatherWarps = 4;   // warps per block (32 z voxels each)
 constexpr int kMaxViewsGather = 200;
 struct GatherView {
