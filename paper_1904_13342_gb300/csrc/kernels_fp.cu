@@ -762,11 +762,40 @@ __device__ __forceinline__ void column_step_pair(f32x2 &acc, const ZSeg &z, floa
     acc = add2(acc, fma2(sub2(FZ, sub2(TZ, MAGIC)), sub2(G1, G0), G0));
 }
 
-// the main phase of the forward: every window active, planes in pairs
+// planes mb .. mb + 31 of the segment anchored at ms: lane i computes plane
+// mb + i and stores its weights and column for the whole warp
+__device__ __forceinline__ void plane_batch(const TrackSeg &ts, int mb, int ms, int lane, int sxp, int syp, float4 *pw,
+                                            int *pc)
+{
+    const PlaneXY q = plane_xy(ts, (float)(mb - ms + lane), sxp, syp);  // lanes past the segment: unused
+    float a0, a1, b0, b1;
+    upk2(q.wa, a0, a1);
+    upk2(q.wb, b0, b1);
+    __syncwarp();  // the previous batch is no longer read
+    pw[lane] = make_float4(a0, a1, b0, b1);
+    pc[lane] = q.col;
+    __syncwarp();
+}
+
+__device__ __forceinline__ PlaneXY plane_from_batch(const float4 *pw, const int *pc, int i)
+{
+    const float4 w = pw[i];
+    PlaneXY q;
+    q.wa = pk2(w.x, w.y);
+    q.wb = pk2(w.z, w.w);
+    q.col = pc[i];
+    return q;
+}
+
+// the main phase of the forward: every window active, planes in pairs.
+// The (x, y) cell and weights of 32 planes at a time are computed one plane
+// per lane and handed to the warp through shared memory (pw, pc: 32 entries
+// of the warp's own), so that each plane's set-up costs a lane 1/32 of its
+// arithmetic plus two broadcast loads; the values are those of plane_pair.
 template <typename T, int R>
 __device__ __forceinline__ void column_planes_paired(ColumnWindow (&W)[R], const ZSeg (&zs)[R], const float4 *track,
                                                      int mz, int m0, int m1, const T *vp, const FP3DParams &p,
-                                                     int sxp, int syp)
+                                                     int sxp, int syp, float4 *pw, int *pc, int lane)
 {
     f32x2 acc[R];
 #pragma unroll
@@ -774,19 +803,31 @@ __device__ __forceinline__ void column_planes_paired(ColumnWindow (&W)[R], const
     for (int ms = m0; ms <= m1; ms += kFPSegment) {
         const int me = min(ms + kFPSegment - 1, m1);
         const TrackSeg ts = track_seg(track, ms, sxp, syp);
-        float dx = 0.0f, dz = (float)(ms - mz);
-        int m = ms;
+        for (int mb = ms; mb <= me; mb += 32) {
+            const int n = min(32, me - mb + 1);
+            plane_batch(ts, mb, ms, lane, sxp, syp, pw, pc);
+            float dz = (float)(mb - mz);
+            int i = 0;
 #pragma unroll 4
-        for (; m + 1 <= me; m += 2, dx += 2.0f, dz += 2.0f) {
-            const PlanePair<T> q = plane_pair(ts, dx, vp, sxp, syp);
+            for (; i + 1 < n; i += 2, dz += 2.0f) {
+                const float4 w0 = pw[i], w1 = pw[i + 1];
+                const int2 c = *reinterpret_cast<const int2 *>(pc + i);  // i even: 8-byte aligned
+                PlanePair<T> q;
+                q.wa0 = pk2(w0.x, w0.y);
+                q.wb0 = pk2(w0.z, w0.w);
+                q.wa1 = pk2(w1.x, w1.y);
+                q.wb1 = pk2(w1.z, w1.w);
+                q.c0 = vp + 4 * (size_t)c.x;
+                q.c1 = vp + 4 * (size_t)c.y;
 #pragma unroll
-            for (int r = 0; r < R; ++r) column_step_pair(acc[r], zs[r], dz, p.nz + 1, q);
-        }
-        if (m <= me) {  // an odd plane left in the segment
-            const PlaneXY q = plane_xy(ts, dx, sxp, syp);
-            const T *cq = vp + 4 * (size_t)q.col;
+                for (int r = 0; r < R; ++r) column_step_pair(acc[r], zs[r], dz, p.nz + 1, q);
+            }
+            if (i < n) {  // an odd plane left in the segment
+                const PlaneXY q = plane_from_batch(pw, pc, i);
+                const T *cq = vp + 4 * (size_t)q.col;
 #pragma unroll
-            for (int r = 0; r < R; ++r) column_step(W[r], zs[r], dz, p.nz + 1, cq, q);
+                for (int r = 0; r < R; ++r) column_step(W[r], zs[r], dz, p.nz + 1, cq, q);
+            }
         }
     }
 #pragma unroll
@@ -923,7 +964,7 @@ __device__ __forceinline__ void column_setup(const FP3DParams &p, int v, int k, 
 template <typename T, int R>
 __device__ __forceinline__ void column_march(ColumnWindow (&W)[R], const float4 *track, const float4 *zray,
                                              int last_low, int mlo, int mhi, int clo, int chi, int lane, const T *vp,
-                                             const FP3DParams &p)
+                                             const FP3DParams &p, float4 *pw, int *pc)
 {
     const int sxp = p.nz + 2, syp = (p.nx + 2 * kFPPadXY) * (p.nz + 2);
     const int mz = mlo + (mhi - mlo) / 2;
@@ -931,17 +972,19 @@ __device__ __forceinline__ void column_march(ColumnWindow (&W)[R], const float4 
 #pragma unroll
     for (int r = 0; r < R; ++r) zs[r] = zseg(zray[32 * r + lane], (last_low >> r & 1) ? 31 : 0, lane, mz);
     column_planes<T, R, true>(W, zs, track, mz, mlo, clo - 1, vp, p, sxp, syp);
-    column_planes_paired<T, R>(W, zs, track, mz, clo, chi, vp, p, sxp, syp);
+    column_planes_paired<T, R>(W, zs, track, mz, clo, chi, vp, p, sxp, syp, pw, pc, lane);
     column_planes<T, R, true>(W, zs, track, mz, max(chi + 1, clo), mhi, vp, p, sxp, syp);
 }
 
 template <typename T, typename TO, int R>
-__global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__restrict__ vp,
+__global__ void __launch_bounds__(32 * kFPCWarps, 4) fp3d_column_kernel(const T *__restrict__ vp,
                                                                      TO *__restrict__ sino,
                                                                      const __grid_constant__ FP3DParams p, int b)
 {
     __shared__ float4 zrays[kFPCWarps][R * 32];
     __shared__ float4 tracks[kFPCWarps][2];
+    __shared__ float4 pws[kFPCWarps][32];
+    __shared__ int pcs[kFPCWarps][32];
     const int lane = threadIdx.x;
     const int k = blockIdx.y * kFPCWarps + threadIdx.y;
     const int v = blockIdx.x;
@@ -952,7 +995,8 @@ __global__ void __launch_bounds__(32 * kFPCWarps) fp3d_column_kernel(const T *__
     column_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
                     -1.0f, (float)p.nz);
     if (mlo <= mhi)
-        column_march<T, R>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp, p);
+        column_march<T, R>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp, p,
+                           pws[threadIdx.y], pcs[threadIdx.y]);
 #pragma unroll
     for (int r = 0; r < R; ++r) {
         const int l = row0 + 32 * r + lane;
@@ -1097,10 +1141,36 @@ __device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], const Z
     }
 }
 
+// the main phase (every window active): the planes' set-up shared through
+// 32-plane batches, as in column_planes_paired
+template <typename T, int R>
+__device__ __forceinline__ void pair_rows_planes_batched(PairRowsWindow (&W)[R], const ZSeg2 (&zs)[R],
+                                                         const float4 *track, int mz, int m0, int m1, const T *vp,
+                                                         const FP3DParams &p, int sxp, int syp, float4 *pw, int *pc,
+                                                         int lane)
+{
+    for (int ms = m0; ms <= m1; ms += kFPSegment) {
+        const int me = min(ms + kFPSegment - 1, m1);
+        const TrackSeg ts = track_seg(track, ms, sxp, syp);
+        for (int mb = ms; mb <= me; mb += 32) {
+            const int n = min(32, me - mb + 1);
+            plane_batch(ts, mb, ms, lane, sxp, syp, pw, pc);
+            float dz = (float)(mb - mz);
+#pragma unroll 4
+            for (int i = 0; i < n; ++i, dz += 1.0f) {
+                const PlaneXY q = plane_from_batch(pw, pc, i);
+                const T *cq = vp + 4 * (size_t)q.col;
+#pragma unroll
+                for (int r = 0; r < R; ++r) pair_rows_step(W[r], zs[r], dz, p.nz + 1, cq, q);
+            }
+        }
+    }
+}
+
 template <typename T, int R>
 __device__ __forceinline__ void pair_rows_march(PairRowsWindow (&W)[R], const float4 *track, const float4 *zray,
                                                 int last_low, int mlo, int mhi, int clo, int chi, int lane, const T *vp,
-                                                const FP3DParams &p)
+                                                const FP3DParams &p, float4 *pw, int *pc)
 {
     const int sxp = p.nz + 2, syp = (p.nx + 2 * kFPPadXY) * (p.nz + 2);
     const int mz = mlo + (mhi - mlo) / 2;
@@ -1111,7 +1181,7 @@ __device__ __forceinline__ void pair_rows_march(PairRowsWindow (&W)[R], const fl
         zs[r] = zseg2(zray[(2 * r) * 32 + lane], zray[(2 * r + 1) * 32 + lane], hi ? p.pair_rows - 33 : 0, hi, lane, mz);
     }
     pair_rows_planes<T, R, true>(W, zs, track, mz, mlo, clo - 1, vp, p, sxp, syp);
-    pair_rows_planes<T, R, false>(W, zs, track, mz, clo, chi, vp, p, sxp, syp);
+    pair_rows_planes_batched<T, R>(W, zs, track, mz, clo, chi, vp, p, sxp, syp, pw, pc, lane);
     pair_rows_planes<T, R, true>(W, zs, track, mz, max(chi + 1, clo), mhi, vp, p, sxp, syp);
 }
 
@@ -1122,6 +1192,8 @@ __global__ void __launch_bounds__(32 * kFPPWarps) fp3d_pair_rows_kernel(const T 
 {
     __shared__ float4 zrays[kFPPWarps][2 * R * 32];
     __shared__ float4 tracks[kFPPWarps][2];
+    __shared__ float4 pws[kFPPWarps][32];
+    __shared__ int pcs[kFPPWarps][32];
     const int lane = threadIdx.x;
     const int k = blockIdx.y * kFPPWarps + threadIdx.y;
     const int v = blockIdx.x;
@@ -1133,7 +1205,8 @@ __global__ void __launch_bounds__(32 * kFPPWarps) fp3d_pair_rows_kernel(const T 
     pair_rows_setup<R>(p, v, k, row0, lane, tracks[threadIdx.y], W, zrays[threadIdx.y], last_low, mlo, mhi, clo, chi,
                        -1.0f, (float)p.nz);
     if (mlo <= mhi)
-        pair_rows_march<T, R>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp, p);
+        pair_rows_march<T, R>(W, tracks[threadIdx.y], zrays[threadIdx.y], last_low, mlo, mhi, clo, chi, lane, vp, p,
+                              pws[threadIdx.y], pcs[threadIdx.y]);
 #pragma unroll
     for (int r = 0; r < R; ++r)
 #pragma unroll
