@@ -839,26 +839,32 @@ __device__ __forceinline__ void column_planes_paired(ColumnWindow (&W)[R], const
 }
 
 // Depth planes m0..m1 of all R windows, the track re-anchored every
-// kFPSegment planes.  CHECK skips the windows whose rows cannot touch the
-// volume on a plane (outside the planes every window reaches; elsewhere the
-// skipped terms would be exact zeros anyway: the taps read the zero padding).
-template <typename T, int R, bool CHECK>
+// kFPSegment planes and the planes' set-up shared through 32-plane batches.
+// Skips the windows whose rows cannot touch the volume on a plane (the
+// planes outside those every window reaches; elsewhere the skipped terms
+// would be exact zeros anyway: the taps read the zero padding).
+template <typename T, int R>
 __device__ __forceinline__ void column_planes(ColumnWindow (&W)[R], const ZSeg (&zs)[R], const float4 *track, int mz,
-                                              int m0, int m1, const T *vp, const FP3DParams &p, int sxp, int syp)
+                                              int m0, int m1, const T *vp, const FP3DParams &p, int sxp, int syp,
+                                              float4 *pw, int *pc, int lane)
 {
-    // unrolled by 4 (measured 1 % faster than 2, while 1, 6 and 8 were slower)
     for (int ms = m0; ms <= m1; ms += kFPSegment) {
         const int me = min(ms + kFPSegment - 1, m1);
         const TrackSeg ts = track_seg(track, ms, sxp, syp);
-        float dx = 0.0f, dz = (float)(ms - mz);
+        for (int mb = ms; mb <= me; mb += 32) {
+            const int n = min(32, me - mb + 1);
+            plane_batch(ts, mb, ms, lane, sxp, syp, pw, pc);
+            float dz = (float)(mb - mz);
 #pragma unroll 4
-        for (int m = ms; m <= me; ++m, dx += 1.0f, dz += 1.0f) {
-            const PlaneXY q = plane_xy(ts, dx, sxp, syp);
-            const T *cq = vp + 4 * (size_t)q.col;
+            for (int i = 0; i < n; ++i, dz += 1.0f) {
+                const int m = mb + i;
+                const PlaneXY q = plane_from_batch(pw, pc, i);
+                const T *cq = vp + 4 * (size_t)q.col;
 #pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-                column_step(W[r], zs[r], dz, p.nz + 1, cq, q);
+                for (int r = 0; r < R; ++r) {
+                    if (m < W[r].ma || m > W[r].mb) continue;  // whole warp
+                    column_step(W[r], zs[r], dz, p.nz + 1, cq, q);
+                }
             }
         }
     }
@@ -971,9 +977,9 @@ __device__ __forceinline__ void column_march(ColumnWindow (&W)[R], const float4 
     ZSeg zs[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) zs[r] = zseg(zray[32 * r + lane], (last_low >> r & 1) ? 31 : 0, lane, mz);
-    column_planes<T, R, true>(W, zs, track, mz, mlo, clo - 1, vp, p, sxp, syp);
+    column_planes<T, R>(W, zs, track, mz, mlo, clo - 1, vp, p, sxp, syp, pw, pc, lane);
     column_planes_paired<T, R>(W, zs, track, mz, clo, chi, vp, p, sxp, syp, pw, pc, lane);
-    column_planes<T, R, true>(W, zs, track, mz, max(chi + 1, clo), mhi, vp, p, sxp, syp);
+    column_planes<T, R>(W, zs, track, mz, max(chi + 1, clo), mhi, vp, p, sxp, syp, pw, pc, lane);
 }
 
 template <typename T, typename TO, int R>
@@ -1119,32 +1125,11 @@ __device__ __forceinline__ void pair_rows_step(PairRowsWindow &W, const ZSeg2 &z
     }
 }
 
+// planes m0..m1 with the planes' set-up shared through 32-plane batches, as
+// in column_planes; CHECK skips the windows whose rows cannot touch the
+// volume on a plane (outside the planes every window reaches)
 template <typename T, int R, bool CHECK>
-__device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], const ZSeg2 (&zs)[R], const float4 *track,
-                                                 int mz, int m0, int m1, const T *vp, const FP3DParams &p, int sxp,
-                                                 int syp)
-{
-    for (int ms = m0; ms <= m1; ms += kFPSegment) {
-        const int me = min(ms + kFPSegment - 1, m1);
-        const TrackSeg ts = track_seg(track, ms, sxp, syp);
-        float dx = 0.0f, dz = (float)(ms - mz);
-#pragma unroll 4
-        for (int m = ms; m <= me; ++m, dx += 1.0f, dz += 1.0f) {
-            const PlaneXY q = plane_xy(ts, dx, sxp, syp);
-            const T *cq = vp + 4 * (size_t)q.col;
-#pragma unroll
-            for (int r = 0; r < R; ++r) {
-                if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
-                pair_rows_step(W[r], zs[r], dz, p.nz + 1, cq, q);
-            }
-        }
-    }
-}
-
-// the main phase (every window active): the planes' set-up shared through
-// 32-plane batches, as in column_planes_paired
-template <typename T, int R>
-__device__ __forceinline__ void pair_rows_planes_batched(PairRowsWindow (&W)[R], const ZSeg2 (&zs)[R],
+__device__ __forceinline__ void pair_rows_planes(PairRowsWindow (&W)[R], const ZSeg2 (&zs)[R],
                                                          const float4 *track, int mz, int m0, int m1, const T *vp,
                                                          const FP3DParams &p, int sxp, int syp, float4 *pw, int *pc,
                                                          int lane)
@@ -1158,10 +1143,14 @@ __device__ __forceinline__ void pair_rows_planes_batched(PairRowsWindow (&W)[R],
             float dz = (float)(mb - mz);
 #pragma unroll 4
             for (int i = 0; i < n; ++i, dz += 1.0f) {
+                const int m = mb + i;
                 const PlaneXY q = plane_from_batch(pw, pc, i);
                 const T *cq = vp + 4 * (size_t)q.col;
 #pragma unroll
-                for (int r = 0; r < R; ++r) pair_rows_step(W[r], zs[r], dz, p.nz + 1, cq, q);
+                for (int r = 0; r < R; ++r) {
+                    if (CHECK && (m < W[r].ma || m > W[r].mb)) continue;  // whole warp
+                    pair_rows_step(W[r], zs[r], dz, p.nz + 1, cq, q);
+                }
             }
         }
     }
@@ -1180,9 +1169,9 @@ __device__ __forceinline__ void pair_rows_march(PairRowsWindow (&W)[R], const fl
         const bool hi = last_low >> r & 1;
         zs[r] = zseg2(zray[(2 * r) * 32 + lane], zray[(2 * r + 1) * 32 + lane], hi ? p.pair_rows - 33 : 0, hi, lane, mz);
     }
-    pair_rows_planes<T, R, true>(W, zs, track, mz, mlo, clo - 1, vp, p, sxp, syp);
-    pair_rows_planes_batched<T, R>(W, zs, track, mz, clo, chi, vp, p, sxp, syp, pw, pc, lane);
-    pair_rows_planes<T, R, true>(W, zs, track, mz, max(chi + 1, clo), mhi, vp, p, sxp, syp);
+    pair_rows_planes<T, R, true>(W, zs, track, mz, mlo, clo - 1, vp, p, sxp, syp, pw, pc, lane);
+    pair_rows_planes<T, R, false>(W, zs, track, mz, clo, chi, vp, p, sxp, syp, pw, pc, lane);
+    pair_rows_planes<T, R, true>(W, zs, track, mz, max(chi + 1, clo), mhi, vp, p, sxp, syp, pw, pc, lane);
 }
 
 template <typename T, typename TO, int R>
