@@ -229,13 +229,18 @@ __device__ __forceinline__ void stockham_pass(const float2 *src, float2 *dst, co
         float2 *d = dst + g * sp(pn);
         const int k = j & (ns - 1);
         float2 v[R];
-        const float2 w1 = tw[k];
-        float2 w = make_float2(1.0f, 0.0f);
+        if (ns == 1) {  // the first pass: every twiddle is 1
 #pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const float2 x = s[sp(j + r * nb)];
-            v[r] = r == 0 ? x : cmul(x, w);
-            w = cmul(w, w1);
+            for (int r = 0; r < R; ++r) v[r] = s[sp(j + r * nb)];
+        } else {
+            const float2 w1 = tw[k];
+            float2 w = w1;
+            v[0] = s[sp(j)];
+#pragma unroll
+            for (int r = 1; r < R; ++r) {
+                v[r] = cmul(s[sp(j + r * nb)], w);
+                if (r + 1 < R) w = cmul(w, w1);
+            }
         }
         if (R == 8) dft8(v);
         if (R == 4) dft4(v);
@@ -250,11 +255,19 @@ __device__ __forceinline__ void stockham_pass(const float2 *src, float2 *dst, co
     }
 }
 
-// Full forward transform of `groups` rows; returns the buffer holding the result.
-__device__ float2 *stockham_fft(float2 *a, float2 *b, const float2 *tw, int log2pn, int pn, int groups)
+// Full forward transform of `groups` rows; returns the buffer holding the
+// result.  LOG2 > 0 fixes log2(pn) at compile time (the passes unrolled,
+// their strides constants); 0 takes it from log2pn.
+template <int LOG2>
+__device__ __forceinline__ float2 *stockham_fft(float2 *a, float2 *b, const float2 *tw, int log2pn, int pn, int groups)
 {
+    if (LOG2 > 0) {
+        log2pn = LOG2;
+        pn = 1 << LOG2;
+    }
     const int P = n_passes(log2pn);
-    for (int i = 0; i < P; ++i) {
+#pragma unroll
+    for (int i = 0; i < (LOG2 > 0 ? (LOG2 + 2) / 3 : P); ++i) {
         const int ns = 1 << (3 * i);
         const float2 *t = tw + (ns - 1) / 7;
         const int rb = i < P - 1 ? 3 : log2pn - 3 * (P - 1);
@@ -290,7 +303,9 @@ __host__ __device__ inline int pairs_per_cta(int pn)
     return pn >= 2048 ? 1 : 2048 / pn;
 }
 
-template <typename TI, typename TO>
+// LOG2 > 0: the kernel for pn = 2^LOG2 only (the FFT's strides and loop
+// counts constants); 0: any pn.
+template <typename TI, typename TO, int LOG2>
 __global__ void __launch_bounds__(kFilterThreads) filter_stockham_kernel(const TI *__restrict__ in,
                                                                          TO *__restrict__ out,
                                                                          const __grid_constant__ FilterParams p,
@@ -298,16 +313,17 @@ __global__ void __launch_bounds__(kFilterThreads) filter_stockham_kernel(const T
                                                                          const float *__restrict__ customK)
 {
     extern __shared__ float2 smem[];
-    const int pn = p.pn, nu = p.nu;
+    const int pn = LOG2 > 0 ? 1 << LOG2 : p.pn, nu = p.nu;
+    const int log2pn = LOG2 > 0 ? LOG2 : p.log2pn;
     const int ppc = pairs_per_cta(pn);
     const int stride = sp(pn);  // padded length of one transform
     float2 *A = smem;
     float2 *Bf = A + (size_t)ppc * stride;
     float2 *tw = Bf + (size_t)ppc * stride;
-    float *Kh = reinterpret_cast<float *>(tw + twiddle_total(p.log2pn));  // K[0..pn/2] / pn
+    float *Kh = reinterpret_cast<float *>(tw + twiddle_total(log2pn));  // K[0..pn/2] / pn
     float *wrow = Kh + pn / 2 + 1;                                          // W_red of the current view, nu
     int cached_view = -1;
-    init_stockham_twiddles(tw, p.log2pn);
+    init_stockham_twiddles(tw, log2pn);
     const float inv_pn = 1.0f / (float)pn;
     for (int m = threadIdx.x; m <= pn / 2; m += blockDim.x) Kh[m] = (customK ? customK[m] : p.K[m]) * inv_pn;
     __syncthreads();
@@ -333,52 +349,55 @@ __global__ void __launch_bounds__(kFilterThreads) filter_stockham_kernel(const T
             }
         }
         // load: two weighted rows per complex sequence, zero-padded to pn
-        for (int e = threadIdx.x; e < groups * pn; e += blockDim.x) {
-            const int g = e / pn, n = e - g * pn;
+        for (int g = 0; g < groups; ++g) {
             const long r0 = 2 * (pr0 + g), r1 = r0 + 1;
-            float a = 0.0f, c = 0.0f;
-            if (n < nu) {
-                a = ld(in + r0 * nu + n);
-                const bool has1 = r1 < p.n_rows;
-                if (has1) c = ld(in + r1 * nu + n);
-                if (p.apply_weights) {
-                    if (cached_view >= 0) {
-                        // W_cos (and the cached Parker row)
-                        const float u = ((float)n - p.w.cu) * p.w.su;
-                        const float v0 = ((float)(r0 % p.rows_per_view) - p.w.cv) * p.w.sv;
-                        const float v1 = ((float)(r1 % p.rows_per_view) - p.w.cv) * p.w.sv;
-                        const float wr = wrow[n];
-                        a *= wr * cosine_weight(p.w, u, v0);
-                        c *= wr * cosine_weight(p.w, u, v1);
-                    } else {
-                        a *= total_weight(p.w, bt, (int)((r0 / p.rows_per_view) % p.n_views),
-                                          (int)(r0 % p.rows_per_view), n);
-                        if (has1)
-                            c *= total_weight(p.w, bt, (int)((r1 / p.rows_per_view) % p.n_views),
-                                              (int)(r1 % p.rows_per_view), n);
+            const bool has1 = r1 < p.n_rows;
+            const int l0 = (int)(r0 % p.rows_per_view), l1 = (int)(r1 % p.rows_per_view);
+            const int view0 = (int)((r0 / p.rows_per_view) % p.n_views), view1 = (int)((r1 / p.rows_per_view) % p.n_views);
+            const float v0 = ((float)l0 - p.w.cv) * p.w.sv, v1 = ((float)l1 - p.w.cv) * p.w.sv;
+            const TI *in0 = in + r0 * nu, *in1 = in + r1 * nu;
+            float2 *dst = A + g * stride;
+            for (int n = threadIdx.x; n < pn; n += blockDim.x) {
+                float a = 0.0f, c = 0.0f;
+                if (n < nu) {
+                    a = ld(in0 + n);
+                    if (has1) c = ld(in1 + n);
+                    if (p.apply_weights) {
+                        if (cached_view >= 0) {
+                            // W_cos (and the cached Parker row)
+                            const float u = ((float)n - p.w.cu) * p.w.su;
+                            const float wr = wrow[n];
+                            a *= wr * cosine_weight(p.w, u, v0);
+                            c *= wr * cosine_weight(p.w, u, v1);
+                        } else {
+                            a *= total_weight(p.w, bt, view0, l0, n);
+                            if (has1) c *= total_weight(p.w, bt, view1, l1, n);
+                        }
                     }
                 }
+                dst[sp(n)] = make_float2(a, c);
             }
-            A[g * stride + sp(n)] = make_float2(a, c);
         }
         __syncthreads();
-        float2 *X = stockham_fft(A, Bf, tw, p.log2pn, pn, groups);
+        float2 *X = stockham_fft<LOG2>(A, Bf, tw, log2pn, pn, groups);
         float2 *Y = X == A ? Bf : A;
         // conj(K X): the inverse transform as conj(FFT(conj(.)))
-        for (int e = threadIdx.x; e < groups * pn; e += blockDim.x) {
-            const int g = e / pn, m = e - g * pn;
-            const float k = Kh[m <= pn / 2 ? m : pn - m];
-            const int q = g * stride + sp(m);
-            X[q] = make_float2(X[q].x * k, -X[q].y * k);
-        }
+        for (int g = 0; g < groups; ++g)
+            for (int m = threadIdx.x; m < pn; m += blockDim.x) {
+                const float k = Kh[m <= pn / 2 ? m : pn - m];
+                const int q = g * stride + sp(m);
+                X[q] = make_float2(X[q].x * k, -X[q].y * k);
+            }
         __syncthreads();
-        float2 *Z = stockham_fft(X, Y, tw, p.log2pn, pn, groups);
-        for (int e = threadIdx.x; e < groups * nu; e += blockDim.x) {
-            const int g = e / nu, n = e - g * nu;
+        float2 *Z = stockham_fft<LOG2>(X, Y, tw, log2pn, pn, groups);
+        for (int g = 0; g < groups; ++g) {
             const long r0 = 2 * (pr0 + g), r1 = r0 + 1;
-            const float2 z = Z[g * stride + sp(n)];
-            out[r0 * nu + n] = to_storage<TO>(z.x);
-            if (r1 < p.n_rows) out[r1 * nu + n] = to_storage<TO>(-z.y);
+            const bool has1 = r1 < p.n_rows;
+            for (int n = threadIdx.x; n < nu; n += blockDim.x) {
+                const float2 z = Z[g * stride + sp(n)];
+                out[r0 * nu + n] = to_storage<TO>(z.x);
+                if (has1) out[r1 * nu + n] = to_storage<TO>(-z.y);
+            }
         }
         __syncthreads();
     }
@@ -435,15 +454,15 @@ __global__ void __launch_bounds__(kFilterThreads) filter_grad_K_kernel(const flo
     }
 }
 
-template <typename TI, typename TO>
-cudaError_t filter_dispatch(const void *in, void *out, const FilterParams &p, const BetaTable &bt,
-                            const float *customK, cudaStream_t s)
+template <typename TI, typename TO, int LOG2>
+cudaError_t filter_launch(const void *in, void *out, const FilterParams &p, const BetaTable &bt,
+                          const float *customK, cudaStream_t s)
 {
     const int ppc = pairs_per_cta(p.pn);
     const size_t padded = (size_t)p.pn + (p.pn >> 3);
     const size_t smem = sizeof(float2) * (2 * ppc * padded + twiddle_total(p.log2pn)) +
                         sizeof(float) * ((size_t)(p.pn / 2 + 1) + p.nu);
-    auto kern = filter_stockham_kernel<TI, TO>;
+    auto kern = filter_stockham_kernel<TI, TO, LOG2>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -454,6 +473,19 @@ cudaError_t filter_dispatch(const void *in, void *out, const FilterParams &p, co
     const long grid = std::min<long>(ctas, (long)device_sm_count() * std::max(per_sm, 1));
     kern<<<(unsigned)grid, kFilterThreads, smem, s>>>((const TI *)in, (TO *)out, p, bt, customK);
     return cudaGetLastError();
+}
+
+// the detector widths 257..1024 and 1025..2048 (pn 2048, 4096) take kernels
+// specialised to their pn
+template <typename TI, typename TO>
+cudaError_t filter_dispatch(const void *in, void *out, const FilterParams &p, const BetaTable &bt,
+                            const float *customK, cudaStream_t s)
+{
+    switch (p.log2pn) {
+    case 11: return filter_launch<TI, TO, 11>(in, out, p, bt, customK, s);
+    case 12: return filter_launch<TI, TO, 12>(in, out, p, bt, customK, s);
+    default: return filter_launch<TI, TO, 0>(in, out, p, bt, customK, s);
+    }
 }
 
 template <typename TI>
