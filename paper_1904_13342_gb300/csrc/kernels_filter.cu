@@ -475,7 +475,7 @@ cudaError_t filter_launch(const void *in, void *out, const FilterParams &p, cons
     return cudaGetLastError();
 }
 
-// the detector widths 257..1024 and 1025..2048 (pn 2048, 4096) take kernels
+// the detector widths 513..1024 and 1025..2048 (pn 2048, 4096) take kernels
 // specialised to their pn
 template <typename TI, typename TO>
 cudaError_t filter_dispatch(const void *in, void *out, const FilterParams &p, const BetaTable &bt,
