@@ -102,8 +102,15 @@ struct FP3DParams {
 // z = A + m C + (B + m D) l, the detector column coordinate of the voxel
 // column (x, y), (u0 + ui x + uj y) / (w0 + wi x + wj y), and its depth-plane
 // coordinate mc + mi x + mj y.  Pairs are FP64 values as FP32 hi/lo.
-constexpr int kGatherTile = 6;    // voxel columns per tile side
 constexpr int kGatherWarps = 4;   // warps per block (32 z voxels each)
+// voxel columns per tile side: 6 (fewer border points per column), or 4 when
+// 6-column tiles would give the launch fewer than 1024 blocks (small volumes:
+// 128^3 has 484 such blocks for 152 SMs)
+inline int gather_tile(int nx, int ny, int nz)
+{
+    const long blocks6 = (long)((nx + 5) / 6) * ((ny + 5) / 6) * ((nz + 32 * kGatherWarps - 1) / (32 * kGatherWarps));
+    return blocks6 >= 1024 ? 6 : 4;
+}
 constexpr int kMaxViewsGather = 200;
 struct GatherView {
     float px0[2], pxk[2], py0[2], pyk[2];
@@ -119,6 +126,7 @@ struct GatherParams {
     int kmax, plmax;                 // columns and depth planes that can reach a tile (host bounds)
     int wrows;                       // rows of a lane's window (a multiple of 4, at most 32)
     int sc;                          // staged floats per warp (a column's rows at least)
+    int tile;                        // voxel columns per tile side (gather_tile)
     GatherView v[kMaxViewsGather];
 };
 

@@ -10,7 +10,7 @@
 //   sum over views, planes m and columns k of
 //     t_xy(P(k, m) - (i, j)) * Z_km(z),   Z_km(z) = sum_l w_kl y_kl t(z - z_l(m)),
 // t the linear tent (the interpolation weight), w_kl = dt |g_kl| the ray's
-// step.  A block owns a kGT x kGT tile of voxel columns and kGW x 32 z
+// step.  A block owns a T x T tile of voxel columns and kGW x 32 z
 // voxels (one per lane).  Per view it tabulates the points (k, m) whose
 // tents reach the tile (cell and bilinear weights), and every warp stages
 // the rows its 32 z voxels can reach, for every column of the view that
@@ -35,7 +35,6 @@ namespace pyro {
 
 namespace {
 
-constexpr int kGT = kGatherTile;   // voxel columns per tile side
 constexpr int kGW = kGatherWarps;  // warps per block, 32 z voxels each
 constexpr int kGZ = 32 * kGW;
 
@@ -122,26 +121,27 @@ __host__ __device__ inline GatherSmem gather_smem(const GatherParams &g)
     o = align16(o + sizeof(GPlane) * (size_t)kGW * g.plmax);
     s.stage = o;  // float [kGW][sc]
     o = align16(o + 4 * (size_t)kGW * g.sc);
-    s.acc = o;  // float [kGW][kGT * kGT][32]
-    o = align16(o + 4 * (size_t)kGW * kGT * kGT * 32);
+    s.acc = o;  // float [kGW][tile * tile][32]
+    o = align16(o + 4 * (size_t)kGW * g.tile * g.tile * 32);
     s.total = o;
     return s;
 }
 
-// add a point's four corner terms w Z to the warp's accumulators: c packs
-// the offset of corner (0, 0) plus 4096 and, times 65536, the mask of the
-// corners inside the tile
+// add a point's four corner terms w Z to the warp's accumulators (tile side
+// T): c packs the offset of corner (0, 0) plus 4096 and, times 65536, the
+// mask of the corners inside the tile
+template <int T>
 __device__ __forceinline__ void corner_update(float *acc, int c, float4 w, float Z)
 {
     const int mk = c >> 16;
     float *a = acc + ((c & 0xffff) - 4096);
     if (mk & 1) a[0] = fmaf(w.x, Z, a[0]);
     if (mk & 2) a[32] = fmaf(w.y, Z, a[32]);
-    if (mk & 4) a[32 * kGT] = fmaf(w.z, Z, a[32 * kGT]);
-    if (mk & 8) a[32 * kGT + 32] = fmaf(w.w, Z, a[32 * kGT + 32]);
+    if (mk & 4) a[32 * T] = fmaf(w.z, Z, a[32 * T]);
+    if (mk & 8) a[32 * T + 32] = fmaf(w.w, Z, a[32 * T + 32]);
 }
 
-template <int W, int G>
+template <int W, int G, int T>
 __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const float *__restrict__ yT,
                                                                           float *__restrict__ vol,
                                                                           const __grid_constant__ GatherParams g,
@@ -153,19 +153,19 @@ __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const 
     const int t = threadIdx.x, lane = t & 31, warp = t >> 5;
     float4 *rec = reinterpret_cast<float4 *>(gsm + L.rec);
     int *cell = reinterpret_cast<int *>(gsm + L.cell);
-    float *acc = reinterpret_cast<float *>(gsm + L.acc) + (size_t)warp * kGT * kGT * 32 + lane;
+    float *acc = reinterpret_cast<float *>(gsm + L.acc) + (size_t)warp * T * T * 32 + lane;
     unsigned *pmask = reinterpret_cast<unsigned *>(gsm + L.pmask);
     int2 *prange = reinterpret_cast<int2 *>(gsm + L.prange);
     GPlane *zpl = reinterpret_cast<GPlane *>(gsm + L.planes) + (size_t)warp * g.plmax;
     float *stage = reinterpret_cast<float *>(gsm + L.stage) + (size_t)warp * g.sc;
     __shared__ int s_bad;
     const unsigned full = 0xffffffffu;
-    const int i0 = blockIdx.x * kGT, j0 = blockIdx.y * kGT;
+    const int i0 = blockIdx.x * T, j0 = blockIdx.y * T;
     const int zw0 = blockIdx.z * kGZ + 32 * warp;  // the warp's first z
-    // the support of the tile's tents: P in [i0 - 1, i0 + kGT) x [j0 - 1, j0 + kGT)
-    const float bx0 = (float)(i0 - 1), bx1 = (float)(i0 + kGT), by0 = (float)(j0 - 1), by1 = (float)(j0 + kGT);
+    // the support of the tile's tents: P in [i0 - 1, i0 + T) x [j0 - 1, j0 + T)
+    const float bx0 = (float)(i0 - 1), bx1 = (float)(i0 + T), by0 = (float)(j0 - 1), by1 = (float)(j0 + T);
 #pragma unroll
-    for (int c = 0; c < kGT * kGT; ++c) acc[32 * c] = 0.0f;
+    for (int c = 0; c < T * T; ++c) acc[32 * c] = 0.0f;
     if (t == 0) s_bad = 0;
 
     for (int v = 0; v < g.n_views; ++v) {
@@ -227,13 +227,13 @@ __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const 
                 const float fx = floorf(X), fy = floorf(Y);
                 const int cx = (int)fx, cy = (int)fy;
                 const float ax = X - fx, ay = Y - fy;
-                const bool in = cx >= 0 && cx <= kGT && cy >= 0 && cy <= kGT;
+                const bool in = cx >= 0 && cx <= T && cy >= 0 && cy <= T;
                 const int e = p * K + kk;
                 rec[e] = make_float4((1.0f - ax) * (1.0f - ay), ax * (1.0f - ay), (1.0f - ax) * ay, ax * ay);
                 const int tx = cx - 1, ty = cy - 1;
-                const int mk = (tx >= 0 && ty >= 0 ? 1 : 0) | (tx + 1 < kGT && ty >= 0 ? 2 : 0) |
-                               (tx >= 0 && ty + 1 < kGT ? 4 : 0) | (tx + 1 < kGT && ty + 1 < kGT ? 8 : 0);
-                cell[e] = in ? (ty * kGT + tx) * 32 + 4096 + 65536 * mk : 0;
+                const int mk = (tx >= 0 && ty >= 0 ? 1 : 0) | (tx + 1 < T && ty >= 0 ? 2 : 0) |
+                               (tx >= 0 && ty + 1 < T ? 4 : 0) | (tx + 1 < T && ty + 1 < T ? 8 : 0);
+                cell[e] = in ? (ty * T + tx) * 32 + 4096 + 65536 * mk : 0;
                 if (in) {  // integer OR / min / max: the same result in any order
                     atomicOr(&pmask[(p >> 5) * K + kk], 1u << (p & 31));
                     atomicMin(&prange[p].x, kk);
@@ -377,7 +377,7 @@ __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const 
                         if ((bits >> q) & 1u) {  // uniform
                             float za, zb;
                             upk2(Zp[q], za, zb);
-                            corner_update(acc, cq[q], rec[e0 + q * K], za + zb);
+                            corner_update<T>(acc, cq[q], rec[e0 + q * K], za + zb);
                         }
                     }
                 }
@@ -392,8 +392,8 @@ __global__ void __launch_bounds__(32 * kGW, 4) fp3d_gather_adjoint_kernel(const 
     if (z < g.nz) {
         float *out = vol + (size_t)z * g.ny * g.nx;
 #pragma unroll
-        for (int c = 0; c < kGT * kGT; ++c) {
-            const int x = i0 + c % kGT, y = j0 + c / kGT;
+        for (int c = 0; c < T * T; ++c) {
+            const int x = i0 + c % T, y = j0 + c / T;
             if (x < g.nx && y < g.ny) {
                 float *o = out + (size_t)y * g.nx + x;
                 *o = g.accumulate ? *o + acc[32 * c] : acc[32 * c];
@@ -416,40 +416,53 @@ cudaError_t launch_weighted_transpose(const void *sino, void *yT, int b, const F
     return cudaGetLastError();
 }
 
-template <int W, int G>
+template <int W, int G, int T>
 static cudaError_t gather_launch(const void *yT, void *vol, const GatherParams &g, int *status, cudaStream_t s)
 {
-    if (g.sc % 4 != 0 || g.sc < W || g.kmax < 1 || g.plmax < 1) return cudaErrorInvalidValue;
+    if (g.sc % 4 != 0 || g.sc < W || g.kmax < 1 || g.plmax < 1 || g.tile != T) return cudaErrorInvalidValue;
     const size_t smem = gather_smem_bytes(g);
-    cudaError_t e = cudaFuncSetAttribute(fp3d_gather_adjoint_kernel<W, G>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
+    cudaError_t e = cudaFuncSetAttribute(fp3d_gather_adjoint_kernel<W, G, T>,
+                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return e;
-    dim3 grid((g.nx + kGT - 1) / kGT, (g.ny + kGT - 1) / kGT, (g.nz + kGZ - 1) / kGZ);
-    fp3d_gather_adjoint_kernel<W, G><<<grid, 32 * kGW, smem, s>>>((const float *)yT, (float *)vol, g, status);
+    dim3 grid((g.nx + T - 1) / T, (g.ny + T - 1) / T, (g.nz + kGZ - 1) / kGZ);
+    fp3d_gather_adjoint_kernel<W, G, T><<<grid, 32 * kGW, smem, s>>>((const float *)yT, (float *)vol, g, status);
     return cudaGetLastError();
+}
+
+template <int T>
+static cudaError_t gather_by_window(const void *yT, void *vol, const GatherParams &g, int *status, cudaStream_t s)
+{
+    // planes per group: their tent weights stay in registers (G W / 2 pairs)
+    switch (g.wrows) {
+    case 4:
+        return gather_launch<4, 4, T>(yT, vol, g, status, s);
+    case 8:
+        return gather_launch<8, 4, T>(yT, vol, g, status, s);
+    case 12:
+        return gather_launch<12, 4, T>(yT, vol, g, status, s);
+    case 16:
+        return gather_launch<16, 3, T>(yT, vol, g, status, s);
+    case 20:
+        return gather_launch<20, 2, T>(yT, vol, g, status, s);
+    case 24:
+        return gather_launch<24, 2, T>(yT, vol, g, status, s);
+    case 28:
+        return gather_launch<28, 1, T>(yT, vol, g, status, s);
+    case 32:
+        return gather_launch<32, 1, T>(yT, vol, g, status, s);
+    default:
+        return cudaErrorInvalidValue;
+    }
 }
 
 // one batch item: yT holds its transposed, weighted views
 cudaError_t launch_gather_adjoint(const void *yT, void *vol, const GatherParams &g, int *status, cudaStream_t s)
 {
-    // planes per group: their tent weights stay in registers (G W / 2 pairs)
-    switch (g.wrows) {
+    switch (g.tile) {
     case 4:
-        return gather_launch<4, 4>(yT, vol, g, status, s);
-    case 8:
-        return gather_launch<8, 4>(yT, vol, g, status, s);
-    case 12:
-        return gather_launch<12, 4>(yT, vol, g, status, s);
-    case 16:
-        return gather_launch<16, 3>(yT, vol, g, status, s);
-    case 20:
-        return gather_launch<20, 2>(yT, vol, g, status, s);
-    case 24:
-        return gather_launch<24, 2>(yT, vol, g, status, s);
-    case 28:
-        return gather_launch<28, 1>(yT, vol, g, status, s);
-    case 32:
-        return gather_launch<32, 1>(yT, vol, g, status, s);
+        return gather_by_window<4>(yT, vol, g, status, s);
+    case 6:
+        return gather_by_window<6>(yT, vol, g, status, s);
     default:
         return cudaErrorInvalidValue;
     }

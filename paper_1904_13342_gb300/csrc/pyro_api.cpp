@@ -476,7 +476,7 @@ int gather_rows(const Geo3D &G, const CamView &c, GatherRows &r)
 }
 
 // Capacities of the kernel's shared tables are bounds over every tile and
-// view: the support of a tile's tents is (kGatherTile + 1) voxels square;
+// view: the support of a tile's tents is (tile + 1) voxels square;
 // its diagonal, seen from the nearest depth, spans at most kmax detector
 // columns, and its depth at most plmax planes; a warp's 32 z voxels (and a
 // tent on either side) span at most 34 / |beta| rows, widened by the z
@@ -498,7 +498,8 @@ int fill_gather(const Geo3D &G, int v0, int nvw, int accumulate, GatherParams &g
         hl[1] = (float)(x - (double)hl[0]);
     };
     const double cen[3] = {0.5 * (G.nx - 1), 0.5 * (G.ny - 1), 0.5 * (G.nz - 1)};
-    const double side = kGatherTile + 1;
+    g.tile = gather_tile(G.nx, G.ny, G.nz);
+    const double side = g.tile + 1;
     const double diag = std::sqrt(2.0) * side * std::max(G.sx, G.sy);
     double kcols = 0.0, planes = 0.0, rows = 0.0;
     int wrows = 0;
