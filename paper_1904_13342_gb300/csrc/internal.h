@@ -221,7 +221,7 @@ cudaError_t launch_fp3d_adjoint(const void *sino, void *vol, int batch, const FP
 cudaError_t launch_relayout_zmajor(const void *vol, void *vz, int nx, int ny, int nz, pyro_dtype dt, cudaStream_t s);
 // the padded copy of the column kernels: storage FP32 / FP16 / BF16 (a
 // half-size copy of an FP32 volume allowed); the sinogram FP32 or the storage type
-cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt,
+cudaError_t launch_relayout_quad(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt,
                                    pyro_dtype storage, cudaStream_t s);
 cudaError_t launch_fp3d_column(const void *vp, void *sino, int b, const FP3DParams &p, pyro_dtype storage,
                                pyro_dtype sino_dt, cudaStream_t s);

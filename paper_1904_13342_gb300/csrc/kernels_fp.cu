@@ -543,8 +543,9 @@ __global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const
 // volume's z axis (circular and helical-free trajectories: no skew, camera y
 // axis = z), all rays of one detector column k share their (x, y) point on
 // every depth plane; only z differs, and it grows monotonically with the row
-// l.  A warp takes column k and R windows of 32 consecutive rows.  On each
-// depth plane it computes the (x, y) cell and its bilinear weights once; in
+// l.  A warp takes column k and R windows of 32 consecutive rows.  The (x, y)
+// cell and bilinear weights of each depth plane are computed once per warp
+// (32 planes at a time, one per lane, handed over through shared memory); in
 // each window every lane loads the four (x, y) columns at one z of the
 // window's 32-voxel run and combines them in x and y, and each lane then
 // takes the two z taps of its own ray from the lanes holding them (two
@@ -562,7 +563,8 @@ __global__ void __launch_bounds__(kFPZLanes *kFPZWarps) fp3d_zmajor_kernel(const
 // over a whole ray (|q_z| stays near 0.1 voxel per plane for these
 // trajectories), which keeps the FP32 steps from the anchor within ~2e-6
 // voxel.
-// warps (detector columns) per block: 8 for the one-ray kernel, 16 for the
+//
+// Warps (detector columns) per block: 8 for the one-ray kernel, 16 for the
 // two-ray kernel; the adjacent columns of a block follow nearby tracks, so
 // larger blocks share more cells in L1 (256^3 workload: 18.15 ms with 4,
 // 17.85 with 8 and the pair loop unrolled by 4; 512^3 TV geometry: 464 ms
@@ -1452,7 +1454,7 @@ cudaError_t launch_fp3d_zmajor(const void *vz, void *sino, int b, const FP3DPara
 }
 
 // the volume's type and the copy's: the same type, or FP32 into FP16 / BF16
-cudaError_t launch_relayout_padded(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt,
+cudaError_t launch_relayout_quad(const void *vol, void *vp, int nx, int ny, int nz, pyro_dtype dt,
                                    pyro_dtype storage, cudaStream_t s)
 {
     dim3 block(32, 8), grid((nx + 2 * kFPPadXY + 31) / 32, (nz + 2 + 31) / 32, ny + 2 * kFPPadXY);

@@ -936,7 +936,7 @@ int fp3d_staged(const void *vol, void *sino, int batch, const pyro_geom3d *g, vo
     for (int b = 0; b < batch; ++b) {
         const char *vi = (const char *)vol + b * vox * elem_size(dt);
         if (column)
-            PYRO_CUDA(launch_relayout_padded(vi, work, G.nx, G.ny, G.nz, dt, storage, as_stream(stream)));
+            PYRO_CUDA(launch_relayout_quad(vi, work, G.nx, G.ny, G.nz, dt, storage, as_stream(stream)));
         else
             PYRO_CUDA(launch_relayout_zmajor(vi, work, G.nx, G.ny, G.nz, dt, as_stream(stream)));
         for (int v0 = 0; v0 < V; v0 += kMaxViewsConeFP) {
