@@ -47,7 +47,7 @@ std::map<std::pair<int, CUcontext>, void *> g_scratch_addr;
 using CtxGetCurrentFn = CUresult (*)(CUcontext *);
 
 // the calling thread's current context (the runtime's primary context once
-// any runtime call has run on the device); NULL when the driver entry point
+// any runtime call has run on the device); NULL when the CUDA driver entry point
 // is unavailable, which then keys by the device alone
 CUcontext current_context()
 {
